@@ -1,0 +1,174 @@
+"""Oracle: the VQ-NQS autoregressive wave function, float64 on the CPU.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+What it computes (Sec. 2 polar form and chain rule; Sec. 3.1 architecture;
+Sec. 4 phase set to zero by the Marshall sign rule):
+
+  psi(s) = sqrt(P(s)),  P(s) = prod_p P(s_p | s_<p),
+  log psi(s) = 1/2 * sum_p log P(s_p | s_<p).
+
+P is a decoder (causal) transformer with one token per spin.  The input at
+position p is the previous spin s_{p-1} (a begin-of-sequence token at p = 0),
+so the output at p is the conditional of s_p.  Each block is pre-LayerNorm:
+
+  a = LN1(x);  q, k, v = a W_qkv + b_qkv
+  o = causal multi-head softmax(q k^T / sqrt(d/heads)) v       (location mixer)
+  c = argmin_j ||o - W_j||^2, lowest j on ties                  (Eq. vq)
+  y = x + W_o W_c + b_o            (the quantizer sits after the attention,
+                                    before the output projection and residual)
+  x <- y + W_2 GELU(W_1 LN2(y) + b_1) + b_2                     (per location)
+
+and the head is log_softmax(LN_f(x) W_head + b_head) over the two spin values.
+LayerNorm uses eps = 1e-5 and the biased variance; GELU is the erf form.
+
+Readings of the paper used here (it leaves block internals to prior work):
+pre-LN, erf-GELU, biases everywhere, one quantizer head (H = 1), and the
+argmax in Eq. vq read as the argmax of D = -||x - W_j||, i.e. the nearest
+codeword.  The squared distance is expanded as ||o||^2 - 2 o.W_j + ||W_j||^2 in
+float64; its argmin equals the direct one unless two distances agree to ~1e-15
+relative.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+LN_EPS = 1e-5
+BOS = 2
+
+
+@dataclass
+class Params:
+    d: int
+    heads: int
+    K: int
+    layers: int
+    n_max: int
+    t: dict  # name -> float64 tensor
+
+
+def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int) -> Params:
+    """Split a flat float32 weight blob into named float64 tensors.
+
+    The order is the documented blob order: token and position embeddings,
+    then per layer LN1, W_qkv, codebook, W_o, LN2, W_1, W_2 (each matrix
+    followed by its bias), then LN_f and the head."""
+    blob = torch.as_tensor(np.asarray(blob, dtype=np.float32)).double()
+    pos = 0
+    t = {}
+
+    def take(name, *shape):
+        nonlocal pos
+        n = int(np.prod(shape))
+        t[name] = blob[pos:pos + n].reshape(shape).clone()
+        pos += n
+
+    take("tok_emb", 3, d)
+    take("pos_emb", n_max, d)
+    for l in range(layers):
+        take(f"{l}.ln1_g", d); take(f"{l}.ln1_b", d)
+        take(f"{l}.w_qkv", d, 3 * d); take(f"{l}.b_qkv", 3 * d)
+        take(f"{l}.codebook", K, d)
+        take(f"{l}.w_o", d, d); take(f"{l}.b_o", d)
+        take(f"{l}.ln2_g", d); take(f"{l}.ln2_b", d)
+        take(f"{l}.w_1", d, 4 * d); take(f"{l}.b_1", 4 * d)
+        take(f"{l}.w_2", 4 * d, d); take(f"{l}.b_2", d)
+    take("lnf_g", d); take("lnf_b", d)
+    take("w_head", d, 2); take("b_head", 2)
+    if pos != blob.numel():
+        raise ValueError(f"blob has {blob.numel()} values, layout needs {pos}")
+    return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t)
+
+
+def layer_norm(x, g, b):
+    mu = x.mean(dim=-1, keepdim=True)
+    var = ((x - mu) ** 2).mean(dim=-1, keepdim=True)
+    return (x - mu) / torch.sqrt(var + LN_EPS) * g + b
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + torch.erf(x / math.sqrt(2.0)))
+
+
+def causal_attention(a, w_qkv, b_qkv, heads):
+    """Causal multi-head self-attention output before the output projection.
+
+    a: [C, N, d] -> o: [C, N, d] (heads concatenated)."""
+    C, N, d = a.shape
+    dh = d // heads
+    qkv = a @ w_qkv + b_qkv
+    q, k, v = qkv[..., :d], qkv[..., d:2 * d], qkv[..., 2 * d:]
+    q = q.reshape(C, N, heads, dh).transpose(1, 2)
+    k = k.reshape(C, N, heads, dh).transpose(1, 2)
+    v = v.reshape(C, N, heads, dh).transpose(1, 2)
+    scores = (q @ k.transpose(-1, -2)) / math.sqrt(dh)
+    future = torch.ones(N, N, dtype=torch.bool).triu(1)
+    scores = scores.masked_fill(future, float("-inf"))
+    p = torch.softmax(scores, dim=-1)
+    o = p @ v
+    return o.transpose(1, 2).reshape(C, N, d)
+
+
+def sq_distances(o, codebook):
+    """||o - W_j||^2 for every row of o and every codeword j."""
+    return (o * o).sum(-1, keepdim=True) - 2.0 * (o @ codebook.T) + (codebook * codebook).sum(-1)
+
+
+def nearest_code(o, codebook):
+    """Eq. vq: index of the nearest codeword, lowest index on exact ties."""
+    return torch.argmin(sq_distances(o, codebook), dim=-1)
+
+
+def tokens(spins: torch.Tensor) -> torch.Tensor:
+    """Shift right: token at p is s_{p-1}, begin-of-sequence at p = 0."""
+    C, N = spins.shape
+    tok = torch.empty(C, N, dtype=torch.long)
+    tok[:, 0] = BOS
+    tok[:, 1:] = spins[:, :-1].long()
+    return tok
+
+
+def forward(P: Params, spins, quantizer=None, record=None):
+    """Conditional log-probabilities log P(. | s_<p), shape [C, N, 2].
+
+    ``quantizer(l, o) -> (V, codes)`` replaces the plain nearest-codeword
+    lookup (used by the gradient module for the straight-through form);
+    ``record`` (a list) receives the codes of every layer."""
+    spins = torch.as_tensor(np.asarray(spins)).long()
+    C, N = spins.shape
+    t = P.t
+    x = t["tok_emb"][tokens(spins)] + t["pos_emb"][:N]
+    for l in range(P.layers):
+        a = layer_norm(x, t[f"{l}.ln1_g"], t[f"{l}.ln1_b"])
+        o = causal_attention(a, t[f"{l}.w_qkv"], t[f"{l}.b_qkv"], P.heads)
+        if quantizer is None:
+            c = nearest_code(o, t[f"{l}.codebook"])
+            vq = t[f"{l}.codebook"][c]
+        else:
+            vq, c = quantizer(l, o)
+        if record is not None:
+            record.append(c)
+        y = x + vq @ t[f"{l}.w_o"] + t[f"{l}.b_o"]
+        h = gelu(layer_norm(y, t[f"{l}.ln2_g"], t[f"{l}.ln2_b"]) @ t[f"{l}.w_1"] + t[f"{l}.b_1"])
+        x = y + h @ t[f"{l}.w_2"] + t[f"{l}.b_2"]
+    logits = layer_norm(x, t["lnf_g"], t["lnf_b"]) @ t["w_head"] + t["b_head"]
+    return torch.log_softmax(logits, dim=-1)
+
+
+def log_psi(P: Params, spins, batch: int = 64, record=None) -> np.ndarray:
+    """log psi(s) = 1/2 sum_p log P(s_p | s_<p) for each row of ``spins`` (float64)."""
+    spins = np.asarray(spins)
+    out = np.empty(spins.shape[0], dtype=np.float64)
+    with torch.no_grad():
+        for i in range(0, spins.shape[0], batch):
+            s = torch.as_tensor(spins[i:i + batch]).long()
+            rec = [] if record is not None else None
+            lp = forward(P, s, record=rec)
+            out[i:i + batch] = 0.5 * lp.gather(-1, s[..., None])[..., 0].sum(-1).numpy()
+            if record is not None:
+                record.append(rec)
+    return out
