@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Local energies per second of the VQ-NQS path on GB300.
+
+Workload (one step): E_loc of 2048 uniform random S_z = 0 samples of the
+16 x 16 periodic Heisenberg model (J = 1, 512 bonds, ~258 configurations per
+sample) with an 8-layer VQ transformer (d_model 256, 8 heads, codebook 256,
+seeded N(0, 0.02) weights), VQ reuse on.  Every step runs the whole path:
+bond enumeration, embedding, per layer LN/QKV/attention/argmin/dedupe/MLP,
+head, log-ratios and the local-energy reduction.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank evaluates its own 2048
+samples (weak scaling, no data-path collective); the timed region is closed by
+a barrier and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("local energies/sec at 16×16, VQ-reuse BF16 vs plain FP32 on GB300; E_loc err vs FP64")
+UNIT = "local energies/s"
+WORKLOAD = dict(L=16, periodic=True, J=1.0, layers=8, d_model=256, heads=8, K=256, samples_per_gpu=2048)
+FP32_FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 FLOP x max SM clock
+L2_FLUSH_BYTES = 256 << 20
+
+
+def shard(B: int, rank: int, world: int):
+    """Sample indices of one rank under weak scaling: every rank gets its own B samples."""
+    return np.arange(rank * B, (rank + 1) * B)
+
+
+def reduce_max(x: float, dist=None) -> float:
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() and
+                     dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def stage_flops(stage: str, st: dict, w: dict) -> tuple[float, str]:
+    """Algorithmic FLOPs (2 per multiply-add) of one stage over the counted work, and its bound."""
+    d, K, N, Ly = w["d_model"], w["K"], w["L"] ** 2, w["layers"]
+    rows, cfgs = st["rows"], st["configs"]
+    U = st["unique_rows"]
+    if stage == "vq_argmin":
+        return rows * Ly * 2.0 * K * d, "alu"
+    if stage == "attention":
+        return cfgs * Ly * 2.0 * d * N * (N + 1), "alu"
+    if stage == "qkv_gemm":
+        return sum(U[:Ly]) * 6.0 * d * d, "alu"
+    if stage in ("mlp_up", "mlp_down"):
+        return sum(U[1:Ly + 1]) * 8.0 * d * d, "alu"
+    return 0.0, "hbm"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_stage: str):
+    """DRAM bytes per launch recorded by the committed ncu summary of this stage's
+    kernel, or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_stage}.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, rec.get("source", ""))
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if digest != rec.get("source_sha256_16"):
+        return None
+    return rec.get("dram_bytes_per_launch_scaled")
+
+
+def cpu_oracle(spins_np, w, max_seconds=20.0, max_samples=6):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import torch
+    import synthetic_inputs as si
+    from oracle import hamiltonian, model
+    N = w["L"] ** 2
+    blob = si.make_weights(N, w["layers"], w["d_model"], w["K"], seed=0)
+    P = model.parse_blob(blob, N, w["layers"], w["d_model"], w["heads"], w["K"])
+    t0 = time.perf_counter()
+    vals = []
+    for i in range(max_samples):
+        vals.append(float(hamiltonian.local_energy(P, spins_np[i:i + 1], w["L"], w["periodic"], w["J"])[0]))
+        if time.perf_counter() - t0 > max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return np.array(vals), dt, torch.get_num_threads()
+
+
+def run_reference(args, w):
+    """The oracle timed on the host cores: each step is one sample of the workload."""
+    import synthetic_inputs as si
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    from oracle import hamiltonian, model
+    N = w["L"] ** 2
+    blob = si.make_weights(N, w["layers"], w["d_model"], w["K"], seed=0)
+    P = model.parse_blob(blob, N, w["layers"], w["d_model"], w["heads"], w["K"])
+    spins = si.make_samples(w["L"], args.warmup + args.steps, seed=1)
+    for i in range(args.warmup):
+        hamiltonian.local_energy(P, spins[i:i + 1], w["L"], w["periodic"], w["J"])
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        hamiltonian.local_energy(P, spins[i:i + 1], w["L"], w["periodic"], w["J"])
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = torch.get_num_threads()
+    sample = f"1 sample of the 16x16 workload per step (about 258 configurations, full FP64 recompute)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(w, "f64 oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def config_dict(w, path):
+    return {"workload": (f"{w['L']}x{w['L']} periodic Heisenberg J={w['J']:g}, {w['layers']} layers d_model "
+                         f"{w['d_model']} heads {w['heads']} codebook {w['K']}, {w['samples_per_gpu']} uniform "
+                         f"S_z=0 samples per GPU"),
+            "path": path, "L": w["L"], "samples_per_gpu": w["samples_per_gpu"],
+            "l2": "flushed between timed steps (256 MiB write); the step's working set is also far above L2"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--flags", default="reuse", help="comma list of reuse,bf16 for the timed path")
+    ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = dict(WORKLOAD, samples_per_gpu=args.samples)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    import synthetic_inputs as si
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    flags = 0
+    for f in args.flags.split(","):
+        flags |= {"reuse": REUSE, "bf16": BF16, "": 0}[f.strip()]
+    B, L, N = w["samples_per_gpu"], w["L"], w["L"] ** 2
+    blob = si.make_weights(N, w["layers"], w["d_model"], w["K"], seed=0)
+    all_spins = si.make_samples(L, B * world, seed=1)
+    spins_np = np.ascontiguousarray(all_spins[shard(B, rank, world)])
+    m = VQNQS(L, w["periodic"], w["J"], w["layers"], w["d_model"], w["heads"], w["K"], blob)
+    stream = torch.cuda.current_stream()
+    spins = torch.as_tensor(spins_np).cuda()
+    out = torch.empty(B, dtype=torch.float32, device="cuda")
+    ws = m.workspace(flags)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        m.local_energy(spins, flags, out=out, workspace=ws)
+    barrier()
+    m.reset_stats()
+    m.profile(True)
+    m.profile_read()
+    launches0 = m.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            m.local_energy(spins, flags, out=out, workspace=ws)
+            ev[k][1].record(stream)
+        barrier()
+    launches = m.launch_count() - launches0
+    prof = m.profile_read()
+    m.profile(False)
+    st = m.stats()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_ms = reduce_max(t_ms, dist if world > 1 else None)
+    value = B * world * args.steps / (t_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    h_spins = torch.as_tensor(spins_np).pin_memory()
+    h_out = torch.empty(B, dtype=torch.float32).pin_memory()
+    d_spins = torch.empty_like(spins)
+    for _ in range(2):
+        d_spins.copy_(h_spins, non_blocking=True)
+        m.local_energy(d_spins, flags, out=out, workspace=ws)
+        h_out.copy_(out, non_blocking=True)
+    barrier()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e2e_ev[k][0].record(stream)
+        d_spins.copy_(h_spins, non_blocking=True)
+        m.local_energy(d_spins, flags, out=out, workspace=ws)
+        h_out.copy_(out, non_blocking=True)
+        e2e_ev[k][1].record(stream)
+    barrier()
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in e2e_ev), dist if world > 1 else None)
+    e2e_value = B * world * args.steps / (e2e_ms / 1e3)
+    e_gpu = h_out.numpy().astype(np.float64)
+
+    # the plain full-recompute FP32 path on a subset of the same samples
+    n_plain = min(64, B)
+    sub = spins[:n_plain].contiguous()
+    ws0 = m.workspace(0)
+    m.local_energy(sub, 0, workspace=ws0)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    m.local_energy(sub, 0, workspace=ws0)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_value = n_plain / (a.elapsed_time(b) / 1e3)
+
+    # roofline of the dominant stage, from the live CUDA-event stage times
+    per_step = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(per_step, key=lambda k: per_step[k][2])
+    calls, nl, ms = per_step[dom]
+    fl, bound = stage_flops(dom, st, w)
+    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    peak = FP32_FFMA_PEAK_TFLOPS
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic_from_profile(dom),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                "launches": nl, "avg_launch_ms": ms / nl}
+    stages = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[1] / args.steps,
+                  "share": v[2] / max(1e-9, sum(x[2] for x in per_step.values()))} for k, v in per_step.items()}
+
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16" if flags & BF16 else "f32", "data": "synthetic",
+        "config": config_dict(w, ("VQ-reuse" if flags & REUSE else "full recompute") +
+                              (" BF16 GEMMs, FP32 VQ" if flags & BF16 else " FP32")),
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * N),
+                "d2h_bytes_per_step": int(B * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "plain_fp32": {"value": plain_value, "unit": UNIT, "samples": n_plain},
+        "speedup_vs_plain_fp32": value / plain_value,
+        "unique_row_fraction": [u / max(1, st["rows"]) for u in st["unique_rows"]],
+        "flop_reduction": st["flops_full"] / max(1.0, st["flops_done"]),
+        "near_ties_per_row": st["near_ties"] / max(1, st["rows"] * w["layers"]),
+        "device_status": st["device_status"],
+        "stages": stages,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        vals, dt, cores = cpu_oracle(spins_np, w)
+        n = len(vals)
+        rel = np.abs(e_gpu[:n] - vals) / np.maximum(np.abs(vals), 1e-3 * N)
+        res["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {n} samples of the workload, FP64 full recompute"}
+        res["err_vs_fp64"] = {"max_rel": float(rel.max()), "samples": n}
+    print(json.dumps(res))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * vqnqs.h - C ABI of the GB300 (sm_103a) VQ-NQS local-energy library.
+ *
+ * The library evaluates the Vector-Quantized Neural Quantum State of
+ * arXiv 2212.11296 and the variational-Monte-Carlo local energy
+ *
+ *     E_loc(s) = sum_{s'} H_{s s'} psi(s') / psi(s)             (Sec. 2, Eq. local-energy)
+ *
+ * for the spin-1/2 Heisenberg model H = J sum_<ij> S_i . S_j on an L x L
+ * square lattice (Sec. 4), in the Marshall-rotated basis where psi > 0 and
+ * the phase is zero (Sec. 4).  psi(s) = sqrt(P(s)) with P an autoregressive
+ * decoder transformer, one token per spin, whose blocks insert a vector
+ * quantizer between the self-attention and its output projection (Sec. 3.1,
+ * Eq. vq).  Per-location work whose quantized input was already seen is done
+ * once per unique (row, code) key (Sec. 3.2) when VQNQS_REUSE is set.
+ *
+ * Conventions shared by every entry point
+ *  - Spins: uint8 in {0 = down, 1 = up}, raster order p = y * L + x, one row
+ *    of N = L * L bytes per sample.  Any configuration is accepted (S_z = 0 is
+ *    not required).  Values other than 0/1 raise VQNQS_DEV_BAD_SPIN.
+ *  - Array arguments named dev_* are DEVICE pointers owned by the caller;
+ *    weights passed to vqnqs_create are HOST memory and are copied.
+ *  - Calls that take a stream enqueue work on that cudaStream_t (NULL = legacy
+ *    default stream) and return without synchronising; outputs are valid after
+ *    the caller synchronises the stream.  They allocate nothing: all scratch
+ *    lives in the caller's workspace (see vqnqs_workspace_bytes).
+ *  - Every call returns a vqnqs_status; on failure vqnqs_last_error gives a
+ *    message.  Errors detected inside kernels set bits of a device status word
+ *    that vqnqs_get_stats reports; kernels never trap.
+ *  - A context is used by one host thread at a time.
+ *
+ * Weight blob (float32, in this order; d = d_model, n_max = L * L):
+ *   tok_emb[3][d] (token 0 down, 1 up, 2 begin-of-sequence), pos_emb[n_max][d],
+ *   per layer: ln1_g[d] ln1_b[d] w_qkv[d][3d] b_qkv[3d] codebook[K][d]
+ *              w_o[d][d] b_o[d] ln2_g[d] ln2_b[d] w_1[d][4d] b_1[4d]
+ *              w_2[4d][d] b_2[d],
+ *   lnf_g[d] lnf_b[d] w_head[d][2] b_head[2].
+ * Matrices are row-major and multiply from the right (x @ w).
+ */
+#ifndef VQNQS_H
+#define VQNQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vqnqs_ctx vqnqs_ctx;
+
+typedef enum {
+    VQNQS_OK = 0,
+    VQNQS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad flag) */
+    VQNQS_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    VQNQS_ERR_OOM = 3,        /* device allocation failed (vqnqs_create only) */
+    VQNQS_ERR_WORKSPACE = 4,  /* workspace smaller than the one-sample minimum */
+    VQNQS_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+    VQNQS_ERR_INTERNAL = 6
+} vqnqs_status;
+
+/* flags (bitwise or); 0 = plain full recompute in FP32 */
+enum {
+    VQNQS_REUSE = 1,  /* deduplicate per-location work by (row, code) keys (Sec. 3.2) */
+    VQNQS_BF16 = 2    /* BF16 tensor-core GEMMs with FP32 accumulation */
+};
+
+/* bits of the device status word */
+enum {
+    VQNQS_DEV_BAD_SPIN = 1,       /* a spin byte was not 0 or 1 */
+    VQNQS_DEV_HASH_OVERFLOW = 2,  /* a dedupe probe ran past its bound */
+    VQNQS_DEV_TIMEOUT = 4         /* a bounded wait gave up */
+};
+
+#define VQNQS_MAX_LAYERS 64
+
+typedef struct vqnqs_stats {
+    int64_t samples;                          /* samples processed since the last reset */
+    int64_t configs;                          /* configurations evaluated (samples + connected ones) */
+    int64_t rows;                             /* configs * N: token rows per layer */
+    int64_t unique_rows[VQNQS_MAX_LAYERS + 1];/* sum over chunks of the unique per-location rows
+                                                 feeding layer l (index l), and the head (index layers) */
+    int64_t near_ties;                        /* code assignments with relative distance gap < 1e-6 */
+    double flops_full;                        /* analytic FLOPs (2 per MAC) of full recompute */
+    double flops_done;                        /* analytic FLOPs of the work actually executed */
+    int32_t device_status;                    /* OR of VQNQS_DEV_* bits raised so far */
+} vqnqs_stats;
+
+/* Number of floats in the weight blob for the layout above. */
+size_t vqnqs_num_params(int n_max, int layers, int d_model, int K);
+
+/* Create a context.
+ *   L        lattice side (sites N = L * L; 4 <= N <= 512)
+ *   periodic 1 = periodic boundaries (2N bonds), 0 = open (2L(L-1) bonds)
+ *   J        exchange coupling of H = J sum_<ij> S_i . S_j
+ *   layers, d_model, heads, K   model shape: 1 <= layers <= VQNQS_MAX_LAYERS,
+ *            32 <= d_model <= 1024 with d_model % 32 == 0, d_model / heads in
+ *            {8, 16, 32}, 1 <= K <= 65535
+ *   weights  HOST float32 blob of vqnqs_num_params(L*L, layers, d_model, K) values (copied)
+ * The context owns device copies of the weights and of tables derived from
+ * them (codebook projections through W_o, codebook norms, BF16 transposes).
+ * Returns VQNQS_ERR_ARG / VQNQS_ERR_OOM / VQNQS_ERR_CUDA on failure (*out = NULL). */
+int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int heads, int K,
+                 const float* weights, vqnqs_ctx** out);
+
+/* Replace the weights (HOST blob when is_device == 0, DEVICE blob otherwise) and
+ * rebuild the derived tables on `stream`. */
+int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream);
+
+/* Workspace bytes for the calls below with `flags`, sized for chunks of up to
+ * `chunk_samples` samples (<= 0 picks the library default).  A call given a
+ * smaller workspace processes fewer samples per chunk; the minimum is one sample. */
+size_t vqnqs_workspace_bytes(const vqnqs_ctx* ctx, int chunk_samples, int flags);
+
+/* log psi(s) = 1/2 sum_p log P(s_p | s_<p) for B samples (Sec. 2 polar form, chain rule).
+ *   dev_spins   DEVICE uint8 [B][N]
+ *   dev_log_psi DEVICE float [B] (output)
+ *   flags       VQNQS_REUSE | VQNQS_BF16
+ *   dev_ws      DEVICE workspace of ws_bytes bytes, 256-byte aligned */
+int vqnqs_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_log_psi, int flags,
+                  void* dev_ws, size_t ws_bytes, void* stream);
+
+/* Local energies (Sec. 2, Eq. local-energy) of B samples.
+ *   dev_e_loc     DEVICE float [B] (output): per-lattice E_loc(s) in units of J S.S
+ *   dev_mean_var  DEVICE double [2] (output, may be NULL): FP64 mean and variance
+ *                 (1/B normalisation) of the B local energies
+ *   dev_log_psi   DEVICE float [B] (output, may be NULL): log psi of the samples
+ * Every configuration one nearest-neighbour exchange away from a sample is
+ * evaluated (Sec. 2: O(N) non-zero entries per row). */
+int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_e_loc,
+                       double* dev_mean_var, float* dev_log_psi, int flags,
+                       void* dev_ws, size_t ws_bytes, void* stream);
+
+/* Snapshot of the counters; synchronises the device first. */
+int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out);
+
+/* Zero the counters and the device status word. */
+int vqnqs_reset_stats(vqnqs_ctx* ctx);
+
+/* Per-stage timing.  While enabled, every stage of the path is bracketed by
+ * CUDA events recorded on the stream it is launched on; vqnqs_profile_read
+ * synchronises the device and returns, per stage, the number of kernel
+ * launches and the summed event time since the last read (then clears them).
+ * Stage names: config, embed, ln1, qkv_gemm, attention, vq_argmin, dedupe,
+ * post_ln, mlp_up, mlp_down, head, eloc, mean_var. */
+typedef struct vqnqs_stage_time {
+    char name[24];
+    int64_t calls;     /* times the stage ran */
+    int64_t launches;  /* kernel launches it issued */
+    double ms;         /* summed CUDA-event time */
+} vqnqs_stage_time;
+
+#define VQNQS_MAX_STAGES 16
+
+int vqnqs_profile_enable(vqnqs_ctx* ctx, int enable);
+
+/* Fills out[0 .. *n_out-1] (at most max_stages entries). */
+int vqnqs_profile_read(vqnqs_ctx* ctx, vqnqs_stage_time* out, int max_stages, int* n_out);
+
+/* Kernel launches issued by this context since it was created (host counter). */
+int64_t vqnqs_launch_count(const vqnqs_ctx* ctx);
+
+/* Last error message of this context ("" if none); valid until the next call. */
+const char* vqnqs_last_error(const vqnqs_ctx* ctx);
+
+/* Free the context and everything it owns.  NULL is ignored. */
+void vqnqs_destroy(vqnqs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VQNQS_H */

@@ -58,10 +58,12 @@ def connected(spins: np.ndarray, bond_list: np.ndarray, J: float):
     return diag, cfgs, np.full(len(anti), -0.5 * J)
 
 
-def local_energy_fn(log_psi_fn, spins: np.ndarray, L: int, periodic: bool, J: float) -> np.ndarray:
+def local_energy_fn(log_psi_fn, spins: np.ndarray, L: int, periodic: bool, J: float, min_gap=None) -> np.ndarray:
     """E_loc for each row of ``spins`` with an arbitrary real log-amplitude function.
 
-    ``log_psi_fn`` maps an int array [C, N] to float64 [C]."""
+    ``log_psi_fn`` maps an int array [C, N] to float64 [C], or to a pair
+    (log psi [C], diagnostic [C]); with ``min_gap`` given, the per-sample minimum
+    of the diagnostic over the sample's configurations is stored there."""
     bl = bonds(L, periodic)
     spins = np.asarray(spins)
     out = np.empty(spins.shape[0], dtype=np.float64)
@@ -69,18 +71,30 @@ def local_energy_fn(log_psi_fn, spins: np.ndarray, L: int, periodic: bool, J: fl
     # value still comes from its own full forward pass.
     block = 256
     for b0 in range(0, spins.shape[0], block):
-        rows, parts = [], []
+        rows, parts, start = [], [], 0
         for b in range(b0, min(b0 + block, spins.shape[0])):
             diag, cfgs, h = connected(spins[b], bl, J)
-            parts.append((b, diag, h, sum(len(r) for r in rows), len(cfgs)))
+            parts.append((b, diag, h, start, len(cfgs)))
             rows.append(np.concatenate([spins[b][None, :].astype(np.int64), cfgs], axis=0))
-        lp = log_psi_fn(np.concatenate(rows, axis=0))
+            start += 1 + len(cfgs)
+        res = log_psi_fn(np.concatenate(rows, axis=0))
+        lp, aux = (res if isinstance(res, tuple) else (res, None))
         for b, diag, h, start, n in parts:
             out[b] = diag + float(np.sum(h * np.exp(lp[start + 1:start + 1 + n] - lp[start])))
+            if min_gap is not None and aux is not None:
+                min_gap[b] = float(np.min(aux[start:start + 1 + n]))
     return out
 
 
 def local_energy(P: model.Params, spins: np.ndarray, L: int, periodic: bool, J: float = 1.0,
-                 batch: int = 64) -> np.ndarray:
-    """E_loc(s) of the VQ-NQS wave function, every connected configuration recomputed in full."""
-    return local_energy_fn(lambda c: model.log_psi(P, c, batch=batch), spins, L, periodic, J)
+                 batch: int = 64, min_gap=None) -> np.ndarray:
+    """E_loc(s) of the VQ-NQS wave function, every connected configuration recomputed in full.
+
+    ``min_gap`` (float64 array of len(spins)) receives per sample the smallest
+    relative codeword gap met in any of its configurations (a diagnostic)."""
+    def fn(c):
+        if min_gap is None:
+            return model.log_psi(P, c, batch=batch)
+        g = np.empty(len(c))
+        return model.log_psi(P, c, batch=batch, min_gap=g), g
+    return local_energy_fn(fn, spins, L, periodic, J, min_gap=min_gap)

@@ -132,12 +132,22 @@ def tokens(spins: torch.Tensor) -> torch.Tensor:
     return tok
 
 
-def forward(P: Params, spins, quantizer=None, record=None):
+def relative_gap(o, codebook):
+    """(l2 - l1) / l1 for the two smallest squared distances l1 <= l2 of each row
+    (diagnostic: how close a row is to a codeword tie)."""
+    if codebook.shape[0] < 2:
+        return torch.full(o.shape[:-1], float("inf"), dtype=o.dtype)
+    d2 = torch.topk(sq_distances(o, codebook), 2, dim=-1, largest=False).values
+    return (d2[..., 1] - d2[..., 0]) / torch.clamp(d2[..., 0], min=1e-30)
+
+
+def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
     """Conditional log-probabilities log P(. | s_<p), shape [C, N, 2].
 
     ``quantizer(l, o) -> (V, codes)`` replaces the plain nearest-codeword
     lookup (used by the gradient module for the straight-through form);
-    ``record`` (a list) receives the codes of every layer."""
+    ``record`` (a list) receives the codes of every layer and ``gaps`` (a
+    list) the per-row relative gap of every layer."""
     spins = torch.as_tensor(np.asarray(spins)).long()
     C, N = spins.shape
     t = P.t
@@ -152,6 +162,8 @@ def forward(P: Params, spins, quantizer=None, record=None):
             vq, c = quantizer(l, o)
         if record is not None:
             record.append(c)
+        if gaps is not None:
+            gaps.append(relative_gap(o, t[f"{l}.codebook"]))
         y = x + vq @ t[f"{l}.w_o"] + t[f"{l}.b_o"]
         h = gelu(layer_norm(y, t[f"{l}.ln2_g"], t[f"{l}.ln2_b"]) @ t[f"{l}.w_1"] + t[f"{l}.b_1"])
         x = y + h @ t[f"{l}.w_2"] + t[f"{l}.b_2"]
@@ -159,16 +171,22 @@ def forward(P: Params, spins, quantizer=None, record=None):
     return torch.log_softmax(logits, dim=-1)
 
 
-def log_psi(P: Params, spins, batch: int = 64, record=None) -> np.ndarray:
-    """log psi(s) = 1/2 sum_p log P(s_p | s_<p) for each row of ``spins`` (float64)."""
+def log_psi(P: Params, spins, batch: int = 64, record=None, min_gap=None) -> np.ndarray:
+    """log psi(s) = 1/2 sum_p log P(s_p | s_<p) for each row of ``spins`` (float64).
+
+    ``min_gap`` (a float64 array of len(spins)) receives, per configuration, the
+    smallest relative codeword gap over all its rows and layers."""
     spins = np.asarray(spins)
     out = np.empty(spins.shape[0], dtype=np.float64)
     with torch.no_grad():
         for i in range(0, spins.shape[0], batch):
             s = torch.as_tensor(spins[i:i + batch]).long()
             rec = [] if record is not None else None
-            lp = forward(P, s, record=rec)
+            gp = [] if min_gap is not None else None
+            lp = forward(P, s, record=rec, gaps=gp)
             out[i:i + batch] = 0.5 * lp.gather(-1, s[..., None])[..., 0].sum(-1).numpy()
             if record is not None:
                 record.append(rec)
+            if min_gap is not None:
+                min_gap[i:i + batch] = torch.stack([g.min(-1).values for g in gp]).min(0).values.numpy()
     return out

@@ -1,0 +1,77 @@
+"""ctypes binding of libvqnqs.so (the C ABI in include/vqnqs.h).
+
+Argument marshalling only: every step of the local-energy path runs in the
+library's CUDA kernels.  Importing this module fails loudly when the library
+has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvqnqs.so")
+
+VQNQS_OK, VQNQS_ERR_ARG, VQNQS_ERR_CUDA, VQNQS_ERR_OOM, VQNQS_ERR_WORKSPACE, VQNQS_ERR_TIMEOUT, \
+    VQNQS_ERR_INTERNAL = range(7)
+REUSE = 1
+BF16 = 2
+DEV_BAD_SPIN, DEV_HASH_OVERFLOW, DEV_TIMEOUT = 1, 2, 4
+MAX_LAYERS = 64
+
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_WORKSPACE", 5: "ERR_TIMEOUT",
+                6: "ERR_INTERNAL"}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("samples", ctypes.c_int64),
+        ("configs", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("unique_rows", ctypes.c_int64 * (MAX_LAYERS + 1)),
+        ("near_ties", ctypes.c_int64),
+        ("flops_full", ctypes.c_double),
+        ("flops_done", ctypes.c_double),
+        ("device_status", ctypes.c_int32),
+    ]
+
+
+class StageTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("calls", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+
+MAX_STAGES = 16
+
+# (name, restype, argtypes) of every exported symbol of include/vqnqs.h
+SIGNATURES = [
+    ("vqnqs_num_params", ctypes.c_size_t, [ctypes.c_int] * 4),
+    ("vqnqs_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("vqnqs_set_weights", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("vqnqs_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("vqnqs_log_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_local_energy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    ("vqnqs_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
+    ("vqnqs_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("vqnqs_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(StageTime), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    ("vqnqs_launch_count", ctypes.c_int64, [ctypes.c_void_p]),
+    ("vqnqs_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("vqnqs_destroy", None, [ctypes.c_void_p]),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libvqnqs.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib

@@ -1,0 +1,157 @@
+"""Python face of the C ABI: torch tensors and streams in, library calls out."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+REUSE = _lib.REUSE
+BF16 = _lib.BF16
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+class VQNQSError(RuntimeError):
+    pass
+
+
+def _stream_ptr(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _check_dev(t: torch.Tensor, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+class VQNQS:
+    """One model on one lattice: vqnqs_create(L, periodic, J, layers, d_model, heads, K, weights)."""
+
+    def __init__(self, L: int, periodic: bool, J: float, layers: int, d_model: int, heads: int, K: int,
+                 weights: np.ndarray):
+        self.L, self.N = L, L * L
+        self.periodic, self.J = bool(periodic), float(J)
+        self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        n = lib().vqnqs_num_params(self.N, layers, d_model, K)
+        if w.size != n:
+            raise ValueError(f"weight blob has {w.size} floats, layout needs {n}")
+        h = ctypes.c_void_p()
+        rc = lib().vqnqs_create(L, int(periodic), float(J), layers, d_model, heads, K,
+                                w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        if rc != 0:
+            raise VQNQSError(f"vqnqs_create failed: {_lib.STATUS_NAMES.get(rc, rc)}")
+        self._h = h
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vqnqs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc != 0:
+            msg = lib().vqnqs_last_error(self._h).decode()
+            raise VQNQSError(f"{what}: {_lib.STATUS_NAMES.get(rc, rc)}: {msg}")
+
+    def workspace_bytes(self, flags: int = 0, chunk_samples: int = 0) -> int:
+        return int(lib().vqnqs_workspace_bytes(self._h, int(chunk_samples), int(flags)))
+
+    def workspace(self, flags: int = 0, chunk_samples: int = 0) -> torch.Tensor:
+        key = (flags, chunk_samples)
+        if key not in self._ws:
+            self._ws[key] = torch.empty(self.workspace_bytes(flags, chunk_samples), dtype=torch.uint8,
+                                        device="cuda")
+        return self._ws[key]
+
+    def set_weights(self, weights, stream=None):
+        if isinstance(weights, torch.Tensor):
+            _check_dev(weights, torch.float32, "weights")
+            self._check(lib().vqnqs_set_weights(self._h, ctypes.c_void_p(weights.data_ptr()), 1,
+                                                ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_set_weights")
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            self._check(lib().vqnqs_set_weights(self._h, w.ctypes.data_as(ctypes.c_void_p), 0,
+                                                ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_set_weights")
+
+    def log_psi(self, spins: torch.Tensor, flags: int = 0, out: torch.Tensor | None = None,
+                workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _check_dev(spins, torch.uint8, "spins")
+        B = spins.shape[0]
+        out = torch.empty(B, dtype=torch.float32, device=spins.device) if out is None else out
+        ws = self.workspace(flags) if workspace is None else workspace
+        self._check(lib().vqnqs_log_psi(self._h, B, ctypes.c_void_p(spins.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), int(flags),
+                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                        ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_log_psi")
+        return out
+
+    def local_energy(self, spins: torch.Tensor, flags: int = 0, want_mean_var: bool = False,
+                     want_log_psi: bool = False, out: torch.Tensor | None = None,
+                     workspace: torch.Tensor | None = None, stream=None):
+        """Returns e_loc [B] (and the FP64 [mean, var] and log psi when asked)."""
+        _check_dev(spins, torch.uint8, "spins")
+        if spins.dim() != 2 or spins.shape[1] != self.N:
+            raise ValueError(f"spins must be [B, {self.N}]")
+        B = spins.shape[0]
+        dev = spins.device
+        e = torch.empty(B, dtype=torch.float32, device=dev) if out is None else out
+        mv = torch.empty(2, dtype=torch.float64, device=dev) if want_mean_var else None
+        lp = torch.empty(B, dtype=torch.float32, device=dev) if want_log_psi else None
+        ws = self.workspace(flags) if workspace is None else workspace
+        self._check(lib().vqnqs_local_energy(
+            self._h, B, ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+            ctypes.c_void_p(mv.data_ptr() if mv is not None else 0),
+            ctypes.c_void_p(lp.data_ptr() if lp is not None else 0), int(flags),
+            ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+            "vqnqs_local_energy")
+        res = [e]
+        if want_mean_var:
+            res.append(mv)
+        if want_log_psi:
+            res.append(lp)
+        return res[0] if len(res) == 1 else tuple(res)
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        self._check(lib().vqnqs_get_stats(self._h, ctypes.byref(s)), "vqnqs_get_stats")
+        return {
+            "samples": s.samples, "configs": s.configs, "rows": s.rows,
+            "unique_rows": [int(s.unique_rows[i]) for i in range(self.layers + 1)],
+            "near_ties": s.near_ties, "flops_full": s.flops_full, "flops_done": s.flops_done,
+            "device_status": s.device_status,
+        }
+
+    def reset_stats(self):
+        self._check(lib().vqnqs_reset_stats(self._h), "vqnqs_reset_stats")
+
+    def profile(self, enable: bool = True):
+        self._check(lib().vqnqs_profile_enable(self._h, int(enable)), "vqnqs_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{stage: (calls, launches, ms)} since the last read."""
+        arr = (_lib.StageTime * _lib.MAX_STAGES)()
+        n = ctypes.c_int()
+        self._check(lib().vqnqs_profile_read(self._h, arr, _lib.MAX_STAGES, ctypes.byref(n)), "vqnqs_profile_read")
+        return {arr[i].name.decode(): (int(arr[i].calls), int(arr[i].launches), float(arr[i].ms))
+                for i in range(n.value)}
+
+    def launch_count(self) -> int:
+        return int(lib().vqnqs_launch_count(self._h))

@@ -1,0 +1,127 @@
+// Causal multi-head self-attention, FP32 on CUDA cores (Sec. 3.1 location mixer).
+//
+// One CTA per (configuration, head): the configuration's K and V rows for that
+// head are gathered by row id into shared memory, then each thread owns one
+// query position p and runs an online softmax over keys 0..p in chunks of 4.
+// The chunk loop is warp-uniform; chunks past a thread's own p are exact
+// no-ops (scale 1, weight 0), so a row's output never depends on which other
+// rows share its warp.  The attention output (before W_o) goes to O[row].
+#include "vqnqs_internal.cuh"
+
+namespace vq {
+
+template <int DH>
+__global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const float* __restrict__ qkv,
+                                float* __restrict__ O) {
+    extern __shared__ __align__(16) float s_kv[];  // [N][DH] keys then [N][DH] values
+    const int N = ch.N, d = ch.d, H = ch.heads;
+    const int C = ch.counters[CNT_C];
+    const float scale = rsqrtf((float)DH);
+    float* sK = s_kv;
+    float* sV = s_kv + (size_t)N * DH;
+    const int ld = 3 * d;
+    for (int item = blockIdx.x; item < C * H; item += gridDim.x) {
+        const int c = item / H, h = item - c * H;
+        const int* urow = uid + (size_t)c * N;
+        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+            int j = e / (DH / 4), t4 = (e - j * (DH / 4)) * 4;
+            const float* src = qkv + (size_t)urow[j] * ld + h * DH + t4;
+            *reinterpret_cast<float4*>(&sK[j * DH + t4]) = *reinterpret_cast<const float4*>(src + d);
+            *reinterpret_cast<float4*>(&sV[j * DH + t4]) = *reinterpret_cast<const float4*>(src + 2 * d);
+        }
+        __syncthreads();
+        const int p = threadIdx.x;
+        const bool active = p < N;
+        float q[DH], acc[DH];
+        if (active) {
+            const float* src = qkv + (size_t)urow[p] * ld + h * DH;
+#pragma unroll
+            for (int t = 0; t < DH; t += 4) {
+                float4 v = *reinterpret_cast<const float4*>(src + t);
+                q[t] = v.x; q[t + 1] = v.y; q[t + 2] = v.z; q[t + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < DH; ++t) q[t] = 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < DH; ++t) acc[t] = 0.f;
+        float m = -INFINITY, l = 0.f;
+        // warp-uniform bound: the largest p in this warp
+        int pw = min(N - 1, (int)(threadIdx.x | 31));
+        for (int j0 = 0; j0 <= pw; j0 += 4) {
+            float s[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = j0 + i;
+                float dot = 0.f;
+                if (j < N) {
+#pragma unroll
+                    for (int t = 0; t < DH; t += 4) {
+                        float4 k4 = *reinterpret_cast<const float4*>(&sK[j * DH + t]);
+                        dot = fmaf(q[t], k4.x, dot);
+                        dot = fmaf(q[t + 1], k4.y, dot);
+                        dot = fmaf(q[t + 2], k4.z, dot);
+                        dot = fmaf(q[t + 3], k4.w, dot);
+                    }
+                }
+                s[i] = (active && j <= p) ? dot * scale : -INFINITY;
+            }
+            const float mx = fmaxf(fmaxf(s[0], s[1]), fmaxf(s[2], s[3]));
+            const float mn = fmaxf(m, mx);
+            const float corr = (mn == -INFINITY) ? 1.f : expf(m - mn);
+            float e[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) e[i] = (s[i] == -INFINITY) ? 0.f : expf(s[i] - mn);
+            l = l * corr + ((e[0] + e[1]) + (e[2] + e[3]));
+#pragma unroll
+            for (int t = 0; t < DH; t += 4) {
+                float a0 = acc[t] * corr, a1 = acc[t + 1] * corr, a2 = acc[t + 2] * corr, a3 = acc[t + 3] * corr;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = min(j0 + i, N - 1);
+                    float4 v4 = *reinterpret_cast<const float4*>(&sV[j * DH + t]);
+                    a0 = fmaf(e[i], v4.x, a0);
+                    a1 = fmaf(e[i], v4.y, a1);
+                    a2 = fmaf(e[i], v4.z, a2);
+                    a3 = fmaf(e[i], v4.w, a3);
+                }
+                acc[t] = a0; acc[t + 1] = a1; acc[t + 2] = a2; acc[t + 3] = a3;
+            }
+            m = mn;
+        }
+        if (active) {
+            const float inv = 1.f / l;
+            float* dst = O + ((size_t)c * N + p) * d + h * DH;
+#pragma unroll
+            for (int t = 0; t < DH; t += 4)
+                *reinterpret_cast<float4*>(dst + t) =
+                    make_float4(acc[t] * inv, acc[t + 1] * inv, acc[t + 2] * inv, acc[t + 3] * inv);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, cudaStream_t st,
+                                 int grid) {
+    const int DH = ch.d / ch.heads;
+    const int threads = ((ch.N + 31) / 32) * 32;
+    const size_t smem = (size_t)2 * ch.N * DH * sizeof(float);
+    if (threads > 1024) return cudaErrorInvalidValue;
+    switch (DH) {
+#define VQ_ATT_CASE(X)                                                                                  \
+    case X:                                                                                             \
+        if (smem > 48 * 1024)                                                                           \
+            cudaFuncSetAttribute(k_attention_f32<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_attention_f32<X><<<grid, threads, smem, st>>>(ch, uid, qkv, O);                               \
+        break;
+        VQ_ATT_CASE(8)
+        VQ_ATT_CASE(16)
+        VQ_ATT_CASE(32)
+#undef VQ_ATT_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vq

@@ -1,0 +1,147 @@
+// Row-wise per-location operations: LayerNorm, the quantized residual update and
+// the weight-derived tables (Sec. 3.1 block, Sec. 3.2 per-location ops).
+#include "vqnqs_internal.cuh"
+
+namespace vq {
+
+// One warp per row; d % 32 == 0 and d <= 1024 so each lane keeps d / 32 values.
+template <int PER>
+__device__ __forceinline__ void ln_row(const float (&x)[PER], int lane, int d, const float* __restrict__ g,
+                                       const float* __restrict__ b, float (&y)[PER]) {
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) s += x[i];
+    float mu = warp_sum(s) / d;
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) { float t = x[i] - mu; v += t * t; }
+    float rstd = rsqrtf(warp_sum(v) / d + LN_EPS);
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        int k = lane + 32 * i;
+        y[i] = (x[i] - mu) * rstd * g[k] + b[k];
+    }
+}
+
+template <int PER>
+__global__ void k_layernorm(const float* __restrict__ X, const int* __restrict__ counters, int u_slot,
+                            const float* __restrict__ g, const float* __restrict__ b, int d,
+                            float* __restrict__ out_f32, __nv_bfloat16* __restrict__ out_bf16) {
+    const int U = counters[u_slot];
+    int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
+        float x[PER], y[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) x[i] = X[(size_t)u * d + lane + 32 * i];
+        ln_row<PER>(x, lane, d, g, b, y);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            size_t o = (size_t)u * d + lane + 32 * i;
+            if (out_f32) out_f32[o] = y[i];
+            if (out_bf16) out_bf16[o] = __float2bfloat16_rn(y[i]);
+        }
+    }
+}
+
+// y = x[rep_uid] + T[rep_code]  (T = codebook @ W_o + b_o), then A = LN2(y).
+template <int PER>
+__global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restrict__ rep_uid,
+                                 const int* __restrict__ rep_code, const float* __restrict__ T,
+                                 const int* __restrict__ counters, int u_slot, const float* __restrict__ g,
+                                 const float* __restrict__ b, int d, float* __restrict__ Y,
+                                 float* __restrict__ A_f32, __nv_bfloat16* __restrict__ A_bf16) {
+    const int U = counters[u_slot];
+    int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
+        const float* x = X + (size_t)rep_uid[u] * d;
+        const float* t = T + (size_t)rep_code[u] * d;
+        float y[PER], a[PER];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) y[i] = x[lane + 32 * i] + t[lane + 32 * i];
+        ln_row<PER>(y, lane, d, g, b, a);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            size_t o = (size_t)u * d + lane + 32 * i;
+            Y[o] = y[i];
+            if (A_f32) A_f32[o] = a[i];
+            if (A_bf16) A_bf16[o] = __float2bfloat16_rn(a[i]);
+        }
+    }
+}
+
+// T[j] = W_j @ w_o + b_o and cnorm[j] = ||W_j||^2, one block per codeword.
+__global__ void k_table_T(const float* __restrict__ cb, const float* __restrict__ wo, const float* __restrict__ bo,
+                          int K, int d, float* __restrict__ T, float* __restrict__ cnorm) {
+    extern __shared__ float s_w[];
+    for (int j = blockIdx.x; j < K; j += gridDim.x) {
+        for (int k = threadIdx.x; k < d; k += blockDim.x) s_w[k] = cb[(size_t)j * d + k];
+        __syncthreads();
+        for (int n = threadIdx.x; n < d; n += blockDim.x) {
+            float acc = 0.f;
+            for (int k = 0; k < d; ++k) acc = fmaf(s_w[k], wo[(size_t)k * d + n], acc);
+            T[(size_t)j * d + n] = acc + bo[n];
+        }
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int k = 0; k < d; ++k) s = fmaf(s_w[k], s_w[k], s);
+            cnorm[j] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// WT[c][r] = bf16(W[r][c])
+__global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols, __nv_bfloat16* __restrict__ WT) {
+    __shared__ float tile[32][33];
+    for (int by = blockIdx.y; by * 32 < rows; by += gridDim.y)
+        for (int bx = blockIdx.x; bx * 32 < cols; bx += gridDim.x) {
+            int r = by * 32 + threadIdx.y, c = bx * 32 + threadIdx.x;
+            tile[threadIdx.y][threadIdx.x] = (r < rows && c < cols) ? W[(size_t)r * cols + c] : 0.f;
+            __syncthreads();
+            int r2 = by * 32 + threadIdx.x, c2 = bx * 32 + threadIdx.y;
+            if (r2 < rows && c2 < cols) WT[(size_t)c2 * rows + r2] = __float2bfloat16_rn(tile[threadIdx.x][threadIdx.y]);
+            __syncthreads();
+        }
+}
+
+#define VQ_DISPATCH_PER(d, KERNEL, ...)                                 \
+    switch ((d) / 32) {                                                 \
+        case 1: KERNEL<1><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
+        case 2: KERNEL<2><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
+        case 4: KERNEL<4><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
+        case 6: KERNEL<6><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
+        case 8: KERNEL<8><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
+        case 12: KERNEL<12><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
+        case 16: KERNEL<16><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
+        case 24: KERNEL<24><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
+        case 32: KERNEL<32><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
+        default: return cudaErrorInvalidValue;                          \
+    }
+
+cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, const float* g, const float* b, int d,
+                             float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid) {
+    VQ_DISPATCH_PER(d, k_layernorm, X, counters, u_slot, g, b, d, out_f32, out_bf16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
+                                  const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
+                                  float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid) {
+    VQ_DISPATCH_PER(d, k_residual_vq_ln, X, rep_uid, rep_code, T, counters, u_slot, g, b, d, Y, A_f32, A_bf16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, float* T,
+                           float* cnorm, cudaStream_t st) {
+    int grid = K < 1024 ? K : 1024;
+    k_table_T<<<grid, 256, d * sizeof(float), st>>>(codebook, w_o, b_o, K, d, T, cnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st) {
+    dim3 grid((cols + 31) / 32 < 1024 ? (cols + 31) / 32 : 1024, (rows + 31) / 32 < 1024 ? (rows + 31) / 32 : 1024);
+    k_transpose_bf16<<<grid, dim3(32, 32), 0, st>>>(W, rows, cols, WT);
+    return cudaGetLastError();
+}
+
+}  // namespace vq
