@@ -20,6 +20,7 @@
  *    not required).  Values other than 0/1 raise VQNQS_DEV_BAD_SPIN.
  *  - Array arguments named dev_* are DEVICE pointers owned by the caller;
  *    weights passed to vqnqs_create are HOST memory and are copied.
+ *  - VQNQS_BF16 needs d_model % 64 == 0.
  *  - Calls that take a stream enqueue work on that cudaStream_t (NULL = legacy
  *    default stream) and return without synchronising; outputs are valid after
  *    the caller synchronises the stream.  They allocate nothing: all scratch
@@ -131,6 +132,66 @@ int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* d
                        double* dev_mean_var, float* dev_log_psi, int flags,
                        void* dev_ws, size_t ws_bytes, void* stream);
 
+/* Gradient of log psi through the straight-through quantizer (Sec. 3.1,
+ * Eq. st: the forward uses the nearest codeword, the backward flows through
+ * softmax(-||o - W_j||)), and the VMC energy gradient (Sec. 2):
+ *     O[b][k] = d log psi(s_b) / d theta_k        (theta in weight-blob order, P floats)
+ *     grad[k] = sum_b w_b O[b][k]
+ * with w_b = seeds[b] when dev_seeds is given, w_b = 2 (E_loc(s_b) - mean E_loc) / B
+ * (the energy gradient 2 mean[(E_loc - mean E_loc) O_k]) when dev_e_loc is
+ * given, else w_b = 1.
+ *   dev_spins   DEVICE uint8 [B][N]
+ *   dev_seeds   DEVICE float [B] or NULL;  dev_e_loc  DEVICE float [B] or NULL (not both)
+ *   dev_O       DEVICE float [B][P] or NULL (per-sample gradients)
+ *   dev_grad    DEVICE float [P] or NULL (at least one of O, grad)
+ *   flags       accepted for symmetry; the backward always computes in FP32
+ * Activations are recomputed layer by layer from the stored residual stream.
+ * Scratch: vqnqs_grad_workspace_bytes(ctx, B, chunk_samples) bytes. */
+size_t vqnqs_grad_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples);
+int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, const float* dev_seeds,
+                       const float* dev_e_loc, float* dev_O, float* dev_grad, int flags, void* dev_ws,
+                       size_t ws_bytes, void* stream);
+
+/* The per-location tensor-core GEMM on its own (the kernel behind the QKV and
+ * MLP steps of the BF16 path, Sec. 3.2 per-location operations):
+ *     C[M][N] = A[M][K] @ Bt[N][K]^T + bias[N]   (+ epilogue)
+ *   A, Bt      DEVICE bfloat16, row-major with K contiguous (Bt is the weight
+ *              stored [out][in])
+ *   bias       DEVICE float [N]
+ *   epilogue   0: C bfloat16 [M][N];  1: C bfloat16 of GELU(.);
+ *              2: C float [M][N] = . + R[M][N] (R DEVICE float);  3: C float
+ * Needs K % 64 == 0, N % 64 == 0 and 16-byte aligned pointers (else
+ * VQNQS_ERR_ARG).  BF16 x BF16 products, FP32 accumulation; asynchronous on
+ * `stream`; a stalled pipeline sets VQNQS_DEV_TIMEOUT in the status word. */
+int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* dev_A, const void* dev_Bt,
+                    const float* dev_bias, const float* dev_R, void* dev_C, int epilogue, void* stream);
+
+/* Nearest codeword of R vectors under layer `layer`'s codebook (Sec. 3.1, Eq. vq):
+ * code[r] = argmin_j ||W_j||^2 - 2 O[r] . W_j, lowest j on exact ties.
+ *   dev_O     DEVICE float [R][d_model] (16-byte aligned);  dev_code  DEVICE int32 [R] (output)
+ *   use_tensor_cores  0: FP32 FFMA kernel;  1: tensor-core kernel with split-TF32
+ *             products (FP32-grade; needs K % 16 == 0, K <= 512, d_model % 32 == 0)
+ * R is limited to 2^22 per call.  Near ties (relative gap < 1e-6) are counted
+ * in the statistics.  Asynchronous on `stream`. */
+int vqnqs_vq_assign(vqnqs_ctx* ctx, int layer, int R, const float* dev_O, int* dev_code, int use_tensor_cores,
+                    void* stream);
+
+/* The compressed (I, V) representation of Sec. 3.2 as a standalone step: every
+ * distinct (row id, code) pair among R rows gets a dense new id.
+ *   dev_uid, dev_code   DEVICE int32 [R]; 0 <= uid < 2^31, 0 <= code < 65536
+ *   dev_new_id          DEVICE int32 [R] (output): new id of each row
+ *   dev_rep_uid, dev_rep_code  DEVICE int32 [R] (output): the pair of each new
+ *                       id, in entries 0 .. U-1
+ *   dev_count           DEVICE int32 [1] (output): U, the number of distinct pairs
+ *   dev_ws, ws_bytes    DEVICE scratch (256-byte aligned) of at least
+ *                       vqnqs_compress_workspace_bytes(R) bytes for the hash table
+ * New ids are dense in [0, U); which pair gets which id is unspecified.
+ * Asynchronous on `stream`; probe-bound overruns set VQNQS_DEV_HASH_OVERFLOW. */
+size_t vqnqs_compress_workspace_bytes(int R);
+int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* dev_uid, const int* dev_code, int* dev_new_id,
+                        int* dev_rep_uid, int* dev_rep_code, int* dev_count, void* dev_ws, size_t ws_bytes,
+                        void* stream);
+
 /* Snapshot of the counters; synchronises the device first. */
 int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out);
 
@@ -141,8 +202,8 @@ int vqnqs_reset_stats(vqnqs_ctx* ctx);
  * CUDA events recorded on the stream it is launched on; vqnqs_profile_read
  * synchronises the device and returns, per stage, the number of kernel
  * launches and the summed event time since the last read (then clears them).
- * Stage names: config, embed, ln1, qkv_gemm, attention, vq_argmin, dedupe,
- * post_ln, mlp_up, mlp_down, head, eloc, mean_var. */
+ * Stage names: config, active_rows, embed, ln1, qkv_gemm, attention, vq_argmin, dedupe,
+ * post_ln, mlp_up, mlp_down, head, eloc, mean_var, backward. */
 typedef struct vqnqs_stage_time {
     char name[24];
     int64_t calls;     /* times the stage ran */

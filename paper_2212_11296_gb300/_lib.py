@@ -55,6 +55,17 @@ SIGNATURES = [
     ("vqnqs_local_energy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_gemm_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.c_void_p]),
+    ("vqnqs_grad_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("vqnqs_grad_log_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5 +
+     [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_vq_assign", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("vqnqs_compress_workspace_bytes", ctypes.c_size_t, [ctypes.c_int]),
+    ("vqnqs_compress_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 7 +
+     [ctypes.c_size_t, ctypes.c_void_p]),
     ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     ("vqnqs_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("vqnqs_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

@@ -155,3 +155,99 @@ class VQNQS:
 
     def launch_count(self) -> int:
         return int(lib().vqnqs_launch_count(self._h))
+
+    def gemm_bf16(self, A: torch.Tensor, Bt: torch.Tensor, bias: torch.Tensor, epilogue: int = 3,
+                  R: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """C = A @ Bt^T + bias with the library's tensor-core GEMM (see vqnqs_gemm_bf16)."""
+        _check_dev(A, torch.bfloat16, "A")
+        _check_dev(Bt, torch.bfloat16, "Bt")
+        _check_dev(bias, torch.float32, "bias")
+        M, K = A.shape
+        N = Bt.shape[0]
+        if out is None:
+            out = torch.empty(M, N, dtype=torch.bfloat16 if epilogue in (0, 1) else torch.float32, device=A.device)
+        if R is not None:
+            _check_dev(R, torch.float32, "R")
+        self._check(lib().vqnqs_gemm_bf16(self._h, M, N, K, ctypes.c_void_p(A.data_ptr()),
+                                          ctypes.c_void_p(Bt.data_ptr()), ctypes.c_void_p(bias.data_ptr()),
+                                          ctypes.c_void_p(R.data_ptr() if R is not None else 0),
+                                          ctypes.c_void_p(out.data_ptr()), int(epilogue),
+                                          ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_gemm_bf16")
+        return out
+
+    def compress_rows(self, uid: torch.Tensor, code: torch.Tensor, stream=None):
+        """Dense new ids of the distinct (uid, code) pairs (see vqnqs_compress_rows).
+
+        Returns (new_id [R], rep_uid [R], rep_code [R], count [1]) device tensors."""
+        _check_dev(uid, torch.int32, "uid")
+        _check_dev(code, torch.int32, "code")
+        R = uid.numel()
+        dev = uid.device
+        new_id = torch.empty(R, dtype=torch.int32, device=dev)
+        rep_uid = torch.empty(R, dtype=torch.int32, device=dev)
+        rep_code = torch.empty(R, dtype=torch.int32, device=dev)
+        count = torch.empty(1, dtype=torch.int32, device=dev)
+        ws = torch.empty(int(lib().vqnqs_compress_workspace_bytes(R)), dtype=torch.uint8, device=dev)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._check(lib().vqnqs_compress_rows(self._h, R, ptr(uid), ptr(code), ptr(new_id), ptr(rep_uid),
+                                              ptr(rep_code), ptr(count), ptr(ws), ws.numel(),
+                                              ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_compress_rows")
+        return new_id, rep_uid, rep_code, count
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().vqnqs_num_params(self.N, self.layers, self.d, self.K))
+
+    def grad_log_psi(self, spins: torch.Tensor, seeds: torch.Tensor | None = None,
+                     e_loc: torch.Tensor | None = None, want_O: bool = False, want_grad: bool = True,
+                     chunk_samples: int = 0, stream=None):
+        """(O [B, P] or None, grad [P] or None); see vqnqs_grad_log_psi."""
+        _check_dev(spins, torch.uint8, "spins")
+        B = spins.shape[0]
+        P = self.num_params
+        dev = spins.device
+        O = torch.empty(B, P, dtype=torch.float32, device=dev) if want_O else None
+        grad = torch.empty(P, dtype=torch.float32, device=dev) if want_grad else None
+        for t, name in ((seeds, "seeds"), (e_loc, "e_loc")):
+            if t is not None:
+                _check_dev(t, torch.float32, name)
+        ws = torch.empty(int(lib().vqnqs_grad_workspace_bytes(self._h, B, int(chunk_samples))), dtype=torch.uint8,
+                         device=dev)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+        self._check(lib().vqnqs_grad_log_psi(self._h, B, ptr(spins), ptr(seeds), ptr(e_loc), ptr(O), ptr(grad), 0,
+                                             ptr(ws), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_grad_log_psi")
+        return O, grad
+
+    def vq_assign(self, layer: int, O: torch.Tensor, tensor_cores: bool = False, stream=None) -> torch.Tensor:
+        """Nearest codeword of each row of O under layer `layer`'s codebook (see vqnqs_vq_assign)."""
+        _check_dev(O, torch.float32, "O")
+        R = O.shape[0]
+        code = torch.empty(R, dtype=torch.int32, device=O.device)
+        self._check(lib().vqnqs_vq_assign(self._h, int(layer), R, ctypes.c_void_p(O.data_ptr()),
+                                          ctypes.c_void_p(code.data_ptr()), int(tensor_cores),
+                                          ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_vq_assign")
+        return code
+
+
+class LogPsi(torch.autograd.Function):
+    """log psi(spins) as a differentiable function of the flat weight blob.
+
+    forward: uploads the weights into the model (vqnqs_set_weights) and calls
+    vqnqs_log_psi; backward: vqnqs_grad_log_psi seeded with the incoming
+    gradient, i.e. the hand-written straight-through backward with activation
+    recomputation."""
+
+    @staticmethod
+    def forward(ctx, weights: torch.Tensor, spins: torch.Tensor, model: VQNQS, flags: int = 0):
+        model.set_weights(weights.detach().contiguous())
+        lp = model.log_psi(spins, flags)
+        ctx.save_for_backward(spins)
+        ctx.model = model
+        return lp
+
+    @staticmethod
+    def backward(ctx, g):
+        (spins,) = ctx.saved_tensors
+        _, grad = ctx.model.grad_log_psi(spins, seeds=g.detach().float().contiguous())
+        return grad, None, None, None

@@ -6,13 +6,23 @@
 // The chunk loop is warp-uniform; chunks past a thread's own p are exact
 // no-ops (scale 1, weight 0), so a row's output never depends on which other
 // rows share its warp.  The attention output (before W_o) goes to O[row].
+// The Q/K/V input is FP32 (plain path) or BF16 (BF16 path: the QKV GEMM's
+// rounded output); products and sums are FP32 either way.
 #include "vqnqs_internal.cuh"
 
 namespace vq {
 
-template <int DH>
-__global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const float* __restrict__ qkv,
-                                float* __restrict__ O) {
+__device__ __forceinline__ float4 load4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+    uint2 u = *reinterpret_cast<const uint2*>(p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x), b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+template <int DH, typename T>
+__global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* __restrict__ qkv,
+                                float* __restrict__ O, int prefix_reuse) {
     extern __shared__ __align__(16) float s_kv[];  // [N][DH] keys then [N][DH] values
     const int N = ch.N, d = ch.d, H = ch.heads;
     const int C = ch.counters[CNT_C];
@@ -25,19 +35,20 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const flo
         const int* urow = uid + (size_t)c * N;
         for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
             int j = e / (DH / 4), t4 = (e - j * (DH / 4)) * 4;
-            const float* src = qkv + (size_t)urow[j] * ld + h * DH + t4;
-            *reinterpret_cast<float4*>(&sK[j * DH + t4]) = *reinterpret_cast<const float4*>(src + d);
-            *reinterpret_cast<float4*>(&sV[j * DH + t4]) = *reinterpret_cast<const float4*>(src + 2 * d);
+            const T* src = qkv + (size_t)urow[j] * ld + h * DH + t4;
+            *reinterpret_cast<float4*>(&sK[j * DH + t4]) = load4(src + d);
+            *reinterpret_cast<float4*>(&sV[j * DH + t4]) = load4(src + 2 * d);
         }
         __syncthreads();
         const int p = threadIdx.x;
-        const bool active = p < N;
+        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const bool active = p < N && p >= p0;
         float q[DH], acc[DH];
         if (active) {
-            const float* src = qkv + (size_t)urow[p] * ld + h * DH;
+            const T* src = qkv + (size_t)urow[p] * ld + h * DH;
 #pragma unroll
             for (int t = 0; t < DH; t += 4) {
-                float4 v = *reinterpret_cast<const float4*>(src + t);
+                float4 v = load4(src + t);
                 q[t] = v.x; q[t + 1] = v.y; q[t + 2] = v.z; q[t + 3] = v.w;
             }
         } else {
@@ -47,8 +58,10 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const flo
 #pragma unroll
         for (int t = 0; t < DH; ++t) acc[t] = 0.f;
         float m = -INFINITY, l = 0.f;
-        // warp-uniform bound: the largest p in this warp
+        // warp-uniform bound: the largest p in this warp (no keys at all when the
+        // whole warp lies before the first changed position)
         int pw = min(N - 1, (int)(threadIdx.x | 31));
+        if (pw < p0) pw = -1;
         for (int j0 = 0; j0 <= pw; j0 += 4) {
             float s[4];
 #pragma unroll
@@ -102,18 +115,19 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const flo
     }
 }
 
-cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, cudaStream_t st,
-                                 int grid) {
+template <typename T>
+cudaError_t launch_attention_t(const Chunk& ch, const int* uid, const T* qkv, float* O, int prefix_reuse,
+                               cudaStream_t st, int grid) {
     const int DH = ch.d / ch.heads;
     const int threads = ((ch.N + 31) / 32) * 32;
     const size_t smem = (size_t)2 * ch.N * DH * sizeof(float);
     if (threads > 1024) return cudaErrorInvalidValue;
     switch (DH) {
-#define VQ_ATT_CASE(X)                                                                                  \
-    case X:                                                                                             \
-        if (smem > 48 * 1024)                                                                           \
-            cudaFuncSetAttribute(k_attention_f32<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        k_attention_f32<X><<<grid, threads, smem, st>>>(ch, uid, qkv, O);                               \
+#define VQ_ATT_CASE(X)                                                                                        \
+    case X:                                                                                                   \
+        if (smem > 48 * 1024)                                                                                 \
+            cudaFuncSetAttribute(k_attention_f32<X, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        k_attention_f32<X, T><<<grid, threads, smem, st>>>(ch, uid, qkv, O, prefix_reuse);                                  \
         break;
         VQ_ATT_CASE(8)
         VQ_ATT_CASE(16)
@@ -122,6 +136,16 @@ cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* q
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, int prefix_reuse,
+                                 cudaStream_t st, int grid) {
+    return launch_attention_t<float>(ch, uid, qkv, O, prefix_reuse, st, grid);
+}
+
+cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                                   int prefix_reuse, cudaStream_t st, int grid) {
+    return launch_attention_t<__nv_bfloat16>(ch, uid, qkv, O, prefix_reuse, st, grid);
 }
 
 }  // namespace vq

@@ -121,6 +121,64 @@ __global__ void k_fill_configs(const uint8_t* __restrict__ spins, int S, int N, 
     }
 }
 
+// ---- active rows -------------------------------------------------------------------
+__global__ void k_active_count(Chunk ch, int prefix_reuse, int* __restrict__ act_cnt) {
+    const int C = ch.counters[CNT_C];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        act_cnt[c] = ch.N - (prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0);
+}
+
+// Exclusive scan of act_cnt over the chunk's configurations (one block); total -> CNT_A.
+__global__ void k_active_scan(Chunk ch, const int* __restrict__ act_cnt, int* __restrict__ act_off) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int C = ch.counters[CNT_C];
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < C; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = (i < C) ? act_cnt[i] : 0;
+        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int nw = blockDim.x >> 5;
+            int t = (lane < nw) ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nw) s_warp[lane] = t;
+        }
+        __syncthreads();
+        int incl = x + (w > 0 ? s_warp[w - 1] : 0) + s_carry;
+        if (i < C) act_off[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ch.counters[CNT_A] = s_carry;
+}
+
+// One warp per configuration writes its active rows (ascending).
+__global__ void k_active_fill(Chunk ch, int prefix_reuse, const int* __restrict__ act_off,
+                              int* __restrict__ act_rows) {
+    const int C = ch.counters[CNT_C], N = ch.N;
+    int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
+        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int off = act_off[c];
+        for (int p = p0 + lane; p < N; p += 32) act_rows[off + p - p0] = c * N + p;
+    }
+}
+
 // ---- embedding: x0 = tok_emb[token] + pos_emb[p], token = s_{p-1} (BOS at p = 0) --------
 // reuse: rows are keyed by (p, token) -> uid p * 3 + token, table of 3N rows.
 // full:  every (config, position) row gets its own copy.
@@ -298,6 +356,13 @@ cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos
         if (e != cudaSuccess) return e;
     }
     k_embed_rows<<<grid, 256, 0, st>>>(ch, tok_emb, pos_emb, reuse, X0, uid0);
+    return cudaGetLastError();
+}
+cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
+                               cudaStream_t st, int grid) {
+    k_active_count<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_cnt);
+    k_active_scan<<<1, 1024, 0, st>>>(ch, act_cnt, act_off);
+    k_active_fill<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_off, act_rows);
     return cudaGetLastError();
 }
 cudaError_t launch_head(const float* X, const int* counters, int u_slot, const float* g, const float* b,

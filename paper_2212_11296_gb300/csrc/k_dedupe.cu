@@ -36,53 +36,98 @@ __global__ void k_hash_clear(unsigned long long* __restrict__ keys, size_t H, in
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[u_slot_next] = 0;
 }
 
-__global__ void k_dedupe_insert(const int* __restrict__ uid_cur, const int* __restrict__ code,
-                                int* __restrict__ counters, int u_slot_next, unsigned long long* __restrict__ keys,
-                                int* __restrict__ vals, unsigned long long mask, int* __restrict__ rep_uid,
-                                int* __restrict__ rep_code, int* __restrict__ status) {
-    const int R = counters[CNT_R];
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        const int u = uid_cur[r], c = code[r];
-        const unsigned long long key = make_key(u, c);
-        unsigned long long h = mix64(key) & mask;
-        bool done = false;
-        for (unsigned long long probe = 0; probe <= mask; ++probe) {
-            unsigned long long prev = atomicCAS(&keys[h], 0ULL, key);
-            if (prev == 0ULL) {
-                const int id = atomicAdd(&counters[u_slot_next], 1);
-                vals[h] = id;
-                rep_uid[id] = u;
-                rep_code[id] = c;
-                done = true;
-                break;
-            }
-            if (prev == key) { done = true; break; }
-            h = (h + 1) & mask;
-        }
-        if (!done) atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
-    }
+// Code of row r: its own, or (before its configuration's first changed position)
+// the code of the same position in the sample's own configuration, which is
+// the same computation on the same inputs.
+__device__ __forceinline__ int row_code(const Chunk& ch, const int* __restrict__ code, int r) {
+    const int c = r / ch.N, p = r - c * ch.N;
+    if (p < cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c])) return code[ch.cfg_off[ch.cfg_sample[c]] * ch.N + p];
+    return code[r];
 }
 
-__global__ void k_dedupe_lookup(const int* __restrict__ uid_cur, const int* __restrict__ code,
-                                const int* __restrict__ counters, const unsigned long long* __restrict__ keys,
+// Inserts key; the thread that claims the slot takes the next id from *counter
+// and records the representative pair.  Returns false when the probe bound ran out.
+__device__ __forceinline__ bool hash_insert(unsigned long long* __restrict__ keys, int* __restrict__ vals,
+                                            unsigned long long mask, int u, int c, int* __restrict__ counter,
+                                            int* __restrict__ rep_uid, int* __restrict__ rep_code) {
+    const unsigned long long key = make_key(u, c);
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long prev = atomicCAS(&keys[h], 0ULL, key);
+        if (prev == 0ULL) {
+            const int id = atomicAdd(counter, 1);
+            vals[h] = id;
+            rep_uid[id] = u;
+            rep_code[id] = c;
+            return true;
+        }
+        if (prev == key) return true;
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+// Id of an inserted key, or -1 when the probe bound ran out.
+__device__ __forceinline__ int hash_lookup(const unsigned long long* __restrict__ keys, const int* __restrict__ vals,
+                                           unsigned long long mask, int u, int c) {
+    const unsigned long long key = make_key(u, c);
+    unsigned long long h = mix64(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        const unsigned long long k = keys[h];
+        if (k == key) return vals[h];
+        if (k == 0ULL) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+__global__ void k_dedupe_insert(Chunk ch, const int* __restrict__ uid_cur, const int* __restrict__ code,
+                                int u_slot_next, unsigned long long* __restrict__ keys,
+                                int* __restrict__ vals, unsigned long long mask, int* __restrict__ rep_uid,
+                                int* __restrict__ rep_code, int* __restrict__ status) {
+    int* counters = ch.counters;
+    const int R = counters[CNT_R];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+        if (!hash_insert(keys, vals, mask, uid_cur[r], row_code(ch, code, r), &counters[u_slot_next], rep_uid,
+                         rep_code))
+            atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
+}
+
+__global__ void k_dedupe_lookup(Chunk ch, const int* __restrict__ uid_cur, const int* __restrict__ code,
+                                const unsigned long long* __restrict__ keys,
                                 const int* __restrict__ vals, unsigned long long mask, int* __restrict__ uid_next,
                                 int* __restrict__ status) {
-    const int R = counters[CNT_R];
+    const int R = ch.counters[CNT_R];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
-        const unsigned long long key = make_key(uid_cur[r], code[r]);
-        unsigned long long h = mix64(key) & mask;
-        int id = -1;
-        for (unsigned long long probe = 0; probe <= mask; ++probe) {
-            unsigned long long k = keys[h];
-            if (k == key) { id = vals[h]; break; }
-            if (k == 0ULL) break;
-            h = (h + 1) & mask;
-        }
+        int id = hash_lookup(keys, vals, mask, uid_cur[r], row_code(ch, code, r));
         if (id < 0) {
             atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
             id = 0;
         }
         uid_next[r] = id;
+    }
+}
+
+// ---- standalone (I, V) compression of R (row id, code) pairs --------------------
+__global__ void k_pairs_insert(int R, const int* __restrict__ uid, const int* __restrict__ code,
+                               unsigned long long* __restrict__ keys, int* __restrict__ vals, unsigned long long mask,
+                               int* __restrict__ count, int* __restrict__ rep_uid, int* __restrict__ rep_code,
+                               int* __restrict__ status) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+        if (!hash_insert(keys, vals, mask, uid[r], code[r], count, rep_uid, rep_code))
+            atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
+}
+
+__global__ void k_pairs_lookup(int R, const int* __restrict__ uid, const int* __restrict__ code,
+                               const unsigned long long* __restrict__ keys, const int* __restrict__ vals,
+                               unsigned long long mask, int* __restrict__ new_id, int* __restrict__ status) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        int id = hash_lookup(keys, vals, mask, uid[r], code[r]);
+        if (id < 0) {
+            atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
+            id = 0;
+        }
+        new_id[r] = id;
     }
 }
 
@@ -98,9 +143,30 @@ __global__ void k_identity_keys(const int* __restrict__ uid_cur, const int* __re
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[u_slot_next] = R;
 }
 
-cudaError_t launch_dedupe(const int* uid_cur, const int* code, int* counters, int u_slot_next, int Rmax,
+int compress_hash_bits(int R) {
+    int hb = 4;
+    while ((1LL << hb) < 2LL * R) ++hb;
+    return hb;
+}
+
+cudaError_t launch_compress_pairs(int R, const int* uid, const int* code, int* new_id, int* rep_uid, int* rep_code,
+                                  int* count, unsigned long long* keys, int* vals, int hash_bits, int* status,
+                                  cudaStream_t st, int num_sms) {
+    const size_t H = (size_t)1 << hash_bits;
+    const unsigned long long mask = (unsigned long long)H - 1ULL;
+    int grid = (R + 255) / 256;
+    if (grid > 8 * num_sms) grid = 8 * num_sms;
+    if (grid < 1) grid = 1;
+    k_hash_clear<<<8 * num_sms, 256, 0, st>>>(keys, H, count, 0);
+    k_pairs_insert<<<grid, 256, 0, st>>>(R, uid, code, keys, vals, mask, count, rep_uid, rep_code, status);
+    k_pairs_lookup<<<grid, 256, 0, st>>>(R, uid, code, keys, vals, mask, new_id, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dedupe(const Chunk& ch, const int* uid_cur, const int* code, int u_slot_next, int Rmax,
                           unsigned long long* keys, int* vals, int hash_bits, int* uid_next, int* rep_uid,
                           int* rep_code, int reuse, int* status, cudaStream_t st, int num_sms) {
+    int* counters = ch.counters;
     int grid = (Rmax + 255) / 256;
     if (grid > 8 * num_sms) grid = 8 * num_sms;
     if (grid < 1) grid = 1;
@@ -111,9 +177,8 @@ cudaError_t launch_dedupe(const int* uid_cur, const int* code, int* counters, in
     const size_t H = (size_t)1 << hash_bits;
     const unsigned long long mask = (unsigned long long)H - 1ULL;
     k_hash_clear<<<8 * num_sms, 256, 0, st>>>(keys, H, counters, u_slot_next);
-    k_dedupe_insert<<<grid, 256, 0, st>>>(uid_cur, code, counters, u_slot_next, keys, vals, mask, rep_uid, rep_code,
-                                          status);
-    k_dedupe_lookup<<<grid, 256, 0, st>>>(uid_cur, code, counters, keys, vals, mask, uid_next, status);
+    k_dedupe_insert<<<grid, 256, 0, st>>>(ch, uid_cur, code, u_slot_next, keys, vals, mask, rep_uid, rep_code, status);
+    k_dedupe_lookup<<<grid, 256, 0, st>>>(ch, uid_cur, code, keys, vals, mask, uid_next, status);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,288 @@
+// BF16 tensor-core GEMM for the per-location operations (Sec. 3.2: QKV
+// projection, MLP up + GELU, MLP down + residual), FP32 accumulation in TMEM.
+//
+//   C[M, N] = A[M, K] @ Bt[N, K]^T + bias (+ epilogue),  A and Bt K-major BF16.
+//
+// Persistent kernel, one CTA per SM, 6 warps:
+//   warp 0      one thread issues TMA tile loads (128-byte swizzle) into a ring
+//               of STAGES shared-memory slots, completion tracked by mbarriers;
+//   warp 1      one thread issues tcgen05.mma (M = 128, N = BN, K = 16) into a
+//               double-buffered TMEM accumulator and commits slot releases;
+//               the warp also owns the TMEM allocation;
+//   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter, bias /
+//               activation / residual in FP32, stores to global memory, then
+//               release the accumulator buffer so the next tile's MMAs overlap.
+// The row count M is read from device memory (unique rows are only known on
+// the device).  Every wait is bounded; on timeout the kernel sets
+// VQNQS_DEV_TIMEOUT, drains its own in-flight copies and frees its TMEM.
+// A row's result depends only on that row: the K loop order is fixed.
+#include <cstdio>
+
+#include "tc_common.cuh"
+
+namespace vq {
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 192;
+
+template <int BN>
+struct TcCfg {
+    static constexpr int STAGES = BN >= 192 ? 4 : 6;
+    static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+};
+
+__device__ __forceinline__ float gelu_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const float* __restrict__ bias, const float* __restrict__ R, void* __restrict__ Cout,
+          const int* __restrict__ counters, int u_slot, int N, int K, int* __restrict__ status) {
+    using C = TcCfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + C::STAGES * C::A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::STAGES * C::B_BYTES);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* accf = empty + C::STAGES;
+    uint64_t* acce = accf + 2;
+    uint64_t* done = acce + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+
+    const int M = counters[u_slot];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = N / BN, m_tiles = (M + TC_BM - 1) / TC_BM, total = m_tiles * n_tiles;
+    const int KB = K / TC_BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 128); }
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_holder, C::TMEM_COLS);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&tmA);
+            tc::prefetch_tmap(&tmB);
+            bool ok = true;
+            int it = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % C::STAGES;
+                    const uint32_t ph = (it / C::STAGES) & 1;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
+                    tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+                    tc::tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * TC_BK, m0, &full[s]);
+                    tc::tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * TC_BK, n0, &full[s]);
+                }
+            }
+            if (!ok) {  // wait (bounded) for the copies this thread still has in flight
+                for (int j = it - C::STAGES; j < it; ++j)
+                    if (j >= 0) tc::mbar_wait(&full[j % C::STAGES], (j / C::STAGES) & 1, status, 100000000LL);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_BM, BN);
+            bool ok = true;
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
+                const int a = i & 1;
+                const uint32_t aph = (i >> 1) & 1;
+                if (!tc::mbar_wait(&acce[a], aph ^ 1, status)) { ok = false; break; }
+                tc::tc_fence_after();
+                const uint32_t d_tmem = tmem + a * BN;
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % C::STAGES;
+                    const uint32_t ph = (it / C::STAGES) & 1;
+                    if (!tc::mbar_wait(&full[s], ph, status)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint64_t da = tc::desc_kmajor_sw128(tc::smem_u32(sA + s * C::A_BYTES));
+                    const uint64_t db = tc::desc_kmajor_sw128(tc::smem_u32(sB + s * C::B_BYTES));
+#pragma unroll
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        tc::mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&accf[a]);
+            }
+            // every MMA this thread issued has completed before TMEM is freed
+            tc::mma_commit(done);
+            tc::mbar_wait(done, 0, status, 100000000LL);
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are reachable from this warp
+        int i = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            const int a = i & 1;
+            const uint32_t aph = (i >> 1) & 1;
+            if (!tc::mbar_wait(&accf[a], aph, status)) break;
+            tc::tc_fence_after();
+            const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
+            const int row = m0 + q * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * BN + c, r);
+                if (row < M) {
+                    const int n = n0 + c;
+                    float v[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias[n + j];
+                    if (EPI == 2) {  // FP32 out + residual
+                        const float4* rr = reinterpret_cast<const float4*>(R + (size_t)row * N + n);
+                        float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + (size_t)row * N + n);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 x = rr[j];
+                            out[j] = make_float4(v[4 * j] + x.x, v[4 * j + 1] + x.y, v[4 * j + 2] + x.z,
+                                                 v[4 * j + 3] + x.w);
+                        }
+                    } else if (EPI == 3) {  // FP32 out
+                        float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + (size_t)row * N + n);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) out[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    } else {  // BF16 out, optionally GELU
+                        uint32_t p[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            float x0 = v[2 * j], x1 = v[2 * j + 1];
+                            if (EPI == 1) { x0 = gelu_tc(x0); x1 = gelu_tc(x1); }
+                            __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                            p[j] = *reinterpret_cast<uint32_t*>(&h);
+                        }
+                        uint4* out = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + n);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) out[j] = make_uint4(p[4 * j], p[4 * j + 1], p[4 * j + 2], p[4 * j + 3]);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&acce[a]);
+        }
+    }
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+// ---- host side -----------------------------------------------------------------
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+template <int BN, int EPI>
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, const float* R, void* Cout,
+                      const int* counters, int u_slot, int Mmax, int N, int K, int* status, cudaStream_t st,
+                      int num_sms) {
+    using C = TcCfg<BN>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    long long tiles = (long long)((Mmax + TC_BM - 1) / TC_BM) * (N / BN);
+    int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    if (grid < 1) grid = 1;
+    k_gemm_tc<BN, EPI><<<grid, TC_THREADS, C::SMEM, st>>>(ta, tb, bias, R, Cout, counters, u_slot, N, K, status);
+    return cudaGetLastError();
+}
+
+template <int EPI>
+cudaError_t launch_epi(int BN, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, const float* R,
+                       void* Cout, const int* counters, int u_slot, int Mmax, int N, int K, int* status,
+                       cudaStream_t st, int num_sms) {
+    switch (BN) {
+        case 64: return launch_bn<64, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 128: return launch_bn<128, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 192: return launch_bn<192, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 256: return launch_bn<256, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st) {
+    k_set_int<<<1, 1, 0, st>>>(p, v);
+    return cudaGetLastError();
+}
+
+int tc_pick_bn(int N) {
+    if (N % 256 == 0) return 256;
+    if (N % 192 == 0) return 192;
+    if (N % 128 == 0) return 128;
+    if (N % 64 == 0) return 64;
+    return 0;
+}
+
+cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * 2) % 16) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
+                           const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
+                           int* status, cudaStream_t st, int num_sms) {
+    const int BN = tc_pick_bn(N);
+    if (!BN || K % TC_BK || K <= 0) return cudaErrorInvalidValue;
+    CUtensorMap ta;
+    cudaError_t e = make_tmap_bf16(&ta, A, Arows, K, TC_BM);
+    if (e != cudaSuccess) return e;
+    const int Mmax = (int)Arows;
+    switch (epi) {
+        case 0: return launch_epi<0>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 1: return launch_epi<1>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 2: return launch_epi<2>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 3: return launch_epi<3>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace vq

@@ -32,13 +32,13 @@ __device__ __forceinline__ void best_merge(Best& a, float c1, int j1, float c2) 
 }
 
 __global__ void __launch_bounds__(VQ_THREADS, 2)
-k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const float* __restrict__ W,
-            const float* __restrict__ cnorm, int K, int d, int* __restrict__ code,
+k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
+            const float* __restrict__ W, const float* __restrict__ cnorm, int K, int d, int* __restrict__ code,
             long long* __restrict__ near_ties) {
     __shared__ __align__(16) float As[2][VQ_BK][VQ_BM];
     __shared__ __align__(16) float Bs[2][VQ_BK][VQ_BN];  // Bs[k][j] = W[j][k]
     __shared__ int s_ties;
-    const int R = counters[CNT_R];
+    const int R = act_rows ? counters[CNT_A] : counters[CNT_R];  // rows to assign
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int a_row = tid >> 1, a_k = (tid & 1) * 4;
     const int b_j = tid >> 1, b_k = (tid & 1) * 4;  // codeword rows are loaded like A rows
@@ -50,7 +50,8 @@ k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const
 #pragma unroll
         for (int i = 0; i < 8; ++i) { best[i].v1 = INFINITY; best[i].i1 = 0x7fffffff; best[i].v2 = INFINITY; osq[i] = 0.f; }
         const bool a_ok = (m0 + a_row) < R;
-        const float* a_ptr = O + (size_t)(m0 + a_row) * d + a_k;
+        const int a_src = a_ok ? (act_rows ? act_rows[m0 + a_row] : m0 + a_row) : 0;
+        const float* a_ptr = O + (size_t)a_src * d + a_k;
 
         for (int n0 = 0; n0 < K; n0 += VQ_BN) {
             float acc[8][8];
@@ -132,7 +133,7 @@ k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const
             for (int i = 0; i < 8; ++i) {
                 const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
                 if (m < R) {
-                    code[m] = best[i].i1;
+                    code[act_rows ? act_rows[m] : m] = best[i].i1;
                     const float l1 = best[i].v1 + osq[i], l2 = best[i].v2 + osq[i];
                     if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
                 }
@@ -144,13 +145,25 @@ k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const
     if (tid == 0 && s_ties) atomicAdd(reinterpret_cast<unsigned long long*>(near_ties), (unsigned long long)s_ties);
 }
 
-cudaError_t launch_vq_argmin(const float* O, const int* counters, const float* codebook, const float* cnorm, int K,
-                             int d, int* code, long long* near_ties, int Rmax, cudaStream_t st, int num_sms) {
+__global__ void k_assign_setup(int* __restrict__ counters, int* __restrict__ rows, int R) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) rows[i] = i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { counters[CNT_A] = R; counters[CNT_R] = R; }
+}
+
+cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st) {
+    int grid = (R + 255) / 256;
+    k_assign_setup<<<grid < 1024 ? (grid < 1 ? 1 : grid) : 1024, 256, 0, st>>>(counters, rows, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
+                             const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
+                             cudaStream_t st, int num_sms) {
     if (d % VQ_BK) return cudaErrorInvalidValue;
     int tiles = (Rmax + VQ_BM - 1) / VQ_BM;
     int grid = tiles < 2 * num_sms ? tiles : 2 * num_sms;
     if (grid < 1) grid = 1;
-    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, counters, codebook, cnorm, K, d, code, near_ties);
+    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, counters, act_rows, codebook, cnorm, K, d, code, near_ties);
     return cudaGetLastError();
 }
 

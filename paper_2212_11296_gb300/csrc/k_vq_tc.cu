@@ -1,0 +1,302 @@
+// Nearest-codeword assignment on the tensor cores with FP32-grade distances
+// (Sec. 3.1, Eq. vq): code(o) = argmin_j ||W_j||^2 - 2 o . W_j, lowest j on ties.
+//
+// o . W_j is a [rows x d] x [d x K] contraction.  Each FP32 operand x is split
+// into x_hi = tf32(x) and x_lo = tf32(x - x_hi); the product is accumulated as
+// o_hi W_hi + o_hi W_lo + o_lo W_hi (the lo x lo term is below 2^-22 relative),
+// which keeps the dot products at FP32 accuracy on the TF32 tensor pipe.
+//
+// Persistent CTA of 5 warps per SM, one 128-row tile of active rows at a time:
+//   warps 0-3  gather the tile's O rows, split them, write the hi/lo A chunks
+//              (32 columns each, 128-byte swizzle) into a 2-slot ring; then,
+//              per tile, read the K accumulator columns from TMEM and reduce
+//              (best, index, second best) per row;
+//   warp 4     one thread: TMA of the codebook hi/lo chunks (precomputed per
+//              layer) and the tcgen05.mma (kind::tf32, M = 128, N <= 256, K = 8)
+//              issue, slot release by tcgen05.commit.
+// All waits are bounded (VQNQS_DEV_TIMEOUT).
+#include "tc_common.cuh"
+
+namespace vq {
+
+constexpr int VT_BM = 128, VT_BK = 32, VT_THREADS = 160;
+
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// byte offset of element (r, k) (4-byte elements, 32 per row) in a 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+struct VqBest {
+    float v1;
+    int i1;
+    float v2;
+};
+
+__device__ __forceinline__ void vq_merge(VqBest& a, float c, int j) {
+    if (c < a.v1 || (c == a.v1 && j < a.i1)) {
+        a.v2 = a.v1;
+        a.v1 = c;
+        a.i1 = j;
+    } else {
+        a.v2 = fminf(a.v2, c);
+    }
+}
+
+template <int KC>  // codewords per pass (N of the MMA), K <= 2 * KC
+__global__ void __launch_bounds__(VT_THREADS, 1)
+k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+        const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
+        const float* __restrict__ cnorm, int K, int d, int* __restrict__ code, long long* __restrict__ near_ties,
+        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols) {
+    constexpr int A_BYTES = VT_BM * VT_BK * 4;   // 16 KB per part
+    constexpr int B_BYTES = KC * VT_BK * 4;      // per part and pass
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int passes = (K + KC - 1) / KC;
+    // slot s: A_hi, A_lo, then for each pass: B_hi, B_lo
+    const int SLOT = 2 * A_BYTES + passes * 2 * B_BYTES;
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(smem + VT_STAGES * SLOT);
+    uint64_t* fullB = fullA + VT_STAGES;
+    uint64_t* empty = fullB + VT_STAGES;
+    uint64_t* accf = empty + VT_STAGES;
+    uint64_t* acce = accf + 1;
+    uint64_t* done = acce + 1;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_ties;
+
+    const int R = counters[CNT_A];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int tiles = (R + VT_BM - 1) / VT_BM, KB = d / VT_BK;
+    if (tid == 0) {
+        for (int s = 0; s < VT_STAGES; ++s) {
+            tc::mbar_init(&fullA[s], 128);
+            tc::mbar_init(&fullB[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accf, 1);
+        tc::mbar_init(acce, 128);
+        tc::mbar_init(done, 1);
+        tc::fence_barrier_init();
+        s_ties = 0;
+    }
+    if (warp == 4) tc::tmem_alloc(tmem_holder, tmem_cols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            tc::prefetch_tmap(&tm_hi);
+            tc::prefetch_tmap(&tm_lo);
+            constexpr uint32_t idesc = idesc_tf32_f32(VT_BM, KC);
+            bool ok = true;
+            int it = 0, i = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+                if (!tc::mbar_wait(acce, (i & 1) ^ 1, status)) { ok = false; break; }
+                tc::tc_fence_after();
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % VT_STAGES;
+                    const uint32_t ph = (it / VT_STAGES) & 1;
+                    uint8_t* slot = smem + s * SLOT;
+                    // codebook chunk (the A rows are written by the loader warps)
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
+                    tc::mbar_arrive_expect_tx(&fullB[s], passes * 2 * B_BYTES);
+                    for (int ps = 0; ps < passes; ++ps) {
+                        uint8_t* bh = slot + 2 * A_BYTES + ps * 2 * B_BYTES;
+                        tc::tma_load_2d(bh, &tm_hi, kb * VT_BK, ps * KC, &fullB[s]);
+                        tc::tma_load_2d(bh + B_BYTES, &tm_lo, kb * VT_BK, ps * KC, &fullB[s]);
+                    }
+                    if (!tc::mbar_wait(&fullB[s], ph, status) || !tc::mbar_wait(&fullA[s], ph, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint64_t dah = tc::desc_kmajor_sw128(tc::smem_u32(slot));
+                    const uint64_t dal = tc::desc_kmajor_sw128(tc::smem_u32(slot + A_BYTES));
+                    for (int ps = 0; ps < passes; ++ps) {
+                        uint8_t* bh = slot + 2 * A_BYTES + ps * 2 * B_BYTES;
+                        const uint64_t dbh = tc::desc_kmajor_sw128(tc::smem_u32(bh));
+                        const uint64_t dbl = tc::desc_kmajor_sw128(tc::smem_u32(bh + B_BYTES));
+                        const uint32_t dt = tmem + ps * KC;
+#pragma unroll
+                        for (int k = 0; k < VT_BK / 8; ++k) {
+                            const uint32_t acc0 = (kb | k) != 0 ? 1u : 0u;
+                            mma_tf32(dt, dah + 2 * k, dbh + 2 * k, idesc, acc0);
+                            mma_tf32(dt, dah + 2 * k, dbl + 2 * k, idesc, 1u);
+                            mma_tf32(dt, dal + 2 * k, dbh + 2 * k, idesc, 1u);
+                        }
+                    }
+                    tc::mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(accf);
+            }
+            tc::mma_commit(done);
+            tc::mbar_wait(done, 0, status, 100000000LL);
+            if (!ok) {  // drain this thread's own copies still in flight
+                for (int j = it - VT_STAGES; j <= it; ++j)
+                    if (j >= 0) tc::mbar_wait(&fullB[j % VT_STAGES], (j / VT_STAGES) & 1, status, 100000000LL);
+            }
+        }
+    } else {
+        // loaders / epilogue: thread tid owns tile row tid
+        int it = 0, i = 0;
+        int ties = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int m = t * VT_BM + tid;
+            const bool valid = m < R;
+            const float* orow = O + (size_t)(valid ? act_rows[m] : 0) * d;
+            float osq = 0.f;
+            bool ok = true;
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+                const int s = it % VT_STAGES;
+                const uint32_t ph = (it / VT_STAGES) & 1;
+                if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
+                uint8_t* slot = smem + s * SLOT;
+#pragma unroll
+                for (int q = 0; q < VT_BK; q += 4) {
+                    float4 v = valid ? *reinterpret_cast<const float4*>(orow + kb * VT_BK + q) : make_float4(0, 0, 0, 0);
+                    osq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, osq))));
+                    float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+                    float4 lo = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                    const uint32_t off = sw128_off(tid, q);
+                    *reinterpret_cast<float4*>(slot + off) = h;
+                    *reinterpret_cast<float4*>(slot + A_BYTES + off) = lo;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc::mbar_arrive(&fullA[s]);
+            }
+            if (!ok) break;
+            if (!tc::mbar_wait(accf, i & 1, status)) break;
+            tc::tc_fence_after();
+            VqBest best;
+            best.v1 = INFINITY; best.i1 = 0x7fffffff; best.v2 = INFINITY;
+            const uint32_t lb = (uint32_t)(warp * 32) << 16;
+            for (int c0 = 0; c0 < passes * KC; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + lb + c0, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int n = c0 + j;
+                    if (n < K) vq_merge(best, fmaf(-2.f, __uint_as_float(r[j]), cnorm[n]), n);
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(acce);
+            if (valid) {
+                code[act_rows[m]] = best.i1;
+                const float l1 = best.v1 + osq, l2 = best.v2 + osq;
+                if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
+            }
+        }
+        if (ties) atomicAdd(&s_ties, ties);
+    }
+    __syncwarp();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_ties) atomicAdd(reinterpret_cast<unsigned long long*>(near_ties), (unsigned long long)s_ties);
+    if (warp == 4) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+}
+
+// codebook split for the tensor-core argmin: hi = tf32(W), lo = tf32(W - hi)
+__global__ void k_split_tf32(const float* __restrict__ W, size_t n, float* __restrict__ hi, float* __restrict__ lo) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float h = tf32_round(W[i]);
+        hi[i] = h;
+        lo[i] = tf32_round(W[i] - h);
+    }
+}
+
+cudaError_t launch_split_tf32(const float* W, size_t n, float* hi, float* lo, cudaStream_t st) {
+    k_split_tf32<<<256, 256, 0, st>>>(W, n, hi, lo);
+    return cudaGetLastError();
+}
+
+bool vq_tc_supported(int K, int d) {
+    const int KC = K > 256 ? 256 : K;
+    const bool inst = KC == 16 || KC == 32 || KC == 48 || KC == 64 || KC == 96 || KC == 128 || KC == 192 || KC == 256;
+    return inst && K <= 512 && K % KC == 0 && d % VT_BK == 0;
+}
+
+// Tensor map of a [K][d] FP32 codebook part: boxes of 32 columns x KC rows, 128-byte swizzle.
+cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d) {
+    typedef CUresult (*Fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                           const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                           CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Fn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return cudaErrorNotSupported;
+        fn = reinterpret_cast<Fn>(p);
+    }
+    const int KC = K > 256 ? 256 : K;
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)K};
+    cuuint64_t strides[1] = {(cuuint64_t)d * 4};
+    cuuint32_t box[2] = {(cuuint32_t)VT_BK, (cuuint32_t)KC};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
+                         const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
+                         int* status, cudaStream_t st, int num_sms, int Rmax) {
+    if (!vq_tc_supported(K, d)) return cudaErrorInvalidValue;
+    const int KC = K > 256 ? 256 : K;
+    const int passes = (K + KC - 1) / KC;
+    const size_t slot = 2 * (size_t)VT_BM * VT_BK * 4 + (size_t)passes * 2 * KC * VT_BK * 4;
+    const size_t limit = 227 * 1024;
+    int stages = (1024 + 2 * slot + 128 <= limit) ? 2 : 1;
+    size_t smem = 1024 + stages * slot + 128;
+    if (smem > limit) return cudaErrorInvalidValue;
+    uint32_t cols = 32;
+    while ((int)cols < passes * KC) cols <<= 1;
+    // every CTA resident on an SM holds `cols` TMEM columns: cap the residency
+    const size_t max_ctas = 512 / cols;
+    if ((228 * 1024) / smem > max_ctas) smem = (228 * 1024) / (max_ctas + 1) + 1024;
+    int tiles = (Rmax + VT_BM - 1) / VT_BM;
+    int grid = tiles < num_sms ? tiles : num_sms;
+    if (grid < 1) grid = 1;
+#define VQ_TC_CASE(X)                                                                                      \
+    if (KC == X) {                                                                                         \
+        cudaFuncSetAttribute(k_vq_tc<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+        k_vq_tc<X><<<grid, VT_THREADS, smem, st>>>(tm_hi, tm_lo, O, counters, act_rows, cnorm, K, d, code,  \
+                                                   near_ties, status, stages, cols);                       \
+        return cudaGetLastError();                                                                         \
+    }
+    VQ_TC_CASE(16) VQ_TC_CASE(32) VQ_TC_CASE(48) VQ_TC_CASE(64) VQ_TC_CASE(96) VQ_TC_CASE(128) VQ_TC_CASE(192)
+    VQ_TC_CASE(256)
+#undef VQ_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace vq

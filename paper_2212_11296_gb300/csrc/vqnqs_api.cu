@@ -22,6 +22,10 @@ struct vqnqs_ctx {
     std::vector<LayerW> lw;
     int* bonds = nullptr;          // [nb][2]
     int* status = nullptr;         // device status word
+    int* gemm_m = nullptr;         // row count slot of vqnqs_gemm_bf16
+    int* assign_counters = nullptr;  // counter slots of vqnqs_vq_assign
+    int* assign_rows = nullptr;      // identity row list of vqnqs_vq_assign
+    int assign_rows_cap = 1 << 22;
     long long* stats = nullptr;    // ST_* slots
     std::vector<void*> owned;      // device allocations freed by destroy
     std::string err;
@@ -51,10 +55,10 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-enum Stage { S_CONFIG, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_COUNT };
-const char* kStageNames[S_COUNT] = {"config", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
-                                    "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var"};
+enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
+             S_MEANVAR, S_BACKWARD, S_COUNT };
+const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
+                                    "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward"};
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
     if (c->ev_free.empty()) {
@@ -113,8 +117,8 @@ struct Plan {
     int S = 0;
     long long Cmax = 0, Rmax = 0, Umax = 0;
     int hash_bits = 0;
-    size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, uid_a, uid_b, code, X_a, X_b, A, Y, scratch,
-        keys, vals, rep_uid, rep_code, logp, ratio, total;
+    size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b, code,
+        X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, total;
 };
 
 Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
@@ -136,6 +140,9 @@ Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
     p.cfg_sample = take((size_t)p.Cmax * sizeof(int));
     p.cfg_i = take((size_t)p.Cmax * sizeof(int));
     p.cfg_j = take((size_t)p.Cmax * sizeof(int));
+    p.act_cnt = take((size_t)p.Cmax * sizeof(int));
+    p.act_off = take((size_t)p.Cmax * sizeof(int));
+    p.act_rows = take((size_t)p.Rmax * sizeof(int));
     p.uid_a = take((size_t)p.Rmax * sizeof(int));
     p.uid_b = take((size_t)p.Rmax * sizeof(int));
     p.code = take((size_t)p.Rmax * sizeof(int));
@@ -197,6 +204,7 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
         VQ_CK(launch_transpose_bf16(w.w_qkv, d, 3 * d, w.wqkv_t, st));
         VQ_CK(launch_transpose_bf16(w.w_1, d, 4 * d, w.w1_t, st));
         VQ_CK(launch_transpose_bf16(w.w_2, 4 * d, d, w.w2_t, st));
+        VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
     }
     return VQNQS_OK;
 }
@@ -261,26 +269,59 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
     const int g_rows = grid_for(ctx, P.Rmax, 8, 16);
     const int g_urows = grid_for(ctx, P.Umax, 8, 16);
 
+    const bool bf16 = (flags & VQNQS_BF16) != 0;
+    int* act_rows = at<int>(ws, P.act_rows);
+    VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, reuse ? 1 : 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off),
+                                             act_rows, st, grid_for(ctx, P.Cmax, 8, 16)));
+    __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(A);
+    __nv_bfloat16* qkv16 = reinterpret_cast<__nv_bfloat16*>(qkv);
+    __nv_bfloat16* Hid16 = reinterpret_cast<__nv_bfloat16*>(Hid);
     VQ_STAGE(S_EMBED, reuse ? 2 : 1, launch_embed(ch, ctx->tok_emb, ctx->pos_emb, reuse, X_cur, uid_cur, st, g_rows));
     for (int l = 0; l < ctx->layers; ++l) {
         const LayerW& w = ctx->lw[l];
         const int us = CNT_U0 + l, un = CNT_U0 + l + 1;
-        VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, A, nullptr, st, g_urows));
-        VQ_STAGE(S_QKV, 1, launch_sgemm(A, w.w_qkv, w.b_qkv, nullptr, qkv, counters, us, Umax, 3 * d, d, EPI_BIAS, st,
-                                        ctx->num_sms));
-        VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, st, grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
-        VQ_STAGE(S_VQ, 1, launch_vq_argmin(O, counters, w.codebook, w.cnorm, K, d, code, ctx->stats + ST_NEAR_TIES,
-                                           Rmax, st, ctx->num_sms));
+        if (bf16) {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows));
+            VQ_STAGE(S_QKV, 1, launch_gemm_tc(A16, Umax, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, us, 3 * d, d, 0,
+                                              ctx->status, st, ctx->num_sms));
+            if (attention_tc_supported(N, d / ctx->heads))
+                VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, reuse ? 1 : 0, ctx->status, st,
+                                                        grid_for(ctx, P.Cmax * ctx->heads, 1, 4)));
+            else
+                VQ_STAGE(S_ATTN, 1, launch_attention_bf16in(ch, uid_cur, qkv16, O, reuse ? 1 : 0, st,
+                                                            grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
+        } else {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, A, nullptr, st, g_urows));
+            VQ_STAGE(S_QKV, 1, launch_sgemm(A, w.w_qkv, w.b_qkv, nullptr, qkv, counters, us, Umax, 3 * d, d, EPI_BIAS,
+                                            st, ctx->num_sms));
+            VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, reuse ? 1 : 0, st,
+                                                     grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
+        }
+        if (bf16 && vq_tc_supported(K, d))
+            VQ_STAGE(S_VQ, 1, launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, act_rows, w.cnorm, K, d, code,
+                                           ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, Rmax));
+        else
+            VQ_STAGE(S_VQ, 1, launch_vq_argmin(O, counters, act_rows, w.codebook, w.cnorm, K, d, code,
+                                               ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms));
         VQ_STAGE(S_DEDUPE, reuse ? 3 : 1,
-                 launch_dedupe(uid_cur, code, counters, un, Rmax, at<unsigned long long>(ws, P.keys),
+                 launch_dedupe(ch, uid_cur, code, un, Rmax, at<unsigned long long>(ws, P.keys),
                                at<int>(ws, P.vals), P.hash_bits, uid_next, rep_uid, rep_code, reuse, ctx->status, st,
                                ctx->num_sms));
-        VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b, d,
-                                                    Y, A, nullptr, st, g_urows));
-        VQ_STAGE(S_MLP1, 1, launch_sgemm(A, w.w_1, w.b_1, nullptr, Hid, counters, un, Umax, 4 * d, d, EPI_BIAS_GELU,
-                                         st, ctx->num_sms));
-        VQ_STAGE(S_MLP2, 1, launch_sgemm(Hid, w.w_2, w.b_2, Y, X_next, counters, un, Umax, d, 4 * d, EPI_BIAS_RESID,
-                                         st, ctx->num_sms));
+        if (bf16) {
+            VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
+                                                        d, Y, nullptr, A16, st, g_urows));
+            VQ_STAGE(S_MLP1, 1, launch_gemm_tc(A16, Umax, w.tm_w1, w.b_1, nullptr, Hid16, counters, un, 4 * d, d, 1,
+                                               ctx->status, st, ctx->num_sms));
+            VQ_STAGE(S_MLP2, 1, launch_gemm_tc(Hid16, Umax, w.tm_w2, w.b_2, Y, X_next, counters, un, d, 4 * d, 2,
+                                               ctx->status, st, ctx->num_sms));
+        } else {
+            VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
+                                                        d, Y, A, nullptr, st, g_urows));
+            VQ_STAGE(S_MLP1, 1, launch_sgemm(A, w.w_1, w.b_1, nullptr, Hid, counters, un, Umax, 4 * d, d,
+                                             EPI_BIAS_GELU, st, ctx->num_sms));
+            VQ_STAGE(S_MLP2, 1, launch_sgemm(Hid, w.w_2, w.b_2, Y, X_next, counters, un, Umax, d, 4 * d,
+                                             EPI_BIAS_RESID, st, ctx->num_sms));
+        }
         std::swap(uid_cur, uid_next);
         std::swap(X_cur, X_next);
     }
@@ -305,7 +346,8 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     ctx->err.clear();
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
-    if (flags & VQNQS_BF16) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 is not available in this build");
+    if ((flags & VQNQS_BF16) && ctx->d % 64)
+        return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
     if (B == 0) return VQNQS_OK;
     if (!spins) return fail(ctx, VQNQS_ERR_ARG, "spins is NULL");
     if (with_bonds && !e_loc) return fail(ctx, VQNQS_ERR_ARG, "e_loc is NULL");
@@ -326,6 +368,216 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
         if (rc != VQNQS_OK) return rc;
     }
     if (mean_var) VQ_STAGE(S_MEANVAR, 1, launch_mean_var(e_loc, B, mean_var, st));
+    return VQNQS_OK;
+}
+
+// ---- gradient of log psi ---------------------------------------------------------
+struct ParamOff {
+    size_t tok, pos, lnf_g, lnf_b, wh, bh;
+    struct L { size_t ln1_g, ln1_b, wqkv, bqkv, cb, wo, bo, ln2_g, ln2_b, w1, b1, w2, b2; };
+    std::vector<L> l;
+};
+
+ParamOff param_offsets(const vqnqs_ctx* c) {
+    ParamOff o;
+    const size_t d = c->d, K = c->K;
+    size_t p = 0;
+    auto take = [&](size_t n) { size_t r = p; p += n; return r; };
+    o.tok = take(3 * d);
+    o.pos = take((size_t)c->N * d);
+    o.l.resize(c->layers);
+    for (int l = 0; l < c->layers; ++l) {
+        auto& w = o.l[l];
+        w.ln1_g = take(d); w.ln1_b = take(d); w.wqkv = take(3 * d * d); w.bqkv = take(3 * d);
+        w.cb = take(K * d); w.wo = take(d * d); w.bo = take(d); w.ln2_g = take(d); w.ln2_b = take(d);
+        w.w1 = take(4 * d * d); w.b1 = take(4 * d); w.w2 = take(4 * d * d); w.b2 = take(d);
+    }
+    o.lnf_g = take(d); o.lnf_b = take(d); o.wh = take(2 * d); o.bh = take(2);
+    return o;
+}
+
+struct GradPlan {
+    int S = 0, B = 0;
+    long long R = 0;
+    size_t seeds, counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b,
+        rep_uid, rep_code, code, X, dX, dY, A1, Oatt, Y, V, A2, dA, dV, dO, dgam, dbet, Af, QKV, dQKV, H1, G4, dG4, OW,
+        DG, alpha, onehot, arow, dlog, csumK, stat, total;
+};
+
+GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
+    GradPlan p;
+    p.S = S;
+    p.B = B;
+    p.R = (long long)S * c->N;
+    const size_t R = p.R, d = c->d, K = c->K, L = c->layers;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    const size_t f = sizeof(float);
+    p.seeds = take((size_t)(B > 0 ? B : 1) * f);
+    p.counters = take(CNT_SLOTS * sizeof(int));
+    p.cnt = take(S * sizeof(int)); p.cfg_off = take((S + 1) * sizeof(int)); p.diag = take(S * f);
+    p.cfg_sample = take(S * sizeof(int)); p.cfg_i = take(S * sizeof(int)); p.cfg_j = take(S * sizeof(int));
+    p.act_cnt = take(S * sizeof(int)); p.act_off = take(S * sizeof(int)); p.act_rows = take(R * sizeof(int));
+    p.uid_a = take(R * sizeof(int)); p.uid_b = take(R * sizeof(int));
+    p.rep_uid = take(R * sizeof(int)); p.rep_code = take(R * sizeof(int));
+    p.code = take(L * R * sizeof(int));
+    p.X = take((L + 1) * R * d * f);
+    p.dX = take(R * d * f); p.dY = take(R * d * f); p.A1 = take(R * d * f); p.Oatt = take(R * d * f);
+    p.Y = take(R * d * f); p.V = take(R * d * f); p.A2 = take(R * d * f); p.dA = take(R * d * f);
+    p.dV = take(R * d * f); p.dO = take(R * d * f); p.dgam = take(R * d * f); p.dbet = take(R * d * f);
+    p.Af = take(R * d * f);
+    p.QKV = take(R * 3 * d * f); p.dQKV = take(R * 3 * d * f);
+    p.H1 = take(R * 4 * d * f); p.G4 = take(R * 4 * d * f); p.dG4 = take(R * 4 * d * f);
+    p.OW = take(R * K * f); p.DG = take(R * K * f); p.alpha = take(R * K * f); p.onehot = take(R * K * f);
+    p.arow = take(R * f); p.dlog = take(2 * R * f); p.csumK = take((size_t)S * K * f);
+    p.stat = take(R * c->heads * 3 * f);
+    p.total = o;
+    return p;
+}
+
+int grad_default_chunk(const vqnqs_ctx* c) {
+    long long s = (256LL << 10) / c->N;
+    return (int)(s < 1 ? 1 : (s > 65536 ? 65536 : s));
+}
+
+// One chunk: forward with saved residual streams, then the backward.  OUT is the
+// gradient base of this chunk (grad, or O + first sample * P), groups of G rows.
+int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins, int S, const float* seeds,
+               float* OUT, int G, long long ostride, cudaStream_t st) {
+    const int N = ctx->N, d = ctx->d, K = ctx->K, Ly = ctx->layers, H = ctx->heads;
+    const int R = S * N, ng = R / G;
+    const int cap = ctx->num_sms * 16, sms = ctx->num_sms;
+    int* counters = at<int>(ws, P.counters);
+    Chunk ch;
+    ch.spins = spins; ch.S = S; ch.N = N; ch.L = ctx->L; ch.d = d; ch.heads = H; ch.K = K;
+    ch.cfg_sample = at<int>(ws, P.cfg_sample); ch.cfg_i = at<int>(ws, P.cfg_i); ch.cfg_j = at<int>(ws, P.cfg_j);
+    ch.cfg_off = at<int>(ws, P.cfg_off); ch.counters = counters;
+    const ParamOff po = param_offsets(ctx);
+    auto X = [&](int l) { return at<float>(ws, P.X + (size_t)l * R * d * sizeof(float)); };
+    auto code = [&](int l) { return at<int>(ws, P.code + (size_t)l * R * sizeof(int)); };
+    float *dX = at<float>(ws, P.dX), *dY = at<float>(ws, P.dY), *A1 = at<float>(ws, P.A1), *Oatt = at<float>(ws, P.Oatt);
+    float *Y = at<float>(ws, P.Y), *V = at<float>(ws, P.V), *A2 = at<float>(ws, P.A2), *dA = at<float>(ws, P.dA);
+    float *dV = at<float>(ws, P.dV), *dO = at<float>(ws, P.dO), *dgam = at<float>(ws, P.dgam);
+    float *dbet = at<float>(ws, P.dbet), *Af = at<float>(ws, P.Af), *QKV = at<float>(ws, P.QKV);
+    float *dQKV = at<float>(ws, P.dQKV), *H1 = at<float>(ws, P.H1), *G4 = at<float>(ws, P.G4);
+    float *dG4 = at<float>(ws, P.dG4), *OW = at<float>(ws, P.OW), *DG = at<float>(ws, P.DG);
+    float *alpha = at<float>(ws, P.alpha), *onehot = at<float>(ws, P.onehot), *arow = at<float>(ws, P.arow);
+    float *dlog = at<float>(ws, P.dlog), *csumK = at<float>(ws, P.csumK);
+    int *uid = at<int>(ws, P.uid_a), *uid_b = at<int>(ws, P.uid_b), *act = at<int>(ws, P.act_rows);
+    int *rep_uid = at<int>(ws, P.rep_uid), *rep_code = at<int>(ws, P.rep_code);
+    const int g_rows = grid_for(ctx, R, 8, 16);
+
+    // forward, keeping x_l and the codes
+    {
+        StageScope s_(ctx, S_CONFIG, 3, st);
+        VQ_CK(launch_count_configs(spins, S, N, ctx->bonds, ctx->nb, (float)ctx->J, 0, at<int>(ws, P.cnt),
+                                   at<float>(ws, P.diag), ctx->status, st, grid_for(ctx, S, 1, 8)));
+        VQ_CK(launch_scan_configs(at<int>(ws, P.cnt), S, at<int>(ws, P.cfg_off), counters, N, st));
+        VQ_CK(launch_fill_configs(spins, S, N, ctx->bonds, ctx->nb, 0, ch.cfg_off, at<int>(ws, P.cfg_sample),
+                                  at<int>(ws, P.cfg_i), at<int>(ws, P.cfg_j), st, grid_for(ctx, S, 1, 8)));
+    }
+    VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off), act, st,
+                                             grid_for(ctx, S, 8, 16)));
+    VQ_STAGE(S_EMBED, 1, launch_embed(ch, ctx->tok_emb, ctx->pos_emb, 0, X(0), uid, st, g_rows));
+    for (int l = 0; l < Ly; ++l) {
+        const LayerW& w = ctx->lw[l];
+        VQ_STAGE(S_LN1, 1, launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
+        VQ_STAGE(S_QKV, 1, launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
+        VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
+        VQ_STAGE(S_VQ, 1, launch_vq_argmin(Oatt, counters, act, w.codebook, w.cnorm, K, d, code(l),
+                                           ctx->stats + ST_NEAR_TIES, R, st, sms));
+        VQ_STAGE(S_DEDUPE, 1, launch_dedupe(ch, uid, code(l), CNT_U0 + l + 1, R, nullptr, nullptr, 0, uid_b, rep_uid,
+                                            rep_code, 0, ctx->status, st, sms));
+        VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X(l), rep_uid, rep_code, w.T, counters, CNT_R, w.ln2_g, w.ln2_b, d,
+                                                    Y, A2, nullptr, st, g_rows));
+        VQ_STAGE(S_MLP1, 1, launch_sgemm(A2, w.w_1, w.b_1, nullptr, G4, counters, CNT_R, R, 4 * d, d, EPI_BIAS_GELU,
+                                         st, sms));
+        VQ_STAGE(S_MLP2, 1, launch_sgemm(G4, w.w_2, w.b_2, Y, X(l + 1), counters, CNT_R, R, d, 4 * d, EPI_BIAS_RESID,
+                                         st, sms));
+    }
+
+    StageScope s_bwd(ctx, S_BACKWARD, 0, st);
+    auto gg = [&](bool ta, bool tb, const float* A, const float* B, float* C, int M, int Nn, int Kk, int lda, int ldb,
+                  int ldc, long long sA, long long sB, long long sC, int batch, int acc) {
+        ctx->launches += 1;
+        return launch_gemm_gen(ta, tb, A, B, C, M, Nn, Kk, lda, ldb, ldc, sA, sB, sC, batch, acc, st, sms);
+    };
+    auto colsum = [&](const float* Xm, int ncol, size_t off) {
+        ctx->launches += 1;
+        return launch_colsum(Xm, R, G, ncol, OUT + off, ostride, 1, st, cap);
+    };
+    // head
+    ctx->launches += 1;
+    VQ_CK(launch_head_bwd(X(Ly), spins, seeds, R, N, d, ctx->lnf_g, ctx->lnf_b, ctx->w_head, ctx->b_head, dX, Af, dlog,
+                          dgam, dbet, st, cap));
+    VQ_CK(gg(true, false, Af, dlog, OUT + po.wh, d, 2, G, d, 2, 2, (long long)G * d, (long long)G * 2, ostride, ng, 1));
+    VQ_CK(colsum(dlog, 2, po.bh));
+    VQ_CK(colsum(dgam, d, po.lnf_g));
+    VQ_CK(colsum(dbet, d, po.lnf_b));
+    for (int l = Ly - 1; l >= 0; --l) {
+        const LayerW& w = ctx->lw[l];
+        const auto& o = po.l[l];
+        // recompute the block internals from x_l
+        ctx->launches += 7;
+        VQ_CK(launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
+        VQ_CK(launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
+        VQ_CK(launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
+        VQ_CK(launch_quant_residual(X(l), code(l), w.T, w.codebook, R, d, Y, V, st, cap));
+        VQ_CK(launch_layernorm(Y, counters, CNT_R, w.ln2_g, w.ln2_b, d, A2, nullptr, st, g_rows));
+        VQ_CK(launch_sgemm(A2, w.w_1, w.b_1, nullptr, H1, counters, CNT_R, R, 4 * d, d, EPI_BIAS, st, sms));
+        VQ_CK(launch_gelu_fwd(H1, G4, (size_t)R * 4 * d, st, cap));
+        // MLP: x' = y + GELU(LN2(y) W1 + b1) W2 + b2, dX holds d/dx'
+        VQ_CK(gg(true, false, G4, dX, OUT + o.w2, 4 * d, d, G, 4 * d, d, d, (long long)G * 4 * d, (long long)G * d,
+                 ostride, ng, 1));
+        VQ_CK(colsum(dX, d, o.b2));
+        VQ_CK(gg(false, true, dX, w.w_2, dG4, R, 4 * d, d, d, d, 4 * d, 0, 0, 0, 1, 0));
+        ctx->launches += 1;
+        VQ_CK(launch_gelu_bwd(H1, dG4, (size_t)R * 4 * d, st, cap));
+        VQ_CK(gg(true, false, A2, dG4, OUT + o.w1, d, 4 * d, G, d, 4 * d, 4 * d, (long long)G * d,
+                 (long long)G * 4 * d, ostride, ng, 1));
+        VQ_CK(colsum(dG4, 4 * d, o.b1));
+        VQ_CK(gg(false, true, dG4, w.w_1, dA, R, d, 4 * d, 4 * d, 4 * d, d, 0, 0, 0, 1, 0));
+        VQ_CK(cudaMemcpyAsync(dY, dX, (size_t)R * d * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        ctx->launches += 1;
+        VQ_CK(launch_ln_bwd(Y, dA, w.ln2_g, R, d, dY, 1, dgam, dbet, st, cap));
+        VQ_CK(colsum(dgam, d, o.ln2_g));
+        VQ_CK(colsum(dbet, d, o.ln2_b));
+        // y = x + V W_o + b_o
+        VQ_CK(gg(false, true, dY, w.w_o, dV, R, d, d, d, d, d, 0, 0, 0, 1, 0));
+        VQ_CK(gg(true, false, V, dY, OUT + o.wo, d, d, G, d, d, d, (long long)G * d, (long long)G * d, ostride, ng, 1));
+        VQ_CK(colsum(dY, d, o.bo));
+        // straight-through quantizer (Eq. st)
+        VQ_CK(gg(false, true, Oatt, w.codebook, OW, R, K, d, d, d, K, 0, 0, 0, 1, 0));
+        VQ_CK(gg(false, true, dV, w.codebook, DG, R, K, d, d, d, K, 0, 0, 0, 1, 0));
+        ctx->launches += 1;
+        VQ_CK(launch_st_rows(OW, DG, Oatt, w.cnorm, R, K, d, alpha, arow, st, cap));
+        VQ_CK(gg(false, false, alpha, w.codebook, dO, R, d, K, K, d, d, 0, 0, 0, 1, 0));
+        ctx->launches += 1;
+        VQ_CK(launch_st_do(Oatt, arow, R, d, dO, st, cap));
+        VQ_CK(gg(true, false, alpha, Oatt, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d, ostride,
+                 ng, 1));
+        ctx->launches += 3;
+        VQ_CK(launch_colsum(alpha, R, G, K, csumK, K, 0, st, cap));
+        VQ_CK(launch_sub_scaled_rows(OUT + o.cb, csumK, w.codebook, K, d, ng, ostride, st, cap));
+        VQ_CK(launch_onehot(code(l), R, K, onehot, st, cap));
+        VQ_CK(gg(true, false, onehot, dV, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d, ostride,
+                 ng, 1));
+        // attention
+        ctx->launches += 2;
+        VQ_CK(launch_attention_bwd(QKV, dO, S, N, d, H, dQKV, at<float>(ws, P.stat), st, cap));
+        // qkv = LN1(x) W_qkv + b_qkv
+        VQ_CK(gg(true, false, A1, dQKV, OUT + o.wqkv, d, 3 * d, G, d, 3 * d, 3 * d, (long long)G * d,
+                 (long long)G * 3 * d, ostride, ng, 1));
+        VQ_CK(colsum(dQKV, 3 * d, o.bqkv));
+        VQ_CK(gg(false, true, dQKV, w.w_qkv, dA, R, d, 3 * d, 3 * d, 3 * d, d, 0, 0, 0, 1, 0));
+        VQ_CK(cudaMemcpyAsync(dX, dY, (size_t)R * d * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        ctx->launches += 1;
+        VQ_CK(launch_ln_bwd(X(l), dA, w.ln1_g, R, d, dX, 1, dgam, dbet, st, cap));
+        VQ_CK(colsum(dgam, d, o.ln1_g));
+        VQ_CK(colsum(dbet, d, o.ln1_b));
+    }
+    ctx->launches += 1;
+    VQ_CK(launch_embed_bwd(dX, spins, S, N, d, G / N, OUT + po.tok, OUT + po.pos, ostride, 1, st, cap));
     return VQNQS_OK;
 }
 
@@ -378,16 +630,39 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
         w.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * sizeof(__nv_bfloat16)));
         w.w1_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
         w.w2_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
-        if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t) return bail(VQNQS_ERR_OOM);
+        w.cb_hi = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
+        w.cb_lo = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
+        if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo) return bail(VQNQS_ERR_OOM);
     }
     if (!ctx->blob || !ctx->bonds || !ctx->status || !ctx->stats) return bail(VQNQS_ERR_OOM);
     if (cudaMemcpy(ctx->bonds, bonds.data(), bonds.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->stats, 0, ST_SLOTS * sizeof(long long)) != cudaSuccess)
         return bail(VQNQS_ERR_CUDA);
+    ctx->gemm_m = static_cast<int*>(dalloc(sizeof(int)));
+    ctx->assign_counters = static_cast<int*>(dalloc(CNT_SLOTS * sizeof(int)));
+    ctx->assign_rows = static_cast<int*>(dalloc((size_t)ctx->assign_rows_cap * sizeof(int)));
+    if (!ctx->gemm_m || !ctx->assign_counters || !ctx->assign_rows) return bail(VQNQS_ERR_OOM);
     bind_weights(ctx);
     int rc = vqnqs_set_weights(ctx, weights, 0, nullptr);
     if (rc != VQNQS_OK) return bail(rc);
+    if (vq_tc_supported(K, d_model)) {
+        for (int l = 0; l < layers; ++l) {
+            LayerW& w = ctx->lw[l];
+            if (make_tmap_codebook(&w.tm_cb_hi, w.cb_hi, K, d_model) != cudaSuccess ||
+                make_tmap_codebook(&w.tm_cb_lo, w.cb_lo, K, d_model) != cudaSuccess)
+                return bail(VQNQS_ERR_CUDA);
+        }
+    }
+    if (d_model % 64 == 0) {
+        for (int l = 0; l < layers; ++l) {
+            LayerW& w = ctx->lw[l];
+            if (make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 3 * d, d_model, tc_pick_bn(3 * d_model)) != cudaSuccess ||
+                make_tmap_bf16(&w.tm_w1, w.w1_t, 4 * d, d_model, tc_pick_bn(4 * d_model)) != cudaSuccess ||
+                make_tmap_bf16(&w.tm_w2, w.w2_t, d, 4 * d_model, tc_pick_bn(d_model)) != cudaSuccess)
+                return bail(VQNQS_ERR_CUDA);
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(VQNQS_ERR_CUDA);
     *out = ctx;
     return VQNQS_OK;
@@ -453,6 +728,139 @@ int vqnqs_reset_stats(vqnqs_ctx* ctx) {
     VQ_CK(cudaMemset(ctx->stats, 0, ST_SLOTS * sizeof(long long)));
     VQ_CK(cudaMemset(ctx->status, 0, sizeof(int)));
     VQ_CK(cudaDeviceSynchronize());
+    return VQNQS_OK;
+}
+
+int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const void* Bt, const float* bias,
+                    const float* R, void* C, int epilogue, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (M < 0 || N <= 0 || K <= 0 || K % 64 || !tc_pick_bn(N) || epilogue < 0 || epilogue > 3)
+        return fail(ctx, VQNQS_ERR_ARG, "gemm: need M >= 0, K % 64 == 0, N % 64 == 0, epilogue 0..3");
+    if (!A || !Bt || !bias || !C || (epilogue == 2 && !R)) return fail(ctx, VQNQS_ERR_ARG, "gemm: null pointer");
+    auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; };
+    if (misaligned(A) || misaligned(Bt) || misaligned(C) || (R && misaligned(R)))
+        return fail(ctx, VQNQS_ERR_ARG, "gemm: pointers must be 16-byte aligned");
+    if (M == 0) return VQNQS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CUtensorMap tb;
+    VQ_CK(make_tmap_bf16(&tb, Bt, N, K, tc_pick_bn(N)));
+    VQ_CK(launch_set_int(ctx->gemm_m, M, st));
+    ctx->launches += 2;
+    VQ_CK(launch_gemm_tc(static_cast<const __nv_bfloat16*>(A), M, tb, bias, R, C, ctx->gemm_m, 0, N, K, epilogue,
+                         ctx->status, st, ctx->num_sms));
+    return VQNQS_OK;
+}
+
+size_t vqnqs_grad_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples) {
+    if (!ctx || B < 0) return 0;
+    int S = chunk_samples > 0 ? chunk_samples : grad_default_chunk(ctx);
+    if (B > 0 && S > B) S = B;
+    return make_grad_plan(ctx, S, B).total;
+}
+
+int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float* seeds, const float* e_loc, float* O,
+                       float* grad, int flags, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (seeds && e_loc) return fail(ctx, VQNQS_ERR_ARG, "give seeds or e_loc, not both");
+    if (!O && !grad) return fail(ctx, VQNQS_ERR_ARG, "nothing to compute: O and grad are NULL");
+    if (B == 0) return VQNQS_OK;
+    if (!spins || !ws) return fail(ctx, VQNQS_ERR_ARG, "null pointer");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(ctx, VQNQS_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // largest chunk that fits
+    int lo = 0, hi = B < 65536 ? B : 65536;
+    while (lo < hi) {
+        int mid = lo + (hi - lo + 1) / 2;
+        if (make_grad_plan(ctx, mid, B).total <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    if (lo == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "workspace smaller than the one-sample minimum");
+    const GradPlan P = make_grad_plan(ctx, lo, B);
+    const long long Pn = (long long)ctx->nparams;
+    float* sd = at<float>(ws, P.seeds);
+    if (e_loc) {
+        ctx->launches += 1;
+        VQ_CK(launch_seeds_from_eloc(e_loc, B, sd, st));
+    } else if (seeds && !O) {
+        VQ_CK(cudaMemcpyAsync(sd, seeds, (size_t)B * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    const bool weighted = (e_loc || seeds) && !O;
+    if (O) VQ_CK(cudaMemsetAsync(O, 0, (size_t)B * Pn * sizeof(float), st));
+    if (grad) VQ_CK(cudaMemsetAsync(grad, 0, (size_t)Pn * sizeof(float), st));
+    for (int s0 = 0; s0 < B; s0 += lo) {
+        const int S = (B - s0) < lo ? (B - s0) : lo;
+        const uint8_t* sp = spins + (size_t)s0 * ctx->N;
+        int rc;
+        if (O) rc = grad_chunk(ctx, P, ws, sp, S, nullptr, O + (size_t)s0 * Pn, ctx->N, Pn, st);
+        else rc = grad_chunk(ctx, P, ws, sp, S, weighted ? sd + s0 : nullptr, grad, S * ctx->N, 0, st);
+        if (rc != VQNQS_OK) return rc;
+    }
+    if (O && grad) {  // grad = sum_b w_b O_b
+        if (e_loc || seeds) {
+            const float* w = e_loc ? sd : seeds;
+            ctx->launches += 1;
+            VQ_CK(launch_gemm_gen(false, false, w, O, grad, 1, (int)Pn, B, B, (int)Pn, (int)Pn, 0, 0, 0, 1, 0, st,
+                                  ctx->num_sms));
+        } else {
+            ctx->launches += 1;
+            VQ_CK(launch_colsum(O, B, B, (int)Pn, grad, 0, 0, st, ctx->num_sms * 16));
+        }
+    }
+    return VQNQS_OK;
+}
+
+int vqnqs_vq_assign(vqnqs_ctx* ctx, int layer, int R, const float* O, int* code, int use_tensor_cores,
+                    void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (layer < 0 || layer >= ctx->layers || R < 0) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: bad layer or R");
+    if (R > 0 && (!O || !code)) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: null pointer");
+    if ((reinterpret_cast<uintptr_t>(O) & 15)) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: O must be 16-byte aligned");
+    if (use_tensor_cores && !vq_tc_supported(ctx->K, ctx->d))
+        return fail(ctx, VQNQS_ERR_ARG, "vq_assign: tensor-core path needs K % 16 == 0, K <= 512, d % 32 == 0");
+    if (R == 0) return VQNQS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const LayerW& w = ctx->lw[layer];
+    // counters: CNT_A / CNT_R = R, rows listed 0 .. R-1 (identity) in the context's scratch
+    if (ctx->assign_rows_cap < R) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: R above the context's row capacity");
+    ctx->launches += 2;
+    VQ_CK(launch_assign_setup(ctx->assign_counters, ctx->assign_rows, R, st));
+    if (use_tensor_cores)
+        VQ_CK(launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, ctx->assign_counters, ctx->assign_rows, w.cnorm, ctx->K,
+                           ctx->d, code, ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, R));
+    else
+        VQ_CK(launch_vq_argmin(O, ctx->assign_counters, ctx->assign_rows, w.codebook, w.cnorm, ctx->K, ctx->d, code,
+                               ctx->stats + ST_NEAR_TIES, R, st, ctx->num_sms));
+    return VQNQS_OK;
+}
+
+size_t vqnqs_compress_workspace_bytes(int R) {
+    if (R < 0) return 0;
+    const size_t H = (size_t)1 << compress_hash_bits(R);
+    return align256(H * sizeof(unsigned long long)) + align256(H * sizeof(int));
+}
+
+int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* uid, const int* code, int* new_id, int* rep_uid,
+                        int* rep_code, int* count, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (R < 0) return fail(ctx, VQNQS_ERR_ARG, "compress: R must be >= 0");
+    if (!count || (R > 0 && (!uid || !code || !new_id || !rep_uid || !rep_code)))
+        return fail(ctx, VQNQS_ERR_ARG, "compress: null pointer");
+    const size_t need = vqnqs_compress_workspace_bytes(R);
+    if (!ws || ws_bytes < need) return fail(ctx, VQNQS_ERR_WORKSPACE, "compress: workspace too small");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(ctx, VQNQS_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int hb = compress_hash_bits(R);
+    const size_t H = (size_t)1 << hb;
+    ctx->launches += 3;
+    VQ_CK(launch_compress_pairs(R, uid, code, new_id, rep_uid, rep_code, count, static_cast<unsigned long long*>(ws),
+                                at<int>(ws, align256(H * sizeof(unsigned long long))), hb, ctx->status, st,
+                                ctx->num_sms));
     return VQNQS_OK;
 }
 

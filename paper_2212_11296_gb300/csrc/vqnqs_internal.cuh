@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernel translation units of libvqnqs.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -17,8 +18,9 @@ constexpr float NEAR_TIE_REL = 1e-6f;
 enum {
     CNT_C = 0,      // configurations in the chunk
     CNT_R = 1,      // rows = C * N
-    CNT_U0 = 2,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
-    CNT_SLOTS = 2 + VQNQS_MAX_LAYERS + 2
+    CNT_A = 2,      // active rows: rows whose attention and codeword are computed
+    CNT_U0 = 3,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
+    CNT_SLOTS = 3 + VQNQS_MAX_LAYERS + 2
 };
 
 // Slots of the context's persistent device statistics (int64).
@@ -37,6 +39,9 @@ struct LayerW {
     float* T;       // [K][d] codebook @ w_o + b_o: the quantized vector after the output projection
     float* cnorm;   // [K] ||W_j||^2
     __nv_bfloat16 *wqkv_t, *w1_t, *w2_t;  // BF16 transposes [out][in] for the tensor-core GEMMs
+    CUtensorMap tm_wqkv, tm_w1, tm_w2;    // TMA maps of the transposes (valid when d % 64 == 0)
+    float *cb_hi, *cb_lo;                 // codebook split into TF32 hi / lo parts
+    CUtensorMap tm_cb_hi, tm_cb_lo;       // their TMA maps (valid when vq_tc_supported)
 };
 
 // Per-chunk view of the problem handed to the kernels.
@@ -50,6 +55,12 @@ struct Chunk {
     const int* cfg_off;     // [S + 1] first configuration of each sample
     int* counters;          // CNT_* slots
 };
+
+// First position whose rows differ from the sample's own rows.  Exchanging
+// sites i and j changes the inputs (tokens s_{p-1}) only at p = i+1 and
+// p = j+1, and a causal network's rows at p <= min(i, j) see none of them
+// (Sec. 2: conditionals before the changed site are unchanged).
+__device__ __forceinline__ int cfg_first_changed(int ci, int cj) { return ci < 0 ? 0 : min(ci, cj) + 1; }
 
 __device__ __forceinline__ int cfg_spin(const uint8_t* spins, int N, int b, int ci, int cj, int q) {
     int src = q;
@@ -106,17 +117,82 @@ cudaError_t launch_sgemm(const float* A, const float* B, const float* bias, cons
                          const int* counters, int u_slot, int Mmax, int N, int K, int epi, cudaStream_t st,
                          int num_sms);
 
-// attention (k_attn.cu): O[r] for rows r < counters[CNT_R]
-cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, cudaStream_t st,
-                                 int grid);
+// active rows (k_config.cu): with prefix reuse, the rows p >= first changed position of every
+// configuration, listed in act_rows[0 .. counters[CNT_A]); without it every row.
+cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
+                               cudaStream_t st, int grid);
 
-// nearest codeword (k_vq.cu)
-cudaError_t launch_vq_argmin(const float* O, const int* counters, const float* codebook, const float* cnorm, int K,
-                             int d, int* code, long long* near_ties, int Rmax, cudaStream_t st, int num_sms);
+// attention (k_attn.cu): O[r] for the active rows (all rows when prefix_reuse == 0)
+cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, int prefix_reuse,
+                                 cudaStream_t st, int grid);
+cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                                   int prefix_reuse, cudaStream_t st, int grid);
+// tensor-core attention (k_attn_tc.cu): dh in {16, 32}, N <= 448
+bool attention_tc_supported(int N, int dh);
+cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
+                                int* status, cudaStream_t st, int grid);
 
-// dedupe (k_dedupe.cu)
-cudaError_t launch_dedupe(const int* uid_cur, const int* code, int* counters, int u_slot_next, int Rmax,
+// BF16 tensor-core GEMM (k_gemm_tc.cu): C[M,N] = A[M,K] @ Bt[N,K]^T + bias, M = counters[u_slot]
+// epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
+int tc_pick_bn(int N);
+cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows);
+cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
+                           const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
+                           int* status, cudaStream_t st, int num_sms);
+cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
+
+// nearest codeword (k_vq.cu): rows act_rows[0 .. counters[CNT_A]) (or 0 .. counters[CNT_R] when act_rows is NULL)
+cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
+                             const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
+                             cudaStream_t st, int num_sms);
+
+cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st);
+
+// nearest codeword on the tensor cores, split-TF32 (k_vq_tc.cu)
+bool vq_tc_supported(int K, int d);
+cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d);
+cudaError_t launch_split_tf32(const float* W, size_t n, float* hi, float* lo, cudaStream_t st);
+cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
+                         const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
+                         int* status, cudaStream_t st, int num_sms, int Rmax);
+
+// dedupe (k_dedupe.cu); with prefix reuse a row before its configuration's first changed
+// position takes the code of the same position of the sample's own configuration.
+cudaError_t launch_dedupe(const Chunk& ch, const int* uid_cur, const int* code, int u_slot_next, int Rmax,
                           unsigned long long* keys, int* vals, int hash_bits, int* uid_next, int* rep_uid,
                           int* rep_code, int reuse, int* status, cudaStream_t st, int num_sms);
+
+// standalone (I, V) compression of R (row id, code) pairs (k_dedupe.cu)
+int compress_hash_bits(int R);
+cudaError_t launch_compress_pairs(int R, const int* uid, const int* code, int* new_id, int* rep_uid, int* rep_code,
+                                  int* count, unsigned long long* keys, int* vals, int hash_bits, int* status,
+                                  cudaStream_t st, int num_sms);
+
+// ---- backward (k_gemm_f32_gen.cu, k_backward.cu, vqnqs_grad.cu) ----
+cudaError_t launch_gemm_gen(bool ta, bool tb, const float* A, const float* B, float* C, int M, int N, int K, int lda,
+                            int ldb, int ldc, long long sA, long long sB, long long sC, int batch, int accumulate,
+                            cudaStream_t st, int num_sms);
+cudaError_t launch_head_bwd(const float* X, const uint8_t* spins, const float* seed, int R, int N, int d,
+                            const float* g, const float* b, const float* w, const float* bh, float* dX, float* Af,
+                            float* dlog, float* dgam, float* dbet, cudaStream_t st, int cap);
+cudaError_t launch_ln_bwd(const float* X, const float* dA, const float* g, int R, int d, float* dX, int accumulate,
+                          float* dgam, float* dbet, cudaStream_t st, int cap);
+cudaError_t launch_gelu_bwd(const float* H, float* dG, size_t n, cudaStream_t st, int cap);
+cudaError_t launch_gelu_fwd(const float* H, float* G, size_t n, cudaStream_t st, int cap);
+cudaError_t launch_st_rows(const float* OW, const float* DG, const float* O, const float* cnorm, int R, int K, int d,
+                           float* alpha, float* arow, cudaStream_t st, int cap);
+cudaError_t launch_st_do(const float* O, const float* arow, int R, int d, float* dO, cudaStream_t st, int cap);
+cudaError_t launch_onehot(const int* code, int R, int K, float* Hm, cudaStream_t st, int cap);
+cudaError_t launch_quant_residual(const float* X, const int* code, const float* T, const float* cb, int R, int d,
+                                  float* Y, float* V, cudaStream_t st, int cap);
+cudaError_t launch_colsum(const float* X, int rows, int G, int ncol, float* out, long long out_stride, int accumulate,
+                          cudaStream_t st, int cap);
+cudaError_t launch_embed_bwd(const float* dX0, const uint8_t* spins, int S, int N, int d, int G, float* dtok,
+                             float* dpos, long long out_stride, int accumulate, cudaStream_t st, int cap);
+cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N, int d, int H, float* dQKV,
+                                 float* stat, cudaStream_t st, int cap);
+cudaError_t launch_seeds_from_eloc(const float* e_loc, int B, float* seeds, cudaStream_t st);
+cudaError_t launch_sub_scaled_rows(float* out, const float* csum, const float* W, int K, int d, int groups,
+                                   long long stride, cudaStream_t st, int cap);
 
 }  // namespace vq

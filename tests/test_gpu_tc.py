@@ -1,0 +1,91 @@
+"""Tensor-core (tcgen05) BF16 GEMM and the BF16 path, through the C ABI.
+
+GEMM: against torch's FP32 matmul of the same BF16 operands (exact products,
+FP32 sums; only the summation order differs), relative 1e-5 of the row scale
+for FP32 outputs and one BF16 rounding for BF16 outputs.
+BF16 path: E_loc within 2e-3 relative of the FP64 oracle; reuse == full bitwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic_inputs as si
+from oracle import hamiltonian, model
+
+pytestmark = pytest.mark.gpu
+
+_m = {}
+
+
+def ctx():
+    if "m" not in _m:
+        from paper_2212_11296_gb300 import VQNQS
+        _m["m"] = VQNQS(4, True, 1.0, 1, 64, 2, 4, si.make_weights(16, 1, 64, 4))
+    return _m["m"]
+
+
+@pytest.mark.parametrize("M,N,K", [(1, 64, 64), (127, 192, 256), (128, 256, 256), (300, 768, 256),
+                                   (1000, 1024, 256), (513, 256, 1024), (2048, 384, 128)])
+@pytest.mark.parametrize("epi", [0, 1, 2, 3])
+def test_gemm_bf16_matches_fp32_reference(M, N, K, epi):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K + epi)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    Bt = (0.1 * torch.randn(N, K, device="cuda", generator=g)).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    R = torch.randn(M, N, device="cuda", generator=g) if epi == 2 else None
+    out = ctx().gemm_bf16(A, Bt, bias, epilogue=epi, R=R)
+    torch.cuda.synchronize()
+    ref = A.float() @ Bt.float().T + bias
+    if epi == 1:
+        ref = torch.nn.functional.gelu(ref)
+    if epi == 2:
+        ref = ref + R
+    scale = (A.float().abs() @ Bt.float().abs().T).amax(1, keepdim=True) + 1.0
+    if epi in (2, 3):
+        assert out.dtype == torch.float32
+        assert ((out - ref).abs() / scale).max().item() < 1e-5
+    else:
+        assert out.dtype == torch.bfloat16
+        assert ((out.float() - ref).abs() / (ref.abs() + 1e-2)).max().item() < 1.6e-2
+        assert ((out.float() - ref.to(torch.bfloat16).float()).abs() > 0).float().mean().item() < 0.05
+    assert ctx().stats()["device_status"] == 0
+
+
+def test_gemm_rejects_bad_shapes():
+    from paper_2212_11296_gb300 import VQNQSError
+    A = torch.zeros(8, 96, device="cuda", dtype=torch.bfloat16)
+    Bt = torch.zeros(64, 96, device="cuda", dtype=torch.bfloat16)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        ctx().gemm_bf16(A, Bt, torch.zeros(64, device="cuda"))
+
+
+BF16_TOL = 2e-3
+
+
+def rel_err(got, want, N):
+    return np.abs(np.asarray(got, np.float64) - want) / np.maximum(np.abs(want), 1e-3 * N)
+
+
+@pytest.mark.parametrize("name,L,layers,d,heads,K,B,sub", [
+    ("10x10", 10, 4, 128, 8, 64, 1024, 16),
+    ("16x16", 16, 8, 256, 8, 256, 2048, 2),
+])
+def test_bf16_path_against_oracle_and_reuse_bitwise(name, L, layers, d, heads, K, B, sub):
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0)
+    spins = si.make_samples(L, B, seed=1)
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w)
+    s_dev = torch.as_tensor(spins).cuda()
+    m.reset_stats()
+    e = m.local_energy(s_dev, REUSE | BF16)
+    assert m.stats()["device_status"] == 0
+    idx = np.linspace(0, B - 1, sub).astype(int)
+    P = model.parse_blob(w, N, layers, d, heads, K)
+    want = hamiltonian.local_energy(P, spins[idx], L, True, 1.0)
+    err = rel_err(e.cpu().numpy()[idx], want, N)
+    print(name, "BF16 rel err vs FP64: max %.3e median %.3e" % (err.max(), np.median(err)))
+    assert err.max() <= BF16_TOL
+    # reuse and full recompute agree bitwise on a slice of the batch
+    s16 = s_dev[:16].contiguous()
+    assert torch.equal(m.local_energy(s16, BF16), e[:16])
