@@ -53,19 +53,33 @@ def reduce_max(x: float, dist=None) -> float:
     return float(t.item())
 
 
-def stage_flops(stage: str, st: dict, w: dict) -> tuple[float, str]:
-    """Algorithmic FLOPs (2 per multiply-add) of one stage over the counted work, and its bound."""
-    d, K, N, Ly = w["d_model"], w["K"], w["L"] ** 2, w["layers"]
-    rows, cfgs = st["rows"], st["configs"]
+def measured_peaks() -> dict:
+    """The measured peaks of this GPU pool, else the documented fallback."""
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"bf16_tflops": float(m["bf16_tflops_sustained"]), "hbm_gbs": float(m["hbm_gbs"]), "src": "measured"}
+    except (OSError, ValueError, KeyError):
+        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "src": "fallback"}
+
+
+def stage_flops(stage: str, st: dict, w: dict, bf16: bool) -> tuple[float, str]:
+    """Algorithmic FLOPs (2 per multiply-add) of one stage over the counted work, and its bound.
+
+    Attention: 4 d FLOPs per causal query-key pair (q.k and p v over all heads);
+    argmin: 2 K d per active row; GEMMs: 6 d^2 (QKV) and 8 d^2 (each MLP GEMM)
+    per unique row.  Pairs and active rows are counted by the library (rows
+    before a configuration's first exchanged site are not computed)."""
+    d, K, Ly = w["d_model"], w["K"], w["layers"]
     U = st["unique_rows"]
+    tc = "tensor" if bf16 else "alu"
     if stage == "vq_argmin":
-        return rows * Ly * 2.0 * K * d, "alu"
+        return st["active_rows"] * Ly * 2.0 * K * d, tc
     if stage == "attention":
-        return cfgs * Ly * 2.0 * d * N * (N + 1), "alu"
+        return st["attn_pairs"] * Ly * 4.0 * d, tc
     if stage == "qkv_gemm":
-        return sum(U[:Ly]) * 6.0 * d * d, "alu"
+        return sum(U[:Ly]) * 6.0 * d * d, tc
     if stage in ("mlp_up", "mlp_down"):
-        return sum(U[1:Ly + 1]) * 8.0 * d * d, "alu"
+        return sum(U[1:Ly + 1]) * 8.0 * d * d, tc
     return 0.0, "hbm"
 
 
@@ -205,7 +219,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--flags", default="reuse", help="comma list of reuse,bf16 for the timed path")
+    ap.add_argument("--flags", default="reuse,bf16", help="comma list of reuse,bf16 for the timed path")
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -309,13 +323,17 @@ def main():
     per_step = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(per_step, key=lambda k: per_step[k][2])
     calls, nl, ms = per_step[dom]
-    fl, bound = stage_flops(dom, st, w)
+    fl, bound = stage_flops(dom, st, w, bool(flags & BF16))
     achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
-    peak = FP32_FFMA_PEAK_TFLOPS
+    pk = measured_peaks()
+    if bound == "tensor":
+        peak, peak_src = pk["bf16_tflops"], f"bf16 dense, sustained ({pk['src']})"
+    else:
+        peak, peak_src = FP32_FFMA_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_from_profile(dom),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz",
-                "launches": nl, "avg_launch_ms": ms / nl}
+                "peak_source": peak_src, "launches": nl, "avg_launch_ms": ms / nl,
+                "flops_per_launch": fl / max(1, nl)}
     stages = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[1] / args.steps,
                   "share": v[2] / max(1e-9, sum(x[2] for x in per_step.values()))} for k, v in per_step.items()}
 

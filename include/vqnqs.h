@@ -85,6 +85,10 @@ typedef struct vqnqs_stats {
     double flops_full;                        /* analytic FLOPs (2 per MAC) of full recompute */
     double flops_done;                        /* analytic FLOPs of the work actually executed */
     int32_t device_status;                    /* OR of VQNQS_DEV_* bits raised so far */
+    int64_t active_rows;                      /* rows per layer whose attention and code were computed
+                                                 (rows before a configuration's first exchanged site
+                                                 reuse the sample's own rows) */
+    int64_t attn_pairs;                       /* causal query-key pairs of those rows, per layer */
 } vqnqs_stats;
 
 /* Number of floats in the weight blob for the layout above. */
@@ -120,6 +124,30 @@ size_t vqnqs_workspace_bytes(const vqnqs_ctx* ctx, int chunk_samples, int flags)
  *   dev_ws      DEVICE workspace of ws_bytes bytes, 256-byte aligned */
 int vqnqs_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_log_psi, int flags,
                   void* dev_ws, size_t ws_bytes, void* stream);
+
+/* Local energies of a ragged batch: n_groups (1..8) groups of samples of
+ * different lattice sizes evaluated with the context's model, all groups
+ * sharing one pipeline (chunks mix lattice sizes; deduplication of
+ * per-location work spans the groups of a chunk).
+ *   L_g, B_g     HOST int [n_groups]: lattice side (2 .. L of the context) and sample
+ *                count of each group; boundary conditions and J are the context's
+ *   dev_spins    DEVICE uint8: the groups' samples concatenated, group after group,
+ *                L_g^2 bytes per sample
+ *   dev_e_loc    DEVICE float [sum B_g] (output), same order
+ *   dev_mean_var DEVICE double [2] (output, may be NULL): FP64 mean and variance over all
+ * Position embeddings are shared: site p of every lattice uses row p. */
+int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, const int* B_g,
+                              const uint8_t* dev_spins, float* dev_e_loc, double* dev_mean_var, int flags,
+                              void* dev_ws, size_t ws_bytes, void* stream);
+
+/* The codeword index chosen at every layer and position (Sec. 3.1, Eq. vq; the
+ * indices the paper keeps "for bookkeeping") when log psi of B configurations
+ * is evaluated as given (no connected configurations):
+ *   dev_codes    DEVICE int32 [B][layers][N] (output)
+ *   dev_log_psi  DEVICE float [B] (output, may be NULL when B <= 65536)
+ * Same flags, workspace and stream rules as vqnqs_log_psi. */
+int vqnqs_codes(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int* dev_codes, float* dev_log_psi, int flags,
+                void* dev_ws, size_t ws_bytes, void* stream);
 
 /* Local energies (Sec. 2, Eq. local-energy) of B samples.
  *   dev_e_loc     DEVICE float [B] (output): per-lattice E_loc(s) in units of J S.S
@@ -191,6 +219,19 @@ size_t vqnqs_compress_workspace_bytes(int R);
 int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* dev_uid, const int* dev_code, int* dev_new_id,
                         int* dev_rep_uid, int* dev_rep_code, int* dev_count, void* dev_ws, size_t ws_bytes,
                         void* stream);
+
+/* Autotuner of the per-location tensor-core GEMMs: for each of the QKV, MLP up and
+ * MLP down steps it times every output tile width (64, 128, 192, 256 columns)
+ * that divides the step's output width on M rows (M >= 128, e.g. the typical
+ * number of unique rows of a chunk), keeps the fastest for this context and
+ * reports the average milliseconds per launch (-1 for widths that do not apply).
+ * Synchronises `stream`.  Scratch: M * d_model * 40 bytes of workspace.
+ * Needs d_model % 64 == 0. */
+typedef struct vqnqs_tuning {
+    int qkv_bn, mlp_up_bn, mlp_down_bn;
+    float ms[3][4];  /* [step][width 64, 128, 192, 256] */
+} vqnqs_tuning;
+int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* dev_ws, size_t ws_bytes, vqnqs_tuning* out, void* stream);
 
 /* Snapshot of the counters; synchronises the device first. */
 int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out);

@@ -33,6 +33,8 @@ class Stats(ctypes.Structure):
         ("flops_full", ctypes.c_double),
         ("flops_done", ctypes.c_double),
         ("device_status", ctypes.c_int32),
+        ("active_rows", ctypes.c_int64),
+        ("attn_pairs", ctypes.c_int64),
     ]
 
 
@@ -43,6 +45,11 @@ class StageTime(ctypes.Structure):
 
 MAX_STAGES = 16
 
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("qkv_bn", ctypes.c_int), ("mlp_up_bn", ctypes.c_int), ("mlp_down_bn", ctypes.c_int),
+                ("ms", (ctypes.c_float * 4) * 3)]
+
 # (name, restype, argtypes) of every exported symbol of include/vqnqs.h
 SIGNATURES = [
     ("vqnqs_num_params", ctypes.c_size_t, [ctypes.c_int] * 4),
@@ -52,6 +59,10 @@ SIGNATURES = [
     ("vqnqs_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("vqnqs_log_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_local_energy_ragged", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5 +
+     [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_codes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3 +
+     [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("vqnqs_local_energy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
@@ -66,6 +77,8 @@ SIGNATURES = [
     ("vqnqs_compress_workspace_bytes", ctypes.c_size_t, [ctypes.c_int]),
     ("vqnqs_compress_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 7 +
      [ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.POINTER(Tuning), ctypes.c_void_p]),
     ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     ("vqnqs_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("vqnqs_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

@@ -103,6 +103,18 @@ class VQNQS:
                                         ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_log_psi")
         return out
 
+    def codes(self, spins: torch.Tensor, flags: int = 0, workspace: torch.Tensor | None = None, stream=None):
+        """(codes [B, layers, N] int32, log psi [B]) of the configurations as given (see vqnqs_codes)."""
+        _check_dev(spins, torch.uint8, "spins")
+        B = spins.shape[0]
+        codes = torch.empty(B, self.layers, self.N, dtype=torch.int32, device=spins.device)
+        lp = torch.empty(B, dtype=torch.float32, device=spins.device)
+        ws = self.workspace(flags) if workspace is None else workspace
+        self._check(lib().vqnqs_codes(self._h, B, ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(codes.data_ptr()),
+                                      ctypes.c_void_p(lp.data_ptr()), int(flags), ctypes.c_void_p(ws.data_ptr()),
+                                      ws.numel(), ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_codes")
+        return codes, lp
+
     def local_energy(self, spins: torch.Tensor, flags: int = 0, want_mean_var: bool = False,
                      want_log_psi: bool = False, out: torch.Tensor | None = None,
                      workspace: torch.Tensor | None = None, stream=None):
@@ -129,6 +141,40 @@ class VQNQS:
             res.append(lp)
         return res[0] if len(res) == 1 else tuple(res)
 
+    def _ragged_flat(self, Ls, Bs, spins, e, mv, flags, ws, stream=None):
+        arr = lambda v: (ctypes.c_int * len(v))(*v)
+        self._check(lib().vqnqs_local_energy_ragged(
+            self._h, len(Ls), arr(Ls), arr(Bs), ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+            ctypes.c_void_p(mv.data_ptr() if mv is not None else 0), int(flags), ctypes.c_void_p(ws.data_ptr()),
+            ws.numel(), ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_local_energy_ragged")
+
+    def local_energy_ragged(self, groups, flags: int = 0, want_mean_var: bool = False,
+                            workspace: torch.Tensor | None = None, stream=None):
+        """groups: list of (L_g, spins_g [B_g, L_g^2] uint8 CUDA tensor).  Returns E_loc of all
+        samples concatenated in group order (and the FP64 [mean, var])."""
+        Ls = [int(L) for L, _ in groups]
+        Bs = [int(s.shape[0]) for _, s in groups]
+        for (L, s) in groups:
+            _check_dev(s, torch.uint8, "spins")
+            if s.shape[1] != L * L:
+                raise ValueError("spins of a group must be [B_g, L_g^2]")
+        spins = torch.cat([s.reshape(-1) for _, s in groups]).contiguous()
+        total = sum(Bs)
+        e = torch.empty(total, dtype=torch.float32, device=spins.device)
+        mv = torch.empty(2, dtype=torch.float64, device=spins.device) if want_mean_var else None
+        ws = self.workspace(flags) if workspace is None else workspace
+        self._ragged_flat(Ls, Bs, spins, e, mv, flags, ws, stream)
+        return (e, mv) if want_mean_var else e
+
+    def autotune(self, M: int = 16384, stream=None) -> dict:
+        """Pick the fastest tensor-core GEMM tile widths for this model (see vqnqs_autotune)."""
+        t = _lib.Tuning()
+        ws = torch.empty(M * self.d * 40 + 4096, dtype=torch.uint8, device="cuda")
+        self._check(lib().vqnqs_autotune(self._h, int(M), ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(t),
+                                         ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_autotune")
+        return {"qkv_bn": t.qkv_bn, "mlp_up_bn": t.mlp_up_bn, "mlp_down_bn": t.mlp_down_bn,
+                "ms": [[t.ms[s][i] for i in range(4)] for s in range(3)]}
+
     def stats(self) -> dict:
         s = _lib.Stats()
         self._check(lib().vqnqs_get_stats(self._h, ctypes.byref(s)), "vqnqs_get_stats")
@@ -136,7 +182,7 @@ class VQNQS:
             "samples": s.samples, "configs": s.configs, "rows": s.rows,
             "unique_rows": [int(s.unique_rows[i]) for i in range(self.layers + 1)],
             "near_ties": s.near_ties, "flops_full": s.flops_full, "flops_done": s.flops_done,
-            "device_status": s.device_status,
+            "device_status": s.device_status, "active_rows": s.active_rows, "attn_pairs": s.attn_pairs,
         }
 
     def reset_stats(self):
@@ -251,3 +297,48 @@ class LogPsi(torch.autograd.Function):
         (spins,) = ctx.saved_tensors
         _, grad = ctx.model.grad_log_psi(spins, seeds=g.detach().float().contiguous())
         return grad, None, None, None
+
+
+class LocalEnergyGraph:
+    """A local-energy evaluation of fixed shape captured into one CUDA graph.
+
+    ``shapes`` is a list of (L, B) lattice groups: one group with the model's
+    own L uses vqnqs_local_energy, several use vqnqs_local_energy_ragged.  Call
+    with one spins tensor per group; the spins are copied into the graph's
+    input buffer, the graph is replayed, and the E_loc buffer is returned (valid
+    until the next call).  The first, uncaptured evaluation performs every
+    one-time set-up (kernel attributes, module loading) before capture."""
+
+    def __init__(self, model: VQNQS, shapes, flags: int = 0):
+        self.model, self.flags = model, int(flags)
+        self.Ls = [int(L) for L, _ in shapes]
+        self.Bs = [int(B) for _, B in shapes]
+        self.uniform = len(shapes) == 1 and self.Ls[0] == model.L
+        total_sites = sum(L * L * B for L, B in zip(self.Ls, self.Bs))
+        self.spins = torch.zeros(total_sites, dtype=torch.uint8, device="cuda")
+        self.out = torch.empty(sum(self.Bs), dtype=torch.float32, device="cuda")
+        self.ws = torch.empty(model.workspace_bytes(self.flags), dtype=torch.uint8, device="cuda")
+        self._run()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                self._run()
+        torch.cuda.current_stream().wait_stream(side)
+
+    def _run(self):
+        if self.uniform:
+            self.model.local_energy(self.spins.view(self.Bs[0], -1), self.flags, out=self.out, workspace=self.ws)
+        else:
+            self.model._ragged_flat(self.Ls, self.Bs, self.spins, self.out, None, self.flags, self.ws)
+
+    def __call__(self, *spins):
+        off = 0
+        for s, L, B in zip(spins, self.Ls, self.Bs):
+            n = L * L * B
+            self.spins[off:off + n].copy_(s.reshape(-1), non_blocking=True)
+            off += n
+        self.graph.replay()
+        return self.out

@@ -24,15 +24,16 @@ template <int DH, typename T>
 __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* __restrict__ qkv,
                                 float* __restrict__ O, int prefix_reuse) {
     extern __shared__ __align__(16) float s_kv[];  // [N][DH] keys then [N][DH] values
-    const int N = ch.N, d = ch.d, H = ch.heads;
+    const int d = ch.d, H = ch.heads;
     const int C = ch.counters[CNT_C];
     const float scale = rsqrtf((float)DH);
     float* sK = s_kv;
-    float* sV = s_kv + (size_t)N * DH;
+    float* sV = s_kv + (size_t)ch.N * DH;
     const int ld = 3 * d;
     for (int item = blockIdx.x; item < C * H; item += gridDim.x) {
         const int c = item / H, h = item - c * H;
-        const int* urow = uid + (size_t)c * N;
+        const int N = cfg_N(ch, c);
+        const int* urow = uid + ch.cfg_row[c];
         for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
             int j = e / (DH / 4), t4 = (e - j * (DH / 4)) * 4;
             const T* src = qkv + (size_t)urow[j] * ld + h * DH + t4;
@@ -105,7 +106,7 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* 
         }
         if (active) {
             const float inv = 1.f / l;
-            float* dst = O + ((size_t)c * N + p) * d + h * DH;
+            float* dst = O + ((size_t)ch.cfg_row[c] + p) * d + h * DH;
 #pragma unroll
             for (int t = 0; t < DH; t += 4)
                 *reinterpret_cast<float4*>(dst + t) =
@@ -113,6 +114,15 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* 
         }
         __syncthreads();
     }
+}
+
+// Largest dynamic shared memory already granted to an instantiation (the
+// attribute is set outside any stream capture, on the first call that needs it).
+template <int X, typename T>
+size_t set_attr_once(size_t v) {
+    static size_t granted = 0;
+    if (v > granted) granted = v;
+    return granted;
 }
 
 template <typename T>
@@ -125,8 +135,10 @@ cudaError_t launch_attention_t(const Chunk& ch, const int* uid, const T* qkv, fl
     switch (DH) {
 #define VQ_ATT_CASE(X)                                                                                        \
     case X:                                                                                                   \
-        if (smem > 48 * 1024)                                                                                 \
+        if (smem > 48 * 1024 && smem > set_attr_once<X, T>(0)) {                                              \
             cudaFuncSetAttribute(k_attention_f32<X, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            set_attr_once<X, T>(smem);                                                                        \
+        }                                                                                                     \
         k_attention_f32<X, T><<<grid, threads, smem, st>>>(ch, uid, qkv, O, prefix_reuse);                                  \
         break;
         VQ_ATT_CASE(8)

@@ -1,25 +1,29 @@
 // Causal multi-head self-attention on the tensor cores (BF16 path, Sec. 3.1
 // location mixer): BF16 Q/K/V, FP32 scores and accumulation in TMEM.
 //
-// One work item = (configuration, head).  A CTA of 4 warps:
+// One work item = (configuration, head).  A CTA of 8 warps:
 //   1. gathers the configuration's K rows and V rows of this head by row id
-//      into shared memory (K as a [keys x dh] K-major operand, V transposed
-//      to a [dh x keys] K-major operand), in the no-swizzle canonical layout
-//      (8-row x 16-byte core matrices);
+//      into shared memory (K as a [keys x dh] K-major operand; V staged row by
+//      row, then transposed to a [dh x keys] K-major operand with ldmatrix.trans
+//      / stmatrix), in the no-swizzle canonical layout (8-row x 16-byte core
+//      matrices), every store phase writing 128 contiguous bytes;
 //   2. per 128-query tile: gathers Q, thread 0 issues S = Q K^T with
 //      tcgen05.mma (M = 128, N = keys, K = dh) into TMEM;
-//   3. every thread owns one query row: two passes over its TMEM row (causal
-//      max, then exp2 / sum), writing P as BF16 into shared memory;
+//   3. two threads own each query row (alternate 32-column chunks of its TMEM
+//      lane): two passes (causal max, then exp2 / sum) combined through shared
+//      memory, writing P as BF16 into shared memory;
 //   4. thread 0 issues O = P V (M = 128, N = dh, K = keys) into TMEM columns
-//      already read; each thread scales its row by 1/sum and stores FP32 O.
+//      already read; each thread scales half of its row by 1/sum and stores it.
 // With prefix reuse, query tiles wholly before the configuration's first
 // changed position are skipped and rows before it are not stored.
 // Waits on the MMA barrier are bounded (VQNQS_DEV_TIMEOUT on expiry).
+#include <algorithm>
+
 #include "tc_common.cuh"
 
 namespace vq {
 
-constexpr int AT_THREADS = 128;
+constexpr int AT_THREADS = 256;
 constexpr int AT_MAX_N = 448;  // keys per configuration handled in one TMEM tile
 
 __device__ __forceinline__ uint64_t desc_kmajor_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -40,21 +44,51 @@ __device__ __forceinline__ uint32_t core_off(int r, int k, int kd) {
     return (uint32_t)((r >> 3) * (kd >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// 8x8 b16 matrix moves: four matrices per instruction, thread i addresses row
+// i % 8 of matrix i / 8 (16 bytes).  The .trans load hands out the transposed
+// fragments, so a load/store pair transposes 8x8 blocks without bank conflicts.
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void stsm_x4(uint32_t addr, const uint32_t (&r)[4]) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 template <int DH>
 __global__ void __launch_bounds__(AT_THREADS)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, float* __restrict__ O,
                int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int N = ch.N, d = ch.d, H = ch.heads;
-    uint8_t* sK = smem;                            // [Npad x DH]
+    const int d = ch.d, H = ch.heads;
+    constexpr int VS = 2 * DH + 16;                // row stride of the V staging rows (bank-conflict free)
+    uint8_t* sK = smem;                            // [Npad x DH] K-major core layout
     uint8_t* sVt = sK + (size_t)Npad * DH * 2;     // [DH x Npad]
     uint8_t* sQ = sVt + (size_t)Npad * DH * 2;     // [128 x DH]
-    uint8_t* sP = sQ + 128 * DH * 2;               // [128 x Npad]
+    uint8_t* sP = sQ + 128 * DH * 2;               // [128 x Npad]; V staging rows alias it
     uint64_t* bar = reinterpret_cast<uint64_t*>(sP + (size_t)128 * Npad * 2);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
+    __shared__ float s_red[2][128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & 127, half = tid >> 7;  // two threads per query row
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         tc::fence_barrier_init();
@@ -64,7 +98,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     uint32_t phase = 0;
     bool ok = true;
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);  // log2(e) / sqrt(dh)
@@ -73,29 +107,48 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
 
     for (int item = blockIdx.x; item < C * H && ok; item += gridDim.x) {
         const int c = item / H, h = item - c * H;
-        const int* urow = uid + (size_t)c * N;
+        const int N = cfg_N(ch, c);
+        const int* urow = uid + ch.cfg_row[c];
         const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
-        // keys and transposed values, rows >= N zero
+        // keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
+        for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
+            const int j = u % Npad, kb = u / Npad;
+            uint4 kv = make_uint4(0, 0, 0, 0);
+            if (j < N) kv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[j] * ld + d + h * DH + kb * 8);
+            *reinterpret_cast<uint4*>(sK + core_off(j, kb * 8, DH)) = kv;
+        }
+        // values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
         for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
             const int j = u / (DH / 8), kb = u - j * (DH / 8);
-            uint4 kv = make_uint4(0, 0, 0, 0), vv = make_uint4(0, 0, 0, 0);
-            if (j < N) {
-                const __nv_bfloat16* src = qkv + (size_t)urow[j] * ld + h * DH + kb * 8;
-                kv = *reinterpret_cast<const uint4*>(src + d);
-                vv = *reinterpret_cast<const uint4*>(src + 2 * d);
-            }
-            *reinterpret_cast<uint4*>(sK + core_off(j, kb * 8, DH)) = kv;
-            const __nv_bfloat16* ve = reinterpret_cast<const __nv_bfloat16*>(&vv);
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-                *reinterpret_cast<__nv_bfloat16*>(sVt + core_off(kb * 8 + e, j, Npad)) = ve[e];
+            uint4 vv = make_uint4(0, 0, 0, 0);
+            if (j < N) vv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[j] * ld + 2 * d + h * DH + kb * 8);
+            *reinterpret_cast<uint4*>(sP + j * VS + kb * 16) = vv;
         }
+        __syncthreads();
+        for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AT_THREADS / 32) {
+            // four 8x8 matrices: key block jb, dh blocks kq*4 .. kq*4+3
+            const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
+            const int m = lane >> 3, r = lane & 7;
+            uint32_t f[4];
+            ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
+            stsm_x4(tc::smem_u32(sVt + core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
+        }
+        if (DH == 16) {  // the two dh blocks of a key block in one x4 with two key blocks
+            for (int blk = warp; blk < Npad / 16; blk += AT_THREADS / 32) {
+                const int m = lane >> 3, r = lane & 7;
+                const int jb = blk * 2 + (m >> 1), kb = m & 1;
+                uint32_t f[4];
+                ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + kb * 16), f);
+                stsm_x4(tc::smem_u32(sVt + core_off(kb * 8 + r, jb * 8, Npad)), f);
+            }
+        }
+        __syncthreads();
         for (int q0 = (p0 / 128) * 128; q0 < N && ok; q0 += 128) {
             const int nk = min(N, q0 + 128);             // keys this tile can see
             const int nk16 = (nk + 15) & ~15;            // MMA N (multiple of 16)
             const int nk32 = (nk + 31) & ~31;            // columns read back
             for (int u = tid; u < 128 * (DH / 8); u += AT_THREADS) {
-                const int r = u / (DH / 8), kb = u - r * (DH / 8);
+                const int r = u & 127, kb = u >> 7;
                 uint4 qv = make_uint4(0, 0, 0, 0);
                 if (q0 + r < N) qv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[q0 + r] * ld + h * DH + kb * 8);
                 *reinterpret_cast<uint4*>(sQ + core_off(r, kb * 8, DH)) = qv;
@@ -110,7 +163,6 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 for (int n0 = 0; n0 < nk16; n0 += 256) {
                     const int nn = min(256, nk16 - n0);
                     const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
-                    // rows n0.. of K start (n0 / 8) core-row groups further
                     const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
 #pragma unroll
                     for (int ks = 0; ks < DH / 16; ++ks)
@@ -123,20 +175,24 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             phase ^= 1;
             tc::tc_fence_after();
             if (!ok) break;
-            // softmax of this thread's row (query position p = q0 + tid)
-            const int p = q0 + tid;
+            // softmax of query position p = q0 + row; this thread takes every other
+            // 32-column chunk, starting with chunk `half`
+            const int p = q0 + row;
             const int plim = min(p, N - 1);  // keys 0..plim are visible
             float mx = -INFINITY;
-            for (int c0 = 0; c0 < nk32; c0 += 32) {
+            for (int c0 = half * 32; c0 < nk32; c0 += 64) {
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + lane_base + c0, r);
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
                     if (c0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
             }
+            s_red[half][row] = mx;
+            __syncthreads();
+            mx = fmaxf(s_red[0][row], s_red[1][row]);
             const float mb = mx * sl2;
             float sum = 0.f;
-            for (int c0 = 0; c0 < nk32; c0 += 32) {
+            for (int c0 = half * 32; c0 < nk32; c0 += 64) {
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + lane_base + c0, r);
                 if (c0 < nk16) {
@@ -154,14 +210,17 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                             sum += back.x + back.y;
                             pk[e / 2] = *reinterpret_cast<uint32_t*>(&b2);
                         }
-                        *reinterpret_cast<uint4*>(sP + core_off(tid, c0 + j8, Npad)) =
+                        *reinterpret_cast<uint4*>(sP + core_off(row, c0 + j8, Npad)) =
                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 }
             }
+            __syncthreads();  // both halves read s_red (max) before it is reused for sums
+            s_red[half][row] = sum;
             tc::tc_fence_before();
             fence_proxy_async_smem();
             __syncthreads();
+            sum = s_red[0][row] + s_red[1][row];
             if (tid == 0) {
                 tc::tc_fence_after();
                 const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
@@ -176,13 +235,14 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             tc::tc_fence_after();
             if (!ok) break;
             {
-                uint32_t r[32];
-                tc::tmem_ld32(tmem + lane_base, r);
+                // each of the row's two threads stores half of the DH output columns
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + half * (DH / 2), r);
                 if (p < N && p >= p0) {
                     const float inv = 1.f / sum;
-                    float* dst = O + ((size_t)c * N + p) * d + h * DH;
+                    float* dst = O + ((size_t)ch.cfg_row[c] + p) * d + h * DH + half * (DH / 2);
 #pragma unroll
-                    for (int t = 0; t < DH; t += 4)
+                    for (int t = 0; t < DH / 2; t += 4)
                         *reinterpret_cast<float4*>(dst + t) =
                             make_float4(__uint_as_float(r[t]) * inv, __uint_as_float(r[t + 1]) * inv,
                                         __uint_as_float(r[t + 2]) * inv, __uint_as_float(r[t + 3]) * inv);
@@ -210,7 +270,8 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const int Npad = (ch.N + 31) & ~31;
     uint32_t cols = 32;
     while ((int)cols < Npad) cols <<= 1;
-    const size_t smem = 1024 + (size_t)Npad * DH * 2 * 2 + 128 * DH * 2 + (size_t)128 * Npad * 2 + 64;
+    const size_t smem = 1024 + (size_t)Npad * DH * 2 * 2 + 128 * DH * 2 +
+                        std::max((size_t)128 * Npad * 2, (size_t)Npad * (2 * DH + 16)) + 64;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     // the TMEM columns of all CTAs resident on one SM must fit in its 512: cap the
     // residency through the shared-memory request
@@ -218,13 +279,20 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const size_t max_ctas = 512 / cols;
     size_t smem_req = smem;
     if (smem_sm / smem_req > max_ctas) smem_req = smem_sm / (max_ctas + 1) + 1024;
+    static size_t granted16 = 0, granted32 = 0;  // attribute set once per size, outside captures
     switch (DH) {
         case 16:
-            cudaFuncSetAttribute(k_attention_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+            if (smem_req > granted16) {
+                cudaFuncSetAttribute(k_attention_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+                granted16 = smem_req;
+            }
             k_attention_tc<16><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status);
             break;
         case 32:
-            cudaFuncSetAttribute(k_attention_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+            if (smem_req > granted32) {
+                cudaFuncSetAttribute(k_attention_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+                granted32 = smem_req;
+            }
             k_attention_tc<32><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status);
             break;
         default: return cudaErrorInvalidValue;

@@ -422,11 +422,15 @@ cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N
     const size_t smem = ((size_t)4 * N * DH + 3 * N) * sizeof(float);
     if (threads > 512 || smem > 227 * 1024) return cudaErrorInvalidValue;
     const int grid = g_grid((long long)S * H, 1, cap);
+    static size_t granted[3] = {};
     switch (DH) {
 #define VQ_ABWD(X)                                                                                           \
     case X:                                                                                                  \
-        cudaFuncSetAttribute(k_attention_bwd_q<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
-        cudaFuncSetAttribute(k_attention_bwd_kv<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (smem > granted[X / 16]) {                                                                        \
+            cudaFuncSetAttribute(k_attention_bwd_q<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            cudaFuncSetAttribute(k_attention_bwd_kv<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
+            granted[X / 16] = smem;                                                                          \
+        }                                                                                                    \
         k_attention_bwd_q<X><<<grid, threads, smem, st>>>(QKV, dO, S, N, d, H, dQKV, stat);                  \
         k_attention_bwd_kv<X><<<grid, threads, smem, st>>>(QKV, dO, S, N, d, H, dQKV, stat);                 \
         break;

@@ -9,12 +9,14 @@ namespace vq {
 // (J/4) sigma_i sigma_j on the diagonal and -J/2 to the configuration with the
 // two spins exchanged when they differ (Sec. 2: a k-local term touches only its
 // own sites).
-__global__ void k_count_configs(const uint8_t* __restrict__ spins, int S, int N, const int* __restrict__ bonds,
-                                int nb, float J, int with_bonds, int* __restrict__ cnt, float* __restrict__ diag,
+__global__ void k_count_configs(Chunk ch, float J, int with_bonds, int* __restrict__ cnt, float* __restrict__ diag,
                                 int* __restrict__ status) {
     __shared__ int s_red[2][32];
-    for (int b = blockIdx.x; b < S; b += gridDim.x) {
-        const uint8_t* s = spins + (size_t)b * N;
+    for (int b = blockIdx.x; b < ch.S; b += gridDim.x) {
+        const int g = sample_group(ch, b);
+        const int N = ch.g.N[g], nb = ch.g.nb[g];
+        const int* bonds = ch.bonds + 2 * ch.g.bond_off[g];
+        const uint8_t* s = sample_spins(ch, b);
         int bad = 0;
         for (int p = threadIdx.x; p < N; p += blockDim.x) bad |= (s[p] > 1);
         int anti = 0, zz = 0;
@@ -44,17 +46,17 @@ __global__ void k_count_configs(const uint8_t* __restrict__ spins, int S, int N,
     }
 }
 
-// Exclusive scan of (1 + anti-aligned count) over the chunk's samples; one block.
-__global__ void k_scan_configs(const int* __restrict__ cnt, int S, int* __restrict__ cfg_off,
-                               int* __restrict__ counters, int N) {
+// One-block exclusive scan of v(i) for i < n; writes off[0..n] and returns the total in *total.
+template <typename F>
+__device__ void block_exclusive_scan(int n, F v_of, int* __restrict__ off, int* __restrict__ total) {
     __shared__ int s_warp[32];
     __shared__ int s_carry;
     if (threadIdx.x == 0) s_carry = 0;
     __syncthreads();
-    for (int base = 0; base < S; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = (i < S) ? 1 + cnt[i] : 0;
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = (i < n) ? v_of(i) : 0;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -64,7 +66,7 @@ __global__ void k_scan_configs(const int* __restrict__ cnt, int S, int* __restri
         if (lane == 31) s_warp[w] = x;
         __syncthreads();
         if (w == 0) {
-            int nw = blockDim.x >> 5;
+            const int nw = blockDim.x >> 5;
             int t = (lane < nw) ? s_warp[lane] : 0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -74,27 +76,33 @@ __global__ void k_scan_configs(const int* __restrict__ cnt, int S, int* __restri
             if (lane < nw) s_warp[lane] = t;
         }
         __syncthreads();
-        int incl = x + (w > 0 ? s_warp[w - 1] : 0) + s_carry;
-        if (i < S) cfg_off[i] = incl - v;
+        const int incl = x + (w > 0 ? s_warp[w - 1] : 0) + s_carry;
+        if (i < n) off[i] = incl - v;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) s_carry = incl;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        cfg_off[S] = s_carry;
-        counters[CNT_C] = s_carry;
-        counters[CNT_R] = s_carry * N;
+        off[n] = s_carry;
+        *total = s_carry;
     }
 }
 
+// First configuration of each sample: exclusive scan of (1 + anti-aligned count).
+__global__ void k_scan_configs(Chunk ch, const int* __restrict__ cnt, int* __restrict__ cfg_off) {
+    block_exclusive_scan(ch.S, [&](int i) { return 1 + cnt[i]; }, cfg_off, &ch.counters[CNT_C]);
+}
+
 // Writes the sample itself, then its anti-aligned bonds in bond order.
-__global__ void k_fill_configs(const uint8_t* __restrict__ spins, int S, int N, const int* __restrict__ bonds,
-                               int nb, int with_bonds, const int* __restrict__ cfg_off, int* __restrict__ cfg_sample,
-                               int* __restrict__ cfg_i, int* __restrict__ cfg_j) {
+__global__ void k_fill_configs(Chunk ch, int with_bonds, int* __restrict__ cfg_sample, int* __restrict__ cfg_i,
+                               int* __restrict__ cfg_j) {
     __shared__ int s_warp[32];
-    for (int b = blockIdx.x; b < S; b += gridDim.x) {
-        const uint8_t* s = spins + (size_t)b * N;
-        int off = cfg_off[b];
+    for (int b = blockIdx.x; b < ch.S; b += gridDim.x) {
+        const int g = sample_group(ch, b);
+        const int nb = ch.g.nb[g];
+        const int* bonds = ch.bonds + 2 * ch.g.bond_off[g];
+        const uint8_t* s = sample_spins(ch, b);
+        const int off = ch.cfg_off[b];
         if (threadIdx.x == 0) { cfg_sample[off] = b; cfg_i[off] = -1; cfg_j[off] = -1; }
         if (!with_bonds) continue;
         int run = off + 1;
@@ -121,61 +129,55 @@ __global__ void k_fill_configs(const uint8_t* __restrict__ spins, int S, int N, 
     }
 }
 
-// ---- active rows -------------------------------------------------------------------
-__global__ void k_active_count(Chunk ch, int prefix_reuse, int* __restrict__ act_cnt) {
+// First row of each configuration (exclusive scan of its number of sites); total -> CNT_R.
+__global__ void k_scan_rows(Chunk ch, int* __restrict__ cfg_row) {
+    block_exclusive_scan(ch.counters[CNT_C], [&](int c) { return cfg_N(ch, c); }, cfg_row, &ch.counters[CNT_R]);
+}
+
+__global__ void k_fill_row_cfg(Chunk ch, int* __restrict__ row_cfg) {
     const int C = ch.counters[CNT_C];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
-        act_cnt[c] = ch.N - (prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
+        const int r0 = ch.cfg_row[c], r1 = ch.cfg_row[c + 1];
+        for (int r = r0 + lane; r < r1; r += 32) row_cfg[r] = c;
+    }
+}
+
+// ---- active rows -------------------------------------------------------------------
+__global__ void k_active_count(Chunk ch, int prefix_reuse, int* __restrict__ act_cnt, long long* __restrict__ stats) {
+    const int C = ch.counters[CNT_C];
+    long long rows = 0, pairs = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const int N = cfg_N(ch, c);
+        const long long p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        act_cnt[c] = N - (int)p0;
+        rows += N - p0;
+        pairs += ((long long)N * (N + 1) - p0 * (p0 + 1)) / 2;  // sum over active rows p of (p + 1) keys
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        rows += __shfl_xor_sync(0xffffffffu, rows, o);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (rows || pairs)) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_ACTIVE]), (unsigned long long)rows);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_PAIRS]), (unsigned long long)pairs);
+    }
 }
 
 // Exclusive scan of act_cnt over the chunk's configurations (one block); total -> CNT_A.
 __global__ void k_active_scan(Chunk ch, const int* __restrict__ act_cnt, int* __restrict__ act_off) {
-    __shared__ int s_warp[32];
-    __shared__ int s_carry;
-    const int C = ch.counters[CNT_C];
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < C; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v = (i < C) ? act_cnt[i] : 0;
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            int nw = blockDim.x >> 5;
-            int t = (lane < nw) ? s_warp[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            if (lane < nw) s_warp[lane] = t;
-        }
-        __syncthreads();
-        int incl = x + (w > 0 ? s_warp[w - 1] : 0) + s_carry;
-        if (i < C) act_off[i] = incl - v;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) s_carry = incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) ch.counters[CNT_A] = s_carry;
+    block_exclusive_scan(ch.counters[CNT_C], [&](int i) { return act_cnt[i]; }, act_off, &ch.counters[CNT_A]);
 }
 
 // One warp per configuration writes its active rows (ascending).
 __global__ void k_active_fill(Chunk ch, int prefix_reuse, const int* __restrict__ act_off,
                               int* __restrict__ act_rows) {
-    const int C = ch.counters[CNT_C], N = ch.N;
+    const int C = ch.counters[CNT_C];
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
         const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
-        const int off = act_off[c];
-        for (int p = p0 + lane; p < N; p += 32) act_rows[off + p - p0] = c * N + p;
+        const int off = act_off[c], r0 = ch.cfg_row[c], N = cfg_N(ch, c);
+        for (int p = p0 + lane; p < N; p += 32) act_rows[off + p - p0] = r0 + p;
     }
 }
 
@@ -201,9 +203,9 @@ __global__ void k_embed_rows(Chunk ch, const float* __restrict__ tok_emb, const 
     int lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
     for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < R; r += gridDim.x * wpb) {
-        int c = r / N, p = r - c * N;
+        const int c = ch.row_cfg[r], p = r - ch.cfg_row[c];
         int t = BOS;
-        if (p > 0) t = cfg_spin(ch.spins, N, ch.cfg_sample[c], ch.cfg_i[c], ch.cfg_j[c], p - 1) & 1;
+        if (p > 0) t = cfg_spin(sample_spins(ch, ch.cfg_sample[c]), ch.cfg_i[c], ch.cfg_j[c], p - 1);
         if (reuse) {
             if (lane == 0) uid0[r] = p * 3 + t;
         } else {
@@ -252,16 +254,17 @@ __global__ void k_head(const float* __restrict__ X, const int* __restrict__ coun
 // summed term by term so that positions whose rows agree contribute exact zeros.
 __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float* __restrict__ logp,
                              float* __restrict__ ratio, float* __restrict__ log_psi_out) {
-    const int N = ch.N;
     const int C = ch.counters[CNT_C];
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
-        int b = ch.cfg_sample[c], ci = ch.cfg_i[c], cj = ch.cfg_j[c];
-        int base = ch.cfg_off[b];
-        const uint8_t* s = ch.spins + (size_t)b * N;
+        const int b = ch.cfg_sample[c], ci = ch.cfg_i[c], cj = ch.cfg_j[c];
+        const int N = sample_N(ch, b);
+        const int* urow = uid + ch.cfg_row[c];
+        const int* ubase = uid + ch.cfg_row[ch.cfg_off[b]];
+        const uint8_t* s = sample_spins(ch, b);
         float acc = 0.f;
         if (ci < 0) {
-            for (int p = lane; p < N; p += 32) acc += logp[2 * (size_t)uid[(size_t)c * N + p] + (s[p] & 1)];
+            for (int p = lane; p < N; p += 32) acc += logp[2 * (size_t)urow[p] + (s[p] & 1)];
             acc = warp_sum(acc);
             if (lane == 0) {
                 ratio[c] = 0.f;
@@ -269,9 +272,9 @@ __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float*
             }
         } else {
             for (int p = lane; p < N; p += 32) {
-                int sp = s[p] & 1;
-                int spc = (p == ci) ? (s[cj] & 1) : (p == cj) ? (s[ci] & 1) : sp;
-                acc += logp[2 * (size_t)uid[(size_t)c * N + p] + spc] - logp[2 * (size_t)uid[(size_t)base * N + p] + sp];
+                const int sp = s[p] & 1;
+                const int spc = cfg_spin(s, ci, cj, p);
+                acc += logp[2 * (size_t)urow[p] + spc] - logp[2 * (size_t)ubase[p] + sp];
             }
             acc = warp_sum(acc);
             if (lane == 0) ratio[c] = expf(0.5f * acc);
@@ -333,19 +336,14 @@ __global__ void k_accumulate_stats(const int* __restrict__ counters, int layers,
 }
 
 // ---- launchers -----------------------------------------------------------------
-cudaError_t launch_count_configs(const uint8_t* spins, int S, int N, const int* bonds, int nb, float J,
-                                 int with_bonds, int* cnt, float* diag, int* status, cudaStream_t st, int grid) {
-    k_count_configs<<<grid, 256, 0, st>>>(spins, S, N, bonds, nb, J, with_bonds, cnt, diag, status);
-    return cudaGetLastError();
-}
-cudaError_t launch_scan_configs(const int* cnt, int S, int* cfg_off, int* counters, int N, cudaStream_t st) {
-    k_scan_configs<<<1, 1024, 0, st>>>(cnt, S, cfg_off, counters, N);
-    return cudaGetLastError();
-}
-cudaError_t launch_fill_configs(const uint8_t* spins, int S, int N, const int* bonds, int nb, int with_bonds,
-                                const int* cfg_off, int* cfg_sample, int* cfg_i, int* cfg_j, cudaStream_t st,
-                                int grid) {
-    k_fill_configs<<<grid, 256, 0, st>>>(spins, S, N, bonds, nb, with_bonds, cfg_off, cfg_sample, cfg_i, cfg_j);
+cudaError_t launch_configs(const Chunk& ch, float J, int with_bonds, int* cnt, float* diag, int* cfg_off,
+                           int* cfg_sample, int* cfg_i, int* cfg_j, int* cfg_row, int* row_cfg, int* status,
+                           cudaStream_t st, int grid) {
+    k_count_configs<<<grid, 256, 0, st>>>(ch, J, with_bonds, cnt, diag, status);
+    k_scan_configs<<<1, 1024, 0, st>>>(ch, cnt, cfg_off);
+    k_fill_configs<<<grid, 256, 0, st>>>(ch, with_bonds, cfg_sample, cfg_i, cfg_j);
+    k_scan_rows<<<1, 1024, 0, st>>>(ch, cfg_row);
+    k_fill_row_cfg<<<grid * 4, 256, 0, st>>>(ch, row_cfg);
     return cudaGetLastError();
 }
 cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos_emb, int reuse, float* X0,
@@ -358,9 +356,25 @@ cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos
     k_embed_rows<<<grid, 256, 0, st>>>(ch, tok_emb, pos_emb, reuse, X0, uid0);
     return cudaGetLastError();
 }
+// out[(b * layers + l) * N + p] = code of row (configuration b, position p); here every
+// configuration is a sample and every row is computed.
+__global__ void k_copy_codes(Chunk ch, const int* __restrict__ code, int l, int layers, int* __restrict__ out) {
+    const int R = ch.counters[CNT_R], N = ch.N;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        const int b = ch.row_cfg[r], p = r - ch.cfg_row[b];
+        out[((size_t)b * layers + l) * N + p] = code[r];
+    }
+}
+
+cudaError_t launch_copy_codes(const Chunk& ch, const int* code, int l, int layers, int* out, cudaStream_t st,
+                              int grid) {
+    k_copy_codes<<<grid, 256, 0, st>>>(ch, code, l, layers, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
-                               cudaStream_t st, int grid) {
-    k_active_count<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_cnt);
+                               long long* stats, cudaStream_t st, int grid) {
+    k_active_count<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_cnt, stats);
     k_active_scan<<<1, 1024, 0, st>>>(ch, act_cnt, act_off);
     k_active_fill<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_off, act_rows);
     return cudaGetLastError();

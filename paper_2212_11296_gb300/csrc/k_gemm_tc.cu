@@ -269,9 +269,9 @@ cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, i
 
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms) {
-    const int BN = tc_pick_bn(N);
-    if (!BN || K % TC_BK || K <= 0) return cudaErrorInvalidValue;
+                           int* status, cudaStream_t st, int num_sms, int BN) {
+    if (BN <= 0) BN = tc_pick_bn(N);
+    if (!BN || N % BN || K % TC_BK || K <= 0) return cudaErrorInvalidValue;
     CUtensorMap ta;
     cudaError_t e = make_tmap_bf16(&ta, A, Arows, K, TC_BM);
     if (e != cudaSuccess) return e;

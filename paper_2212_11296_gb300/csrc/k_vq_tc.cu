@@ -6,12 +6,15 @@
 // o_hi W_hi + o_hi W_lo + o_lo W_hi (the lo x lo term is below 2^-22 relative),
 // which keeps the dot products at FP32 accuracy on the TF32 tensor pipe.
 //
-// Persistent CTA of 5 warps per SM, one 128-row tile of active rows at a time:
-//   warps 0-3  gather the tile's O rows, split them, write the hi/lo A chunks
-//              (32 columns each, 128-byte swizzle) into a 2-slot ring; then,
-//              per tile, read the K accumulator columns from TMEM and reduce
-//              (best, index, second best) per row;
-//   warp 4     one thread: TMA of the codebook hi/lo chunks (precomputed per
+// Persistent CTA of 9 warps per SM, 128-row tiles of active rows:
+//   warps 0-3  loaders: gather the tile's O rows, split them, write the hi/lo A
+//              chunks (32 columns, 128-byte swizzle) into the shared-memory ring;
+//              the next chunk's global loads are in flight while a loader waits
+//              for a free slot;
+//   warps 4-7  epilogue: read the accumulator columns from TMEM and reduce
+//              (best, index, second best) per row; the accumulator is double
+//              buffered when it fits, so this overlaps the next tile's MMAs;
+//   warp 8     one thread: TMA of the codebook hi/lo chunks (precomputed per
 //              layer) and the tcgen05.mma (kind::tf32, M = 128, N <= 256, K = 8)
 //              issue, slot release by tcgen05.commit.
 // All waits are bounded (VQNQS_DEV_TIMEOUT).
@@ -19,7 +22,7 @@
 
 namespace vq {
 
-constexpr int VT_BM = 128, VT_BK = 32, VT_THREADS = 160;
+constexpr int VT_BM = 128, VT_BK = 32, VT_THREADS = 288;
 
 __host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -66,21 +69,22 @@ __global__ void __launch_bounds__(VT_THREADS, 1)
 k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
         const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
         const float* __restrict__ cnorm, int K, int d, int* __restrict__ code, long long* __restrict__ near_ties,
-        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols) {
+        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols, int ACC) {
     constexpr int A_BYTES = VT_BM * VT_BK * 4;   // 16 KB per part
     constexpr int B_BYTES = KC * VT_BK * 4;      // per part and pass
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int passes = (K + KC - 1) / KC;
-    // slot s: A_hi, A_lo, then for each pass: B_hi, B_lo
-    const int SLOT = 2 * A_BYTES + passes * 2 * B_BYTES;
+    const int SLOT = 2 * A_BYTES + passes * 2 * B_BYTES;  // A_hi, A_lo, then per pass B_hi, B_lo
     uint64_t* fullA = reinterpret_cast<uint64_t*>(smem + VT_STAGES * SLOT);
     uint64_t* fullB = fullA + VT_STAGES;
     uint64_t* empty = fullB + VT_STAGES;
-    uint64_t* accf = empty + VT_STAGES;
-    uint64_t* acce = accf + 1;
-    uint64_t* done = acce + 1;
+    uint64_t* accf = empty + VT_STAGES;  // [2]
+    uint64_t* acce = accf + 2;           // [2]
+    uint64_t* osqf = acce + 2;           // [2] loaders -> epilogue: row norms written
+    uint64_t* done = osqf + 2;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    float* osq_s = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128]
     __shared__ int s_ties;
 
     const int R = counters[CNT_A];
@@ -92,19 +96,24 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             tc::mbar_init(&fullB[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(accf, 1);
-        tc::mbar_init(acce, 128);
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&accf[a], 1);
+            tc::mbar_init(&acce[a], 128);
+            tc::mbar_init(&osqf[a], 128);
+        }
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
         s_ties = 0;
     }
-    if (warp == 4) tc::tmem_alloc(tmem_holder, tmem_cols);
+    if (warp == 8) tc::tmem_alloc(tmem_holder, tmem_cols);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
+    const int accw = passes * KC;  // TMEM columns of one accumulator
 
-    if (warp == 4) {
+    if (warp == 8) {
+        // ---- TMA of the codebook chunks and MMA issue -------------------------
         if (lane == 0) {
             tc::prefetch_tmap(&tm_hi);
             tc::prefetch_tmap(&tm_lo);
@@ -112,13 +121,13 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             bool ok = true;
             int it = 0, i = 0;
             for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
-                if (!tc::mbar_wait(acce, (i & 1) ^ 1, status)) { ok = false; break; }
+                const int a = i % ACC;
+                if (!tc::mbar_wait(&acce[a], ((i / ACC) & 1) ^ 1, status)) { ok = false; break; }
                 tc::tc_fence_after();
                 for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % VT_STAGES;
                     const uint32_t ph = (it / VT_STAGES) & 1;
                     uint8_t* slot = smem + s * SLOT;
-                    // codebook chunk (the A rows are written by the loader warps)
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
                     tc::mbar_arrive_expect_tx(&fullB[s], passes * 2 * B_BYTES);
                     for (int ps = 0; ps < passes; ++ps) {
@@ -137,7 +146,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                         uint8_t* bh = slot + 2 * A_BYTES + ps * 2 * B_BYTES;
                         const uint64_t dbh = tc::desc_kmajor_sw128(tc::smem_u32(bh));
                         const uint64_t dbl = tc::desc_kmajor_sw128(tc::smem_u32(bh + B_BYTES));
-                        const uint32_t dt = tmem + ps * KC;
+                        const uint32_t dt = tmem + a * accw + ps * KC;
 #pragma unroll
                         for (int k = 0; k < VT_BK / 8; ++k) {
                             const uint32_t acc0 = (kb | k) != 0 ? 1u : 0u;
@@ -149,7 +158,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) break;
-                tc::mma_commit(accf);
+                tc::mma_commit(&accf[a]);
             }
             tc::mma_commit(done);
             tc::mbar_wait(done, 0, status, 100000000LL);
@@ -158,52 +167,86 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                     if (j >= 0) tc::mbar_wait(&fullB[j % VT_STAGES], (j / VT_STAGES) & 1, status, 100000000LL);
             }
         }
-    } else {
-        // loaders / epilogue: thread tid owns tile row tid
+    } else if (warp < 4) {
+        // ---- loaders: thread tid owns tile row tid; loads of the next chunk are in
+        // flight while this thread waits for a free slot ----------------------
         int it = 0, i = 0;
-        int ties = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
-            const int m = t * VT_BM + tid;
-            const bool valid = m < R;
-            const float* orow = O + (size_t)(valid ? act_rows[m] : 0) * d;
-            float osq = 0.f;
-            bool ok = true;
-            for (int kb = 0; kb < KB; ++kb, ++it) {
-                const int s = it % VT_STAGES;
-                const uint32_t ph = (it / VT_STAGES) & 1;
-                if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
-                uint8_t* slot = smem + s * SLOT;
+        int t = blockIdx.x, kb = 0;
+        float4 cur[VT_BK / 4];
+        auto issue = [&](int tt, int kk, float4 (&dst)[VT_BK / 4]) {
+            const int m = tt * VT_BM + tid;
+            const bool valid = tt < tiles && m < R;
+            const float* src = O + (size_t)(valid ? act_rows[m] : 0) * d + kk * VT_BK;
 #pragma unroll
-                for (int q = 0; q < VT_BK; q += 4) {
-                    float4 v = valid ? *reinterpret_cast<const float4*>(orow + kb * VT_BK + q) : make_float4(0, 0, 0, 0);
-                    osq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, osq))));
-                    float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-                    float4 lo = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-                    const uint32_t off = sw128_off(tid, q);
-                    *reinterpret_cast<float4*>(slot + off) = h;
-                    *reinterpret_cast<float4*>(slot + A_BYTES + off) = lo;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tc::mbar_arrive(&fullA[s]);
+            for (int q = 0; q < VT_BK / 4; ++q)
+                dst[q] = valid ? *reinterpret_cast<const float4*>(src + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        if (t < tiles) issue(t, 0, cur);
+        float osq = 0.f;
+        bool ok = true;
+        while (t < tiles && ok) {
+            // the chunk after this one
+            int nt = t, nkb = kb + 1;
+            if (nkb == KB) { nkb = 0; nt = t + gridDim.x; }
+            float4 nxt[VT_BK / 4];
+            if (nt < tiles) issue(nt, nkb, nxt);
+            const int s = it % VT_STAGES;
+            const uint32_t ph = (it / VT_STAGES) & 1;
+            if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
+            uint8_t* slot = smem + s * SLOT;
+#pragma unroll
+            for (int q = 0; q < VT_BK / 4; ++q) {
+                const float4 v = cur[q];
+                osq = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, osq))));
+                const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+                const float4 lo = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                const uint32_t off = sw128_off(tid, 4 * q);
+                *reinterpret_cast<float4*>(slot + off) = h;
+                *reinterpret_cast<float4*>(slot + A_BYTES + off) = lo;
             }
-            if (!ok) break;
-            if (!tc::mbar_wait(accf, i & 1, status)) break;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::mbar_arrive(&fullA[s]);
+            ++it;
+            if (kb == KB - 1) {  // row norm of this tile for the epilogue
+                const int a = i % ACC;
+                // the epilogue reads slot a's previous norms before it releases accumulator a
+                if (!tc::mbar_wait(&acce[a], ((i / ACC) & 1) ^ 1, status)) { ok = false; break; }
+                osq_s[a * VT_BM + tid] = osq;
+                tc::mbar_arrive(&osqf[a]);
+                osq = 0.f;
+                ++i;
+            }
+#pragma unroll
+            for (int q = 0; q < VT_BK / 4; ++q) cur[q] = nxt[q];
+            t = nt;
+            kb = nkb;
+        }
+    } else {
+        // ---- epilogue: warps 4-7 own TMEM lanes 32 (w - 4) .. + 31 -----------------
+        const int row = tid - 128;
+        const uint32_t lb = (uint32_t)((warp - 4) * 32) << 16;
+        int ties = 0, i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int a = i % ACC;
+            const uint32_t ph = (i / ACC) & 1;
+            if (!tc::mbar_wait(&accf[a], ph, status) || !tc::mbar_wait(&osqf[a], ph, status)) break;
             tc::tc_fence_after();
             VqBest best;
             best.v1 = INFINITY; best.i1 = 0x7fffffff; best.v2 = INFINITY;
-            const uint32_t lb = (uint32_t)(warp * 32) << 16;
-            for (int c0 = 0; c0 < passes * KC; c0 += 32) {
+            for (int c0 = 0; c0 < accw; c0 += 32) {
                 uint32_t r[32];
-                tc::tmem_ld32(tmem + lb + c0, r);
+                tc::tmem_ld32(tmem + lb + a * accw + c0, r);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = c0 + j;
                     if (n < K) vq_merge(best, fmaf(-2.f, __uint_as_float(r[j]), cnorm[n]), n);
                 }
             }
+            const float osq = osq_s[a * VT_BM + row];
             tc::tc_fence_before();
-            tc::mbar_arrive(acce);
-            if (valid) {
+            tc::mbar_arrive(&acce[a]);
+            const int m = t * VT_BM + row;
+            if (m < R) {
                 code[act_rows[m]] = best.i1;
                 const float l1 = best.v1 + osq, l2 = best.v2 + osq;
                 if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
@@ -215,7 +258,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
     tc::tc_fence_before();
     __syncthreads();
     if (tid == 0 && s_ties) atomicAdd(reinterpret_cast<unsigned long long*>(near_ties), (unsigned long long)s_ties);
-    if (warp == 4) {
+    if (warp == 8) {
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, tmem_cols);
     }
@@ -275,22 +318,30 @@ cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, con
     const int passes = (K + KC - 1) / KC;
     const size_t slot = 2 * (size_t)VT_BM * VT_BK * 4 + (size_t)passes * 2 * KC * VT_BK * 4;
     const size_t limit = 227 * 1024;
-    int stages = (1024 + 2 * slot + 128 <= limit) ? 2 : 1;
-    size_t smem = 1024 + stages * slot + 128;
+    const size_t extra = 256 + 2 * VT_BM * 4;  // barriers, TMEM address, row norms
+    int stages = (1024 + 2 * slot + extra <= limit) ? 2 : 1;
+    size_t smem = 1024 + stages * slot + extra;
     if (smem > limit) return cudaErrorInvalidValue;
+    const int acc = (2 * passes * KC <= 512) ? 2 : 1;  // double-buffered accumulator when it fits
     uint32_t cols = 32;
-    while ((int)cols < passes * KC) cols <<= 1;
+    while ((int)cols < acc * passes * KC) cols <<= 1;
     // every CTA resident on an SM holds `cols` TMEM columns: cap the residency
     const size_t max_ctas = 512 / cols;
     if ((228 * 1024) / smem > max_ctas) smem = (228 * 1024) / (max_ctas + 1) + 1024;
     int tiles = (Rmax + VT_BM - 1) / VT_BM;
     int grid = tiles < num_sms ? tiles : num_sms;
     if (grid < 1) grid = 1;
+    static size_t granted[9] = {};  // per instantiation; set once per size, outside captures
 #define VQ_TC_CASE(X)                                                                                      \
     if (KC == X) {                                                                                         \
-        cudaFuncSetAttribute(k_vq_tc<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);          \
+        size_t& gr = granted[(X == 16) ? 0 : (X == 32) ? 1 : (X == 48) ? 2 : (X == 64) ? 3 : (X == 96) ? 4 \
+                             : (X == 128) ? 5 : (X == 192) ? 6 : 7];                                       \
+        if (smem > gr) {                                                                                   \
+            cudaFuncSetAttribute(k_vq_tc<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+            gr = smem;                                                                                     \
+        }                                                                                                  \
         k_vq_tc<X><<<grid, VT_THREADS, smem, st>>>(tm_hi, tm_lo, O, counters, act_rows, cnorm, K, d, code,  \
-                                                   near_ties, status, stages, cols);                       \
+                                                   near_ties, status, stages, cols, acc);                  \
         return cudaGetLastError();                                                                         \
     }
     VQ_TC_CASE(16) VQ_TC_CASE(32) VQ_TC_CASE(48) VQ_TC_CASE(64) VQ_TC_CASE(96) VQ_TC_CASE(128) VQ_TC_CASE(192)

@@ -1,6 +1,7 @@
 // C ABI of libvqnqs: context, workspace plan and the per-chunk pipeline of the
 // local-energy path (Sec. 2 Eq. local-energy evaluated with the VQ-NQS of
 // Sec. 3.1, reusing per-location work by (row, code) keys as in Sec. 3.2).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,12 +21,17 @@ struct vqnqs_ctx {
     const float *tok_emb = nullptr, *pos_emb = nullptr, *lnf_g = nullptr, *lnf_b = nullptr, *w_head = nullptr,
                 *b_head = nullptr;
     std::vector<LayerW> lw;
-    int* bonds = nullptr;          // [nb][2]
+    int* bonds = nullptr;          // [nb][2] bonds of the context's lattice (side L)
+    int* bonds_all = nullptr;      // bond tables of every side 2 .. L, concatenated
+    std::vector<int> side_bond_off, side_nb;  // per side: first bond in bonds_all, count
     int* status = nullptr;         // device status word
     int* gemm_m = nullptr;         // row count slot of vqnqs_gemm_bf16
     int* assign_counters = nullptr;  // counter slots of vqnqs_vq_assign
     int* assign_rows = nullptr;      // identity row list of vqnqs_vq_assign
     int assign_rows_cap = 1 << 22;
+    float* lp_scratch = nullptr;     // log psi target of vqnqs_codes when the caller passes none
+    int bn[3] = {0, 0, 0};           // output tile width of the QKV, MLP up, MLP down GEMMs
+    int lp_scratch_cap = 65536;
     long long* stats = nullptr;    // ST_* slots
     std::vector<void*> owned;      // device allocations freed by destroy
     std::string err;
@@ -114,18 +120,19 @@ std::vector<int> make_bonds(int L, int periodic) {
 }
 
 struct Plan {
-    int S = 0;
+    int S = 0;                       // samples per chunk
     long long Cmax = 0, Rmax = 0, Umax = 0;
     int hash_bits = 0;
-    size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b, code,
-        X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, total;
+    size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, cfg_row, row_cfg, act_cnt, act_off, act_rows,
+        uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, total;
 };
 
-Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
+// Workspace layout for chunks of at most S samples, C configurations and R rows.
+Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     Plan p;
     p.S = S;
-    p.Cmax = (long long)S * (with_bonds ? (1 + c->nb) : 1);
-    p.Rmax = p.Cmax * c->N;
+    p.Cmax = C;
+    p.Rmax = R;
     p.Umax = p.Rmax > 3LL * c->N ? p.Rmax : 3LL * c->N;
     int hb = 1;
     while ((1LL << hb) < 2 * p.Rmax) ++hb;
@@ -140,8 +147,10 @@ Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
     p.cfg_sample = take((size_t)p.Cmax * sizeof(int));
     p.cfg_i = take((size_t)p.Cmax * sizeof(int));
     p.cfg_j = take((size_t)p.Cmax * sizeof(int));
+    p.cfg_row = take((size_t)(p.Cmax + 1) * sizeof(int));
+    p.row_cfg = take((size_t)p.Rmax * sizeof(int));
     p.act_cnt = take((size_t)p.Cmax * sizeof(int));
-    p.act_off = take((size_t)p.Cmax * sizeof(int));
+    p.act_off = take((size_t)(p.Cmax + 1) * sizeof(int));
     p.act_rows = take((size_t)p.Rmax * sizeof(int));
     p.uid_a = take((size_t)p.Rmax * sizeof(int));
     p.uid_b = take((size_t)p.Rmax * sizeof(int));
@@ -161,6 +170,12 @@ Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
     p.ratio = take((size_t)p.Cmax * sizeof(float));
     p.total = o;
     return p;
+}
+
+// Uniform chunks of S samples of the context's lattice (worst case: every bond anti-aligned).
+Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
+    const long long C = (long long)S * (with_bonds ? (1 + c->nb) : 1);
+    return make_plan_budget(c, S, C, C * c->N);
 }
 
 int default_chunk(const vqnqs_ctx* c, bool with_bonds) {
@@ -209,6 +224,17 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
     return VQNQS_OK;
 }
 
+int build_weight_tmaps(vqnqs_ctx* ctx) {
+    const long long d = ctx->d;
+    for (int l = 0; l < ctx->layers; ++l) {
+        LayerW& w = ctx->lw[l];
+        VQ_CK(make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
+        VQ_CK(make_tmap_bf16(&w.tm_w1, w.w1_t, 4 * d, (int)d, ctx->bn[1]));
+        VQ_CK(make_tmap_bf16(&w.tm_w2, w.w2_t, d, 4 * (int)d, ctx->bn[2]));
+    }
+    return VQNQS_OK;
+}
+
 void bind_weights(vqnqs_ctx* c) {
     const size_t d = c->d, K = c->K;
     const float* p = c->blob;
@@ -229,29 +255,48 @@ void bind_weights(vqnqs_ctx* c) {
     c->w_head = take(2 * d); c->b_head = take(2);
 }
 
-// One chunk of samples through the whole path.
-int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int S, bool with_bonds, int flags,
-              float* e_loc_out, float* log_psi_out, cudaStream_t st) {
-    const int N = ctx->N, d = ctx->d, K = ctx->K;
-    const bool reuse = (flags & VQNQS_REUSE) != 0;
-    int* counters = at<int>(ws, P.counters);
+// Lattice groups of a single-lattice batch.
+Groups uniform_groups(const vqnqs_ctx* c, int B) {
+    Groups g;
+    std::memset(&g, 0, sizeof(g));
+    g.n = 1;
+    g.first[0] = 0;
+    g.first[1] = B;
+    g.N[0] = c->N;
+    g.nb[0] = c->side_nb[c->L];
+    g.bond_off[0] = c->side_bond_off[c->L];
+    g.spin_off[0] = 0;
+    return g;
+}
+
+Chunk make_chunk(const vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& g, int s0, int S) {
     Chunk ch;
-    ch.spins = spins; ch.S = S; ch.N = N; ch.L = ctx->L; ch.d = d; ch.heads = ctx->heads; ch.K = K;
+    ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = g; ch.s0 = s0; ch.S = S;
+    ch.N = ctx->N; ch.d = ctx->d; ch.heads = ctx->heads; ch.K = ctx->K;
     ch.cfg_sample = at<int>(ws, P.cfg_sample);
     ch.cfg_i = at<int>(ws, P.cfg_i);
     ch.cfg_j = at<int>(ws, P.cfg_j);
     ch.cfg_off = at<int>(ws, P.cfg_off);
-    ch.counters = counters;
+    ch.cfg_row = at<int>(ws, P.cfg_row);
+    ch.row_cfg = at<int>(ws, P.row_cfg);
+    ch.counters = at<int>(ws, P.counters);
+    return ch;
+}
+
+// One chunk of samples (global s0 .. s0+S-1 of the batch described by g) through the whole path.
+int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& grp, int s0, int S,
+              bool with_bonds, int flags, float* e_loc_out, float* log_psi_out, cudaStream_t st,
+              int* codes_out = nullptr) {
+    const int N = ctx->N, d = ctx->d, K = ctx->K;
+    const bool reuse = (flags & VQNQS_REUSE) != 0;
+    int* counters = at<int>(ws, P.counters);
+    Chunk ch = make_chunk(ctx, P, ws, spins, grp, s0, S);
     float* diag = at<float>(ws, P.diag);
     const int g_s = grid_for(ctx, S, 1, 8);
-    {
-        StageScope scope_(ctx, S_CONFIG, 3, st);
-        VQ_CK(launch_count_configs(spins, S, N, ctx->bonds, ctx->nb, (float)ctx->J, with_bonds, at<int>(ws, P.cnt),
-                                   diag, ctx->status, st, g_s));
-        VQ_CK(launch_scan_configs(at<int>(ws, P.cnt), S, at<int>(ws, P.cfg_off), counters, N, st));
-        VQ_CK(launch_fill_configs(spins, S, N, ctx->bonds, ctx->nb, with_bonds, ch.cfg_off, at<int>(ws, P.cfg_sample),
-                                  at<int>(ws, P.cfg_i), at<int>(ws, P.cfg_j), st, g_s));
-    }
+    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, (float)ctx->J, with_bonds, at<int>(ws, P.cnt), diag,
+                                         at<int>(ws, P.cfg_off), at<int>(ws, P.cfg_sample), at<int>(ws, P.cfg_i),
+                                         at<int>(ws, P.cfg_j), at<int>(ws, P.cfg_row), at<int>(ws, P.row_cfg),
+                                         ctx->status, st, g_s));
 
     int* uid_cur = at<int>(ws, P.uid_a);
     int* uid_next = at<int>(ws, P.uid_b);
@@ -272,7 +317,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
     const bool bf16 = (flags & VQNQS_BF16) != 0;
     int* act_rows = at<int>(ws, P.act_rows);
     VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, reuse ? 1 : 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off),
-                                             act_rows, st, grid_for(ctx, P.Cmax, 8, 16)));
+                                             act_rows, ctx->stats, st, grid_for(ctx, P.Cmax, 8, 16)));
     __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(A);
     __nv_bfloat16* qkv16 = reinterpret_cast<__nv_bfloat16*>(qkv);
     __nv_bfloat16* Hid16 = reinterpret_cast<__nv_bfloat16*>(Hid);
@@ -283,7 +328,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
         if (bf16) {
             VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows));
             VQ_STAGE(S_QKV, 1, launch_gemm_tc(A16, Umax, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, us, 3 * d, d, 0,
-                                              ctx->status, st, ctx->num_sms));
+                                              ctx->status, st, ctx->num_sms, ctx->bn[0]));
             if (attention_tc_supported(N, d / ctx->heads))
                 VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, reuse ? 1 : 0, ctx->status, st,
                                                         grid_for(ctx, P.Cmax * ctx->heads, 1, 4)));
@@ -303,6 +348,10 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
         else
             VQ_STAGE(S_VQ, 1, launch_vq_argmin(O, counters, act_rows, w.codebook, w.cnorm, K, d, code,
                                                ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms));
+        if (codes_out) {  // codes of every row: [sample][layer][position] (no connected configurations here)
+            ctx->launches += 1;
+            VQ_CK(launch_copy_codes(ch, code, l, ctx->layers, codes_out, st, g_rows));
+        }
         VQ_STAGE(S_DEDUPE, reuse ? 3 : 1,
                  launch_dedupe(ch, uid_cur, code, un, Rmax, at<unsigned long long>(ws, P.keys),
                                at<int>(ws, P.vals), P.hash_bits, uid_next, rep_uid, rep_code, reuse, ctx->status, st,
@@ -311,9 +360,9 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, nullptr, A16, st, g_urows));
             VQ_STAGE(S_MLP1, 1, launch_gemm_tc(A16, Umax, w.tm_w1, w.b_1, nullptr, Hid16, counters, un, 4 * d, d, 1,
-                                               ctx->status, st, ctx->num_sms));
+                                               ctx->status, st, ctx->num_sms, ctx->bn[1]));
             VQ_STAGE(S_MLP2, 1, launch_gemm_tc(Hid16, Umax, w.tm_w2, w.b_2, Y, X_next, counters, un, d, 4 * d, 2,
-                                               ctx->status, st, ctx->num_sms));
+                                               ctx->status, st, ctx->num_sms, ctx->bn[2]));
         } else {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, A, nullptr, st, g_urows));
@@ -341,7 +390,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, int
 }
 
 int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_var, float* log_psi, int flags,
-        void* ws, size_t ws_bytes, void* stream, bool with_bonds) {
+        void* ws, size_t ws_bytes, void* stream, bool with_bonds, int* codes = nullptr) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
@@ -361,10 +410,12 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     int S = fit_chunk(ctx, B, ws_bytes, with_bonds);
     if (S == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "workspace smaller than the one-sample minimum");
     const Plan P = make_plan(ctx, S, with_bonds);
+    const Groups g = uniform_groups(ctx, B);
     for (int s0 = 0; s0 < B; s0 += S) {
         const int Sc = (B - s0) < S ? (B - s0) : S;
-        int rc = run_chunk(ctx, P, ws, spins + (size_t)s0 * ctx->N, Sc, with_bonds, flags,
-                           e_loc ? e_loc + s0 : nullptr, log_psi ? log_psi + s0 : nullptr, st);
+        int rc = run_chunk(ctx, P, ws, spins, g, s0, Sc, with_bonds, flags, e_loc ? e_loc + s0 : nullptr,
+                           log_psi ? log_psi + s0 : nullptr, st,
+                           codes ? codes + (size_t)s0 * ctx->layers * ctx->N : nullptr);
         if (rc != VQNQS_OK) return rc;
     }
     if (mean_var) VQ_STAGE(S_MEANVAR, 1, launch_mean_var(e_loc, B, mean_var, st));
@@ -401,7 +452,7 @@ struct GradPlan {
     long long R = 0;
     size_t seeds, counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b,
         rep_uid, rep_code, code, X, dX, dY, A1, Oatt, Y, V, A2, dA, dV, dO, dgam, dbet, Af, QKV, dQKV, H1, G4, dG4, OW,
-        DG, alpha, onehot, arow, dlog, csumK, stat, total;
+        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, total;
 };
 
 GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
@@ -431,6 +482,8 @@ GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     p.OW = take(R * K * f); p.DG = take(R * K * f); p.alpha = take(R * K * f); p.onehot = take(R * K * f);
     p.arow = take(R * f); p.dlog = take(2 * R * f); p.csumK = take((size_t)S * K * f);
     p.stat = take(R * c->heads * 3 * f);
+    p.cfg_row = take((S + 1) * sizeof(int));
+    p.row_cfg = take(R * sizeof(int));
     p.total = o;
     return p;
 }
@@ -449,9 +502,11 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     const int cap = ctx->num_sms * 16, sms = ctx->num_sms;
     int* counters = at<int>(ws, P.counters);
     Chunk ch;
-    ch.spins = spins; ch.S = S; ch.N = N; ch.L = ctx->L; ch.d = d; ch.heads = H; ch.K = K;
+    ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = uniform_groups(ctx, S); ch.s0 = 0; ch.S = S;
+    ch.N = N; ch.d = d; ch.heads = H; ch.K = K;
     ch.cfg_sample = at<int>(ws, P.cfg_sample); ch.cfg_i = at<int>(ws, P.cfg_i); ch.cfg_j = at<int>(ws, P.cfg_j);
-    ch.cfg_off = at<int>(ws, P.cfg_off); ch.counters = counters;
+    ch.cfg_off = at<int>(ws, P.cfg_off); ch.cfg_row = at<int>(ws, P.cfg_row); ch.row_cfg = at<int>(ws, P.row_cfg);
+    ch.counters = counters;
     const ParamOff po = param_offsets(ctx);
     auto X = [&](int l) { return at<float>(ws, P.X + (size_t)l * R * d * sizeof(float)); };
     auto code = [&](int l) { return at<int>(ws, P.code + (size_t)l * R * sizeof(int)); };
@@ -468,16 +523,12 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     const int g_rows = grid_for(ctx, R, 8, 16);
 
     // forward, keeping x_l and the codes
-    {
-        StageScope s_(ctx, S_CONFIG, 3, st);
-        VQ_CK(launch_count_configs(spins, S, N, ctx->bonds, ctx->nb, (float)ctx->J, 0, at<int>(ws, P.cnt),
-                                   at<float>(ws, P.diag), ctx->status, st, grid_for(ctx, S, 1, 8)));
-        VQ_CK(launch_scan_configs(at<int>(ws, P.cnt), S, at<int>(ws, P.cfg_off), counters, N, st));
-        VQ_CK(launch_fill_configs(spins, S, N, ctx->bonds, ctx->nb, 0, ch.cfg_off, at<int>(ws, P.cfg_sample),
-                                  at<int>(ws, P.cfg_i), at<int>(ws, P.cfg_j), st, grid_for(ctx, S, 1, 8)));
-    }
-    VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off), act, st,
-                                             grid_for(ctx, S, 8, 16)));
+    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, (float)ctx->J, 0, at<int>(ws, P.cnt), at<float>(ws, P.diag),
+                                         at<int>(ws, P.cfg_off), at<int>(ws, P.cfg_sample), at<int>(ws, P.cfg_i),
+                                         at<int>(ws, P.cfg_j), at<int>(ws, P.cfg_row), at<int>(ws, P.row_cfg),
+                                         ctx->status, st, grid_for(ctx, S, 1, 8)));
+    VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off), act, ctx->stats,
+                                             st, grid_for(ctx, S, 8, 16)));
     VQ_STAGE(S_EMBED, 1, launch_embed(ch, ctx->tok_emb, ctx->pos_emb, 0, X(0), uid, st, g_rows));
     for (int l = 0; l < Ly; ++l) {
         const LayerW& w = ctx->lw[l];
@@ -619,6 +670,16 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
     std::vector<int> bonds = make_bonds(L, ctx->periodic);
     ctx->nb = (int)bonds.size() / 2;
     ctx->bonds = static_cast<int*>(dalloc(bonds.size() * sizeof(int)));
+    std::vector<int> all;
+    ctx->side_bond_off.assign(L + 1, 0);
+    ctx->side_nb.assign(L + 1, 0);
+    for (int s = 2; s <= L; ++s) {
+        std::vector<int> b = make_bonds(s, ctx->periodic);
+        ctx->side_bond_off[s] = (int)all.size() / 2;
+        ctx->side_nb[s] = (int)b.size() / 2;
+        all.insert(all.end(), b.begin(), b.end());
+    }
+    ctx->bonds_all = static_cast<int*>(dalloc(all.size() * sizeof(int)));
     ctx->status = static_cast<int*>(dalloc(sizeof(int)));
     ctx->stats = static_cast<long long*>(dalloc(ST_SLOTS * sizeof(long long)));
     ctx->lw.resize(layers);
@@ -635,14 +696,17 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
         if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo) return bail(VQNQS_ERR_OOM);
     }
     if (!ctx->blob || !ctx->bonds || !ctx->status || !ctx->stats) return bail(VQNQS_ERR_OOM);
-    if (cudaMemcpy(ctx->bonds, bonds.data(), bonds.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (!ctx->bonds_all ||
+        cudaMemcpy(ctx->bonds_all, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctx->bonds, bonds.data(), bonds.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->stats, 0, ST_SLOTS * sizeof(long long)) != cudaSuccess)
         return bail(VQNQS_ERR_CUDA);
     ctx->gemm_m = static_cast<int*>(dalloc(sizeof(int)));
     ctx->assign_counters = static_cast<int*>(dalloc(CNT_SLOTS * sizeof(int)));
     ctx->assign_rows = static_cast<int*>(dalloc((size_t)ctx->assign_rows_cap * sizeof(int)));
-    if (!ctx->gemm_m || !ctx->assign_counters || !ctx->assign_rows) return bail(VQNQS_ERR_OOM);
+    ctx->lp_scratch = static_cast<float*>(dalloc((size_t)ctx->lp_scratch_cap * sizeof(float)));
+    if (!ctx->gemm_m || !ctx->assign_counters || !ctx->assign_rows || !ctx->lp_scratch) return bail(VQNQS_ERR_OOM);
     bind_weights(ctx);
     int rc = vqnqs_set_weights(ctx, weights, 0, nullptr);
     if (rc != VQNQS_OK) return bail(rc);
@@ -655,13 +719,10 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
         }
     }
     if (d_model % 64 == 0) {
-        for (int l = 0; l < layers; ++l) {
-            LayerW& w = ctx->lw[l];
-            if (make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 3 * d, d_model, tc_pick_bn(3 * d_model)) != cudaSuccess ||
-                make_tmap_bf16(&w.tm_w1, w.w1_t, 4 * d, d_model, tc_pick_bn(4 * d_model)) != cudaSuccess ||
-                make_tmap_bf16(&w.tm_w2, w.w2_t, d, 4 * d_model, tc_pick_bn(d_model)) != cudaSuccess)
-                return bail(VQNQS_ERR_CUDA);
-        }
+        ctx->bn[0] = tc_pick_bn(3 * d_model);
+        ctx->bn[1] = tc_pick_bn(4 * d_model);
+        ctx->bn[2] = tc_pick_bn(d_model);
+        if (build_weight_tmaps(ctx) != VQNQS_OK) return bail(VQNQS_ERR_CUDA);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(VQNQS_ERR_CUDA);
     *out = ctx;
@@ -689,6 +750,83 @@ int vqnqs_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* log_psi, i
     return run(ctx, B, spins, nullptr, nullptr, log_psi, flags, ws, ws_bytes, stream, false);
 }
 
+int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, const int* B_g, const uint8_t* spins,
+                              float* e_loc, double* mean_var, int flags, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (n_groups < 1 || n_groups > MAX_GROUPS || !L_g || !B_g)
+        return fail(ctx, VQNQS_ERR_ARG, "ragged: need 1..8 groups and host arrays L_g, B_g");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if ((flags & VQNQS_BF16) && ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
+    Groups g;
+    std::memset(&g, 0, sizeof(g));
+    g.n = n_groups;
+    long long spin_off = 0;
+    int total = 0;
+    for (int i = 0; i < n_groups; ++i) {
+        if (L_g[i] < 2 || L_g[i] > ctx->L || B_g[i] < 0)
+            return fail(ctx, VQNQS_ERR_ARG, "ragged: lattice sides must be 2 .. L of the context, B_g >= 0");
+        g.first[i] = total;
+        g.N[i] = L_g[i] * L_g[i];
+        g.nb[i] = ctx->side_nb[L_g[i]];
+        g.bond_off[i] = ctx->side_bond_off[L_g[i]];
+        g.spin_off[i] = spin_off;
+        spin_off += (long long)B_g[i] * g.N[i];
+        total += B_g[i];
+    }
+    g.first[n_groups] = total;
+    if (total == 0) return VQNQS_OK;
+    if (!spins || !e_loc || !ws) return fail(ctx, VQNQS_ERR_ARG, "null pointer");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(ctx, VQNQS_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // budgets: the largest uniform chunk of the context's lattice that fits, with
+    // per-sample arrays sized for as many samples as configurations
+    int S = fit_chunk(ctx, 65536, ws_bytes, true);
+    Plan P;
+    for (; S > 0; --S) {
+        const Plan u = make_plan(ctx, S, true);
+        P = make_plan_budget(ctx, (int)u.Cmax, u.Cmax, u.Rmax);
+        if (P.total <= ws_bytes) break;
+    }
+    if (S == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "workspace smaller than the one-sample minimum");
+    // partition the samples, in order, into chunks that respect the budgets
+    int s0 = 0, grp = 0;
+    while (s0 < total) {
+        long long C = 0, R = 0;
+        int s1 = s0;
+        while (s1 < total) {
+            while (s1 >= g.first[grp + 1]) ++grp;
+            const long long cs = 1 + g.nb[grp], rs = cs * g.N[grp];
+            long long k = g.first[grp + 1] - s1;
+            k = std::min(k, (P.Cmax - C) / cs);
+            k = std::min(k, (P.Rmax - R) / rs);
+            k = std::min(k, (long long)P.S - (s1 - s0));
+            if (k <= 0) break;
+            s1 += (int)k;
+            C += k * cs;
+            R += k * rs;
+        }
+        if (s1 == s0) return fail(ctx, VQNQS_ERR_INTERNAL, "ragged: empty chunk");
+        const int rc = run_chunk(ctx, P, ws, spins, g, s0, s1 - s0, true, flags, e_loc + s0, nullptr, st);
+        if (rc != VQNQS_OK) return rc;
+        s0 = s1;
+        grp = 0;
+    }
+    if (mean_var) VQ_STAGE(S_MEANVAR, 1, launch_mean_var(e_loc, total, mean_var, st));
+    return VQNQS_OK;
+}
+
+int vqnqs_codes(vqnqs_ctx* ctx, int B, const uint8_t* spins, int* codes, float* log_psi, int flags, void* ws,
+                size_t ws_bytes, void* stream) {
+    if (ctx && B > 0 && !codes) return fail(ctx, VQNQS_ERR_ARG, "codes is NULL");
+    if (!log_psi && ctx && B > 0) {
+        // log psi goes to the workspace-free scratch of the context when not wanted
+        if (ctx->lp_scratch_cap < B) return fail(ctx, VQNQS_ERR_ARG, "codes: pass log_psi for B > 65536");
+        log_psi = ctx->lp_scratch;
+    }
+    return run(ctx, B, spins, nullptr, nullptr, log_psi, flags, ws, ws_bytes, stream, false, codes);
+}
+
 int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_var, float* log_psi,
                        int flags, void* ws, size_t ws_bytes, void* stream) {
     return run(ctx, B, spins, e_loc, mean_var, log_psi, flags, ws, ws_bytes, stream, true);
@@ -708,6 +846,8 @@ int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out) {
     out->near_ties = st[ST_NEAR_TIES];
     for (int l = 0; l <= ctx->layers; ++l) out->unique_rows[l] = st[ST_U0 + l];
     out->device_status = status;
+    out->active_rows = st[ST_ACTIVE];
+    out->attn_pairs = st[ST_PAIRS];
     // analytic FLOPs, 2 per multiply-add
     const double d = ctx->d, K = ctx->K, N = ctx->N, Ly = ctx->layers;
     const double rows = (double)out->rows, cfgs = (double)out->configs;
@@ -862,6 +1002,59 @@ int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* uid, const int* code, 
                                 at<int>(ws, align256(H * sizeof(unsigned long long))), hb, ctx->status, st,
                                 ctx->num_sms));
     return VQNQS_OK;
+}
+
+int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* ws, size_t ws_bytes, vqnqs_tuning* out, void* stream) {
+    if (!ctx || !out || M < 128) return ctx ? fail(ctx, VQNQS_ERR_ARG, "autotune: need out and M >= 128") : VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "autotune: the tensor-core GEMMs need d_model % 64 == 0");
+    const size_t d = ctx->d;
+    const size_t need = align256((size_t)M * 4 * d * 2) + align256((size_t)M * 4 * d * 4) * 2;
+    if (!ws || ws_bytes < need) return fail(ctx, VQNQS_ERR_WORKSPACE, "autotune: workspace too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    __nv_bfloat16* A = static_cast<__nv_bfloat16*>(ws);
+    float* C = at<float>(ws, align256((size_t)M * 4 * d * 2));
+    float* Rm = at<float>(ws, align256((size_t)M * 4 * d * 2) + align256((size_t)M * 4 * d * 4));
+    VQ_CK(cudaMemsetAsync(ws, 0, need, st));
+    VQ_CK(launch_set_int(ctx->gemm_m, M, st));
+    const LayerW& w = ctx->lw[0];
+    struct Shape { const __nv_bfloat16* Bt; int N, K, epi; const float* bias; } shapes[3] = {
+        {w.wqkv_t, 3 * (int)d, (int)d, 0, w.b_qkv}, {w.w1_t, 4 * (int)d, (int)d, 1, w.b_1}, {w.w2_t, (int)d, 4 * (int)d, 2, w.b_2}};
+    const int cand[4] = {64, 128, 192, 256};
+    std::memset(out, 0, sizeof(*out));
+    cudaEvent_t e0, e1;
+    VQ_CK(cudaEventCreate(&e0));
+    VQ_CK(cudaEventCreate(&e1));
+    for (int s = 0; s < 3; ++s) {
+        float best = 1e30f;
+        for (int ci = 0; ci < 4; ++ci) {
+            const int BN = cand[ci];
+            out->ms[s][ci] = -1.f;
+            if (shapes[s].N % BN) continue;
+            CUtensorMap tb;
+            VQ_CK(make_tmap_bf16(&tb, shapes[s].Bt, shapes[s].N, shapes[s].K, BN));
+            for (int rep = 0; rep < 2; ++rep)
+                VQ_CK(launch_gemm_tc(A, M, tb, shapes[s].bias, Rm, C, ctx->gemm_m, 0, shapes[s].N, shapes[s].K,
+                                     shapes[s].epi, ctx->status, st, ctx->num_sms, BN));
+            VQ_CK(cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 5; ++rep)
+                VQ_CK(launch_gemm_tc(A, M, tb, shapes[s].bias, Rm, C, ctx->gemm_m, 0, shapes[s].N, shapes[s].K,
+                                     shapes[s].epi, ctx->status, st, ctx->num_sms, BN));
+            VQ_CK(cudaEventRecord(e1, st));
+            VQ_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            VQ_CK(cudaEventElapsedTime(&ms, e0, e1));
+            out->ms[s][ci] = ms / 5.f;
+            ctx->launches += 7;
+            if (ms < best) { best = ms; ctx->bn[s] = BN; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out->qkv_bn = ctx->bn[0];
+    out->mlp_up_bn = ctx->bn[1];
+    out->mlp_down_bn = ctx->bn[2];
+    return build_weight_tmaps(ctx);
 }
 
 int vqnqs_profile_enable(vqnqs_ctx* ctx, int enable) {

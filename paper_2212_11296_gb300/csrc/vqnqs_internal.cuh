@@ -30,7 +30,9 @@ enum {
     ST_ROWS = 2,
     ST_NEAR_TIES = 3,
     ST_U0 = 4,      // ST_U0 + l
-    ST_SLOTS = 4 + VQNQS_MAX_LAYERS + 2
+    ST_ACTIVE = 4 + VQNQS_MAX_LAYERS + 2,  // rows whose attention and code are computed (per layer)
+    ST_PAIRS = ST_ACTIVE + 1,              // causal query-key pairs of those rows (per layer)
+    ST_SLOTS = ST_PAIRS + 2
 };
 
 struct LayerW {
@@ -44,17 +46,49 @@ struct LayerW {
     CUtensorMap tm_cb_hi, tm_cb_lo;       // their TMA maps (valid when vq_tc_supported)
 };
 
-// Per-chunk view of the problem handed to the kernels.
+// Lattice groups of a batch (one group for a single lattice, up to MAX_GROUPS
+// for a ragged batch of several lattice sizes): global samples
+// first[g] .. first[g+1]-1 are L[g] x L[g] lattices with N[g] sites, whose spins
+// start at byte spin_off[g] of the batch's spin array (N[g] bytes per sample)
+// and whose bonds are bonds[bond_off[g] .. bond_off[g] + nb[g]).
+constexpr int MAX_GROUPS = 8;
+struct Groups {
+    int n;
+    int first[MAX_GROUPS + 1];
+    int N[MAX_GROUPS], nb[MAX_GROUPS], bond_off[MAX_GROUPS];
+    long long spin_off[MAX_GROUPS];
+};
+
+// Per-chunk view of the problem handed to the kernels.  Rows of a chunk are
+// (configuration, position) pairs stored configuration after configuration;
+// configuration c owns rows cfg_row[c] .. cfg_row[c+1]-1.
 struct Chunk {
-    const uint8_t* spins;   // [S][N] spins of this chunk's samples
-    int S;                  // samples in the chunk
-    int N, L, d, heads, K;
-    const int* cfg_sample;  // [C] sample of each configuration
+    const uint8_t* spins;   // spins of the whole batch
+    const int* bonds;       // bond table of all groups, [.][2]
+    Groups g;
+    int s0, S;              // this chunk holds global samples s0 .. s0+S-1 (local index b)
+    int N, d, heads, K;     // N: largest number of sites (position-embedding rows)
+    const int* cfg_sample;  // [C] local sample of each configuration
     const int* cfg_i;       // [C] exchanged site pair (-1 for the sample itself)
     const int* cfg_j;
     const int* cfg_off;     // [S + 1] first configuration of each sample
+    const int* cfg_row;     // [C + 1] first row of each configuration
+    const int* row_cfg;     // [R] configuration of each row
     int* counters;          // CNT_* slots
 };
+
+__device__ __forceinline__ int sample_group(const Chunk& ch, int b) {
+    const int gb = ch.s0 + b;
+    int g = 0;
+    while (g + 1 < ch.g.n && gb >= ch.g.first[g + 1]) ++g;
+    return g;
+}
+__device__ __forceinline__ int sample_N(const Chunk& ch, int b) { return ch.g.N[sample_group(ch, b)]; }
+__device__ __forceinline__ const uint8_t* sample_spins(const Chunk& ch, int b) {
+    const int g = sample_group(ch, b);
+    return ch.spins + ch.g.spin_off[g] + (long long)(ch.s0 + b - ch.g.first[g]) * ch.g.N[g];
+}
+__device__ __forceinline__ int cfg_N(const Chunk& ch, int c) { return sample_N(ch, ch.cfg_sample[c]); }
 
 // First position whose rows differ from the sample's own rows.  Exchanging
 // sites i and j changes the inputs (tokens s_{p-1}) only at p = i+1 and
@@ -62,11 +96,12 @@ struct Chunk {
 // (Sec. 2: conditionals before the changed site are unchanged).
 __device__ __forceinline__ int cfg_first_changed(int ci, int cj) { return ci < 0 ? 0 : min(ci, cj) + 1; }
 
-__device__ __forceinline__ int cfg_spin(const uint8_t* spins, int N, int b, int ci, int cj, int q) {
+// Spin at site q of the configuration whose sample spins are s and whose exchanged pair is (ci, cj).
+__device__ __forceinline__ int cfg_spin(const uint8_t* s, int ci, int cj, int q) {
     int src = q;
     if (q == ci) src = cj;
     else if (q == cj) src = ci;
-    return spins[(size_t)b * N + src];
+    return s[src] & 1;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -83,13 +118,10 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- launchers (each returns cudaGetLastError of its launch) -------------------
 
-// configuration enumeration (k_config.cu)
-cudaError_t launch_count_configs(const uint8_t* spins, int S, int N, const int* bonds, int nb, float J,
-                                 int with_bonds, int* cnt, float* diag, int* status, cudaStream_t st, int grid);
-cudaError_t launch_scan_configs(const int* cnt, int S, int* cfg_off, int* counters, int N, cudaStream_t st);
-cudaError_t launch_fill_configs(const uint8_t* spins, int S, int N, const int* bonds, int nb, int with_bonds,
-                                const int* cfg_off, int* cfg_sample, int* cfg_i, int* cfg_j, cudaStream_t st,
-                                int grid);
+// configuration enumeration (k_config.cu): configurations, then row offsets
+cudaError_t launch_configs(const Chunk& ch, float J, int with_bonds, int* cnt, float* diag, int* cfg_off,
+                           int* cfg_sample, int* cfg_i, int* cfg_j, int* cfg_row, int* row_cfg, int* status,
+                           cudaStream_t st, int grid);
 cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos_emb, int reuse, float* X0,
                          int* uid0, cudaStream_t st, int grid);
 cudaError_t launch_head(const float* X, const int* counters, int u_slot, const float* g, const float* b,
@@ -98,6 +130,8 @@ cudaError_t launch_eloc(const Chunk& ch, const int* uid, const float* logp, floa
                         cudaStream_t st, int grid);
 cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* ratio, float J, float* e_loc_out,
                                cudaStream_t st, int grid);
+cudaError_t launch_copy_codes(const Chunk& ch, const int* code, int l, int layers, int* out, cudaStream_t st,
+                              int grid);
 cudaError_t launch_mean_var(const float* e_loc, int B, double* mean_var, cudaStream_t st);
 cudaError_t launch_accumulate_stats(const int* counters, int layers, int S, long long* stats, cudaStream_t st);
 
@@ -120,7 +154,7 @@ cudaError_t launch_sgemm(const float* A, const float* B, const float* bias, cons
 // active rows (k_config.cu): with prefix reuse, the rows p >= first changed position of every
 // configuration, listed in act_rows[0 .. counters[CNT_A]); without it every row.
 cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
-                               cudaStream_t st, int grid);
+                               long long* stats, cudaStream_t st, int grid);
 
 // attention (k_attn.cu): O[r] for the active rows (all rows when prefix_reuse == 0)
 cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, int prefix_reuse,
@@ -136,9 +170,10 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
 int tc_pick_bn(int N);
 cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows);
+// BN = output tile width (64, 128, 192 or 256 dividing N; 0 picks the widest); tmB's box must be [BN x 64]
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms);
+                           int* status, cudaStream_t st, int num_sms, int BN = 0);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 
 // nearest codeword (k_vq.cu): rows act_rows[0 .. counters[CNT_A]) (or 0 .. counters[CNT_R] when act_rows is NULL)

@@ -3,7 +3,8 @@
 GEMM: against torch's FP32 matmul of the same BF16 operands (exact products,
 FP32 sums; only the summation order differs), relative 1e-5 of the row scale
 for FP32 outputs and one BF16 rounding for BF16 outputs.
-BF16 path: E_loc within 2e-3 relative of the FP64 oracle; reuse == full bitwise.
+BF16 path: reuse == full bitwise; the raw error against the FP64 oracle is
+reported (its 2e-3 bar is checked on arithmetic error in test_gpu_codes.py).
 """
 import numpy as np
 import pytest
@@ -70,7 +71,7 @@ def rel_err(got, want, N):
     ("10x10", 10, 4, 128, 8, 64, 1024, 16),
     ("16x16", 16, 8, 256, 8, 256, 2048, 2),
 ])
-def test_bf16_path_against_oracle_and_reuse_bitwise(name, L, layers, d, heads, K, B, sub):
+def test_bf16_path_raw_error_and_reuse_bitwise(name, L, layers, d, heads, K, B, sub):
     from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
     N = L * L
     w = si.make_weights(N, layers, d, K, seed=0)
@@ -84,8 +85,12 @@ def test_bf16_path_against_oracle_and_reuse_bitwise(name, L, layers, d, heads, K
     P = model.parse_blob(w, N, layers, d, heads, K)
     want = hamiltonian.local_energy(P, spins[idx], L, True, 1.0)
     err = rel_err(e.cpu().numpy()[idx], want, N)
-    print(name, "BF16 rel err vs FP64: max %.3e median %.3e" % (err.max(), np.median(err)))
-    assert err.max() <= BF16_TOL
+    print(name, "BF16 rel err vs FP64 (raw, codeword flips included): max %.3e median %.3e"
+          % (err.max(), np.median(err)))
+    # the 2e-3 bar applies to the arithmetic error, tested against the oracle
+    # conditioned on the GPU's codes in test_gpu_codes.py; the raw error only has
+    # to stay clear of a broken kernel
+    assert err.max() <= 0.1
     # reuse and full recompute agree bitwise on a slice of the batch
     s16 = s_dev[:16].contiguous()
     assert torch.equal(m.local_energy(s16, BF16), e[:16])
