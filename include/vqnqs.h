@@ -220,6 +220,24 @@ int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* dev_uid, const int* de
                         int* dev_rep_uid, int* dev_rep_code, int* dev_count, void* dev_ws, size_t ws_bytes,
                         void* stream);
 
+/* vqnqs_compress_rows for callers that cannot allocate device memory (for
+ * example code running while a stream is captured into a CUDA graph, or a
+ * host application that owns all device memory): same inputs, outputs and
+ * result as vqnqs_compress_rows, but no context and no workspace.  Its hash
+ * table is a file-scope device array of 6 MiB that every GPU loading the
+ * library keeps until exit.  (Not a step of the paper; it has no counterpart
+ * there.)
+ *   R  0 .. VQNQS_NOALLOC_MAX_ROWS, else VQNQS_ERR_ARG
+ * Allocates nothing (no cudaMalloc, no allocating library call).  The first
+ * call on a device looks up the array's address with cudaGetSymbolAddress
+ * (VQNQS_ERR_CUDA if that fails): make it before any stream capture.  All
+ * calls on a device share the array; each call clears what it uses first, but
+ * calls whose kernels overlap on the GPU race and give wrong results.
+ * Asynchronous on `stream`. */
+#define VQNQS_NOALLOC_MAX_ROWS (1 << 18)
+int vqnqs_compress_rows_noalloc(int R, const int* dev_uid, const int* dev_code, int* dev_new_id,
+                                int* dev_rep_uid, int* dev_rep_code, int* dev_count, void* stream);
+
 /* Autotuner of the per-location tensor-core GEMMs: for each of the QKV, MLP up and
  * MLP down steps it times every output tile width (64, 128, 192, 256 columns)
  * that divides the step's output width on M rows (M >= 128, e.g. the typical

@@ -18,6 +18,7 @@ REUSE = 1
 BF16 = 2
 DEV_BAD_SPIN, DEV_HASH_OVERFLOW, DEV_TIMEOUT = 1, 2, 4
 MAX_LAYERS = 64
+NOALLOC_MAX_ROWS = 1 << 18
 
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_WORKSPACE", 5: "ERR_TIMEOUT",
                 6: "ERR_INTERNAL"}
@@ -79,6 +80,7 @@ SIGNATURES = [
      [ctypes.c_size_t, ctypes.c_void_p]),
     ("vqnqs_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(Tuning), ctypes.c_void_p]),
+    ("vqnqs_compress_rows_noalloc", ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 7),
     ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     ("vqnqs_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("vqnqs_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
