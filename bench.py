@@ -57,9 +57,10 @@ def measured_peaks() -> dict:
     """The measured peaks of this GPU pool, else the documented fallback."""
     try:
         m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return {"bf16_tflops": float(m["bf16_tflops_sustained"]), "hbm_gbs": float(m["hbm_gbs"]), "src": "measured"}
+        return {"bf16_tflops": float(m["bf16_tflops_sustained"]), "bf16_tflops_burst": float(m["bf16_tflops"]),
+                "hbm_gbs": float(m["hbm_gbs"]), "src": "measured"}
     except (OSError, ValueError, KeyError):
-        return {"bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "src": "fallback"}
+        return {"bf16_tflops": 1700.0, "bf16_tflops_burst": 1900.0, "hbm_gbs": 6800.0, "src": "fallback"}
 
 
 def stage_flops(stage: str, st: dict, w: dict, bf16: bool) -> tuple[float, str]:
@@ -222,6 +223,7 @@ def main():
     ap.add_argument("--flags", default="reuse,bf16", help="comma list of reuse,bf16 for the timed path")
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -306,6 +308,27 @@ def main():
     e2e_value = B * world * args.steps / (e2e_ms / 1e3)
     e_gpu = h_out.numpy().astype(np.float64)
 
+    # the same step replayed from one CUDA graph (launch overhead removed)
+    graph_value = None
+    if not args.no_graph:
+        from paper_2212_11296_gb300 import LocalEnergyGraph
+        g = LocalEnergyGraph(m, [(L, B)], flags)
+        for _ in range(2):
+            g(spins)
+        barrier()
+        g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            g_ev[k][0].record(stream)
+            g(spins)
+            g_ev[k][1].record(stream)
+        barrier()
+        g_ms = reduce_max(sum(a.elapsed_time(b) for a, b in g_ev), dist if world > 1 else None)
+        graph_value = B * world * args.steps / (g_ms / 1e3)
+        if not torch.equal(g.out, out):
+            raise RuntimeError("graph replay differs from the eager step")
+        del g
+
     # the plain full-recompute FP32 path on a subset of the same samples
     n_plain = min(64, B)
     sub = spins[:n_plain].contiguous()
@@ -318,6 +341,34 @@ def main():
     b.record(stream)
     torch.cuda.synchronize()
     plain_value = n_plain / (a.elapsed_time(b) / 1e3)
+
+    # the three per-location tensor-core GEMM shapes on a large M (the reuse
+    # path only feeds them the few unique rows), each with its fused epilogue
+    gemm = None
+    if flags & BF16:
+        pk = measured_peaks()
+        dm = w["d_model"]
+        Mg = 131072
+        gemm = {"M": Mg, "peak_tflops": pk["bf16_tflops_burst"], "peak_source": f"bf16 dense, burst ({pk['src']})",
+                "shapes": {}}
+        for name, Ng, Kg, epi in (("qkv_bias_bf16", 3 * dm, dm, 0), ("mlp_up_bias_gelu_bf16", 4 * dm, dm, 1),
+                                  ("mlp_down_bias_residual_f32", dm, 4 * dm, 2)):
+            A = torch.randn(Mg, Kg, device="cuda").to(torch.bfloat16)
+            Bt = (0.05 * torch.randn(Ng, Kg, device="cuda")).to(torch.bfloat16)
+            bias = torch.zeros(Ng, device="cuda")
+            Rg = torch.zeros(Mg, Ng, device="cuda") if epi == 2 else None
+            Cg = torch.empty(Mg, Ng, dtype=torch.bfloat16 if epi < 2 else torch.float32, device="cuda")
+            for _ in range(3):
+                m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(20):
+                m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            tf = 2.0 * Mg * Ng * Kg * 20 / (a0.elapsed_time(a1) / 1e3) / 1e12
+            gemm["shapes"][name] = {"N": Ng, "K": Kg, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"]}
+            del A, Bt, Rg, Cg
 
     # roofline of the dominant stage, from the live CUDA-event stage times
     per_step = {k: v for k, v in prof.items() if v[1] > 0}
@@ -351,12 +402,14 @@ def main():
                 "d2h_bytes_per_step": int(B * 4)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "graph_replay": {"value": graph_value, "unit": UNIT} if graph_value else None,
         "plain_fp32": {"value": plain_value, "unit": UNIT, "samples": n_plain},
         "speedup_vs_plain_fp32": value / plain_value,
         "unique_row_fraction": [u / max(1, st["rows"]) for u in st["unique_rows"]],
         "flop_reduction": st["flops_full"] / max(1.0, st["flops_done"]),
         "near_ties_per_row": st["near_ties"] / max(1, st["rows"] * w["layers"]),
         "device_status": st["device_status"],
+        "gemm_tc": gemm,
         "stages": stages,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -254,6 +254,13 @@ int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* dev_ws, size_t ws_bytes, vqnqs_t
 /* Snapshot of the counters; synchronises the device first. */
 int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out);
 
+/* Failure-path check: launches a kernel whose bounded wait on an mbarrier that
+ * nothing arrives on gives up after about limit_cycles SM cycles (1 .. 4e9) and
+ * sets VQNQS_DEV_TIMEOUT in the device status word, the same path every
+ * tensor-core kernel takes when a pipeline stalls.  The context stays usable.
+ * Asynchronous on `stream`; read the bit with vqnqs_get_stats. */
+int vqnqs_check_timeout_path(vqnqs_ctx* ctx, long long limit_cycles, void* stream);
+
 /* Zero the counters and the device status word. */
 int vqnqs_reset_stats(vqnqs_ctx* ctx);
 

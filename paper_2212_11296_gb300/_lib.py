@@ -81,6 +81,7 @@ SIGNATURES = [
     ("vqnqs_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(Tuning), ctypes.c_void_p]),
     ("vqnqs_compress_rows_noalloc", ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 7),
+    ("vqnqs_check_timeout_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     ("vqnqs_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("vqnqs_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),

@@ -185,6 +185,11 @@ class VQNQS:
             "device_status": s.device_status, "active_rows": s.active_rows, "attn_pairs": s.attn_pairs,
         }
 
+    def check_timeout_path(self, limit_cycles: int = 1_000_000, stream=None):
+        """Run the bounded-wait failure probe (see vqnqs_check_timeout_path)."""
+        self._check(lib().vqnqs_check_timeout_path(self._h, int(limit_cycles), ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_check_timeout_path")
+
     def reset_stats(self):
         self._check(lib().vqnqs_reset_stats(self._h), "vqnqs_reset_stats")
 

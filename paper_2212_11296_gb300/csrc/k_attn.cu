@@ -20,18 +20,24 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
     return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
 
+// cfg_list (optional): the configurations to process, n_list of them (all
+// configurations of the chunk when NULL).  stats (optional): the softmax
+// maximum of the scaled scores and the sum of exp(score - maximum) of every
+// computed (row, head), at [(sample * N + p) * heads + head].
 template <int DH, typename T>
 __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* __restrict__ qkv,
-                                float* __restrict__ O, int prefix_reuse) {
+                                float* __restrict__ O, int prefix_reuse, const int* __restrict__ cfg_list,
+                                int n_list, float2* __restrict__ stats) {
     extern __shared__ __align__(16) float s_kv[];  // [N][DH] keys then [N][DH] values
     const int d = ch.d, H = ch.heads;
-    const int C = ch.counters[CNT_C];
+    const int C = cfg_list ? n_list : ch.counters[CNT_C];
     const float scale = rsqrtf((float)DH);
     float* sK = s_kv;
     float* sV = s_kv + (size_t)ch.N * DH;
     const int ld = 3 * d;
     for (int item = blockIdx.x; item < C * H; item += gridDim.x) {
-        const int c = item / H, h = item - c * H;
+        const int ci = item / H, h = item - ci * H;
+        const int c = cfg_list ? cfg_list[ci] : ci;
         const int N = cfg_N(ch, c);
         const int* urow = uid + ch.cfg_row[c];
         for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
@@ -105,6 +111,7 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* 
             m = mn;
         }
         if (active) {
+            if (stats) stats[((size_t)ch.cfg_sample[c] * ch.N + p) * H + h] = make_float2(m, l);
             const float inv = 1.f / l;
             float* dst = O + ((size_t)ch.cfg_row[c] + p) * d + h * DH;
 #pragma unroll
@@ -127,7 +134,7 @@ size_t set_attr_once(size_t v) {
 
 template <typename T>
 cudaError_t launch_attention_t(const Chunk& ch, const int* uid, const T* qkv, float* O, int prefix_reuse,
-                               cudaStream_t st, int grid) {
+                               cudaStream_t st, int grid, const int* cfg_list, int n_list, float2* stats) {
     const int DH = ch.d / ch.heads;
     const int threads = ((ch.N + 31) / 32) * 32;
     const size_t smem = (size_t)2 * ch.N * DH * sizeof(float);
@@ -139,7 +146,7 @@ cudaError_t launch_attention_t(const Chunk& ch, const int* uid, const T* qkv, fl
             cudaFuncSetAttribute(k_attention_f32<X, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
             set_attr_once<X, T>(smem);                                                                        \
         }                                                                                                     \
-        k_attention_f32<X, T><<<grid, threads, smem, st>>>(ch, uid, qkv, O, prefix_reuse);                                  \
+        k_attention_f32<X, T><<<grid, threads, smem, st>>>(ch, uid, qkv, O, prefix_reuse, cfg_list, n_list, stats); \
         break;
         VQ_ATT_CASE(8)
         VQ_ATT_CASE(16)
@@ -151,13 +158,14 @@ cudaError_t launch_attention_t(const Chunk& ch, const int* uid, const T* qkv, fl
 }
 
 cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, int prefix_reuse,
-                                 cudaStream_t st, int grid) {
-    return launch_attention_t<float>(ch, uid, qkv, O, prefix_reuse, st, grid);
+                                 cudaStream_t st, int grid, const int* cfg_list, int n_list, float2* stats) {
+    return launch_attention_t<float>(ch, uid, qkv, O, prefix_reuse, st, grid, cfg_list, n_list, stats);
 }
 
 cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                                   int prefix_reuse, cudaStream_t st, int grid) {
-    return launch_attention_t<__nv_bfloat16>(ch, uid, qkv, O, prefix_reuse, st, grid);
+                                   int prefix_reuse, cudaStream_t st, int grid, const int* cfg_list, int n_list,
+                                   float2* stats) {
+    return launch_attention_t<__nv_bfloat16>(ch, uid, qkv, O, prefix_reuse, st, grid, cfg_list, n_list, stats);
 }
 
 }  // namespace vq

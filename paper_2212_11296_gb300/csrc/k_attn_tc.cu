@@ -11,11 +11,12 @@
 //      tcgen05.mma (M = 128, N = keys, K = dh) into TMEM;
 //   3. two threads own each query row (alternate 32-column chunks of its TMEM
 //      lane): two passes (causal max, then exp2 / sum) combined through shared
-//      memory, writing P as BF16 into shared memory;
+//      memory, writing P as BF16 into shared memory; chunks wholly left of the
+//      diagonal take a compare-free path, chunks right of it are skipped;
 //   4. thread 0 issues O = P V (M = 128, N = dh, K = keys) into TMEM columns
 //      already read; each thread scales half of its row by 1/sum and stores it.
-// With prefix reuse, query tiles wholly before the configuration's first
-// changed position are skipped and rows before it are not stored.
+// With prefix reuse, query tiles start at the configuration's first changed
+// position: rows before it are neither computed nor stored.
 // Waits on the MMA barrier are bounded (VQNQS_DEV_TIMEOUT on expiry).
 #include <algorithm>
 
@@ -59,6 +60,14 @@ __device__ __forceinline__ void stsm_x4(uint32_t addr, const uint32_t (&r)[4]) {
                  : "memory");
 }
 
+// 2^x with the SFU's approximate exponential (flushes denormals); the softmax
+// weights it feeds are rounded to BF16 right after.
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // 16 consecutive 32-bit TMEM columns of this thread's lane
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
@@ -74,7 +83,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 template <int DH>
 __global__ void __launch_bounds__(AT_THREADS)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, float* __restrict__ O,
-               int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status) {
+               int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
+               const int* __restrict__ cfg_list, int n_list, float2* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int d = ch.d, H = ch.heads;
@@ -102,11 +112,12 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint32_t phase = 0;
     bool ok = true;
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);  // log2(e) / sqrt(dh)
-    const int C = ch.counters[CNT_C];
+    const int C = cfg_list ? n_list : ch.counters[CNT_C];
     const int ld = 3 * d;
 
     for (int item = blockIdx.x; item < C * H && ok; item += gridDim.x) {
-        const int c = item / H, h = item - c * H;
+        const int ci = item / H, h = item - ci * H;
+        const int c = cfg_list ? cfg_list[ci] : ci;
         const int N = cfg_N(ch, c);
         const int* urow = uid + ch.cfg_row[c];
         const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
@@ -143,7 +154,8 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             }
         }
         __syncthreads();
-        for (int q0 = (p0 / 128) * 128; q0 < N && ok; q0 += 128) {
+        // query tiles start at the first changed position: no row before it is computed
+        for (int q0 = p0; q0 < N && ok; q0 += 128) {
             const int nk = min(N, q0 + 128);             // keys this tile can see
             const int nk16 = (nk + 15) & ~15;            // MMA N (multiple of 16)
             const int nk32 = (nk + 31) & ~31;            // columns read back
@@ -179,41 +191,60 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             // 32-column chunk, starting with chunk `half`
             const int p = q0 + row;
             const int plim = min(p, N - 1);  // keys 0..plim are visible
+            // tcgen05.ld is warp-collective: which chunks are read is decided by the
+            // warp's last row (q0 need not be 32-aligned), the masks per row
+            const int plim_w = min(q0 + (warp & 3) * 32 + 31, N - 1);
             float mx = -INFINITY;
             for (int c0 = half * 32; c0 < nk32; c0 += 64) {
+                if (c0 > plim_w) break;  // chunks wholly past the warp's diagonal are invisible
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + lane_base + c0, r);
+                if (c0 + 31 <= plim) {
+                    float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (c0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
+                    for (int j = 2; j < 32; j += 2) {
+                        m0 = fmaxf(m0, __uint_as_float(r[j]));
+                        m1 = fmaxf(m1, __uint_as_float(r[j + 1]));
+                    }
+                    mx = fmaxf(mx, fmaxf(m0, m1));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
+                }
             }
             s_red[half][row] = mx;
             __syncthreads();
             mx = fmaxf(s_red[0][row], s_red[1][row]);
             const float mb = mx * sl2;
             float sum = 0.f;
-            for (int c0 = half * 32; c0 < nk32; c0 += 64) {
-                uint32_t r[32];
-                tc::tmem_ld32(tmem + lane_base + c0, r);
-                if (c0 < nk16) {
+            for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
+                uint32_t pk[16];
+                if (c0 > plim_w) {  // invisible chunk: P = 0 (still read by the PV MMA up to nk16)
 #pragma unroll
-                    for (int j8 = 0; j8 < 32; j8 += 8) {
-                        if (c0 + j8 >= nk16) break;
-                        uint32_t pk[4];
+                    for (int j = 0; j < 16; ++j) pk[j] = 0u;
+                } else {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + lane_base + c0, r);
+                    const bool full = c0 + 31 <= plim;
 #pragma unroll
-                        for (int e = 0; e < 8; e += 2) {
-                            const int j = c0 + j8 + e;
-                            float e0 = (j <= plim) ? exp2f(fmaf(__uint_as_float(r[j8 + e]), sl2, -mb)) : 0.f;
-                            float e1 = (j + 1 <= plim) ? exp2f(fmaf(__uint_as_float(r[j8 + e + 1]), sl2, -mb)) : 0.f;
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
-                            float2 back = __bfloat1622float2(b2);
-                            sum += back.x + back.y;
-                            pk[e / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                    for (int j = 0; j < 32; j += 2) {
+                        float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
+                        float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
+                        if (!full) {
+                            e0 = (c0 + j <= plim) ? e0 : 0.f;
+                            e1 = (c0 + j + 1 <= plim) ? e1 : 0.f;
                         }
-                        *reinterpret_cast<uint4*>(sP + core_off(row, c0 + j8, Npad)) =
-                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        sum += e0 + e1;
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
+                        pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
                     }
                 }
+#pragma unroll
+                for (int j8 = 0; j8 < 4; ++j8)
+                    if (c0 + j8 * 8 < nk16)
+                        *reinterpret_cast<uint4*>(sP + core_off(row, c0 + j8 * 8, Npad)) =
+                            make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
             }
             __syncthreads();  // both halves read s_red (max) before it is reused for sums
             s_red[half][row] = sum;
@@ -239,6 +270,8 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 uint32_t r[16];
                 tmem_ld16(tmem + lane_base + half * (DH / 2), r);
                 if (p < N && p >= p0) {
+                    if (stats && half == 0)  // natural-log units: exp(s / sqrt(dh) - m)
+                        stats[((size_t)ch.cfg_sample[c] * ch.N + p) * H + h] = make_float2(mx * rsqrtf((float)DH), sum);
                     const float inv = 1.f / sum;
                     float* dst = O + ((size_t)ch.cfg_row[c] + p) * d + h * DH + half * (DH / 2);
 #pragma unroll
@@ -264,7 +297,8 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
 bool attention_tc_supported(int N, int dh) { return (dh == 16 || dh == 32) && N <= AT_MAX_N; }
 
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
-                                int* status, cudaStream_t st, int grid) {
+                                int* status, cudaStream_t st, int grid, const int* cfg_list, int n_list,
+                                float2* stats) {
     const int DH = ch.d / ch.heads;
     if (!attention_tc_supported(ch.N, DH)) return cudaErrorInvalidValue;
     const int Npad = (ch.N + 31) & ~31;
@@ -279,24 +313,24 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const size_t max_ctas = 512 / cols;
     size_t smem_req = smem;
     if (smem_sm / smem_req > max_ctas) smem_req = smem_sm / (max_ctas + 1) + 1024;
-    static size_t granted16 = 0, granted32 = 0;  // attribute set once per size, outside captures
-    switch (DH) {
-        case 16:
-            if (smem_req > granted16) {
-                cudaFuncSetAttribute(k_attention_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-                granted16 = smem_req;
-            }
-            k_attention_tc<16><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status);
-            break;
-        case 32:
-            if (smem_req > granted32) {
-                cudaFuncSetAttribute(k_attention_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-                granted32 = smem_req;
-            }
-            k_attention_tc<32><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status);
-            break;
-        default: return cudaErrorInvalidValue;
+    static size_t granted[2] = {};  // attribute set once per instantiation and size, outside captures
+#define VQ_ATC(D, SLOT)                                                                                        \
+    {                                                                                                          \
+        if (smem_req > granted[SLOT]) {                                                                        \
+            cudaFuncSetAttribute(k_attention_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req); \
+            granted[SLOT] = smem_req;                                                                          \
+        }                                                                                                      \
+        k_attention_tc<D><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status,   \
+                                                              cfg_list, n_list, stats);                      \
     }
+    if (DH == 16) {
+        VQ_ATC(16, 0)
+    } else if (DH == 32) {
+        VQ_ATC(32, 1)
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef VQ_ATC
     return cudaGetLastError();
 }
 

@@ -3,15 +3,16 @@
 //
 //   C[M, N] = A[M, K] @ Bt[N, K]^T + bias (+ epilogue),  A and Bt K-major BF16.
 //
-// Persistent kernel, one CTA per SM, 6 warps:
+// Persistent kernel, one CTA per SM, 10 warps:
 //   warp 0      one thread issues TMA tile loads (128-byte swizzle) into a ring
 //               of STAGES shared-memory slots, completion tracked by mbarriers;
 //   warp 1      one thread issues tcgen05.mma (M = 128, N = BN, K = 16) into a
 //               double-buffered TMEM accumulator and commits slot releases;
 //               the warp also owns the TMEM allocation;
-//   warps 2-5   epilogue: tcgen05.ld of their 32-lane quarter, bias /
-//               activation / residual in FP32, stores to global memory, then
-//               release the accumulator buffer so the next tile's MMAs overlap.
+//   warps 2-9   epilogue (two warps per 32-lane TMEM quarter, alternate
+//               32-column chunks): tcgen05.ld, bias / activation / residual in
+//               FP32, stores to global memory, then release the accumulator
+//               buffer so the next tile's MMAs overlap.
 // The row count M is read from device memory (unique rows are only known on
 // the device).  Every wait is bounded; on timeout the kernel sets
 // VQNQS_DEV_TIMEOUT, drains its own in-flight copies and frees its TMEM.
@@ -22,7 +23,7 @@
 
 namespace vq {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 192;
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 320;
 
 template <int BN>
 struct TcCfg {
@@ -60,7 +61,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 128); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 256); }
         tc::mbar_init(done, 1);
         tc::fence_barrier_init();
     }
@@ -123,7 +124,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             tc::mbar_wait(done, 0, status, 100000000LL);
         }
     } else {
+        // warps 2..9: two warps per TMEM lane quarter, each taking alternate 32-column chunks
         const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are reachable from this warp
+        const int part = (warp - 2) >> 2;
         int i = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
             const int a = i & 1;
@@ -133,7 +136,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
             const int row = m0 + q * 32 + lane;
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
+            for (int c = part * 32; c < BN; c += 64) {
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * BN + c, r);
                 if (row < M) {
@@ -183,6 +186,24 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
+
+// A bounded wait on an mbarrier that no thread arrives on: it must give up
+// after about limit_cycles and record VQNQS_DEV_TIMEOUT (exercises the
+// failure path every tensor-core kernel relies on, without a fault).
+__global__ void k_timeout_probe(int* status, long long limit_cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) tc::mbar_wait(&bar, 0, status, limit_cycles);
+}
+
+cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream_t st) {
+    k_timeout_probe<<<1, 32, 0, st>>>(status, limit_cycles);
+    return cudaGetLastError();
+}
 
 // ---- host side -----------------------------------------------------------------
 namespace {

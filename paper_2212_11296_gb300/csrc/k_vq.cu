@@ -34,11 +34,11 @@ __device__ __forceinline__ void best_merge(Best& a, float c1, int j1, float c2) 
 __global__ void __launch_bounds__(VQ_THREADS, 2)
 k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
             const float* __restrict__ W, const float* __restrict__ cnorm, int K, int d, int* __restrict__ code,
-            long long* __restrict__ near_ties) {
+            long long* __restrict__ near_ties, int a_slot) {
     __shared__ __align__(16) float As[2][VQ_BK][VQ_BM];
     __shared__ __align__(16) float Bs[2][VQ_BK][VQ_BN];  // Bs[k][j] = W[j][k]
     __shared__ int s_ties;
-    const int R = act_rows ? counters[CNT_A] : counters[CNT_R];  // rows to assign
+    const int R = act_rows ? counters[a_slot] : counters[CNT_R];  // rows to assign
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     const int a_row = tid >> 1, a_k = (tid & 1) * 4;
     const int b_j = tid >> 1, b_k = (tid & 1) * 4;  // codeword rows are loaded like A rows
@@ -158,12 +158,12 @@ cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st
 
 cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
                              const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
-                             cudaStream_t st, int num_sms) {
+                             cudaStream_t st, int num_sms, int a_slot) {
     if (d % VQ_BK) return cudaErrorInvalidValue;
     int tiles = (Rmax + VQ_BM - 1) / VQ_BM;
     int grid = tiles < 2 * num_sms ? tiles : 2 * num_sms;
     if (grid < 1) grid = 1;
-    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, counters, act_rows, codebook, cnorm, K, d, code, near_ties);
+    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, counters, act_rows, codebook, cnorm, K, d, code, near_ties, a_slot);
     return cudaGetLastError();
 }
 

@@ -6,23 +6,24 @@
 // o_hi W_hi + o_hi W_lo + o_lo W_hi (the lo x lo term is below 2^-22 relative),
 // which keeps the dot products at FP32 accuracy on the TF32 tensor pipe.
 //
-// Persistent CTA of 9 warps per SM, 128-row tiles of active rows:
+// Persistent CTA of 10 warps per SM, 128-row tiles of active rows:
 //   warps 0-3  loaders: gather the tile's O rows, split them, write the hi/lo A
 //              chunks (32 columns, 128-byte swizzle) into the shared-memory ring;
-//              the next chunk's global loads are in flight while a loader waits
-//              for a free slot;
+//              the next two chunks' global loads are in flight while a loader
+//              waits for a free slot;
 //   warps 4-7  epilogue: read the accumulator columns from TMEM and reduce
 //              (best, index, second best) per row; the accumulator is double
 //              buffered when it fits, so this overlaps the next tile's MMAs;
-//   warp 8     one thread: TMA of the codebook hi/lo chunks (precomputed per
-//              layer) and the tcgen05.mma (kind::tf32, M = 128, N <= 256, K = 8)
-//              issue, slot release by tcgen05.commit.
+//   warp 8     one thread issues the tcgen05.mma (kind::tf32, M = 128,
+//              N <= 256, K = 8) and releases slots by tcgen05.commit;
+//   warp 9     one thread: TMA of the codebook hi/lo chunks (precomputed per
+//              layer), running a ring slot ahead of the MMAs.
 // All waits are bounded (VQNQS_DEV_TIMEOUT).
 #include "tc_common.cuh"
 
 namespace vq {
 
-constexpr int VT_BM = 128, VT_BK = 32, VT_THREADS = 288;
+constexpr int VT_BM = 128, VT_BK = 32, VT_THREADS = 320;
 
 __host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(VT_THREADS, 1)
 k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
         const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
         const float* __restrict__ cnorm, int K, int d, int* __restrict__ code, long long* __restrict__ near_ties,
-        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols, int ACC) {
+        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols, int ACC, int a_slot) {
     constexpr int A_BYTES = VT_BM * VT_BK * 4;   // 16 KB per part
     constexpr int B_BYTES = KC * VT_BK * 4;      // per part and pass
     extern __shared__ uint8_t smem_raw[];
@@ -85,9 +86,10 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
     uint64_t* done = osqf + 2;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
     float* osq_s = reinterpret_cast<float*>(tmem_holder + 4);  // [2][128]
+    float* cn_s = osq_s + 2 * VT_BM;                            // [K] codeword norms
     __shared__ int s_ties;
 
-    const int R = counters[CNT_A];
+    const int R = counters[a_slot];  // rows listed in act_rows
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
     const int tiles = (R + VT_BM - 1) / VT_BM, KB = d / VT_BK;
     if (tid == 0) {
@@ -105,6 +107,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
         tc::fence_barrier_init();
         s_ties = 0;
     }
+    for (int j = tid; j < K; j += blockDim.x) cn_s[j] = cnorm[j];
     if (warp == 8) tc::tmem_alloc(tmem_holder, tmem_cols);
     tc::tc_fence_before();
     __syncthreads();
@@ -112,11 +115,35 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_holder;
     const int accw = passes * KC;  // TMEM columns of one accumulator
 
-    if (warp == 8) {
-        // ---- TMA of the codebook chunks and MMA issue -------------------------
+    if (warp == 9) {
+        // ---- TMA producer: codebook hi/lo chunks, one ring slot ahead of the MMAs ----
         if (lane == 0) {
             tc::prefetch_tmap(&tm_hi);
             tc::prefetch_tmap(&tm_lo);
+            bool ok = true;
+            int it = 0;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                for (int kb = 0; kb < KB; ++kb, ++it) {
+                    const int s = it % VT_STAGES;
+                    const uint32_t ph = (it / VT_STAGES) & 1;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
+                    uint8_t* slot = smem + s * SLOT;
+                    tc::mbar_arrive_expect_tx(&fullB[s], passes * 2 * B_BYTES);
+                    for (int ps = 0; ps < passes; ++ps) {
+                        uint8_t* bh = slot + 2 * A_BYTES + ps * 2 * B_BYTES;
+                        tc::tma_load_2d(bh, &tm_hi, kb * VT_BK, ps * KC, &fullB[s]);
+                        tc::tma_load_2d(bh + B_BYTES, &tm_lo, kb * VT_BK, ps * KC, &fullB[s]);
+                    }
+                }
+            }
+            if (!ok) {  // drain this thread's own copies still in flight
+                for (int j = it - VT_STAGES; j < it; ++j)
+                    if (j >= 0) tc::mbar_wait(&fullB[j % VT_STAGES], (j / VT_STAGES) & 1, status, 100000000LL);
+            }
+        }
+    } else if (warp == 8) {
+        // ---- MMA issue ------------------------------------------------------------------
+        if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32_f32(VT_BM, KC);
             bool ok = true;
             int it = 0, i = 0;
@@ -128,13 +155,6 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                     const int s = it % VT_STAGES;
                     const uint32_t ph = (it / VT_STAGES) & 1;
                     uint8_t* slot = smem + s * SLOT;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
-                    tc::mbar_arrive_expect_tx(&fullB[s], passes * 2 * B_BYTES);
-                    for (int ps = 0; ps < passes; ++ps) {
-                        uint8_t* bh = slot + 2 * A_BYTES + ps * 2 * B_BYTES;
-                        tc::tma_load_2d(bh, &tm_hi, kb * VT_BK, ps * KC, &fullB[s]);
-                        tc::tma_load_2d(bh + B_BYTES, &tm_lo, kb * VT_BK, ps * KC, &fullB[s]);
-                    }
                     if (!tc::mbar_wait(&fullB[s], ph, status) || !tc::mbar_wait(&fullA[s], ph, status)) {
                         ok = false;
                         break;
@@ -162,14 +182,10 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             }
             tc::mma_commit(done);
             tc::mbar_wait(done, 0, status, 100000000LL);
-            if (!ok) {  // drain this thread's own copies still in flight
-                for (int j = it - VT_STAGES; j <= it; ++j)
-                    if (j >= 0) tc::mbar_wait(&fullB[j % VT_STAGES], (j / VT_STAGES) & 1, status, 100000000LL);
-            }
         }
     } else if (warp < 4) {
-        // ---- loaders: thread tid owns tile row tid; loads of the next chunk are in
-        // flight while this thread waits for a free slot ----------------------
+        // ---- loaders: thread tid owns tile row tid; loads of the next two chunks
+        // are in flight while this thread waits for a free slot -----------------
         int it = 0, i = 0;
         int t = blockIdx.x, kb = 0;
         float4 cur[VT_BK / 4];
@@ -181,15 +197,22 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             for (int q = 0; q < VT_BK / 4; ++q)
                 dst[q] = valid ? *reinterpret_cast<const float4*>(src + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
+        // register ring: the chunks at distance 1 and 2 are in flight while this one is stored
+        float4 n1[VT_BK / 4], n2[VT_BK / 4];
+        auto advance = [&](int& tt, int& kk) {
+            if (++kk == KB) { kk = 0; tt += gridDim.x; }
+        };
+        int t1 = t, k1 = 0, t2, k2;
+        advance(t1, k1);
+        t2 = t1; k2 = k1;
+        advance(t2, k2);
         if (t < tiles) issue(t, 0, cur);
+        if (t1 < tiles) issue(t1, k1, n1);
         float osq = 0.f;
         bool ok = true;
         while (t < tiles && ok) {
-            // the chunk after this one
-            int nt = t, nkb = kb + 1;
-            if (nkb == KB) { nkb = 0; nt = t + gridDim.x; }
-            float4 nxt[VT_BK / 4];
-            if (nt < tiles) issue(nt, nkb, nxt);
+            float4 n3[VT_BK / 4];
+            if (t2 < tiles) issue(t2, k2, n3);
             const int s = it % VT_STAGES;
             const uint32_t ph = (it / VT_STAGES) & 1;
             if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
@@ -217,9 +240,10 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                 ++i;
             }
 #pragma unroll
-            for (int q = 0; q < VT_BK / 4; ++q) cur[q] = nxt[q];
-            t = nt;
-            kb = nkb;
+            for (int q = 0; q < VT_BK / 4; ++q) { cur[q] = n1[q]; n1[q] = n3[q]; }
+            t = t1; kb = k1;
+            t1 = t2; k1 = k2;
+            advance(t2, k2);
         }
     } else {
         // ---- epilogue: warps 4-7 own TMEM lanes 32 (w - 4) .. + 31 -----------------
@@ -239,7 +263,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = c0 + j;
-                    if (n < K) vq_merge(best, fmaf(-2.f, __uint_as_float(r[j]), cnorm[n]), n);
+                    if (n < K) vq_merge(best, fmaf(-2.f, __uint_as_float(r[j]), cn_s[n]), n);
                 }
             }
             const float osq = osq_s[a * VT_BM + row];
@@ -312,13 +336,13 @@ cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d
 
 cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
                          const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
-                         int* status, cudaStream_t st, int num_sms, int Rmax) {
+                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot) {
     if (!vq_tc_supported(K, d)) return cudaErrorInvalidValue;
     const int KC = K > 256 ? 256 : K;
     const int passes = (K + KC - 1) / KC;
     const size_t slot = 2 * (size_t)VT_BM * VT_BK * 4 + (size_t)passes * 2 * KC * VT_BK * 4;
     const size_t limit = 227 * 1024;
-    const size_t extra = 256 + 2 * VT_BM * 4;  // barriers, TMEM address, row norms
+    const size_t extra = 256 + 2 * VT_BM * 4 + (size_t)K * 4;  // barriers, TMEM address, row and codeword norms
     int stages = (1024 + 2 * slot + extra <= limit) ? 2 : 1;
     size_t smem = 1024 + stages * slot + extra;
     if (smem > limit) return cudaErrorInvalidValue;
@@ -341,7 +365,7 @@ cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, con
             gr = smem;                                                                                     \
         }                                                                                                  \
         k_vq_tc<X><<<grid, VT_THREADS, smem, st>>>(tm_hi, tm_lo, O, counters, act_rows, cnorm, K, d, code,  \
-                                                   near_ties, status, stages, cols, acc);                  \
+                                                   near_ties, status, stages, cols, acc, a_slot);          \
         return cudaGetLastError();                                                                         \
     }
     VQ_TC_CASE(16) VQ_TC_CASE(32) VQ_TC_CASE(48) VQ_TC_CASE(64) VQ_TC_CASE(96) VQ_TC_CASE(128) VQ_TC_CASE(192)

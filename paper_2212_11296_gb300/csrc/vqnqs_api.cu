@@ -1057,6 +1057,16 @@ int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* ws, size_t ws_bytes, vqnqs_tunin
     return build_weight_tmaps(ctx);
 }
 
+int vqnqs_check_timeout_path(vqnqs_ctx* ctx, long long limit_cycles, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL)
+        return fail(ctx, VQNQS_ERR_ARG, "limit_cycles must be 1 .. 4e9");
+    ctx->launches += 1;
+    VQ_CK(launch_timeout_probe(ctx->status, limit_cycles, static_cast<cudaStream_t>(stream)));
+    return VQNQS_OK;
+}
+
 int vqnqs_profile_enable(vqnqs_ctx* ctx, int enable) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->prof = enable != 0;

@@ -19,8 +19,9 @@ enum {
     CNT_C = 0,      // configurations in the chunk
     CNT_R = 1,      // rows = C * N
     CNT_A = 2,      // active rows: rows whose attention and codeword are computed
-    CNT_U0 = 3,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
-    CNT_SLOTS = 3 + VQNQS_MAX_LAYERS + 2
+    CNT_V = 3,      // incremental path: rows of the current layer listed for the codeword search
+    CNT_U0 = 4,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
+    CNT_SLOTS = 4 + VQNQS_MAX_LAYERS + 2
 };
 
 // Slots of the context's persistent device statistics (int64).
@@ -32,7 +33,26 @@ enum {
     ST_U0 = 4,      // ST_U0 + l
     ST_ACTIVE = 4 + VQNQS_MAX_LAYERS + 2,  // rows whose attention and code are computed (per layer)
     ST_PAIRS = ST_ACTIVE + 1,              // causal query-key pairs of those rows (per layer)
-    ST_SLOTS = ST_PAIRS + 2
+    ST_INC_BASE = ST_PAIRS + 1,            // incremental path, summed over layers: samples' own rows
+    ST_INC_PATCHED,                        //   rows corrected for the changed keys only
+    ST_INC_CERT,                           //   patched rows whose code was proved to be the sample's
+    ST_INC_FULL,                           //   rows recomputed over all keys
+    ST_INC_VQ,                             //   rows given to the codeword search
+    ST_INC_PPAIRS,                         //   (patched row, changed key) pairs, per head
+    ST_INC_FPAIRS,                         //   query-key pairs of the recomputed rows, per head
+    ST_SLOTS
+};
+
+// Incremental path (k_incremental.cu): the certificate of one of a sample's rows.
+// Codeword j (!= code) cannot become the nearest while ||delta|| < rho of j; the
+// CERT_T smallest radii are listed ascending, `next` is the one after them.
+constexpr int CERT_T = 8;
+constexpr int INC_MAX_KEYS = 64;  // changed positions patched per configuration (more: recompute)
+struct CertRow {
+    float next, eta;
+    int n, code;
+    int j[CERT_T];
+    float rho[CERT_T], gap[CERT_T];
 };
 
 struct LayerW {
@@ -42,6 +62,7 @@ struct LayerW {
     float* cnorm;   // [K] ||W_j||^2
     __nv_bfloat16 *wqkv_t, *w1_t, *w2_t;  // BF16 transposes [out][in] for the tensor-core GEMMs
     CUtensorMap tm_wqkv, tm_w1, tm_w2;    // TMA maps of the transposes (valid when d % 64 == 0)
+    float* wd;                            // [K][K] ||W_a - W_c|| (incremental path's certificates)
     float *cb_hi, *cb_lo;                 // codebook split into TF32 hi / lo parts
     CUtensorMap tm_cb_hi, tm_cb_lo;       // their TMA maps (valid when vq_tc_supported)
 };
@@ -156,15 +177,20 @@ cudaError_t launch_sgemm(const float* A, const float* B, const float* bias, cons
 cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
                                long long* stats, cudaStream_t st, int grid);
 
-// attention (k_attn.cu): O[r] for the active rows (all rows when prefix_reuse == 0)
+// attention (k_attn.cu): O[r] for the active rows (all rows when prefix_reuse == 0) of the
+// configurations cfg_list[0 .. n_list) (all of the chunk's when cfg_list is NULL); with
+// stats, also (max scaled score, sum of exp(score - max)) per (sample * N + p, head)
 cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* qkv, float* O, int prefix_reuse,
-                                 cudaStream_t st, int grid);
+                                 cudaStream_t st, int grid, const int* cfg_list = nullptr, int n_list = 0,
+                                 float2* stats = nullptr);
 cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                                   int prefix_reuse, cudaStream_t st, int grid);
-// tensor-core attention (k_attn_tc.cu): dh in {16, 32}, N <= 448
+                                   int prefix_reuse, cudaStream_t st, int grid, const int* cfg_list = nullptr,
+                                   int n_list = 0, float2* stats = nullptr);
+// tensor-core attention (k_attn_tc.cu): dh in {16, 32}, N <= 448; cfg_list and stats as above
 bool attention_tc_supported(int N, int dh);
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
-                                int* status, cudaStream_t st, int grid);
+                                int* status, cudaStream_t st, int grid, const int* cfg_list = nullptr,
+                                int n_list = 0, float2* stats = nullptr);
 
 // BF16 tensor-core GEMM (k_gemm_tc.cu): C[M,N] = A[M,K] @ Bt[N,K]^T + bias, M = counters[u_slot]
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
@@ -175,11 +201,12 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
                            int* status, cudaStream_t st, int num_sms, int BN = 0);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
+cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream_t st);
 
 // nearest codeword (k_vq.cu): rows act_rows[0 .. counters[CNT_A]) (or 0 .. counters[CNT_R] when act_rows is NULL)
 cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
                              const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
-                             cudaStream_t st, int num_sms);
+                             cudaStream_t st, int num_sms, int a_slot = CNT_A);
 
 cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st);
 
@@ -189,7 +216,24 @@ cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d
 cudaError_t launch_split_tf32(const float* W, size_t n, float* hi, float* lo, cudaStream_t st);
 cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
                          const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
-                         int* status, cudaStream_t st, int num_sms, int Rmax);
+                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot = CNT_A);
+
+// incremental evaluation of the connected configurations (k_incremental.cu)
+bool incremental_supported(int d, int heads);
+cudaError_t launch_codeword_dist(const float* W, int K, int d, float* wd, cudaStream_t st);
+cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
+                             const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
+                             int* counters, cudaStream_t st);
+cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, float* O, const float2* bstat,
+                             const CertRow* cert, const float* codebook, int* code, uint8_t* mode, int* vq_rows,
+                             long long* stats, cudaStream_t st, int grid);
+cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                             const float2* bstat, const CertRow* cert, const float* codebook, int* code, uint8_t* mode,
+                             int* vq_rows, long long* stats, cudaStream_t st, int grid);
+cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const uint8_t* mode,
+                                 long long* stats, cudaStream_t st, int num_sms);
+cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                                 const uint8_t* mode, long long* stats, cudaStream_t st, int num_sms);
 
 // dedupe (k_dedupe.cu); with prefix reuse a row before its configuration's first changed
 // position takes the code of the same position of the sample's own configuration.

@@ -197,3 +197,17 @@ def test_duplicate_codewords_tie_on_every_row():
     assert st["near_ties"] == st["rows"] * layers
     want = hamiltonian.local_energy(P, spins, L, True, 1.0)
     assert rel_err(e, want, N).max() <= FP32_TOL
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """A wait that nothing satisfies ends after its bound with VQNQS_DEV_TIMEOUT
+    in the status word (no trap, no hang); the same context computes correctly
+    afterwards."""
+    m, P, spins, s_dev = setup("4x4")
+    m.reset_stats()
+    m.check_timeout_path(2_000_000)
+    assert m.stats()["device_status"] & 4
+    m.reset_stats()
+    e = m.local_energy(s_dev, 1)
+    assert m.stats()["device_status"] == 0
+    assert torch.equal(e, m.local_energy(s_dev, 0))
