@@ -63,20 +63,39 @@ def measured_peaks() -> dict:
         return {"bf16_tflops": 1700.0, "bf16_tflops_burst": 1900.0, "hbm_gbs": 6800.0, "src": "fallback"}
 
 
-def stage_flops(stage: str, st: dict, w: dict, bf16: bool) -> tuple[float, str]:
+def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) -> tuple[float, str]:
     """Algorithmic FLOPs (2 per multiply-add) of one stage over the counted work, and its bound.
 
     Attention: 4 d FLOPs per causal query-key pair (q.k and p v over all heads);
-    argmin: 2 K d per active row; GEMMs: 6 d^2 (QKV) and 8 d^2 (each MLP GEMM)
-    per unique row.  Pairs and active rows are counted by the library (rows
-    before a configuration's first exchanged site are not computed)."""
+    argmin: 2 K d per searched row; GEMMs: 6 d^2 (QKV) and 8 d^2 (each MLP GEMM)
+    per unique row.  Pairs and rows are counted by the library (rows before a
+    configuration's first exchanged site are not computed).  Incremental path:
+    the attention stage covers the samples' own rows only; the certificate is a
+    2 K d distance pass per sample row; a patch costs 8 d per (row, changed
+    key) pair (two scores and two value updates per head); a recomputed row 4 d
+    per query-key pair.  The BF16 patch runs its few products on the tensor
+    cores and is bound by the rows' data instead: bytes, 6 d per patched row
+    (its BF16 query and the sample's FP32 output) and 4 d per searched row (its
+    FP32 output written)."""
     d, K, Ly = w["d_model"], w["K"], w["layers"]
     U = st["unique_rows"]
     tc = "tensor" if bf16 else "alu"
     if stage == "vq_argmin":
-        return st["active_rows"] * Ly * 2.0 * K * d, tc
+        rows = st["inc_searched_rows"] if inc else st["active_rows"] * Ly
+        return rows * 2.0 * K * d, tc
     if stage == "attention":
+        if inc:
+            N = w["L"] ** 2
+            return st["samples"] * Ly * N * (N + 1) / 2 * 4.0 * d, tc
         return st["attn_pairs"] * Ly * 4.0 * d, tc
+    if stage == "inc_certificate":
+        return st["inc_base_rows"] * 2.0 * K * d, "alu"
+    if stage == "inc_patch":
+        if bf16:  # tensor-core scores and sums are negligible: the bound is the rows' data (bytes)
+            return st["inc_patched_rows"] * 6.0 * d + st["inc_searched_rows"] * 4.0 * d, "hbm"
+        return st["inc_patch_pairs"] * 8.0 * d, "alu"
+    if stage == "inc_recompute":
+        return st["inc_full_pairs"] * 4.0 * d, "alu"
     if stage == "qkv_gemm":
         return sum(U[:Ly]) * 6.0 * d * d, tc
     if stage in ("mlp_up", "mlp_down"):
@@ -220,7 +239,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--flags", default="reuse,bf16", help="comma list of reuse,bf16 for the timed path")
+    ap.add_argument("--flags", default="reuse,bf16,incremental",
+                    help="comma list of reuse,bf16,incremental for the timed path")
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
@@ -234,7 +254,7 @@ def main():
     import torch
     import torch.distributed as dist
     import synthetic_inputs as si
-    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    from paper_2212_11296_gb300 import BF16, INCREMENTAL, REUSE, VQNQS
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -244,7 +264,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     flags = 0
     for f in args.flags.split(","):
-        flags |= {"reuse": REUSE, "bf16": BF16, "": 0}[f.strip()]
+        flags |= {"reuse": REUSE, "bf16": BF16, "incremental": INCREMENTAL, "": 0}[f.strip()]
     B, L, N = w["samples_per_gpu"], w["L"], w["L"] ** 2
     blob = si.make_weights(N, w["layers"], w["d_model"], w["K"], seed=0)
     all_spins = si.make_samples(L, B * world, seed=1)
@@ -374,17 +394,22 @@ def main():
     per_step = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(per_step, key=lambda k: per_step[k][2])
     calls, nl, ms = per_step[dom]
-    fl, bound = stage_flops(dom, st, w, bool(flags & BF16))
-    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    fl, bound = stage_flops(dom, st, w, bool(flags & BF16), bool(flags & INCREMENTAL))
     pk = measured_peaks()
-    if bound == "tensor":
-        peak, peak_src = pk["bf16_tflops"], f"bf16 dense, sustained ({pk['src']})"
+    if bound == "hbm":  # fl is bytes
+        achieved = fl / (ms / 1e3) / 1e9 if ms > 0 else None
+        peak, peak_src, unit = pk["hbm_gbs"], f"HBM copy ({pk['src']})", "GB/s"
     else:
-        peak, peak_src = FP32_FFMA_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+        unit = "TFLOP/s"
+        if bound == "tensor":
+            peak, peak_src = pk["bf16_tflops"], f"bf16 dense, sustained ({pk['src']})"
+        else:
+            peak, peak_src = FP32_FFMA_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak if achieved else None, "traffic": traffic_from_profile(dom),
                 "peak_source": peak_src, "launches": nl, "avg_launch_ms": ms / nl,
-                "flops_per_launch": fl / max(1, nl)}
+                ("bytes_per_launch" if bound == "hbm" else "flops_per_launch"): fl / max(1, nl)}
     stages = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[1] / args.steps,
                   "share": v[2] / max(1e-9, sum(x[2] for x in per_step.values()))} for k, v in per_step.items()}
 
@@ -396,6 +421,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16" if flags & BF16 else "f32", "data": "synthetic",
         "config": config_dict(w, ("VQ-reuse" if flags & REUSE else "full recompute") +
+                              (" incremental" if flags & INCREMENTAL else "") +
                               (" BF16 GEMMs, FP32 VQ" if flags & BF16 else " FP32")),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * N),
@@ -412,6 +438,10 @@ def main():
         "gemm_tc": gemm,
         "stages": stages,
     }
+    if flags & INCREMENTAL:  # row outcomes over the timed steps, summed over layers
+        res["incremental"] = {k: st[k] for k in ("inc_base_rows", "inc_patched_rows", "inc_certified_rows",
+                                                 "inc_full_rows", "inc_searched_rows", "inc_patch_pairs",
+                                                 "inc_full_pairs")}
     if world == 1 and not args.no_cpu_baseline:
         vals, dt, cores = cpu_oracle(spins_np, w)
         n = len(vals)

@@ -62,8 +62,15 @@ typedef enum {
 
 /* flags (bitwise or); 0 = plain full recompute in FP32 */
 enum {
-    VQNQS_REUSE = 1,  /* deduplicate per-location work by (row, code) keys (Sec. 3.2) */
-    VQNQS_BF16 = 2    /* BF16 tensor-core GEMMs with FP32 accumulation */
+    VQNQS_REUSE = 1,       /* deduplicate per-location work by (row, code) keys (Sec. 3.2) */
+    VQNQS_BF16 = 2,        /* BF16 tensor-core GEMMs with FP32 accumulation */
+    VQNQS_INCREMENTAL = 4  /* with VQNQS_REUSE, local energies only: a connected configuration's
+                              attention rows whose query is the sample's are corrected for the
+                              changed keys only, and their codeword is taken from the sample's row
+                              when a distance bound proves it unchanged (else searched).  Exact up
+                              to rounding; the paper leaves attention dense (Sec. 3.2).  Needs
+                              d_model in {32, 64, 128, 256, 512} and d_model / heads in {16, 32},
+                              a multiple of d_model / 32. */
 };
 
 /* bits of the device status word */
@@ -89,6 +96,14 @@ typedef struct vqnqs_stats {
                                                  (rows before a configuration's first exchanged site
                                                  reuse the sample's own rows) */
     int64_t attn_pairs;                       /* causal query-key pairs of those rows, per layer */
+    /* VQNQS_INCREMENTAL, summed over layers: */
+    int64_t inc_base_rows;                    /* samples' own rows (full attention, codeword certificate) */
+    int64_t inc_patched_rows;                 /* rows whose attention was corrected for the changed keys */
+    int64_t inc_certified_rows;               /* patched rows whose codeword was proved to be the sample's */
+    int64_t inc_full_rows;                    /* rows whose attention was recomputed over all keys */
+    int64_t inc_searched_rows;                /* rows given to the nearest-codeword search */
+    int64_t inc_patch_pairs;                  /* (patched row, changed key) pairs, per head */
+    int64_t inc_full_pairs;                   /* causal query-key pairs of the recomputed rows, per head */
 } vqnqs_stats;
 
 /* Number of floats in the weight blob for the layout above. */
@@ -155,7 +170,8 @@ int vqnqs_codes(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int* dev_codes,
  *                 (1/B normalisation) of the B local energies
  *   dev_log_psi   DEVICE float [B] (output, may be NULL): log psi of the samples
  * Every configuration one nearest-neighbour exchange away from a sample is
- * evaluated (Sec. 2: O(N) non-zero entries per row). */
+ * evaluated (Sec. 2: O(N) non-zero entries per row).
+ *   flags         VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL (the last needs the first) */
 int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_e_loc,
                        double* dev_mean_var, float* dev_log_psi, int flags,
                        void* dev_ws, size_t ws_bytes, void* stream);
@@ -277,7 +293,7 @@ typedef struct vqnqs_stage_time {
     double ms;         /* summed CUDA-event time */
 } vqnqs_stage_time;
 
-#define VQNQS_MAX_STAGES 16
+#define VQNQS_MAX_STAGES 32
 
 int vqnqs_profile_enable(vqnqs_ctx* ctx, int enable);
 

@@ -16,6 +16,7 @@ VQNQS_OK, VQNQS_ERR_ARG, VQNQS_ERR_CUDA, VQNQS_ERR_OOM, VQNQS_ERR_WORKSPACE, VQN
     VQNQS_ERR_INTERNAL = range(7)
 REUSE = 1
 BF16 = 2
+INCREMENTAL = 4
 DEV_BAD_SPIN, DEV_HASH_OVERFLOW, DEV_TIMEOUT = 1, 2, 4
 MAX_LAYERS = 64
 NOALLOC_MAX_ROWS = 1 << 18
@@ -36,6 +37,13 @@ class Stats(ctypes.Structure):
         ("device_status", ctypes.c_int32),
         ("active_rows", ctypes.c_int64),
         ("attn_pairs", ctypes.c_int64),
+        ("inc_base_rows", ctypes.c_int64),
+        ("inc_patched_rows", ctypes.c_int64),
+        ("inc_certified_rows", ctypes.c_int64),
+        ("inc_full_rows", ctypes.c_int64),
+        ("inc_searched_rows", ctypes.c_int64),
+        ("inc_patch_pairs", ctypes.c_int64),
+        ("inc_full_pairs", ctypes.c_int64),
     ]
 
 
@@ -44,7 +52,7 @@ class StageTime(ctypes.Structure):
                 ("ms", ctypes.c_double)]
 
 
-MAX_STAGES = 16
+MAX_STAGES = 32
 
 
 class Tuning(ctypes.Structure):

@@ -10,6 +10,7 @@ from . import _lib
 
 REUSE = _lib.REUSE
 BF16 = _lib.BF16
+INCREMENTAL = _lib.INCREMENTAL
 
 _LIB = None
 
@@ -183,6 +184,10 @@ class VQNQS:
             "unique_rows": [int(s.unique_rows[i]) for i in range(self.layers + 1)],
             "near_ties": s.near_ties, "flops_full": s.flops_full, "flops_done": s.flops_done,
             "device_status": s.device_status, "active_rows": s.active_rows, "attn_pairs": s.attn_pairs,
+            "inc_base_rows": s.inc_base_rows, "inc_patched_rows": s.inc_patched_rows,
+            "inc_certified_rows": s.inc_certified_rows, "inc_full_rows": s.inc_full_rows,
+            "inc_searched_rows": s.inc_searched_rows, "inc_patch_pairs": s.inc_patch_pairs,
+            "inc_full_pairs": s.inc_full_pairs,
         }
 
     def check_timeout_path(self, limit_cycles: int = 1_000_000, stream=None):

@@ -59,7 +59,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
-        run([exe, *ARCH, "-shared", "-cudart", "static", "-o", LIB, *objs])
+        # --no-undefined: a declaration without a definition fails here, not at load time
+        run([exe, *ARCH, "-shared", "-cudart", "static", "-Xlinker", "--no-undefined", "-o", LIB, *objs])
     return LIB
 
 

@@ -1,0 +1,386 @@
+// Causal attention of listed rows of many connected configurations that share
+// one sample's keys and values except at a few changed positions (BF16 path,
+// dh = 32; tensor cores for the sample's keys, CUDA cores for the changes).
+//
+// A configuration one exchange away from sample s has the same row ids as s
+// except at its changed positions D (Sec. 3.2 keys rows on their quantized
+// history, so equal ids mean equal keys and values).  For a listed row
+// (configuration c, position p) with query q:
+//   softmax over s's keys 0..p   ->  maximum m, sum l, numerator A = sum_j P_j v_j
+// computed for 128 rows at once (S = Q K_s^T and A = P V_s on the tensor cores,
+// P rounded to BF16), then each row swaps its configuration's keys in at the
+// changed positions k <= p, exactly as the softmax identity allows:
+//   m' = max(m, q.k_c / sqrt(dh)),  r = exp(m - m'),
+//   A' = r (A - sum_k bf16(e_s,k) v_s,k) + sum_k e'_c,k v_c,k,
+//   l' = r (l - sum_k e_s,k) + sum_k e'_c,k,     o = A' / l'
+// (e_s,k = exp(q.k_s / sqrt(dh) - m) removed the way it was added; e'_c,k
+// against m').  One work item = (sample, head, slice): s's K and V of the head
+// are staged once for all the item's tiles.
+//
+// Rows come from a per-sample list of (row, position) pairs laid out like the
+// active rows (sample b's entries start at act_off[first configuration of b];
+// count[b] of them, or the whole region when count is NULL).  Each
+// configuration's changed positions are dpos[c][0 .. dcnt[c]) (at most
+// INC_MAX_KEYS).  Waits on the MMA barrier are bounded.
+#include <algorithm>
+
+#include "tc_common.cuh"
+
+namespace vq {
+
+namespace {
+
+constexpr int AR_THREADS = 256;
+constexpr int DH = 32;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// n consecutive BF16 values (n a multiple of 8, 16-byte aligned) as floats
+template <int NV>
+__device__ __forceinline__ void ld_bf16(const __nv_bfloat16* p, float (&out)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; i += 8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(p + i);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = __bfloat1622float2(h[k]);
+            out[i + 2 * k] = f.x;
+            out[i + 2 * k + 1] = f.y;
+        }
+    }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(AR_THREADS, 2)
+k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
+                    float* __restrict__ O, const int2* __restrict__ list, const int* __restrict__ act_off,
+                    const int* __restrict__ count, const short* __restrict__ dpos, const int* __restrict__ dcnt,
+                    int slices, int Npad, uint32_t tmem_cols, int* __restrict__ status, long long* __restrict__ stats) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int VS = 2 * DH + 16;               // row stride of the V staging rows (bank-conflict free)
+    const int d = ch.d, H = ch.heads;
+    uint8_t* sK = smem;                           // [Npad x DH] K-major
+    uint8_t* sVt = sK + (size_t)Npad * DH * 2;    // [DH x Npad]
+    uint8_t* sQ = sVt + (size_t)Npad * DH * 2;    // [128 x DH]
+    uint8_t* sP = sQ + 128 * DH * 2;              // [128 x Npad]; V staging rows alias it
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + (size_t)128 * Npad * 2);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
+    __shared__ float s_red[2][128];
+    __shared__ int s_pw[4];
+    __shared__ unsigned long long s_pairs;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & 127, half = tid >> 7;  // two threads per query row
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::fence_barrier_init();
+        s_pairs = 0;
+    }
+    unsigned long long pairs = 0;  // query-key pairs of this thread's rows (head 0, first half)
+    if (blockIdx.x == 0 && tid == 0 && stats)  // the layer's search list is complete: count it
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_VQ]), (unsigned long long)ch.counters[CNT_V]);
+    if (warp == 0) tc::tmem_alloc(tmem_holder, tmem_cols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+    const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);  // log2(e) / sqrt(dh)
+    const int ld = 3 * d;
+    const int items = ch.S * H * slices;
+
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const int z = item % slices, bh = item / slices;
+        const int b = bh / H, h = bh - b * H;
+        const int c0b = ch.cfg_off[b];
+        const int start = act_off[c0b];
+        int n;
+        if (count) {
+            n = count[b];
+        } else {  // the sample's whole region of active rows
+            const int c1b = ch.cfg_off[b + 1];
+            n = (c1b < ch.counters[CNT_C] ? act_off[c1b] : ch.counters[CNT_A]) - start;
+        }
+        if (z * 128 >= n) continue;  // block-uniform: no tile for this slice
+        const int2* lst = list + start;
+        const int rb = ch.cfg_row[ch.cfg_off[b]];
+        const int N = sample_N(ch, b);
+        const int* ub = uid + rb;
+        __syncthreads();  // the previous item's readers of the shared tiles are done
+        // s's keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
+        for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
+            const int j = u % Npad, kb = u / Npad;
+            uint4 kv = make_uint4(0, 0, 0, 0);
+            if (j < N) kv = *reinterpret_cast<const uint4*>(qkv + (size_t)ub[j] * ld + d + h * DH + kb * 8);
+            *reinterpret_cast<uint4*>(sK + tc::core_off(j, kb * 8, DH)) = kv;
+        }
+        // s's values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
+        for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
+            const int j = u / (DH / 8), kb = u - j * (DH / 8);
+            uint4 vv = make_uint4(0, 0, 0, 0);
+            if (j < N) vv = *reinterpret_cast<const uint4*>(qkv + (size_t)ub[j] * ld + 2 * d + h * DH + kb * 8);
+            *reinterpret_cast<uint4*>(sP + j * VS + kb * 16) = vv;
+        }
+        __syncthreads();
+        for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AR_THREADS / 32) {
+            const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
+            const int m = lane >> 3, r = lane & 7;
+            uint32_t f[4];
+            tc::ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
+            tc::stsm_x4(tc::smem_u32(sVt + tc::core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
+        }
+        __syncthreads();
+        for (int t0 = z * 128; t0 < n && ok; t0 += slices * 128) {
+            // this thread's row: (row index, position), or none
+            int rrow = -1, p = -1;
+            if (t0 + row < n) {
+                const int2 e = lst[t0 + row];
+                rrow = e.x;
+                p = e.y;
+            }
+            for (int u = tid; u < 128 * (DH / 8); u += AR_THREADS) {
+                const int r = u & 127, kb = u >> 7;
+                uint4 qv = make_uint4(0, 0, 0, 0);
+                if (t0 + r < n) {
+                    const int2 e = lst[t0 + r];
+                    qv = *reinterpret_cast<const uint4*>(qkv + (size_t)uid[e.x] * ld + h * DH + kb * 8);
+                }
+                *reinterpret_cast<uint4*>(sQ + tc::core_off(r, kb * 8, DH)) = qv;
+            }
+            // the tile's key range: up to its largest position (warp maxima for uniform TMEM reads)
+            const int pw = __reduce_max_sync(0xffffffffu, p);
+            if (lane == 0 && half == 0) s_pw[warp] = pw;
+            tc::fence_proxy_async_smem();
+            tc::tc_fence_before();
+            __syncthreads();
+            const int plim_w = s_pw[warp & 3];  // the warp's rows: keys 0..plim_w cover them all
+            const int ptile = max(max(s_pw[0], s_pw[1]), max(s_pw[2], s_pw[3]));
+            const int nk16 = ((ptile + 1) + 15) & ~15;  // MMA N
+            const int nk32 = ((ptile + 1) + 31) & ~31;  // columns read back
+            if (ptile < 0) {  // only skipped rows in this tile
+                tc::tc_fence_after();
+                __syncthreads();
+                continue;
+            }
+            if (tid == 0) {
+                tc::tc_fence_after();
+                const uint64_t dq = tc::desc_kmajor_none(tc::smem_u32(sQ), 128, (DH / 8) * 128);
+                const uint64_t dk = tc::desc_kmajor_none(tc::smem_u32(sK), 128, (DH / 8) * 128);
+                for (int n0 = 0; n0 < nk16; n0 += 256) {
+                    const int nn = min(256, nk16 - n0);
+                    const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < DH / 16; ++ks)
+                        tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16),
+                                     tc::idesc_bf16_f32(128, nn), ks > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(bar);
+            }
+            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
+            phase ^= 1;
+            tc::tc_fence_after();
+            if (!ok) break;
+            // softmax over s's keys 0..p; this thread takes every other 32-column chunk
+            const int plim = p;  // -1: no keys
+            float mx = -INFINITY;
+            for (int c0 = half * 32; c0 < nk32; c0 += 64) {
+                if (c0 > plim_w) break;  // warp-uniform
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + lane_base + c0, r);
+                if (c0 + 31 <= plim) {
+                    float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
+#pragma unroll
+                    for (int j = 2; j < 32; j += 2) {
+                        m0 = fmaxf(m0, __uint_as_float(r[j]));
+                        m1 = fmaxf(m1, __uint_as_float(r[j + 1]));
+                    }
+                    mx = fmaxf(mx, fmaxf(m0, m1));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
+                }
+            }
+            s_red[half][row] = mx;
+            __syncthreads();
+            mx = fmaxf(s_red[0][row], s_red[1][row]);
+            const float mb = (p >= 0) ? mx * sl2 : 0.f;
+            float sum = 0.f;
+            for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
+                uint32_t pk[16];
+                if (c0 > plim_w) {  // invisible to every row of the warp: P = 0
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) pk[j] = 0u;
+                } else {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + lane_base + c0, r);
+                    const bool full = c0 + 31 <= plim;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
+                        float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
+                        if (!full) {
+                            e0 = (c0 + j <= plim) ? e0 : 0.f;
+                            e1 = (c0 + j + 1 <= plim) ? e1 : 0.f;
+                        }
+                        sum += e0 + e1;
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
+                        pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                    }
+                }
+#pragma unroll
+                for (int j8 = 0; j8 < 4; ++j8)
+                    if (c0 + j8 * 8 < nk16)
+                        *reinterpret_cast<uint4*>(sP + tc::core_off(row, c0 + j8 * 8, Npad)) =
+                            make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+            }
+            __syncthreads();  // both halves read s_red (max) before it is reused for sums
+            s_red[half][row] = sum;
+            tc::tc_fence_before();
+            tc::fence_proxy_async_smem();
+            __syncthreads();
+            sum = s_red[0][row] + s_red[1][row];
+            if (tid == 0) {
+                tc::tc_fence_after();
+                const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
+                const uint64_t dp = tc::desc_kmajor_none(tc::smem_u32(sP), 128, (Npad / 8) * 128);
+                const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt), 128, (Npad / 8) * 128);
+                for (int ks = 0; ks < nk16 / 16; ++ks)
+                    tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc, ks > 0 ? 1u : 0u);
+                tc::mma_commit(bar);
+            }
+            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
+            phase ^= 1;
+            tc::tc_fence_after();
+            if (!ok) break;
+            {
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + half * (DH / 2), r);  // this thread's half of the dims
+                if (p >= 0) {
+                    float a[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) a[t] = __uint_as_float(r[t]);
+                    // swap the configuration's keys in at its changed positions k <= p
+                    const int c = ch.row_cfg[rrow];
+                    const int nd = dcnt[c];
+                    const int* uc = uid + (rrow - p);
+                    const short* dp = dpos + (size_t)c * INC_MAX_KEYS;
+                    float q[DH];
+                    ld_bf16<DH>(qkv + (size_t)uid[rrow] * ld + h * DH, q);
+                    float m2 = mb, lsub = 0.f;  // log2-unit maximum; removed weight
+                    // the new maximum first
+                    for (int i = 0; i < nd; ++i) {
+                        const int k = dp[i];
+                        if (k > p) break;  // ascending
+                        float kc[DH];
+                        ld_bf16<DH>(qkv + (size_t)uc[k] * ld + d + h * DH, kc);
+                        float sc = 0.f;
+#pragma unroll
+                        for (int t = 0; t < DH; ++t) sc = fmaf(q[t], kc[t], sc);
+                        m2 = fmaxf(m2, sc * sl2);
+                    }
+                    const float rs = ex2_approx(mb - m2);  // rescale of s's part (1 if no new maximum)
+                    float add[16];
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) add[t] = 0.f;
+                    float ladd = 0.f;
+                    for (int i = 0; i < nd; ++i) {
+                        const int k = dp[i];
+                        if (k > p) break;
+                        float kb[DH], kc[DH];
+                        ld_bf16<DH>(qkv + (size_t)ub[k] * ld + d + h * DH, kb);
+                        ld_bf16<DH>(qkv + (size_t)uc[k] * ld + d + h * DH, kc);
+                        float sb = 0.f, sc = 0.f;
+#pragma unroll
+                        for (int t = 0; t < DH; ++t) {
+                            sb = fmaf(q[t], kb[t], sb);
+                            sc = fmaf(q[t], kc[t], sc);
+                        }
+                        const float eb = ex2_approx(fmaf(sb, sl2, -mb));  // as s's softmax added it
+                        const float ebq = __bfloat162float(__float2bfloat16_rn(eb));
+                        const float ec = ex2_approx(fmaf(sc, sl2, -m2));
+                        float vb[16], vc[16];
+                        ld_bf16<16>(qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, vb);
+                        ld_bf16<16>(qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, vc);
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            a[t] = fmaf(-ebq, vb[t], a[t]);
+                            add[t] = fmaf(ec, vc[t], add[t]);
+                        }
+                        lsub += eb;
+                        ladd += ec;
+                    }
+                    if (h == 0 && half == 0) pairs += p + 1;
+                    const float inv = 1.f / (rs * (sum - lsub) + ladd);
+                    float* dst = O + (size_t)rrow * d + h * DH + half * 16;
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4)
+                        *reinterpret_cast<float4*>(dst + t) =
+                            make_float4((rs * a[t] + add[t]) * inv, (rs * a[t + 1] + add[t + 1]) * inv,
+                                        (rs * a[t + 2] + add[t + 2]) * inv, (rs * a[t + 3] + add[t + 3]) * inv);
+                }
+            }
+            tc::tc_fence_before();
+            __syncthreads();
+        }
+    }
+    if (pairs) atomicAdd(&s_pairs, pairs);
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, tmem_cols);
+    }
+    if (tid == 0 && s_pairs && stats) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_FPAIRS]), s_pairs);
+}
+
+bool attention_rows_tc_supported(int N, int d, int heads) { return d / heads == DH && N <= 256; }
+
+cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                                     const int2* list, const int* act_off, const int* count, const short* dpos,
+                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms) {
+    if (!attention_rows_tc_supported(ch.N, ch.d, ch.heads)) return cudaErrorInvalidValue;
+    const int Npad = (ch.N + 31) & ~31;
+    uint32_t cols = 32;
+    while ((int)cols < Npad) cols <<= 1;
+    const size_t smem = 1024 + (size_t)Npad * DH * 2 * 2 + 128 * DH * 2 +
+                        std::max((size_t)128 * Npad * 2, (size_t)Npad * (2 * DH + 16)) + 64;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const size_t max_ctas = 512 / cols;  // TMEM columns of the CTAs resident on one SM
+    size_t smem_req = smem;
+    if ((228 * 1024) / smem_req > max_ctas) smem_req = (228 * 1024) / (max_ctas + 1) + 1024;
+    static size_t granted = 0;
+    if (smem_req > granted) {
+        cudaFuncSetAttribute(k_attention_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+        granted = smem_req;
+    }
+    const int sh = ch.S * ch.heads;
+    int slices = (2 * num_sms + sh - 1) / sh;
+    if (slices < 1) slices = 1;
+    if (slices > 64) slices = 64;
+    k_attention_rows_tc<<<sh * slices, AR_THREADS, smem_req, st>>>(ch, uid, qkv, O, list, act_off, count, dpos,
+                                                                   dcnt, slices, Npad, cols, status, stats);
+    return cudaGetLastError();
+}
+
+}  // namespace vq

@@ -27,38 +27,12 @@ namespace vq {
 constexpr int AT_THREADS = 256;
 constexpr int AT_MAX_N = 448;  // keys per configuration handled in one TMEM tile
 
-__device__ __forceinline__ uint64_t desc_kmajor_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;  // version; layout type 0 = no swizzle
-    return d;
-}
+using tc::core_off;
+using tc::desc_kmajor_none;
+using tc::fence_proxy_async_smem;
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// byte offset of element (r, k) in a K-major no-swizzle tile with kd columns
-__device__ __forceinline__ uint32_t core_off(int r, int k, int kd) {
-    return (uint32_t)((r >> 3) * (kd >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// 8x8 b16 matrix moves: four matrices per instruction, thread i addresses row
-// i % 8 of matrix i / 8 (16 bytes).  The .trans load hands out the transposed
-// fragments, so a load/store pair transposes 8x8 blocks without bank conflicts.
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t (&r)[4]) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(addr)
-                 : "memory");
-}
-__device__ __forceinline__ void stsm_x4(uint32_t addr, const uint32_t (&r)[4]) {
-    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(r[0]), "r"(r[1]),
-                 "r"(r[2]), "r"(r[3])
-                 : "memory");
-}
+using tc::ldsm_x4_trans;
+using tc::stsm_x4;
 
 // 2^x with the SFU's approximate exponential (flushes denormals); the softmax
 // weights it feeds are rounded to BF16 right after.
@@ -84,7 +58,8 @@ template <int DH>
 __global__ void __launch_bounds__(AT_THREADS)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, float* __restrict__ O,
                int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
-               const int* __restrict__ cfg_list, int n_list, float2* __restrict__ stats) {
+               const int* __restrict__ cfg_list, int n_list, const int* __restrict__ n_list_dev,
+               float2* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int d = ch.d, H = ch.heads;
@@ -112,7 +87,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint32_t phase = 0;
     bool ok = true;
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);  // log2(e) / sqrt(dh)
-    const int C = cfg_list ? n_list : ch.counters[CNT_C];
+    const int C = cfg_list ? (n_list_dev ? *n_list_dev : n_list) : ch.counters[CNT_C];
     const int ld = 3 * d;
 
     for (int item = blockIdx.x; item < C * H && ok; item += gridDim.x) {
@@ -298,7 +273,7 @@ bool attention_tc_supported(int N, int dh) { return (dh == 16 || dh == 32) && N 
 
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list, int n_list,
-                                float2* stats) {
+                                float2* stats, const int* n_list_dev) {
     const int DH = ch.d / ch.heads;
     if (!attention_tc_supported(ch.N, DH)) return cudaErrorInvalidValue;
     const int Npad = (ch.N + 31) & ~31;
@@ -321,7 +296,7 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
             granted[SLOT] = smem_req;                                                                          \
         }                                                                                                      \
         k_attention_tc<D><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status,   \
-                                                              cfg_list, n_list, stats);                      \
+                                                              cfg_list, n_list, n_list_dev, stats);          \
     }
     if (DH == 16) {
         VQ_ATC(16, 0)

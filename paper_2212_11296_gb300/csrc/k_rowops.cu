@@ -104,17 +104,41 @@ __global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols
         }
 }
 
+// every d_model the context accepts: 32 .. 1024 in steps of 32
 #define VQ_DISPATCH_PER(d, KERNEL, ...)                                 \
     switch ((d) / 32) {                                                 \
-        case 1: KERNEL<1><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
-        case 2: KERNEL<2><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
-        case 4: KERNEL<4><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
-        case 6: KERNEL<6><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
-        case 8: KERNEL<8><<<grid, 256, 0, st>>>(__VA_ARGS__); break;    \
-        case 12: KERNEL<12><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
-        case 16: KERNEL<16><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
-        case 24: KERNEL<24><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
-        case 32: KERNEL<32><<<grid, 256, 0, st>>>(__VA_ARGS__); break;  \
+        case 1: KERNEL<1><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 2: KERNEL<2><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 3: KERNEL<3><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 4: KERNEL<4><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 5: KERNEL<5><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 6: KERNEL<6><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 7: KERNEL<7><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 8: KERNEL<8><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 9: KERNEL<9><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 10: KERNEL<10><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 11: KERNEL<11><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 12: KERNEL<12><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 13: KERNEL<13><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 14: KERNEL<14><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 15: KERNEL<15><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 16: KERNEL<16><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 17: KERNEL<17><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 18: KERNEL<18><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 19: KERNEL<19><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 20: KERNEL<20><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 21: KERNEL<21><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 22: KERNEL<22><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 23: KERNEL<23><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 24: KERNEL<24><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 25: KERNEL<25><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 26: KERNEL<26><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 27: KERNEL<27><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 28: KERNEL<28><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 29: KERNEL<29><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 30: KERNEL<30><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 31: KERNEL<31><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
+        case 32: KERNEL<32><<<grid, 256, 0, st>>>(__VA_ARGS__); break; \
         default: return cudaErrorInvalidValue;                          \
     }
 

@@ -62,9 +62,11 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_BACKWARD, S_COUNT };
+             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_COUNT };
 const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
-                                    "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward"};
+                                    "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward",
+                                    "inc_certificate", "inc_classify", "inc_patch", "inc_recompute"};
+static_assert(S_COUNT <= VQNQS_MAX_STAGES, "stage table larger than the ABI's VQNQS_MAX_STAGES");
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
     if (c->ev_free.empty()) {
@@ -124,7 +126,8 @@ struct Plan {
     long long Cmax = 0, Rmax = 0, Umax = 0;
     int hash_bits = 0;
     size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, cfg_row, row_cfg, act_cnt, act_off, act_rows,
-        uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, total;
+        uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, bstat, cert,
+        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, total;
 };
 
 // Workspace layout for chunks of at most S samples, C configurations and R rows.
@@ -168,6 +171,16 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.rep_code = take((size_t)p.Umax * sizeof(int));
     p.logp = take((size_t)p.Umax * 2 * sizeof(float));
     p.ratio = take((size_t)p.Cmax * sizeof(float));
+    // incremental path: samples' softmax statistics and certificates, search and recompute lists
+    p.bstat = take((size_t)S * c->N * c->heads * sizeof(float2));
+    p.cert = take((size_t)S * c->N * sizeof(CertRow));
+    p.vq_rows = take((size_t)p.Rmax * sizeof(int));
+    p.rc_rows = take((size_t)p.Rmax * sizeof(int2));
+    p.rc_cnt = take((size_t)2 * S * sizeof(int));  // per sample: head and tail counts of the recompute list
+    p.list_tc = take((size_t)p.Cmax * sizeof(int));
+    p.list_simt = take((size_t)p.Cmax * sizeof(int));
+    p.dpos = take((size_t)p.Cmax * INC_MAX_KEYS * sizeof(short));
+    p.dcnt = take((size_t)p.Cmax * sizeof(int));
     p.total = o;
     return p;
 }
@@ -220,6 +233,7 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
         VQ_CK(launch_transpose_bf16(w.w_1, d, 4 * d, w.w1_t, st));
         VQ_CK(launch_transpose_bf16(w.w_2, 4 * d, d, w.w2_t, st));
         VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
+        VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
     }
     return VQNQS_OK;
 }
@@ -315,7 +329,19 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
     const int g_urows = grid_for(ctx, P.Umax, 8, 16);
 
     const bool bf16 = (flags & VQNQS_BF16) != 0;
+    const bool inc = with_bonds && (flags & VQNQS_INCREMENTAL) != 0;
     int* act_rows = at<int>(ws, P.act_rows);
+    const int* cfg_off = at<int>(ws, P.cfg_off);
+    float2* bstat = at<float2>(ws, P.bstat);
+    CertRow* cert = at<CertRow>(ws, P.cert);
+    int* vq_rows = at<int>(ws, P.vq_rows);
+    int2* rc_rows = at<int2>(ws, P.rc_rows);
+    int* rc_cnt = at<int>(ws, P.rc_cnt);
+    const int* act_off = at<int>(ws, P.act_off);
+    int* list_tc = at<int>(ws, P.list_tc);
+    int* list_simt = at<int>(ws, P.list_simt);
+    short* dpos = at<short>(ws, P.dpos);
+    int* dcnt = at<int>(ws, P.dcnt);
     VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, reuse ? 1 : 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off),
                                              act_rows, ctx->stats, st, grid_for(ctx, P.Cmax, 8, 16)));
     __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(A);
@@ -329,7 +355,16 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows));
             VQ_STAGE(S_QKV, 1, launch_gemm_tc(A16, Umax, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, us, 3 * d, d, 0,
                                               ctx->status, st, ctx->num_sms, ctx->bn[0]));
-            if (attention_tc_supported(N, d / ctx->heads))
+            if (inc) {  // the samples' own configurations only, with their softmax statistics
+                if (attention_tc_supported(N, d / ctx->heads))
+                    VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
+                                                            grid_for(ctx, (long long)S * ctx->heads, 1, 4), cfg_off, S,
+                                                            bstat));
+                else
+                    VQ_STAGE(S_ATTN, 1, launch_attention_bf16in(ch, uid_cur, qkv16, O, 1, st,
+                                                                grid_for(ctx, (long long)S * ctx->heads, 1, 8), cfg_off,
+                                                                S, bstat));
+            } else if (attention_tc_supported(N, d / ctx->heads))
                 VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, reuse ? 1 : 0, ctx->status, st,
                                                         grid_for(ctx, P.Cmax * ctx->heads, 1, 4)));
             else
@@ -339,15 +374,57 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, A, nullptr, st, g_urows));
             VQ_STAGE(S_QKV, 1, launch_sgemm(A, w.w_qkv, w.b_qkv, nullptr, qkv, counters, us, Umax, 3 * d, d, EPI_BIAS,
                                             st, ctx->num_sms));
-            VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, reuse ? 1 : 0, st,
-                                                     grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
+            if (inc)
+                VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, 1, st,
+                                                         grid_for(ctx, (long long)S * ctx->heads, 1, 8), cfg_off, S,
+                                                         bstat));
+            else
+                VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, reuse ? 1 : 0, st,
+                                                         grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
         }
+        if (inc) {
+            // the samples' rows: codeword and certificate; then the connected configurations
+            VQ_STAGE(S_CERT, 1, launch_base_cert(ch, O, w.codebook, w.cnorm, w.wd, K, d, code, cert, ctx->stats,
+                                                 counters, rc_cnt, st));
+            const int g_cfg = grid_for(ctx, P.Cmax, 1, 3);
+            const bool tc_inc = bf16 && patch_tc_supported(d, ctx->heads) && attention_tc_supported(N, d / ctx->heads) &&
+                                attention_rows_tc_supported(N, d, ctx->heads);
+            VQ_STAGE(S_CLASSIFY, 1, launch_inc_classify(ch, uid_cur, tc_inc ? 1 : 0, list_tc, list_simt, dpos, dcnt,
+                                                        vq_rows, ctx->stats, st, grid_for(ctx, P.Cmax, 8, 8)));
+            if (tc_inc) {
+                // tensor cores: rows patched, their changed rows recomputed against the sample's keys,
+                // configurations with many changes recomputed whole
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
+                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 1,
+                                                      ctx->status, ctx->stats, st, g_cfg));
+                StageScope scope_(ctx, S_RECOMP, 2, st);
+                VQ_CK(launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos, dcnt, ctx->status,
+                                               ctx->stats, st, ctx->num_sms));
+                VQ_CK(launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
+                                          grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
+                                          counters + CNT_SCL));
+            } else if (bf16) {
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
+                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 0,
+                                                      ctx->status, ctx->stats, st, g_cfg));
+                VQ_STAGE(S_RECOMP, 1, launch_inc_attention(ch, uid_cur, qkv16, O, act_off, rc_rows, rc_cnt, 0,
+                                                           ctx->stats, st, ctx->num_sms));
+            } else {
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv, O, bstat, cert, w.codebook, code, vq_rows,
+                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 0,
+                                                      ctx->status, ctx->stats, st, g_cfg));
+                VQ_STAGE(S_RECOMP, 1, launch_inc_attention(ch, uid_cur, qkv, O, act_off, rc_rows, rc_cnt, 0, ctx->stats,
+                                                           st, ctx->num_sms));
+            }
+        }
+        const int* vq_list = inc ? vq_rows : act_rows;
+        const int vq_slot = inc ? CNT_V : CNT_A;
         if (bf16 && vq_tc_supported(K, d))
-            VQ_STAGE(S_VQ, 1, launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, act_rows, w.cnorm, K, d, code,
-                                           ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, Rmax));
+            VQ_STAGE(S_VQ, 1, launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, vq_list, w.cnorm, K, d, code,
+                                           ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, Rmax, vq_slot));
         else
-            VQ_STAGE(S_VQ, 1, launch_vq_argmin(O, counters, act_rows, w.codebook, w.cnorm, K, d, code,
-                                               ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms));
+            VQ_STAGE(S_VQ, 1, launch_vq_argmin(O, counters, vq_list, w.codebook, w.cnorm, K, d, code,
+                                               ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms, vq_slot));
         if (codes_out) {  // codes of every row: [sample][layer][position] (no connected configurations here)
             ctx->launches += 1;
             VQ_CK(launch_copy_codes(ch, code, l, ctx->layers, codes_out, st, g_rows));
@@ -394,7 +471,14 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & VQNQS_INCREMENTAL) {
+        if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (!incremental_supported(ctx->d, ctx->heads))
+            return fail(ctx, VQNQS_ERR_ARG,
+                        "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
+                        "a multiple of d_model/32");
+    }
     if ((flags & VQNQS_BF16) && ctx->d % 64)
         return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
     if (B == 0) return VQNQS_OK;
@@ -693,7 +777,9 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
         w.w2_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
         w.cb_hi = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
         w.cb_lo = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
-        if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo) return bail(VQNQS_ERR_OOM);
+        w.wd = static_cast<float*>(dalloc((size_t)K * K * sizeof(float)));
+        if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo || !w.wd)
+            return bail(VQNQS_ERR_OOM);
     }
     if (!ctx->blob || !ctx->bonds || !ctx->status || !ctx->stats) return bail(VQNQS_ERR_OOM);
     if (!ctx->bonds_all ||
@@ -756,7 +842,14 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
     ctx->err.clear();
     if (n_groups < 1 || n_groups > MAX_GROUPS || !L_g || !B_g)
         return fail(ctx, VQNQS_ERR_ARG, "ragged: need 1..8 groups and host arrays L_g, B_g");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & VQNQS_INCREMENTAL) {
+        if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (!incremental_supported(ctx->d, ctx->heads))
+            return fail(ctx, VQNQS_ERR_ARG,
+                        "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
+                        "a multiple of d_model/32");
+    }
     if ((flags & VQNQS_BF16) && ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
     Groups g;
     std::memset(&g, 0, sizeof(g));
@@ -848,6 +941,13 @@ int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out) {
     out->device_status = status;
     out->active_rows = st[ST_ACTIVE];
     out->attn_pairs = st[ST_PAIRS];
+    out->inc_base_rows = st[ST_INC_BASE];
+    out->inc_patched_rows = st[ST_INC_PATCHED];
+    out->inc_certified_rows = st[ST_INC_CERT];
+    out->inc_full_rows = st[ST_INC_FULL];
+    out->inc_searched_rows = st[ST_INC_VQ];
+    out->inc_patch_pairs = st[ST_INC_PPAIRS];
+    out->inc_full_pairs = st[ST_INC_FPAIRS];
     // analytic FLOPs, 2 per multiply-add
     const double d = ctx->d, K = ctx->K, N = ctx->N, Ly = ctx->layers;
     const double rows = (double)out->rows, cfgs = (double)out->configs;
@@ -904,7 +1004,14 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & VQNQS_INCREMENTAL) {
+        if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (!incremental_supported(ctx->d, ctx->heads))
+            return fail(ctx, VQNQS_ERR_ARG,
+                        "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
+                        "a multiple of d_model/32");
+    }
     if (seeds && e_loc) return fail(ctx, VQNQS_ERR_ARG, "give seeds or e_loc, not both");
     if (!O && !grad) return fail(ctx, VQNQS_ERR_ARG, "nothing to compute: O and grad are NULL");
     if (B == 0) return VQNQS_OK;

@@ -20,8 +20,12 @@ enum {
     CNT_R = 1,      // rows = C * N
     CNT_A = 2,      // active rows: rows whose attention and codeword are computed
     CNT_V = 3,      // incremental path: rows of the current layer listed for the codeword search
-    CNT_U0 = 4,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
-    CNT_SLOTS = 4 + VQNQS_MAX_LAYERS + 2
+    CNT_TCL = 4,    //   connected configurations patched on the tensor cores (list length)
+    CNT_SCL = 5,    //   connected configurations patched on the CUDA cores (list length)
+    CNT_TCW = 6,    //   work counters of the two patch kernels (next list entry)
+    CNT_SCW = 7,
+    CNT_U0 = 8,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
+    CNT_SLOTS = 8 + VQNQS_MAX_LAYERS + 2
 };
 
 // Slots of the context's persistent device statistics (int64).
@@ -190,7 +194,7 @@ cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_
 bool attention_tc_supported(int N, int dh);
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list = nullptr,
-                                int n_list = 0, float2* stats = nullptr);
+                                int n_list = 0, float2* stats = nullptr, const int* n_list_dev = nullptr);
 
 // BF16 tensor-core GEMM (k_gemm_tc.cu): C[M,N] = A[M,K] @ Bt[N,K]^T + bias, M = counters[u_slot]
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
@@ -220,20 +224,36 @@ cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, con
 
 // incremental evaluation of the connected configurations (k_incremental.cu)
 bool incremental_supported(int d, int heads);
+bool patch_tc_supported(int d, int heads);  // BF16 path: rows patched on the tensor cores
+// attention of listed rows sharing a sample's keys except at changed positions (k_attn_rows_tc.cu)
+bool attention_rows_tc_supported(int N, int d, int heads);
+cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
+                                     const int2* list, const int* act_off, const int* count, const short* dpos,
+                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms);
+// per connected configuration: changed positions (first INC_MAX_KEYS), their count, and the work list it joins
+// (BF16 path: tensor-core patch, or recomputed whole with its rows searched; FP32 path: CUDA-core patch)
+cudaError_t launch_inc_classify(const Chunk& ch, const int* uid, int tc_ok, int* list_tc, int* list_simt, short* dpos,
+                                int* dcnt, int* vq_rows, long long* stats, cudaStream_t st, int grid);
 cudaError_t launch_codeword_dist(const float* W, int K, int d, float* wd, cudaStream_t st);
 cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
                              const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
-                             int* counters, cudaStream_t st);
+                             int* counters, int* rc_cnt, cudaStream_t st);
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, float* O, const float2* bstat,
-                             const CertRow* cert, const float* codebook, int* code, uint8_t* mode, int* vq_rows,
-                             long long* stats, cudaStream_t st, int grid);
+                             const CertRow* cert, const float* codebook, int* code, int* vq_rows,
+                             const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
+                             const int* dcnt, int use_tc, int* status, long long* stats, cudaStream_t st,
+                             int grid);
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                             const float2* bstat, const CertRow* cert, const float* codebook, int* code, uint8_t* mode,
-                             int* vq_rows, long long* stats, cudaStream_t st, int grid);
-cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const uint8_t* mode,
-                                 long long* stats, cudaStream_t st, int num_sms);
+                             const float2* bstat, const CertRow* cert, const float* codebook, int* code,
+                             int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
+                             const int* dcnt, int use_tc, int* status, long long* stats,
+                             cudaStream_t st, int grid);
+cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
+                                 const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,
+                                 int num_sms);
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                                 const uint8_t* mode, long long* stats, cudaStream_t st, int num_sms);
+                                 const int* act_off, const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats,
+                                 cudaStream_t st, int num_sms);
 
 // dedupe (k_dedupe.cu); with prefix reuse a row before its configuration's first changed
 // position takes the code of the same position of the sample's own configuration.
