@@ -127,3 +127,12 @@ def make_samples(L: int, B: int, seed: int = 1) -> np.ndarray:
         up = np.argsort(keys, kind="stable")[: N // 2]
         out[b, up] = 1
     return out
+
+
+def make_chain_samples(N: int, B: int, seed: int = 1) -> np.ndarray:
+    """B configurations of an N-site chain with independent uniform spins, uint8 [B, N]
+    (spin p of sample b is up when uniform number p of stream seed * 2^32 + b is below 1/2)."""
+    out = np.zeros((B, N), dtype=np.uint8)
+    for b in range(B):
+        out[b] = (uniforms((seed << 32) + b, N) < 0.5).astype(np.uint8)
+    return out
