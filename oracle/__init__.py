@@ -13,6 +13,7 @@ Modules:
   model        the autoregressive VQ transformer  log psi  (Sec. 3.1, Eq. vq)
   hamiltonian  bonds and the local energy  (Sec. 2 Eq. local-energy, Sec. 4)
   tfim         the chain transverse-field Ising model's local energy (Sec. 2, Sec. 4)
+  sampler      exact autoregressive sampling with given uniforms (Sec. 2)
   sector       S_z = 0 sector, independently built H, Rayleigh quotient,
                Lanczos  (Sec. 2 Rayleigh quotient)
   gradient     straight-through O_k and the VMC energy gradient
@@ -22,4 +23,4 @@ Parity status: the forward pass has no printed value in the paper; it is
 pinned by invariants (autoregressive normalisation, causality, a composition of
 library modules, closed forms) rather than by a worked example.
 """
-from . import model, hamiltonian, sector, gradient, tfim  # noqa: F401
+from . import model, hamiltonian, sector, gradient, sampler, tfim  # noqa: F401
