@@ -8,7 +8,8 @@
  *
  * for the spin-1/2 Heisenberg model H = J sum_<ij> S_i . S_j on an L x L
  * square lattice (Sec. 4), in the Marshall-rotated basis where psi > 0 and
- * the phase is zero (Sec. 4).  psi(s) = sqrt(P(s)) with P an autoregressive
+ * the phase is zero (Sec. 4), or for the transverse-field Ising chain of
+ * Sec. 4 (vqnqs_create_tfim).  psi(s) = sqrt(P(s)) with P an autoregressive
  * decoder transformer, one token per spin, whose blocks insert a vector
  * quantizer between the self-attention and its output projection (Sec. 3.1,
  * Eq. vq).  Per-location work whose quantized input was already seen is done
@@ -123,6 +124,18 @@ size_t vqnqs_num_params(int n_max, int layers, int d_model, int K);
 int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int heads, int K,
                  const float* weights, vqnqs_ctx** out);
 
+/* Create a context for the transverse-field Ising chain of Sec. 4,
+ *     H = -J sum_<ij> sigma^z_i sigma^z_j - Gamma sum_i sigma^x_i,
+ * whose connected configurations are the N single spin flips (Sec. 2; all
+ * off-diagonal elements -Gamma, so psi > 0 with zero phase).
+ *   N        sites (2 <= N <= 512); bonds (p, p+1), and (N-1, 0) when periodic (N > 2)
+ *   J, Gamma couplings (the paper's workload: open chain, J = Gamma = 1, N up to 384)
+ *   other arguments as vqnqs_create, with n_max = N in the weight blob.
+ * Every entry point except vqnqs_local_energy_ragged accepts such a context;
+ * any configuration of N bits is a valid sample. */
+int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, int d_model, int heads, int K,
+                      const float* weights, vqnqs_ctx** out);
+
 /* Replace the weights (HOST blob when is_device == 0, DEVICE blob otherwise) and
  * rebuild the derived tables on `stream`. */
 int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream);
@@ -163,6 +176,42 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
  * Same flags, workspace and stream rules as vqnqs_log_psi. */
 int vqnqs_codes(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int* dev_codes, float* dev_log_psi, int flags,
                 void* dev_ws, size_t ws_bytes, void* stream);
+
+/* Autoregressive direct sampling (Sec. 2: psi = sqrt(P) with P a product of
+ * conditionals, so configurations are drawn exactly from |psi|^2 one site at a
+ * time, without a Markov chain).  Site p of sample b is up when
+ * dev_uniforms[b][p] < P(s_p = up | s_<p); the random numbers are the caller's.
+ *   dev_uniforms DEVICE float [B][N], values in [0, 1)
+ *   dev_spins    DEVICE uint8 [B][N] (output)
+ *   dev_log_psi  DEVICE float [B] (output): log psi of the drawn configurations
+ *   flags        VQNQS_BF16 for the tensor-core GEMMs (others ignored)
+ *   dev_ws       DEVICE workspace (vqnqs_sample_workspace_bytes), 256-byte aligned;
+ *                a smaller one draws fewer samples at a time (minimum one)
+ * Each position runs every block on the batch's rows with the keys and values
+ * of the earlier positions kept in the workspace. */
+size_t vqnqs_sample_workspace_bytes(const vqnqs_ctx* ctx, int chunk_samples, int flags);
+int vqnqs_sample(vqnqs_ctx* ctx, int B, const float* dev_uniforms, uint8_t* dev_spins, float* dev_log_psi,
+                 int flags, void* dev_ws, size_t ws_bytes, void* stream);
+
+/* One variational Monte Carlo step (Sec. 2): B configurations drawn from
+ * |psi|^2 with the given uniforms (vqnqs_sample), their local energies, the
+ * energy gradient grad_k = 2 mean[(E_loc - mean E_loc) O_k] (vqnqs_grad_log_psi,
+ * Eq. st for the quantizers), then the weights updated in place,
+ * theta <- theta - lr * grad (in FP32, the product and the difference each
+ * rounded), and their derived tables rebuilt.
+ *   dev_uniforms DEVICE float [B][N];  lr the step size
+ *   dev_spins    DEVICE uint8 [B][N] (output: the drawn configurations)
+ *   dev_e_loc    DEVICE float [B] (output)
+ *   dev_grad     DEVICE float [P] (output: the gradient that was applied)
+ *   dev_mean_var DEVICE double [2] (output: FP64 mean and variance of E_loc)
+ *   flags        as vqnqs_local_energy (they also select the sampler's GEMMs)
+ *   dev_ws       DEVICE workspace of vqnqs_vmc_workspace_bytes(ctx, B, flags) bytes */
+size_t vqnqs_vmc_workspace_bytes(const vqnqs_ctx* ctx, int B, int flags);
+int vqnqs_vmc_step(vqnqs_ctx* ctx, int B, const float* dev_uniforms, float lr, uint8_t* dev_spins, float* dev_e_loc,
+                   float* dev_grad, double* dev_mean_var, int flags, void* dev_ws, size_t ws_bytes, void* stream);
+
+/* Copies the context's current weight blob (vqnqs_num_params floats) to dev_weights. */
+int vqnqs_get_weights(vqnqs_ctx* ctx, float* dev_weights, void* stream);
 
 /* Local energies (Sec. 2, Eq. local-energy) of B samples.
  *   dev_e_loc     DEVICE float [B] (output): per-lattice E_loc(s) in units of J S.S

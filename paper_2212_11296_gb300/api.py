@@ -56,6 +56,27 @@ class VQNQS:
         self._h = h
         self._ws = {}
 
+    @classmethod
+    def tfim_chain(cls, N: int, periodic: bool, J: float, Gamma: float, layers: int, d_model: int, heads: int,
+                   K: int, weights: np.ndarray) -> "VQNQS":
+        """The transverse-field Ising chain of N sites: vqnqs_create_tfim(N, periodic, J, Gamma, ...)."""
+        self = cls.__new__(cls)
+        self.L, self.N = None, N
+        self.periodic, self.J, self.Gamma = bool(periodic), float(J), float(Gamma)
+        self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        n = lib().vqnqs_num_params(N, layers, d_model, K)
+        if w.size != n:
+            raise ValueError(f"weight blob has {w.size} floats, layout needs {n}")
+        h = ctypes.c_void_p()
+        rc = lib().vqnqs_create_tfim(N, int(periodic), float(J), float(Gamma), layers, d_model, heads, K,
+                                     w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        if rc != 0:
+            raise VQNQSError(f"vqnqs_create_tfim failed: {_lib.STATUS_NAMES.get(rc, rc)}")
+        self._h = h
+        self._ws = {}
+        return self
+
     def close(self):
         if getattr(self, "_h", None):
             lib().vqnqs_destroy(self._h)
@@ -103,6 +124,49 @@ class VQNQS:
                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                         ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_log_psi")
         return out
+
+    def sample(self, uniforms: torch.Tensor, flags: int = 0, chunk_samples: int = 0, stream=None):
+        """Configurations drawn from |psi|^2 with the given uniforms [B, N] (see vqnqs_sample);
+        returns (spins uint8 [B, N], log psi float [B])."""
+        _check_dev(uniforms, torch.float32, "uniforms")
+        if uniforms.dim() != 2 or uniforms.shape[1] != self.N:
+            raise ValueError(f"uniforms must be [B, {self.N}]")
+        B = uniforms.shape[0]
+        spins = torch.empty(B, self.N, dtype=torch.uint8, device=uniforms.device)
+        lp = torch.empty(B, dtype=torch.float32, device=uniforms.device)
+        n = int(lib().vqnqs_sample_workspace_bytes(self._h, int(chunk_samples or min(B, 1024)), int(flags)))
+        ws = torch.empty(n, dtype=torch.uint8, device=uniforms.device)
+        self._check(lib().vqnqs_sample(self._h, B, ctypes.c_void_p(uniforms.data_ptr()),
+                                       ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(lp.data_ptr()), int(flags),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_sample")
+        return spins, lp
+
+    def vmc_step(self, uniforms: torch.Tensor, lr: float, flags: int = 0, stream=None) -> dict:
+        """One VMC step (see vqnqs_vmc_step); returns the drawn spins, E_loc, the applied
+        gradient and the FP64 [mean, var] of E_loc (device tensors)."""
+        _check_dev(uniforms, torch.float32, "uniforms")
+        B = uniforms.shape[0]
+        dev = uniforms.device
+        out = {"spins": torch.empty(B, self.N, dtype=torch.uint8, device=dev),
+               "e_loc": torch.empty(B, dtype=torch.float32, device=dev),
+               "grad": torch.empty(self.num_params, dtype=torch.float32, device=dev),
+               "mean_var": torch.empty(2, dtype=torch.float64, device=dev)}
+        ws = torch.empty(int(lib().vqnqs_vmc_workspace_bytes(self._h, B, int(flags))), dtype=torch.uint8, device=dev)
+        self._check(lib().vqnqs_vmc_step(self._h, B, ctypes.c_void_p(uniforms.data_ptr()), float(lr),
+                                         ctypes.c_void_p(out["spins"].data_ptr()), ctypes.c_void_p(out["e_loc"].data_ptr()),
+                                         ctypes.c_void_p(out["grad"].data_ptr()),
+                                         ctypes.c_void_p(out["mean_var"].data_ptr()), int(flags),
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_vmc_step")
+        return out
+
+    def weights(self, stream=None) -> torch.Tensor:
+        """The current weight blob (device copy)."""
+        w = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        self._check(lib().vqnqs_get_weights(self._h, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_get_weights")
+        return w
 
     def codes(self, spins: torch.Tensor, flags: int = 0, workspace: torch.Tensor | None = None, stream=None):
         """(codes [B, layers, N] int32, log psi [B]) of the configurations as given (see vqnqs_codes)."""

@@ -4,13 +4,15 @@
 
 namespace vq {
 
-// ---- bonds: diagonal energy and anti-aligned count per sample ------------------
-// Sec. 4: H = J sum_<ij> S_i.S_j.  In the Marshall-rotated S^z basis a bond gives
-// (J/4) sigma_i sigma_j on the diagonal and -J/2 to the configuration with the
-// two spins exchanged when they differ (Sec. 2: a k-local term touches only its
-// own sites).
-__global__ void k_count_configs(Chunk ch, float J, int with_bonds, int* __restrict__ cnt, float* __restrict__ diag,
-                                int* __restrict__ status) {
+// ---- bonds: diagonal energy and connected-configuration count per sample -----------
+// Sec. 4 Heisenberg model, H = J sum_<ij> S_i.S_j: in the Marshall-rotated S^z
+// basis a bond gives (J/4) sigma_i sigma_j on the diagonal and -J/2 to the
+// configuration with the two spins exchanged when they differ (Sec. 2: a
+// k-local term touches only its own sites).  Sec. 4 transverse-field Ising
+// chain, H = -J sum sigma^z sigma^z - Gamma sum sigma^x: -J sigma_i sigma_j per
+// bond on the diagonal, -Gamma to each of the N single flips (Sec. 2).
+__global__ void k_count_configs(Chunk ch, float diag_coef, int with_bonds, int* __restrict__ cnt,
+                                float* __restrict__ diag, int* __restrict__ status) {
     __shared__ int s_red[2][32];
     for (int b = blockIdx.x; b < ch.S; b += gridDim.x) {
         const int g = sample_group(ch, b);
@@ -39,8 +41,8 @@ __global__ void k_count_configs(Chunk ch, float J, int with_bonds, int* __restri
         if (threadIdx.x == 0) {
             int a = 0, z = 0;
             for (int i = 0; i < nw; ++i) { a += s_red[0][i]; z += s_red[1][i]; }
-            cnt[b] = a;
-            diag[b] = 0.25f * J * (float)z;
+            cnt[b] = (ch.model == MODEL_TFIM_CHAIN && with_bonds) ? N : a;
+            diag[b] = diag_coef * (float)z;
         }
         __syncthreads();
     }
@@ -105,6 +107,14 @@ __global__ void k_fill_configs(Chunk ch, int with_bonds, int* __restrict__ cfg_s
         const int off = ch.cfg_off[b];
         if (threadIdx.x == 0) { cfg_sample[off] = b; cfg_i[off] = -1; cfg_j[off] = -1; }
         if (!with_bonds) continue;
+        if (ch.model == MODEL_TFIM_CHAIN) {  // every single flip, in site order
+            for (int q = threadIdx.x; q < ch.g.N[g]; q += blockDim.x) {
+                cfg_sample[off + 1 + q] = b;
+                cfg_i[off + 1 + q] = q;
+                cfg_j[off + 1 + q] = CFG_FLIP;
+            }
+            continue;
+        }
         int run = off + 1;
         for (int base = 0; base < nb; base += blockDim.x) {
             int t = base + threadIdx.x;
@@ -283,7 +293,7 @@ __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float*
 }
 
 // E_loc(s) = (J/4) sum_b sigma_i sigma_j - (J/2) sum_c psi(s^c)/psi(s); one warp per sample.
-__global__ void k_eloc_reduce(Chunk ch, const float* __restrict__ diag, const float* __restrict__ ratio, float J,
+__global__ void k_eloc_reduce(Chunk ch, const float* __restrict__ diag, const float* __restrict__ ratio, float offdiag,
                               float* __restrict__ e_loc) {
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < ch.S; b += gridDim.x * wpb) {
@@ -291,7 +301,7 @@ __global__ void k_eloc_reduce(Chunk ch, const float* __restrict__ diag, const fl
         float acc = 0.f;
         for (int c = c0 + lane; c < c1; c += 32) acc += ratio[c];
         acc = warp_sum(acc);
-        if (lane == 0) e_loc[b] = diag[b] - 0.5f * J * acc;
+        if (lane == 0) e_loc[b] = diag[b] + offdiag * acc;
     }
 }
 
@@ -336,10 +346,10 @@ __global__ void k_accumulate_stats(const int* __restrict__ counters, int layers,
 }
 
 // ---- launchers -----------------------------------------------------------------
-cudaError_t launch_configs(const Chunk& ch, float J, int with_bonds, int* cnt, float* diag, int* cfg_off,
+cudaError_t launch_configs(const Chunk& ch, float diag_coef, int with_bonds, int* cnt, float* diag, int* cfg_off,
                            int* cfg_sample, int* cfg_i, int* cfg_j, int* cfg_row, int* row_cfg, int* status,
                            cudaStream_t st, int grid) {
-    k_count_configs<<<grid, 256, 0, st>>>(ch, J, with_bonds, cnt, diag, status);
+    k_count_configs<<<grid, 256, 0, st>>>(ch, diag_coef, with_bonds, cnt, diag, status);
     k_scan_configs<<<1, 1024, 0, st>>>(ch, cnt, cfg_off);
     k_fill_configs<<<grid, 256, 0, st>>>(ch, with_bonds, cfg_sample, cfg_i, cfg_j);
     k_scan_rows<<<1, 1024, 0, st>>>(ch, cfg_row);
@@ -389,9 +399,9 @@ cudaError_t launch_eloc(const Chunk& ch, const int* uid, const float* logp, floa
     k_eloc_ratio<<<grid, 256, 0, st>>>(ch, uid, logp, ratio, log_psi_out);
     return cudaGetLastError();
 }
-cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* ratio, float J, float* e_loc_out,
-                               cudaStream_t st, int grid) {
-    k_eloc_reduce<<<grid, 256, 0, st>>>(ch, diag, ratio, J, e_loc_out);
+cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* ratio, float offdiag,
+                               float* e_loc_out, cudaStream_t st, int grid) {
+    k_eloc_reduce<<<grid, 256, 0, st>>>(ch, diag, ratio, offdiag, e_loc_out);
     return cudaGetLastError();
 }
 cudaError_t launch_mean_var(const float* e_loc, int B, double* mean_var, cudaStream_t st) {

@@ -14,7 +14,9 @@ using namespace vq;
 
 struct vqnqs_ctx {
     int L = 0, N = 0, periodic = 0, layers = 0, d = 0, heads = 0, K = 0, nb = 0;
-    double J = 1.0;
+    int model = MODEL_HEISENBERG;
+    int max_conn = 0;  // connected configurations per sample at most (bonds, or sites for the Ising chain)
+    double J = 1.0, Gamma = 0.0;
     int device = 0, num_sms = 0;
     size_t nparams = 0;
     float* blob = nullptr;  // device copy of the weight blob
@@ -187,13 +189,13 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
 
 // Uniform chunks of S samples of the context's lattice (worst case: every bond anti-aligned).
 Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
-    const long long C = (long long)S * (with_bonds ? (1 + c->nb) : 1);
+    const long long C = (long long)S * (with_bonds ? (1 + c->max_conn) : 1);
     return make_plan_budget(c, S, C, C * c->N);
 }
 
 int default_chunk(const vqnqs_ctx* c, bool with_bonds) {
     // aim for about 2M token rows per chunk in the worst case
-    long long per = (long long)(with_bonds ? (1 + c->nb) : 1) * c->N;
+    long long per = (long long)(with_bonds ? (1 + c->max_conn) : 1) * c->N;
     long long s = (2LL << 20) / per;
     if (s < 1) s = 1;
     if (s > 65536) s = 65536;
@@ -286,7 +288,7 @@ Groups uniform_groups(const vqnqs_ctx* c, int B) {
 Chunk make_chunk(const vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& g, int s0, int S) {
     Chunk ch;
     ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = g; ch.s0 = s0; ch.S = S;
-    ch.N = ctx->N; ch.d = ctx->d; ch.heads = ctx->heads; ch.K = ctx->K;
+    ch.N = ctx->N; ch.d = ctx->d; ch.heads = ctx->heads; ch.K = ctx->K; ch.model = ctx->model;
     ch.cfg_sample = at<int>(ws, P.cfg_sample);
     ch.cfg_i = at<int>(ws, P.cfg_i);
     ch.cfg_j = at<int>(ws, P.cfg_j);
@@ -307,7 +309,9 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
     Chunk ch = make_chunk(ctx, P, ws, spins, grp, s0, S);
     float* diag = at<float>(ws, P.diag);
     const int g_s = grid_for(ctx, S, 1, 8);
-    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, (float)ctx->J, with_bonds, at<int>(ws, P.cnt), diag,
+    const float diag_coef = ctx->model == MODEL_TFIM_CHAIN ? (float)-ctx->J : (float)(0.25 * ctx->J);
+    const float offdiag = ctx->model == MODEL_TFIM_CHAIN ? (float)-ctx->Gamma : (float)(-0.5 * ctx->J);
+    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, diag_coef, with_bonds, at<int>(ws, P.cnt), diag,
                                          at<int>(ws, P.cfg_off), at<int>(ws, P.cfg_sample), at<int>(ws, P.cfg_i),
                                          at<int>(ws, P.cfg_j), at<int>(ws, P.cfg_row), at<int>(ws, P.row_cfg),
                                          ctx->status, st, g_s));
@@ -459,7 +463,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         StageScope scope_(ctx, S_ELOC, e_loc_out ? 2 : 1, st);
         VQ_CK(launch_eloc(ch, uid_cur, logp, ratio, log_psi_out, st, grid_for(ctx, P.Cmax, 8, 16)));
         if (e_loc_out)
-            VQ_CK(launch_eloc_reduce(ch, diag, ratio, (float)ctx->J, e_loc_out, st, grid_for(ctx, S, 8, 16)));
+            VQ_CK(launch_eloc_reduce(ch, diag, ratio, offdiag, e_loc_out, st, grid_for(ctx, S, 8, 16)));
     }
     ctx->launches += 1;
     VQ_CK(launch_accumulate_stats(counters, ctx->layers, S, ctx->stats, st));
@@ -587,6 +591,7 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     int* counters = at<int>(ws, P.counters);
     Chunk ch;
     ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = uniform_groups(ctx, S); ch.s0 = 0; ch.S = S;
+    ch.model = ctx->model;
     ch.N = N; ch.d = d; ch.heads = H; ch.K = K;
     ch.cfg_sample = at<int>(ws, P.cfg_sample); ch.cfg_i = at<int>(ws, P.cfg_i); ch.cfg_j = at<int>(ws, P.cfg_j);
     ch.cfg_off = at<int>(ws, P.cfg_off); ch.cfg_row = at<int>(ws, P.cfg_row); ch.row_cfg = at<int>(ws, P.row_cfg);
@@ -607,7 +612,7 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     const int g_rows = grid_for(ctx, R, 8, 16);
 
     // forward, keeping x_l and the codes
-    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, (float)ctx->J, 0, at<int>(ws, P.cnt), at<float>(ws, P.diag),
+    VQ_STAGE(S_CONFIG, 5, launch_configs(ch, 0.f, 0, at<int>(ws, P.cnt), at<float>(ws, P.diag),
                                          at<int>(ws, P.cfg_off), at<int>(ws, P.cfg_sample), at<int>(ws, P.cfg_i),
                                          at<int>(ws, P.cfg_j), at<int>(ws, P.cfg_row), at<int>(ws, P.row_cfg),
                                          ctx->status, st, grid_for(ctx, S, 1, 8)));
@@ -727,17 +732,20 @@ size_t vqnqs_num_params(int n_max, int layers, int d_model, int K) {
     return 3 * d + (size_t)n_max * d + (size_t)layers * per + 2 * d + 2 * d + 2;
 }
 
-int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int heads, int K, const float* weights,
-                 vqnqs_ctx** out) {
+namespace {
+// Shared by vqnqs_create (L x L Heisenberg lattice) and vqnqs_create_tfim (N-site chain).
+int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, int layers, int d_model, int heads,
+               int K, const float* weights, vqnqs_ctx** out) {
     if (!out) return VQNQS_ERR_ARG;
     *out = nullptr;
-    if (L < 2 || L * L > 512 || layers < 1 || layers > VQNQS_MAX_LAYERS || d_model < 32 || d_model % 32 ||
+    if (N < 2 || N > 512 || layers < 1 || layers > VQNQS_MAX_LAYERS || d_model < 32 || d_model % 32 ||
         d_model > 1024 || heads < 1 || d_model % heads || K < 1 || K > 65535 || !weights)
         return VQNQS_ERR_ARG;
     const int dh = d_model / heads;
     if (!(dh == 8 || dh == 16 || dh == 32)) return VQNQS_ERR_ARG;
     vqnqs_ctx* ctx = new vqnqs_ctx();
-    ctx->L = L; ctx->N = L * L; ctx->periodic = periodic ? 1 : 0; ctx->J = J;
+    ctx->model = model;
+    ctx->L = L; ctx->N = N; ctx->periodic = periodic ? 1 : 0; ctx->J = J; ctx->Gamma = Gamma;
     ctx->layers = layers; ctx->d = d_model; ctx->heads = heads; ctx->K = K;
     auto bail = [&](int code) { vqnqs_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(VQNQS_ERR_CUDA);
@@ -751,18 +759,27 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
         return p;
     };
     ctx->blob = static_cast<float*>(dalloc(ctx->nparams * sizeof(float)));
-    std::vector<int> bonds = make_bonds(L, ctx->periodic);
-    ctx->nb = (int)bonds.size() / 2;
-    ctx->bonds = static_cast<int*>(dalloc(bonds.size() * sizeof(int)));
-    std::vector<int> all;
-    ctx->side_bond_off.assign(L + 1, 0);
-    ctx->side_nb.assign(L + 1, 0);
-    for (int s = 2; s <= L; ++s) {
-        std::vector<int> b = make_bonds(s, ctx->periodic);
-        ctx->side_bond_off[s] = (int)all.size() / 2;
-        ctx->side_nb[s] = (int)b.size() / 2;
-        all.insert(all.end(), b.begin(), b.end());
+    std::vector<int> bonds, all;
+    if (model == MODEL_TFIM_CHAIN) {  // (p, p+1), and (N-1, 0) when periodic; one bond table (index 0)
+        for (int q = 0; q + 1 < N; ++q) { bonds.push_back(q); bonds.push_back(q + 1); }
+        if (ctx->periodic && N > 2) { bonds.push_back(N - 1); bonds.push_back(0); }
+        all = bonds;
+        ctx->side_bond_off.assign(1, 0);
+        ctx->side_nb.assign(1, (int)bonds.size() / 2);
+    } else {  // the lattice's bonds, and those of every side 2 .. L for ragged batches
+        bonds = make_bonds(L, ctx->periodic);
+        ctx->side_bond_off.assign(L + 1, 0);
+        ctx->side_nb.assign(L + 1, 0);
+        for (int s = 2; s <= L; ++s) {
+            std::vector<int> b = make_bonds(s, ctx->periodic);
+            ctx->side_bond_off[s] = (int)all.size() / 2;
+            ctx->side_nb[s] = (int)b.size() / 2;
+            all.insert(all.end(), b.begin(), b.end());
+        }
     }
+    ctx->nb = (int)bonds.size() / 2;
+    ctx->max_conn = model == MODEL_TFIM_CHAIN ? N : ctx->nb;
+    ctx->bonds = static_cast<int*>(dalloc(bonds.size() * sizeof(int)));
     ctx->bonds_all = static_cast<int*>(dalloc(all.size() * sizeof(int)));
     ctx->status = static_cast<int*>(dalloc(sizeof(int)));
     ctx->stats = static_cast<long long*>(dalloc(ST_SLOTS * sizeof(long long)));
@@ -814,6 +831,21 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
     *out = ctx;
     return VQNQS_OK;
 }
+}  // namespace
+
+int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int heads, int K, const float* weights,
+                 vqnqs_ctx** out) {
+    if (L < 2 || L * L > 512) {
+        if (out) *out = nullptr;
+        return VQNQS_ERR_ARG;
+    }
+    return create_ctx(MODEL_HEISENBERG, L, L * L, periodic, J, 0.0, layers, d_model, heads, K, weights, out);
+}
+
+int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, int d_model, int heads, int K,
+                      const float* weights, vqnqs_ctx** out) {
+    return create_ctx(MODEL_TFIM_CHAIN, 0, N, periodic, J, Gamma, layers, d_model, heads, K, weights, out);
+}
 
 int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream) {
     if (!ctx || !weights) return VQNQS_ERR_ARG;
@@ -840,6 +872,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
                               float* e_loc, double* mean_var, int flags, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
+    if (ctx->model != MODEL_HEISENBERG) return fail(ctx, VQNQS_ERR_ARG, "ragged: square-lattice contexts only");
     if (n_groups < 1 || n_groups > MAX_GROUPS || !L_g || !B_g)
         return fail(ctx, VQNQS_ERR_ARG, "ragged: need 1..8 groups and host arrays L_g, B_g");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
@@ -1162,6 +1195,183 @@ int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* ws, size_t ws_bytes, vqnqs_tunin
     out->mlp_up_bn = ctx->bn[1];
     out->mlp_down_bn = ctx->bn[2];
     return build_weight_tmaps(ctx);
+}
+
+// ---- autoregressive sampling -----------------------------------------------------
+namespace {
+struct SamplePlan {
+    int S = 0;
+    size_t counters, rows, X, Xn, Y, A, qkv, O, H1, code, logp, cache, total;
+};
+
+// Workspace of a chunk of S samples: per-row buffers of one position and the
+// keys and values of every layer and position ([layer][S][N][2d], FP32 or BF16).
+SamplePlan make_sample_plan(const vqnqs_ctx* c, int S, bool bf16) {
+    SamplePlan p;
+    p.S = S;
+    const size_t d = c->d, f = sizeof(float), e = bf16 ? 2 : 4;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    p.counters = take(CNT_SLOTS * sizeof(int));
+    p.rows = take((size_t)S * sizeof(int));
+    p.X = take((size_t)S * d * f);
+    p.Xn = take((size_t)S * d * f);
+    p.Y = take((size_t)S * d * f);
+    p.A = take((size_t)S * d * f);
+    p.qkv = take((size_t)S * 3 * d * f);
+    p.O = take((size_t)S * d * f);
+    p.H1 = take((size_t)S * 4 * d * f);
+    p.code = take((size_t)S * sizeof(int));
+    p.logp = take((size_t)S * 2 * f);
+    p.cache = take((size_t)c->layers * S * c->N * 2 * d * e);
+    p.total = o;
+    return p;
+}
+}  // namespace
+
+size_t vqnqs_sample_workspace_bytes(const vqnqs_ctx* ctx, int chunk_samples, int flags) {
+    if (!ctx) return 0;
+    const int S = chunk_samples > 0 ? chunk_samples : 1024;
+    return make_sample_plan(ctx, S, (flags & VQNQS_BF16) != 0).total;
+}
+
+int vqnqs_sample(vqnqs_ctx* ctx, int B, const float* uniforms, uint8_t* spins, float* log_psi, int flags, void* ws,
+                 size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    const bool bf16 = (flags & VQNQS_BF16) != 0;
+    if (bf16 && ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
+    if (B == 0) return VQNQS_OK;
+    if (!uniforms || !spins || !log_psi) return fail(ctx, VQNQS_ERR_ARG, "uniforms, spins and log_psi are required");
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return fail(ctx, VQNQS_ERR_ARG, "workspace must be 256-byte aligned");
+    // largest chunk whose workspace fits
+    int lo = 0, hi = B;
+    while (lo < hi) {
+        const int mid = lo + (hi - lo + 1) / 2;
+        if (make_sample_plan(ctx, mid, bf16).total <= ws_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    if (lo == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "workspace smaller than the one-sample minimum");
+    const SamplePlan P = make_sample_plan(ctx, lo, bf16);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N = ctx->N, d = ctx->d, K = ctx->K, H = ctx->heads;
+    int* counters = at<int>(ws, P.counters);
+    int* rows = at<int>(ws, P.rows);
+    float* X = at<float>(ws, P.X);
+    float* Xn = at<float>(ws, P.Xn);
+    float* Y = at<float>(ws, P.Y);
+    float* A = at<float>(ws, P.A);
+    float* qkv = at<float>(ws, P.qkv);
+    float* O = at<float>(ws, P.O);
+    float* H1 = at<float>(ws, P.H1);
+    int* code = at<int>(ws, P.code);
+    float* logp = at<float>(ws, P.logp);
+    __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(A);
+    __nv_bfloat16* qkv16 = reinterpret_cast<__nv_bfloat16*>(qkv);
+    __nv_bfloat16* H16 = reinterpret_cast<__nv_bfloat16*>(H1);
+    const size_t cache_layer = (size_t)P.S * N * 2 * d;
+    for (int s0 = 0; s0 < B; s0 += P.S) {
+        const int S = std::min(P.S, B - s0);
+        const float* u = uniforms + (size_t)s0 * N;
+        uint8_t* sp = spins + (size_t)s0 * N;
+        float* lp = log_psi + s0;
+        const int g_rows = grid_for(ctx, S, 8, 16);
+        ctx->launches += 1;
+        VQ_CK(launch_assign_setup(counters, rows, S, st));  // S rows, listed 0 .. S-1
+        for (int p = 0; p < N; ++p) {
+            ctx->launches += 1;
+            VQ_CK(launch_sample_embed(S, p, N, d, sp, ctx->tok_emb, ctx->pos_emb, X, st));
+            for (int l = 0; l < ctx->layers; ++l) {
+                const LayerW& w = ctx->lw[l];
+                ctx->launches += 7;
+                if (bf16) {
+                    __nv_bfloat16* cache = reinterpret_cast<__nv_bfloat16*>(at<uint8_t>(ws, P.cache)) + l * cache_layer;
+                    VQ_CK(launch_layernorm(X, counters, CNT_A, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_rows));
+                    VQ_CK(launch_gemm_tc(A16, P.S, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, CNT_A, 3 * d, d, 0,
+                                         ctx->status, st, ctx->num_sms, ctx->bn[0]));
+                    VQ_CK(launch_decode_attention(S, p, N, d, H, qkv16, cache, O, st));
+                } else {
+                    float* cache = at<float>(ws, P.cache) + l * cache_layer;
+                    VQ_CK(launch_layernorm(X, counters, CNT_A, w.ln1_g, w.ln1_b, d, A, nullptr, st, g_rows));
+                    VQ_CK(launch_sgemm(A, w.w_qkv, w.b_qkv, nullptr, qkv, counters, CNT_A, P.S, 3 * d, d, EPI_BIAS, st,
+                                       ctx->num_sms));
+                    VQ_CK(launch_decode_attention(S, p, N, d, H, qkv, cache, O, st));
+                }
+                if (bf16 && vq_tc_supported(K, d))
+                    VQ_CK(launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, rows, w.cnorm, K, d, code,
+                                       ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, P.S));
+                else
+                    VQ_CK(launch_vq_argmin(O, counters, rows, w.codebook, w.cnorm, K, d, code, ctx->stats + ST_NEAR_TIES,
+                                           P.S, st, ctx->num_sms));
+                if (bf16) {
+                    VQ_CK(launch_residual_vq_ln(X, rows, code, w.T, counters, CNT_A, w.ln2_g, w.ln2_b, d, Y, nullptr,
+                                                A16, st, g_rows));
+                    VQ_CK(launch_gemm_tc(A16, P.S, w.tm_w1, w.b_1, nullptr, H16, counters, CNT_A, 4 * d, d, 1,
+                                         ctx->status, st, ctx->num_sms, ctx->bn[1]));
+                    VQ_CK(launch_gemm_tc(H16, P.S, w.tm_w2, w.b_2, Y, Xn, counters, CNT_A, d, 4 * d, 2, ctx->status, st,
+                                         ctx->num_sms, ctx->bn[2]));
+                } else {
+                    VQ_CK(launch_residual_vq_ln(X, rows, code, w.T, counters, CNT_A, w.ln2_g, w.ln2_b, d, Y, A, nullptr,
+                                                st, g_rows));
+                    VQ_CK(launch_sgemm(A, w.w_1, w.b_1, nullptr, H1, counters, CNT_A, P.S, 4 * d, d, EPI_BIAS_GELU, st,
+                                       ctx->num_sms));
+                    VQ_CK(launch_sgemm(H1, w.w_2, w.b_2, Y, Xn, counters, CNT_A, P.S, d, 4 * d, EPI_BIAS_RESID, st,
+                                       ctx->num_sms));
+                }
+                std::swap(X, Xn);
+            }
+            ctx->launches += 2;
+            VQ_CK(launch_head(X, counters, CNT_A, ctx->lnf_g, ctx->lnf_b, ctx->w_head, ctx->b_head, d, logp, st,
+                              g_rows));
+            VQ_CK(launch_sample_draw(S, p, N, logp, u, sp, lp, st));
+        }
+    }
+    return VQNQS_OK;
+}
+
+// ---- variational Monte Carlo step --------------------------------------------------
+namespace {
+__global__ void k_sgd(float* __restrict__ w, const float* __restrict__ g, size_t n, float lr) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        w[i] = __fsub_rn(w[i], __fmul_rn(lr, g[i]));  // product and difference rounded apart (no FMA)
+}
+}  // namespace
+
+size_t vqnqs_vmc_workspace_bytes(const vqnqs_ctx* ctx, int B, int flags) {
+    if (!ctx || B <= 0) return 0;
+    const size_t a = vqnqs_sample_workspace_bytes(ctx, std::min(B, 1024), flags);
+    const size_t b = vqnqs_workspace_bytes(ctx, 0, flags);
+    const size_t c = vqnqs_grad_workspace_bytes(ctx, B, 0);
+    return std::max(a, std::max(b, c));
+}
+
+int vqnqs_vmc_step(vqnqs_ctx* ctx, int B, const float* uniforms, float lr, uint8_t* spins, float* e_loc, float* grad,
+                   double* mean_var, int flags, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B <= 0 || !uniforms || !spins || !e_loc || !grad || !mean_var)
+        return fail(ctx, VQNQS_ERR_ARG, "vmc step: B > 0 and every buffer are required");
+    // e_loc holds the drawn configurations' log psi until the local energies overwrite it
+    int rc = vqnqs_sample(ctx, B, uniforms, spins, e_loc, flags, ws, ws_bytes, stream);
+    if (rc != VQNQS_OK) return rc;
+    rc = vqnqs_local_energy(ctx, B, spins, e_loc, mean_var, nullptr, flags, ws, ws_bytes, stream);
+    if (rc != VQNQS_OK) return rc;
+    rc = vqnqs_grad_log_psi(ctx, B, spins, nullptr, e_loc, nullptr, grad, flags, ws, ws_bytes, stream);
+    if (rc != VQNQS_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches += 1;
+    k_sgd<<<grid_for(ctx, (long long)ctx->nparams, 256, 8), 256, 0, st>>>(ctx->blob, grad, ctx->nparams, lr);
+    VQ_CK(cudaGetLastError());
+    return build_tables(ctx, st);  // the weights changed: rebuild their derived tables
+}
+
+int vqnqs_get_weights(vqnqs_ctx* ctx, float* weights, void* stream) {
+    if (!ctx || !weights) return VQNQS_ERR_ARG;
+    VQ_CK(cudaMemcpyAsync(weights, ctx->blob, ctx->nparams * sizeof(float), cudaMemcpyDeviceToDevice,
+                          static_cast<cudaStream_t>(stream)));
+    return VQNQS_OK;
 }
 
 int vqnqs_check_timeout_path(vqnqs_ctx* ctx, long long limit_cycles, void* stream) {

@@ -84,6 +84,12 @@ struct Groups {
     long long spin_off[MAX_GROUPS];
 };
 
+// Hamiltonians: the square-lattice Heisenberg model (connected configurations:
+// one nearest-neighbour exchange) and the transverse-field Ising chain
+// (connected configurations: one spin flip; cfg_j = CFG_FLIP).
+enum { MODEL_HEISENBERG = 0, MODEL_TFIM_CHAIN = 1 };
+constexpr int CFG_FLIP = 0x3fffffff;
+
 // Per-chunk view of the problem handed to the kernels.  Rows of a chunk are
 // (configuration, position) pairs stored configuration after configuration;
 // configuration c owns rows cfg_row[c] .. cfg_row[c+1]-1.
@@ -93,6 +99,7 @@ struct Chunk {
     Groups g;
     int s0, S;              // this chunk holds global samples s0 .. s0+S-1 (local index b)
     int N, d, heads, K;     // N: largest number of sites (position-embedding rows)
+    int model;              // MODEL_*
     const int* cfg_sample;  // [C] local sample of each configuration
     const int* cfg_i;       // [C] exchanged site pair (-1 for the sample itself)
     const int* cfg_j;
@@ -121,12 +128,12 @@ __device__ __forceinline__ int cfg_N(const Chunk& ch, int c) { return sample_N(c
 // (Sec. 2: conditionals before the changed site are unchanged).
 __device__ __forceinline__ int cfg_first_changed(int ci, int cj) { return ci < 0 ? 0 : min(ci, cj) + 1; }
 
-// Spin at site q of the configuration whose sample spins are s and whose exchanged pair is (ci, cj).
+// Spin at site q of the configuration whose sample spins are s and whose exchanged
+// pair is (ci, cj), or whose site ci is flipped when cj == CFG_FLIP.
 __device__ __forceinline__ int cfg_spin(const uint8_t* s, int ci, int cj, int q) {
-    int src = q;
-    if (q == ci) src = cj;
-    else if (q == cj) src = ci;
-    return s[src] & 1;
+    if (q == ci) return cj == CFG_FLIP ? 1 - (s[q] & 1) : s[cj] & 1;
+    if (q == cj) return s[ci] & 1;
+    return s[q] & 1;
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -143,8 +150,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // ---- launchers (each returns cudaGetLastError of its launch) -------------------
 
-// configuration enumeration (k_config.cu): configurations, then row offsets
-cudaError_t launch_configs(const Chunk& ch, float J, int with_bonds, int* cnt, float* diag, int* cfg_off,
+// configuration enumeration (k_config.cu): configurations, then row offsets; the
+// diagonal element is diag_coef * sum over bonds of sigma_i sigma_j
+cudaError_t launch_configs(const Chunk& ch, float diag_coef, int with_bonds, int* cnt, float* diag, int* cfg_off,
                            int* cfg_sample, int* cfg_i, int* cfg_j, int* cfg_row, int* row_cfg, int* status,
                            cudaStream_t st, int grid);
 cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos_emb, int reuse, float* X0,
@@ -153,8 +161,9 @@ cudaError_t launch_head(const float* X, const int* counters, int u_slot, const f
                         const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid);
 cudaError_t launch_eloc(const Chunk& ch, const int* uid, const float* logp, float* ratio, float* log_psi_out,
                         cudaStream_t st, int grid);
-cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* ratio, float J, float* e_loc_out,
-                               cudaStream_t st, int grid);
+// e_loc = diag + offdiag * sum over connected configurations of psi(s') / psi(s)
+cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* ratio, float offdiag,
+                               float* e_loc_out, cudaStream_t st, int grid);
 cudaError_t launch_copy_codes(const Chunk& ch, const int* code, int l, int layers, int* out, cudaStream_t st,
                               int grid);
 cudaError_t launch_mean_var(const float* e_loc, int B, double* mean_var, cudaStream_t st);
@@ -213,6 +222,16 @@ cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act
                              cudaStream_t st, int num_sms, int a_slot = CNT_A);
 
 cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st);
+
+// autoregressive sampling steps (k_sample.cu)
+cudaError_t launch_sample_embed(int S, int p, int N, int d, const uint8_t* spins, const float* tok_emb,
+                                const float* pos_emb, float* X, cudaStream_t st);
+cudaError_t launch_decode_attention(int S, int p, int N, int d, int H, const float* qkv, float* cache, float* O,
+                                    cudaStream_t st);
+cudaError_t launch_decode_attention(int S, int p, int N, int d, int H, const __nv_bfloat16* qkv,
+                                    __nv_bfloat16* cache, float* O, cudaStream_t st);
+cudaError_t launch_sample_draw(int S, int p, int N, const float* logp, const float* u, uint8_t* spins,
+                               float* log_psi, cudaStream_t st);
 
 // nearest codeword on the tensor cores, split-TF32 (k_vq_tc.cu)
 bool vq_tc_supported(int K, int d);
