@@ -335,10 +335,12 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 }
 
 // ---- connected configurations on the tensor cores (BF16 path, dh = 32) ----------------
-// One CTA of 128 threads takes configurations from the tensor-core list.  Per
-// tile of up to 128 patched rows (thread t = TMEM lane t = tile row t):
-//   1. the rows' queries are gathered into shared memory (K-major, d columns),
-//      the changed positions' keys and values per head beside them;
+// One CTA of 256 threads takes configurations from the tensor-core list.  Per
+// tile of up to 128 patched rows, tile row r is TMEM lane r and belongs to two
+// threads, r and r + 128, each of which takes half of the heads:
+//   1. the rows' queries (the sample's: a patched row's input is unchanged) are
+//      copied into shared memory with cp.async (K-major, d columns), the
+//      changed positions' keys beside them and their values transposed;
 //   2. per head h: S_h = Q_h [K_s; K_c]_h^T (M = 128, N = 32): the sample's keys
 //      at the changed positions in columns 0..15, the configuration's in 16..31;
 //   3. per row and head: the BF16 weights e = exp(s / sqrt(dh) - m) of the
@@ -346,11 +348,23 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 //   4. per head: E_h [V_s; V_c]_h (N = 32) into the TMEM columns the scores came
 //      from: sum_k e_c v_c - e_s v_s;
 //   5. per row: delta = (acc - (sum e_c - sum e_s) o) / l' with the sample's
-//      outputs o staged into shared memory four heads at a time (coalesced);
-//      o + delta is written to O (read only if the row is searched), delta goes
-//      back to TMEM, and the certificate is checked as in k_inc_patch, with the
-//      norm enlarged by 2% for the rounding of the BF16 weights.
-__global__ void __launch_bounds__(128)
+//      outputs o read by the row's own threads; delta goes back to TMEM, the two
+//      threads' partial norms are added, and the certificate is checked as in
+//      k_inc_patch with the norm enlarged by 2% for the rounding of the BF16
+//      weights (the listed candidates' projections also in two halves);
+//   6. only a row that is searched (certificate not met) has o + delta written
+//      to O; a certified row keeps the sample's codeword and writes nothing else.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+size_t patch_tc_smem(int d, int heads, int N) {
+    return 128 + (size_t)128 * d * 2 + (size_t)heads * 4096 + (size_t)2 * 128 * (1 + CERT_T) * 4 + 256 * 4 + 64 +
+           (size_t)4 * N * 4 + (size_t)((N + 15) & ~15);
+}
+
+__global__ void __launch_bounds__(256, 2)
 k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
                float* __restrict__ O, const float2* __restrict__ bstat, const CertRow* __restrict__ cert,
                const float* __restrict__ codebook, int* __restrict__ code, int* __restrict__ vq_rows,
@@ -358,15 +372,17 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                const int* __restrict__ list_tc, const short* __restrict__ dpos, const int* __restrict__ dcnt,
                uint32_t tmem_cols, int* __restrict__ status, long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     constexpr int DH = 32;
-    constexpr int OBS = 132;                    // staged output row stride (floats): conflict-free 16-byte reads
-    const int d = ch.d, H = ch.heads, NM = ch.N;
-    uint8_t* sQE = smem;                        // [128 x d] queries, then [128 x 4*64] weights of four heads
-    uint8_t* sK = sQE + 128 * max(d, 256) * 2;  // per head [32 keys x 32 dims]
-    uint8_t* sVt = sK + H * 2048;               // per head [32 dims x 32 keys]
-    float* sOb = reinterpret_cast<float*>(smem);  // [128 x OBS]: four heads of o (over the tiles above, once free)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sVt + H * 2048);
+    const int d = ch.d, H = ch.heads, NM = ch.N;  // d == 32 H
+    const int HH = H / 2;                         // heads per thread
+    uint8_t* sQE = smem;                          // [128 x d] queries, then [128 x d] weights
+    uint8_t* sK = sQE + 128 * d * 2;              // per head [32 keys x 32 dims]
+    uint8_t* sVt = sK + H * 2048;                 // per head [32 dims x 32 keys]
+    float* sN2 = reinterpret_cast<float*>(sVt + H * 2048);  // [2 halves][128]: partial norms
+    float* sP = sN2 + 256;                                  // [2 halves][128][CERT_T]: partial projections
+    int* sGd = reinterpret_cast<int*>(sP + 256 * CERT_T);   // [2 halves][128]: guard flags
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sGd + 256);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
     int* sD = reinterpret_cast<int*>(tmem_holder + 4);  // [PATCH_TC_KEYS]
     int* sRows = sD + PATCH_TC_KEYS;                    // [NM]
@@ -377,6 +393,8 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     __shared__ int sNvq, sNfull, sBase[2], s_item;
     __shared__ long long sCnt[4];
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int half = tid >> 7, r = tid & 127;
+    const int h0 = half * HH;
     const int ld = 3 * d;
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);
     if (tid == 0) {
@@ -389,7 +407,7 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share TMEM lanes
     uint32_t phase = 0;
     bool ok = true;
     long long n_patched = 0, n_cert = 0, n_full = 0, n_pairs = 0;
@@ -418,31 +436,49 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
         n_full += tid == 0 ? nd : 0;
         for (int t0 = 0; t0 < np && ok; t0 += 128) {
             const int nrow = min(128, np - t0);
-            const int p = tid < nrow ? sRows[t0 + tid] : -1;
-            // keys and values of the changed positions, zero-padded to 16 + 16 per head
+            const int p = r < nrow ? sRows[t0 + r] : -1;
+            // keys of the changed positions, zero-filled to 16 + 16 per head
             for (int u = tid; u < H * 32 * (DH / 8); u += blockDim.x) {
                 const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
                 const int n = rem & 31, t8 = (rem >> 5) * 8;  // key slot, first of 8 dims
                 const int kk = n & 15;
-                uint4 kv = make_uint4(0, 0, 0, 0), vv = make_uint4(0, 0, 0, 0);
-                if (kk < nd) {
-                    const int k = sD[kk];
-                    const __nv_bfloat16* x = qkv + (size_t)(n < 16 ? ub[k] : uc[k]) * ld + h * DH + t8;
-                    kv = *reinterpret_cast<const uint4*>(x + d);
-                    vv = *reinterpret_cast<const uint4*>(x + 2 * d);
-                }
-                *reinterpret_cast<uint4*>(sK + h * 2048 + tc::core_off(n, t8, DH)) = kv;
-                const __nv_bfloat16* ve = reinterpret_cast<const __nv_bfloat16*>(&vv);
+                const __nv_bfloat16* x = qkv;
+                if (kk < nd) x = qkv + (size_t)(n < 16 ? ub[sD[kk]] : uc[sD[kk]]) * ld + d + h * DH + t8;
+                cp_async16(tc::smem_u32(sK + h * 2048 + tc::core_off(n, t8, DH)), x, kk < nd ? 16 : 0);
+            }
+            // the row's query: thread (r, half) copies chunks half, half + 2, ...
+            {
+                const __nv_bfloat16* qrow = p >= 0 ? qkv + (size_t)ub[p] * ld : qkv;
+                const int nb = p >= 0 ? 16 : 0;
+                for (int k8 = half * 8; k8 < d; k8 += 16)
+                    cp_async16(tc::smem_u32(sQE + tc::core_off(r, k8, d)), qrow + k8, nb);
+            }
+            // values, transposed: dims are the rows of the [dims x keys] operand
+            for (int u0 = tid; u0 < H * 32 * (DH / 8); u0 += 4 * blockDim.x) {
+                uint4 vv[4];
 #pragma unroll
-                for (int e = 0; e < 8; ++e)  // transposed: dims are the rows of the [dims x keys] operand
-                    *reinterpret_cast<__nv_bfloat16*>(sVt + h * 2048 + tc::core_off(t8 + e, n, 32)) = ve[e];
+                for (int i = 0; i < 4; ++i) {
+                    const int u = u0 + i * blockDim.x;
+                    const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
+                    const int n = rem & 31, t8 = (rem >> 5) * 8, kk = n & 15;
+                    vv[i] = make_uint4(0, 0, 0, 0);
+                    if (u < H * 32 * (DH / 8) && kk < nd)
+                        vv[i] = *reinterpret_cast<const uint4*>(
+                            qkv + (size_t)(n < 16 ? ub[sD[kk]] : uc[sD[kk]]) * ld + 2 * d + h * DH + t8);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int u = u0 + i * blockDim.x;
+                    if (u >= H * 32 * (DH / 8)) break;
+                    const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
+                    const int n = rem & 31, t8 = (rem >> 5) * 8;
+                    const __nv_bfloat16* ve = reinterpret_cast<const __nv_bfloat16*>(&vv[i]);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        *reinterpret_cast<__nv_bfloat16*>(sVt + h * 2048 + tc::core_off(t8 + e, n, 32)) = ve[e];
+                }
             }
-            for (int u = tid; u < 128 * (d / 8); u += blockDim.x) {
-                const int r = u & 127, k8 = (u >> 7) * 8;
-                uint4 qv = make_uint4(0, 0, 0, 0);
-                if (r < nrow) qv = *reinterpret_cast<const uint4*>(qkv + (size_t)uc[sRows[t0 + r]] * ld + k8);
-                *reinterpret_cast<uint4*>(sQE + tc::core_off(r, k8, d)) = qv;
-            }
+            cp_async_wait_all();
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
@@ -462,16 +498,26 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             phase ^= 1;
             tc::tc_fence_after();
             if (!ok) break;
-            float w[8], inv[8];  // per head: sum e_c - sum e_s, 1 / l'
+            float w[4], inv[4];  // per own head: sum e_c - sum e_s, 1 / l'
             bool guard = false;
-            int pairs = 0;
             int nk = 0;  // changed keys before this row
             while (p >= 0 && nk < nd && sD[nk] < p) ++nk;
-            for (int h = 0; h < H; ++h) {
+            float2 mls[4];
+            if (p >= 0) {
+                const float2* bs = bstat + ((size_t)b * NM + p) * H + h0;
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) mls[hh] = hh < HH ? bs[hh] : make_float2(0.f, 1.f);
+            } else {
+#pragma unroll
+                for (int hh = 0; hh < 4; ++hh) mls[hh] = make_float2(0.f, 1.f);
+            }
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                if (hh >= HH) break;
+                const int h = h0 + hh;
                 uint32_t s[32];
                 tc::tmem_ld32(tmem + lane_base + h * 32, s);
-                float2 ml = make_float2(0.f, 1.f);
-                if (p >= 0) ml = bstat[((size_t)b * NM + p) * H + h];
+                const float2 ml = mls[hh];
                 const float m2 = ml.x * 1.4426950408889634f;
                 float seb = 0.f, sec = 0.f;
 #pragma unroll
@@ -496,19 +542,18 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 }
 #pragma unroll
                 for (int c8 = 0; c8 < 4; ++c8)
-                    *reinterpret_cast<uint4*>(sQE + tc::core_off(tid, h * 32 + c8 * 8, H * 32)) =
+                    *reinterpret_cast<uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d)) =
                         make_uint4(e16[4 * c8], e16[4 * c8 + 1], e16[4 * c8 + 2], e16[4 * c8 + 3]);
                 if (!(seb <= 0.5f * ml.y)) guard = true;  // cancellation
-                w[h] = sec - seb;
-                inv[h] = 1.f / (ml.y - seb + sec);
+                w[hh] = sec - seb;
+                inv[hh] = 1.f / (ml.y - seb + sec);
             }
-            pairs = nk;
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
             if (tid == 0) {
                 tc::tc_fence_after();
-                const uint64_t de = tc::desc_kmajor_none(tc::smem_u32(sQE), 128, (H * 32 / 8) * 128);
+                const uint64_t de = tc::desc_kmajor_none(tc::smem_u32(sQE), 128, (d / 8) * 128);
                 for (int h = 0; h < H; ++h) {
                     const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt + h * 2048), 128, (32 / 8) * 128);
 #pragma unroll
@@ -522,46 +567,38 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             phase ^= 1;
             tc::tc_fence_after();
             if (!ok) break;
-            // the sample's outputs o of head group g (four heads), coalesced into shared memory
-            auto stage_ob = [&](int g) {
-                __syncthreads();  // readers of the previous contents are done
-                for (int u = tid; u < 128 * 32; u += blockDim.x) {
-                    const int r = u >> 5, c4 = (u & 31) * 4;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (r < nrow) v = *reinterpret_cast<const float4*>(O + (size_t)(rb + sRows[t0 + r]) * d + g * 128 + c4);
-                    *reinterpret_cast<float4*>(sOb + r * OBS + c4) = v;
-                }
-                __syncthreads();
-            };
-            // pass A: delta = (acc - w o) / l' per head; o + delta goes to O (read only
-            // if the row is searched); delta goes back to TMEM for the candidate check
-            const bool act = p >= 0 && !guard;
+            // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm
+            const float* orow = O + (size_t)(rb + (p >= 0 ? p : 0)) * d;
             float n2 = 0.f;
-            for (int g = 0; g < H / 4; ++g) {
-                stage_ob(g);
-                for (int hh = 0; hh < 4; ++hh) {
-                    const int h = 4 * g + hh;
-                    uint32_t a[32];
-                    tc::tmem_ld32(tmem + lane_base + h * 32, a);
-                    const float* ob = sOb + tid * OBS + hh * 32;
-                    float* xo = O + (size_t)(rc + (p >= 0 ? p : 0)) * d + h * 32;
 #pragma unroll
-                    for (int t = 0; t < 32; t += 4) {
-                        const float4 o4 = *reinterpret_cast<const float4*>(ob + t);
-                        const float d0 = (__uint_as_float(a[t]) - w[h] * o4.x) * inv[h];
-                        const float d1 = (__uint_as_float(a[t + 1]) - w[h] * o4.y) * inv[h];
-                        const float d2 = (__uint_as_float(a[t + 2]) - w[h] * o4.z) * inv[h];
-                        const float d3 = (__uint_as_float(a[t + 3]) - w[h] * o4.w) * inv[h];
-                        n2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, n2))));
-                        if (act) *reinterpret_cast<float4*>(xo + t) = make_float4(o4.x + d0, o4.y + d1, o4.z + d2, o4.w + d3);
-                        a[t] = __float_as_uint(d0);
-                        a[t + 1] = __float_as_uint(d1);
-                        a[t + 2] = __float_as_uint(d2);
-                        a[t + 3] = __float_as_uint(d3);
-                    }
-                    tc::tmem_st32(tmem + lane_base + h * 32, a);
+            for (int hh = 0; hh < 4; ++hh) {
+                if (hh >= HH) break;
+                const int h = h0 + hh;
+                float4 o4[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    o4[t] = p >= 0 ? *reinterpret_cast<const float4*>(orow + h * 32 + 4 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t a[32];
+                tc::tmem_ld32(tmem + lane_base + h * 32, a);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float d0 = (__uint_as_float(a[4 * t]) - w[hh] * o4[t].x) * inv[hh];
+                    const float d1 = (__uint_as_float(a[4 * t + 1]) - w[hh] * o4[t].y) * inv[hh];
+                    const float d2 = (__uint_as_float(a[4 * t + 2]) - w[hh] * o4[t].z) * inv[hh];
+                    const float d3 = (__uint_as_float(a[4 * t + 3]) - w[hh] * o4[t].w) * inv[hh];
+                    n2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, n2))));
+                    a[4 * t] = __float_as_uint(d0);
+                    a[4 * t + 1] = __float_as_uint(d1);
+                    a[4 * t + 2] = __float_as_uint(d2);
+                    a[4 * t + 3] = __float_as_uint(d3);
                 }
+                tc::tmem_st32(tmem + lane_base + h * 32, a);
             }
+            sN2[tid] = n2;
+            sGd[tid] = guard ? 1 : 0;
+            __syncthreads();
+            n2 = sN2[r] + sN2[128 + r];  // the same sum, in the same order, for both threads of the row
+            guard = (sGd[r] | sGd[128 + r]) != 0;
             const CertRow* cr = cert + ((size_t)b * NM + (p >= 0 ? p : 0));
             int md = -1, nc = 0;
             if (p >= 0) {
@@ -578,12 +615,15 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, md == 3)) {  // pass B: exact check of the listed candidates
+            // pass B: exact check of the listed candidates, each thread over its heads
+            // (md agrees between warps w and w + 4, so their TMEM loads stay warp-uniform)
+            if (__any_sync(0xffffffffu, md == 3)) {
                 float proj[CERT_T];
 #pragma unroll
                 for (int i = 0; i < CERT_T; ++i) proj[i] = 0.f;
                 const float* wc = codebook + (size_t)(md == 3 ? cr->code : 0) * d;
-                for (int h = 0; h < H; ++h) {
+                for (int hh = 0; hh < HH; ++hh) {
+                    const int h = h0 + hh;
                     uint32_t a[32];
                     tc::tmem_ld32(tmem + lane_base + h * 32, a);
                     if (md == 3) {
@@ -604,18 +644,43 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                     }
                 }
                 if (md == 3) {
-                    md = 0;
-                    for (int i = 0; i < nc; ++i)
-                        if (!(cr->gap[i] - 2.f * proj[i] > cr->eta)) md = 1;
+#pragma unroll
+                    for (int i = 0; i < CERT_T; ++i) sP[tid * CERT_T + i] = proj[i];
                 }
             }
-            if (md == 0) code[rc + p] = cr->code;
-            if (md >= 1) sVq[atomicAdd(&sNvq, 1)] = rc + p;
-            if (md == 2) sFull[atomicAdd(&sNfull, 1)] = rc + p;
-            n_patched += (md == 0 || md == 1);
-            n_cert += md == 0;
-            n_full += md == 2;
-            n_pairs += pairs;
+            __syncthreads();
+            if (md == 3) {
+                md = 0;
+                for (int i = 0; i < nc; ++i)
+                    if (!(cr->gap[i] - 2.f * (sP[r * CERT_T + i] + sP[(128 + r) * CERT_T + i]) > cr->eta)) md = 1;
+            }
+            // a searched row: o + delta goes to O for the vector quantizer
+            if (__any_sync(0xffffffffu, md == 1)) {
+                float* xo = O + (size_t)(rc + (p >= 0 ? p : 0)) * d;
+                for (int hh = 0; hh < HH; ++hh) {
+                    const int h = h0 + hh;
+                    uint32_t a[32];
+                    tc::tmem_ld32(tmem + lane_base + h * 32, a);
+                    if (md == 1) {
+#pragma unroll
+                        for (int t = 0; t < 32; t += 4) {
+                            const float4 o4 = *reinterpret_cast<const float4*>(orow + h * 32 + t);
+                            *reinterpret_cast<float4*>(xo + h * 32 + t) =
+                                make_float4(o4.x + __uint_as_float(a[t]), o4.y + __uint_as_float(a[t + 1]),
+                                            o4.z + __uint_as_float(a[t + 2]), o4.w + __uint_as_float(a[t + 3]));
+                        }
+                    }
+                }
+            }
+            if (half == 0) {
+                if (md == 0) code[rc + p] = cr->code;
+                if (md >= 1) sVq[atomicAdd(&sNvq, 1)] = rc + p;
+                if (md == 2) sFull[atomicAdd(&sNfull, 1)] = rc + p;
+                n_patched += (md == 0 || md == 1);
+                n_cert += md == 0;
+                n_full += md == 2;
+                n_pairs += p >= 0 ? nk : 0;
+            }
             tc::tc_fence_before();
             __syncthreads();  // TMEM and the staging space are free for the next tile
         }
@@ -1197,8 +1262,7 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
         if (use_tc) {  // the classify kernel left no configuration to the CUDA cores
             const uint32_t cols = ch.heads * 32 <= 128 ? 128 : 256;
-            size_t smem_tc = 1024 + (size_t)128 * std::max(ch.d, 256) * 2 + (size_t)ch.heads * 4096 + 64 +
-                             (size_t)4 * ch.N * 4 + (size_t)((ch.N + 15) & ~15);
+            size_t smem_tc = patch_tc_smem(ch.d, ch.heads, ch.N);
             if (smem_tc > 227 * 1024) return cudaErrorInvalidValue;
             // the TMEM columns of the CTAs resident on one SM must fit in its 512
             const size_t max_ctas = 512 / cols;
@@ -1208,7 +1272,7 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                 cudaFuncSetAttribute(k_inc_patch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
                 granted_tc = smem_tc;
             }
-            k_inc_patch_tc<<<grid, 128, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, code, vq_rows, act_off,
+            k_inc_patch_tc<<<grid, 256, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, code, vq_rows, act_off,
                                                       rc_rows, rc_cnt, list_tc, dpos, dcnt, cols, status, stats);
             return cudaGetLastError();
         }
