@@ -102,7 +102,8 @@ __device__ int block_compact(int lo, int hi, Pred pred, int* out, int cap, int* 
 }  // namespace
 
 // ---- s's rows: nearest codeword and its certificate ---------------------------------
-// One CTA of 256 threads per RB rows of the chunk's samples (row r = b * N + p).
+// One CTA of 256 threads per RB rows of the chunk's samples (row r = b * N + p),
+// thread j computing codeword j's distances to the RB rows.
 // Distances are expanded as ||o||^2 - 2 o.W_j + ||W_j||^2 in FP32 (as the
 // ordinary search does); the certificate radii use the table wd[c][j] = ||W_c - W_j||.
 template <int RB>
@@ -159,19 +160,26 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
         float acc[RB];
 #pragma unroll
         for (int r = 0; r < RB; ++r) acc[r] = 0.f;
+        // codeword j's next 32 dims travel in registers while the current ones are used
+        float4 wn[8];
+        auto load_w = [&](int d0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                wn[q] = j < K ? *reinterpret_cast<const float4*>(codebook + (size_t)j * d + d0 + 4 * q)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        load_w(0);
         for (int d0 = 0; d0 < d; d0 += 32) {
             __syncthreads();
-            if (j < K) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 w = *reinterpret_cast<const float4*>(codebook + (size_t)j * d + d0 + 4 * q);
-                    sW[(4 * q) * 256 + tid] = w.x;
-                    sW[(4 * q + 1) * 256 + tid] = w.y;
-                    sW[(4 * q + 2) * 256 + tid] = w.z;
-                    sW[(4 * q + 3) * 256 + tid] = w.w;
-                }
+            for (int q = 0; q < 8; ++q) {
+                sW[(4 * q) * 256 + tid] = wn[q].x;
+                sW[(4 * q + 1) * 256 + tid] = wn[q].y;
+                sW[(4 * q + 2) * 256 + tid] = wn[q].z;
+                sW[(4 * q + 3) * 256 + tid] = wn[q].w;
             }
             __syncthreads();
+            if (d0 + 32 < d) load_w(d0 + 32);
 #pragma unroll 2
             for (int dd = 0; dd < 32; dd += 4) {
                 const float w0 = sW[dd * 256 + tid], w1 = sW[(dd + 1) * 256 + tid];
@@ -364,6 +372,33 @@ size_t patch_tc_smem(int d, int heads, int N) {
            (size_t)4 * N * 4 + (size_t)((N + 15) & ~15);
 }
 
+// The BF16 weights of one head for a row with nk changed keys before it (nk <= NKB):
+// e_s = exp(s_s / sqrt(dh) - m) negated in slots 0..15, e_c in 16..31, zeros beyond
+// nk; seb, sec their sums; guard set when a new score overflows the sample's max.
+template <int NKB>
+__device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float sl2, float m2, bool& guard, float& seb,
+                                              float& sec, uint32_t (&e16)[16]) {
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        float eb = 0.f, ec = 0.f;
+        if (kk < NKB && kk < nk) {
+            const float xc = __uint_as_float(s[16 + kk]) * sl2 - m2;
+            if (xc > 115.f) guard = true;
+            eb = ex2_approx(__uint_as_float(s[kk]) * sl2 - m2);
+            ec = ex2_approx(fminf(xc, 115.f));
+        }
+        seb += eb;
+        sec += ec;
+        s[kk] = __float_as_uint(-eb);
+        s[16 + kk] = __float_as_uint(ec);
+    }
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {
+        const __nv_bfloat162 v2 = __floats2bfloat162_rn(__uint_as_float(s[2 * j2]), __uint_as_float(s[2 * j2 + 1]));
+        e16[j2] = *reinterpret_cast<const uint32_t*>(&v2);
+    }
+}
+
 __global__ void __launch_bounds__(256, 2)
 k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
                float* __restrict__ O, const float2* __restrict__ bstat, const CertRow* __restrict__ cert,
@@ -502,51 +537,38 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             bool guard = false;
             int nk = 0;  // changed keys before this row
             while (p >= 0 && nk < nd && sD[nk] < p) ++nk;
-            float2 mls[4];
-            if (p >= 0) {
-                const float2* bs = bstat + ((size_t)b * NM + p) * H + h0;
+            // warps w and w + 4 hold the same rows: both skip a tile's padding rows together
+            const bool wact = __any_sync(0xffffffffu, p >= 0);
+            const int nkw = __reduce_max_sync(0xffffffffu, nk);
+            if (wact) {
+                float2 mls[4];
+                const float2* bs = bstat + ((size_t)b * NM + (p >= 0 ? p : 0)) * H + h0;
 #pragma unroll
-                for (int hh = 0; hh < 4; ++hh) mls[hh] = hh < HH ? bs[hh] : make_float2(0.f, 1.f);
-            } else {
+                for (int hh = 0; hh < 4; ++hh) mls[hh] = (hh < HH && p >= 0) ? bs[hh] : make_float2(0.f, 1.f);
 #pragma unroll
-                for (int hh = 0; hh < 4; ++hh) mls[hh] = make_float2(0.f, 1.f);
-            }
+                for (int hh = 0; hh < 4; ++hh) {
+                    if (hh >= HH) break;
+                    const int h = h0 + hh;
+                    uint32_t s[32];
+                    tc::tmem_ld32(tmem + lane_base + h * 32, s);
+                    const float2 ml = mls[hh];
+                    const float m2 = ml.x * 1.4426950408889634f;
+                    float seb = 0.f, sec = 0.f;
+                    uint32_t e16[16];  // the 32 weights as packed BF16 pairs
+                    if (nkw <= 4)
+                        patch_weights<4>(s, nk, sl2, m2, guard, seb, sec, e16);
+                    else if (nkw <= 8)
+                        patch_weights<8>(s, nk, sl2, m2, guard, seb, sec, e16);
+                    else
+                        patch_weights<16>(s, nk, sl2, m2, guard, seb, sec, e16);
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-                if (hh >= HH) break;
-                const int h = h0 + hh;
-                uint32_t s[32];
-                tc::tmem_ld32(tmem + lane_base + h * 32, s);
-                const float2 ml = mls[hh];
-                const float m2 = ml.x * 1.4426950408889634f;
-                float seb = 0.f, sec = 0.f;
-#pragma unroll
-                for (int kk = 0; kk < 16; ++kk) {
-                    float eb = 0.f, ec = 0.f;
-                    if (kk < nk) {
-                        const float xc = __uint_as_float(s[16 + kk]) * sl2 - m2;
-                        if (xc > 115.f) guard = true;
-                        eb = ex2_approx(__uint_as_float(s[kk]) * sl2 - m2);
-                        ec = ex2_approx(fminf(xc, 115.f));
-                    }
-                    seb += eb;
-                    sec += ec;
-                    s[kk] = __float_as_uint(-eb);
-                    s[16 + kk] = __float_as_uint(ec);
+                    for (int c8 = 0; c8 < 4; ++c8)
+                        *reinterpret_cast<uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d)) =
+                            make_uint4(e16[4 * c8], e16[4 * c8 + 1], e16[4 * c8 + 2], e16[4 * c8 + 3]);
+                    if (!(seb <= 0.5f * ml.y)) guard = true;  // cancellation
+                    w[hh] = sec - seb;
+                    inv[hh] = 1.f / (ml.y - seb + sec);
                 }
-                uint32_t e16[16];  // the 32 weights as packed BF16 pairs
-#pragma unroll
-                for (int j2 = 0; j2 < 16; ++j2) {
-                    const __nv_bfloat162 v2 = __floats2bfloat162_rn(__uint_as_float(s[2 * j2]), __uint_as_float(s[2 * j2 + 1]));
-                    e16[j2] = *reinterpret_cast<const uint32_t*>(&v2);
-                }
-#pragma unroll
-                for (int c8 = 0; c8 < 4; ++c8)
-                    *reinterpret_cast<uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d)) =
-                        make_uint4(e16[4 * c8], e16[4 * c8 + 1], e16[4 * c8 + 2], e16[4 * c8 + 3]);
-                if (!(seb <= 0.5f * ml.y)) guard = true;  // cancellation
-                w[hh] = sec - seb;
-                inv[hh] = 1.f / (ml.y - seb + sec);
             }
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
@@ -572,7 +594,7 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             float n2 = 0.f;
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
-                if (hh >= HH) break;
+                if (hh >= HH || !wact) break;
                 const int h = h0 + hh;
                 float4 o4[8];
 #pragma unroll
@@ -1209,7 +1231,7 @@ bool incremental_supported(int d, int heads) {
            dh % per == 0;
 }
 
-constexpr int CERT_RB = 32;  // sample rows per CTA
+constexpr int CERT_RB = 16;  // sample rows per CTA (240 CTAs for 15 samples of 256 sites)
 size_t base_cert_smem(int d, int K) {
     return ((size_t)CERT_RB * d + 32 * 256 + CERT_RB * (size_t)K + 8 * (size_t)K) * 4;
 }

@@ -64,10 +64,11 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_COUNT };
+             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_COUNT };
 const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
                                     "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward",
-                                    "inc_certificate", "inc_classify", "inc_patch", "inc_recompute"};
+                                    "inc_certificate", "inc_classify", "inc_patch", "inc_recompute",
+                                    "inc_recompute_whole"};
 static_assert(S_COUNT <= VQNQS_MAX_STAGES, "stage table larger than the ABI's VQNQS_MAX_STAGES");
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
@@ -401,12 +402,12 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
                                                       act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 1,
                                                       ctx->status, ctx->stats, st, g_cfg));
-                StageScope scope_(ctx, S_RECOMP, 2, st);
-                VQ_CK(launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos, dcnt, ctx->status,
-                                               ctx->stats, st, ctx->num_sms));
-                VQ_CK(launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
-                                          grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
-                                          counters + CNT_SCL));
+                VQ_STAGE(S_RECOMP, 1, launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos,
+                                                               dcnt, ctx->status, ctx->stats, st, ctx->num_sms));
+                VQ_STAGE(S_RECOMP_WHOLE, 1,
+                         launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
+                                             grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
+                                             counters + CNT_SCL));
             } else if (bf16) {
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
                                                       act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 0,
