@@ -160,20 +160,25 @@ class ClockSampler:
 
 def traffic_from_profile(kernel_stage: str):
     """DRAM bytes per launch recorded by the committed ncu summary of this stage's
-    kernel, or None when the kernel source changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_stage}.json")
+    kernel (profiles/traffic_<stage>.md, `key: value` lines), or None when the
+    kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel_stage}.md")
+    rec = {}
     try:
-        rec = json.load(open(path))
-    except (OSError, ValueError):
+        for line in open(path):
+            k, sep, v = line.partition(":")
+            if sep and k.strip() in ("source", "source_sha256_16", "dram_bytes_per_launch"):
+                rec[k.strip()] = v.strip()
+    except OSError:
         return None
     src = os.path.join(ROOT, rec.get("source", ""))
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    if digest != rec.get("source_sha256_16"):
+    if digest != rec.get("source_sha256_16") or "dram_bytes_per_launch" not in rec:
         return None
-    return rec.get("dram_bytes_per_launch_scaled")
+    return float(rec["dram_bytes_per_launch"])
 
 
 def cpu_oracle(spins_np, w, max_seconds=20.0, max_samples=6):
