@@ -252,7 +252,11 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, const fl
  *              stored [out][in])
  *   bias       DEVICE float [N]
  *   epilogue   0: C bfloat16 [M][N];  1: C bfloat16 of GELU(.);
- *              2: C float [M][N] = . + R[M][N] (R DEVICE float);  3: C float
+ *              2: C float [M][N] = . + R[M][N] (R DEVICE float);  3: C float;
+ *              4: C float of GELU(.).  GELU(x) = x (1 + erf(x / sqrt 2)) / 2 with
+ *              erf by Abramowitz & Stegun 7.1.26 (absolute error <= 1.5e-7 plus
+ *              FP32 rounding).  Output chunks of 32 full rows leave through TMA
+ *              stores, the others row by row; C rows at or past M are not written.
  * Needs K % 64 == 0, N % 64 == 0 and 16-byte aligned pointers (else
  * VQNQS_ERR_ARG).  BF16 x BF16 products, FP32 accumulation; asynchronous on
  * `stream`; a stalled pipeline sets VQNQS_DEV_TIMEOUT in the status word. */

@@ -25,6 +25,8 @@ namespace vq {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 320;
 
+constexpr int EPI_WARPS = 8, SLOT_BYTES = 4096;  // per epilogue warp: one 32 x 32 output chunk
+
 template <int BN>
 struct TcCfg {
     static constexpr int STAGES = BN >= 192 ? 4 : 6;
@@ -32,14 +34,43 @@ struct TcCfg {
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * SLOT_BYTES + 256;
 };
 
-__device__ __forceinline__ float gelu_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7 for all real x):
+// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p |z|),
+// odd in z.  Evaluated with the SFU's reciprocal and exponential; the BF16 outputs
+// it feeds resolve 4e-3 relative.
+__device__ __forceinline__ float erf_as(float z) {
+    const float s = fabsf(z);
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, s, 1.0f)));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-s * s * 1.4426950408889634f));
+    return copysignf(fmaf(-poly, e, 1.0f), z);
+}
+__device__ __forceinline__ float gelu_tc(float x) {
+    const float h = 0.5f * x;
+    return fmaf(h, erf_as(x * 0.70710678118654752f), h);
+}
+
+// 2D TMA store of a shared-memory box (bulk group of this thread) and the waits on it.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(tc::smem_u32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
           const float* __restrict__ bias, const float* __restrict__ R, void* __restrict__ Cout,
           const int* __restrict__ counters, int u_slot, int N, int K, int* __restrict__ status) {
     using C = TcCfg<BN>;
@@ -47,12 +78,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = smem;
     uint8_t* sB = smem + C::STAGES * C::A_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::STAGES * C::B_BYTES);
+    uint8_t* sOut = sB + C::STAGES * C::B_BYTES;  // [EPI_WARPS][SLOT_BYTES], 1024-byte aligned
+    uint64_t* full = reinterpret_cast<uint64_t*>(sOut + EPI_WARPS * SLOT_BYTES);
     uint64_t* empty = full + C::STAGES;
     uint64_t* accf = empty + C::STAGES;
     uint64_t* acce = accf + 2;
     uint64_t* done = acce + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(done + 1);
+    uint64_t* rbar = done + 1;  // [EPI_WARPS]: residual chunk loads
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(rbar + EPI_WARPS);
 
     const int M = counters[u_slot];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -63,6 +96,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 256); }
         tc::mbar_init(done, 1);
+        for (int w = 0; w < EPI_WARPS; ++w) tc::mbar_init(&rbar[w], 1);
         tc::fence_barrier_init();
     }
     if (warp == 1) tc::tmem_alloc(tmem_holder, C::TMEM_COLS);
@@ -124,46 +158,103 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             tc::mbar_wait(done, 0, status, 100000000LL);
         }
     } else {
-        // warps 2..9: two warps per TMEM lane quarter, each taking alternate 32-column chunks
+        // warps 2..9: two warps per TMEM lane quarter, each taking alternate 32-column chunks.
+        // A chunk of 32 rows x 32 columns whose rows all exist goes out through the warp's
+        // shared-memory slot and a TMA store (rows 128 bytes apart for FP32 with the 128-byte
+        // swizzle, 64 bytes apart for BF16 with the 64-byte swizzle: conflict-free writes);
+        // a chunk reaching past the M rows is stored row by row.  The residual chunk
+        // (epilogue 2) arrives in the same slot by TMA before the accumulator is read.
         const int q = warp & 3;  // TMEM lanes 32q .. 32q+31 are reachable from this warp
         const int part = (warp - 2) >> 2;
+        const int ew = warp - 2;
+        uint8_t* slot = sOut + ew * SLOT_BYTES;
+        constexpr bool F32OUT = EPI >= 2;
+        uint32_t rph = 0;  // residual barrier phase
         int i = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+        bool ok = true;
+        for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++i) {
             const int a = i & 1;
             const uint32_t aph = (i >> 1) & 1;
-            if (!tc::mbar_wait(&accf[a], aph, status)) break;
+            if (!tc::mbar_wait(&accf[a], aph, status)) { ok = false; break; }
             tc::tc_fence_after();
             const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
-            const int row = m0 + q * 32 + lane;
+            const int rb = m0 + q * 32;  // the chunk's first row
+            const int row = rb + lane;
+            const bool boxed = rb + 32 <= M;  // warp-uniform
 #pragma unroll 1
-            for (int c = part * 32; c < BN; c += 64) {
+            for (int c = part * 32; c < BN && ok; c += 64) {
+                const int n = n0 + c;
+                if (boxed) {  // the slot is free once the previous store has read it
+                    if (lane == 0) {
+                        bulk_wait_read0();
+                        if (EPI == 2) {
+                            tc::mbar_arrive_expect_tx(&rbar[ew], SLOT_BYTES);
+                            tc::tma_load_2d(slot, &tmR, n, rb, &rbar[ew]);
+                        }
+                    }
+                    __syncwarp();
+                }
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + a * BN + c, r);
-                if (row < M) {
-                    const int n = n0 + c;
-                    float v[32];
+                float v[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias[n + j];
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias[n + j];
+                if (EPI == 1 || EPI == 4) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = gelu_tc(v[j]);
+                }
+                if (boxed) {
+                    if (F32OUT) {  // row `lane` at lane * 128 bytes, 16-byte chunk k at k ^ (lane & 7)
+                        float4* srow = reinterpret_cast<float4*>(slot + lane * 128);
+                        if (EPI == 2) {
+                            if (!tc::mbar_wait(&rbar[ew], rph, status)) {
+                                ok = false;  // drain the load into the slot (bounded) before leaving
+                                tc::mbar_wait(&rbar[ew], rph, status, 100000000LL);
+                            }
+                            rph ^= 1;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float4 x = srow[k ^ (lane & 7)];
+                                v[4 * k] += x.x; v[4 * k + 1] += x.y; v[4 * k + 2] += x.z; v[4 * k + 3] += x.w;
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            srow[k ^ (lane & 7)] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    } else {  // row `lane` at lane * 64 bytes, 16-byte chunk k at k ^ ((lane >> 1) & 3)
+                        uint4* srow = reinterpret_cast<uint4*>(slot + lane * 64);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            uint32_t p[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * k + 2 * j], v[8 * k + 2 * j + 1]);
+                                p[j] = *reinterpret_cast<uint32_t*>(&h);
+                            }
+                            srow[k ^ ((lane >> 1) & 3)] = make_uint4(p[0], p[1], p[2], p[3]);
+                        }
+                    }
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && ok) tma_store_2d(&tmC, slot, n, rb);
+                } else if (row < M) {
                     if (EPI == 2) {  // FP32 out + residual
                         const float4* rr = reinterpret_cast<const float4*>(R + (size_t)row * N + n);
-                        float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + (size_t)row * N + n);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            float4 x = rr[j];
-                            out[j] = make_float4(v[4 * j] + x.x, v[4 * j + 1] + x.y, v[4 * j + 2] + x.z,
-                                                 v[4 * j + 3] + x.w);
+                            const float4 x = rr[j];
+                            v[4 * j] += x.x; v[4 * j + 1] += x.y; v[4 * j + 2] += x.z; v[4 * j + 3] += x.w;
                         }
-                    } else if (EPI == 3) {  // FP32 out
+                    }
+                    if (F32OUT) {
                         float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + (size_t)row * N + n);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) out[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                    } else {  // BF16 out, optionally GELU
+                    } else {
                         uint32_t p[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            float x0 = v[2 * j], x1 = v[2 * j + 1];
-                            if (EPI == 1) { x0 = gelu_tc(x0); x1 = gelu_tc(x1); }
-                            __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                             p[j] = *reinterpret_cast<uint32_t*>(&h);
                         }
                         uint4* out = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + n);
@@ -175,6 +266,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             tc::tc_fence_before();
             tc::mbar_arrive(&acce[a]);
         }
+        if (lane == 0) bulk_wait0();  // this warp's stores have landed before the kernel ends
     }
     __syncwarp();
     tc::tc_fence_before();
@@ -228,7 +320,8 @@ EncodeTiledFn encode_fn() {
 }
 
 template <int BN, int EPI>
-cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, const float* R, void* Cout,
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm, const CUtensorMap& trm,
+                      const float* bias, const float* R, void* Cout,
                       const int* counters, int u_slot, int Mmax, int N, int K, int* status, cudaStream_t st,
                       int num_sms) {
     using C = TcCfg<BN>;
@@ -242,21 +335,42 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const float*
     long long tiles = (long long)((Mmax + TC_BM - 1) / TC_BM) * (N / BN);
     int grid = (int)(tiles < num_sms ? tiles : num_sms);
     if (grid < 1) grid = 1;
-    k_gemm_tc<BN, EPI><<<grid, TC_THREADS, C::SMEM, st>>>(ta, tb, bias, R, Cout, counters, u_slot, N, K, status);
+    k_gemm_tc<BN, EPI><<<grid, TC_THREADS, C::SMEM, st>>>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, N, K,
+                                                          status);
     return cudaGetLastError();
 }
 
 template <int EPI>
-cudaError_t launch_epi(int BN, const CUtensorMap& ta, const CUtensorMap& tb, const float* bias, const float* R,
-                       void* Cout, const int* counters, int u_slot, int Mmax, int N, int K, int* status,
-                       cudaStream_t st, int num_sms) {
+cudaError_t launch_epi(int BN, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm,
+                       const CUtensorMap& trm, const float* bias, const float* R, void* Cout, const int* counters,
+                       int u_slot, int Mmax, int N, int K, int* status, cudaStream_t st, int num_sms) {
+#define VQ_BN(B) launch_bn<B, EPI>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms)
     switch (BN) {
-        case 64: return launch_bn<64, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 128: return launch_bn<128, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 192: return launch_bn<192, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 256: return launch_bn<256, EPI>(ta, tb, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 64: return VQ_BN(64);
+        case 128: return VQ_BN(128);
+        case 192: return VQ_BN(192);
+        case 256: return VQ_BN(256);
         default: return cudaErrorInvalidValue;
     }
+#undef VQ_BN
+}
+
+// Output (and residual) maps: [rows][cols] row-major, boxes of 32 x 32 elements, the
+// 64-byte swizzle for BF16 rows of a box (64 bytes), the 128-byte one for FP32 (128 bytes).
+cudaError_t make_tmap_out(CUtensorMap* map, const void* base, long long rows, int cols, bool f32) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    const int es = f32 ? 4 : 2;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * es) % 16 || rows < 1) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * es};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    f32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -292,18 +406,30 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
                            int* status, cudaStream_t st, int num_sms, int BN) {
     if (BN <= 0) BN = tc_pick_bn(N);
-    if (!BN || N % BN || K % TC_BK || K <= 0) return cudaErrorInvalidValue;
-    CUtensorMap ta;
+    if (!BN || N % BN || K % TC_BK || K <= 0 || epi < 0 || epi > 4 || (epi == 2 && !R)) return cudaErrorInvalidValue;
+    if (Arows < 1) return cudaSuccess;  // no rows to compute
+    CUtensorMap ta, tcm, trm;
     cudaError_t e = make_tmap_bf16(&ta, A, Arows, K, TC_BM);
     if (e != cudaSuccess) return e;
+    e = make_tmap_out(&tcm, Cout, Arows, N, epi >= 2);
+    if (e != cudaSuccess) return e;
+    if (epi == 2) {
+        e = make_tmap_out(&trm, R, Arows, N, true);
+        if (e != cudaSuccess) return e;
+    } else {
+        trm = tcm;  // not read
+    }
     const int Mmax = (int)Arows;
+#define VQ_EPI(E) launch_epi<E>(BN, ta, tmB, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms)
     switch (epi) {
-        case 0: return launch_epi<0>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 1: return launch_epi<1>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 2: return launch_epi<2>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
-        case 3: return launch_epi<3>(BN, ta, tmB, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms);
+        case 0: return VQ_EPI(0);
+        case 1: return VQ_EPI(1);
+        case 2: return VQ_EPI(2);
+        case 3: return VQ_EPI(3);
+        case 4: return VQ_EPI(4);
         default: return cudaErrorInvalidValue;
     }
+#undef VQ_EPI
 }
 
 }  // namespace vq

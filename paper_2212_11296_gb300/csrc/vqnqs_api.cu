@@ -1009,8 +1009,8 @@ int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const vo
                     const float* R, void* C, int epilogue, void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
-    if (M < 0 || N <= 0 || K <= 0 || K % 64 || !tc_pick_bn(N) || epilogue < 0 || epilogue > 3)
-        return fail(ctx, VQNQS_ERR_ARG, "gemm: need M >= 0, K % 64 == 0, N % 64 == 0, epilogue 0..3");
+    if (M < 0 || N <= 0 || K <= 0 || K % 64 || !tc_pick_bn(N) || epilogue < 0 || epilogue > 4)
+        return fail(ctx, VQNQS_ERR_ARG, "gemm: need M >= 0, K % 64 == 0, N % 64 == 0, epilogue 0..4");
     if (!A || !Bt || !bias || !C || (epilogue == 2 && !R)) return fail(ctx, VQNQS_ERR_ARG, "gemm: null pointer");
     auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; };
     if (misaligned(A) || misaligned(Bt) || misaligned(C) || (R && misaligned(R)))

@@ -27,7 +27,7 @@ def ctx():
 
 @pytest.mark.parametrize("M,N,K", [(1, 64, 64), (127, 192, 256), (128, 256, 256), (300, 768, 256),
                                    (1000, 1024, 256), (513, 256, 1024), (2048, 384, 128)])
-@pytest.mark.parametrize("epi", [0, 1, 2, 3])
+@pytest.mark.parametrize("epi", [0, 1, 2, 3, 4])
 def test_gemm_bf16_matches_fp32_reference(M, N, K, epi):
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K + epi)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
@@ -37,12 +37,12 @@ def test_gemm_bf16_matches_fp32_reference(M, N, K, epi):
     out = ctx().gemm_bf16(A, Bt, bias, epilogue=epi, R=R)
     torch.cuda.synchronize()
     ref = A.float() @ Bt.float().T + bias
-    if epi == 1:
+    if epi in (1, 4):
         ref = torch.nn.functional.gelu(ref)
     if epi == 2:
         ref = ref + R
     scale = (A.float().abs() @ Bt.float().abs().T).amax(1, keepdim=True) + 1.0
-    if epi in (2, 3):
+    if epi in (2, 3, 4):
         assert out.dtype == torch.float32
         assert ((out - ref).abs() / scale).max().item() < 1e-5
     else:
@@ -50,6 +50,28 @@ def test_gemm_bf16_matches_fp32_reference(M, N, K, epi):
         assert ((out.float() - ref).abs() / (ref.abs() + 1e-2)).max().item() < 1.6e-2
         assert ((out.float() - ref.to(torch.bfloat16).float()).abs() > 0).float().mean().item() < 0.05
     assert ctx().stats()["device_status"] == 0
+
+
+def test_gelu_epilogue_error_bound():
+    """GELU(x) = x (1 + erf(x / sqrt 2)) / 2 with erf by Abramowitz & Stegun 7.1.26
+    (|error| <= 1.5e-7): against the float64 definition, within that bound scaled by
+    x / 2 plus FP32 rounding, and against CUDA's erff (torch, FP32) as well."""
+    M, K, N = 64, 64, 4096
+    A = torch.zeros(M, K, device="cuda", dtype=torch.bfloat16)
+    Bt = torch.zeros(N, K, device="cuda", dtype=torch.bfloat16)
+    x = torch.linspace(-9.0, 9.0, N, device="cuda")
+    out = ctx().gemm_bf16(A, Bt, x, epilogue=4)  # every row is GELU(bias)
+    torch.cuda.synchronize()
+    x64 = x.double()
+    exact = 0.5 * x64 * (1.0 + torch.erf(x64 / np.sqrt(2.0)))
+    err = (out.double() - exact).abs()
+    # approximation error, plus a few FP32 ulps of the erf evaluation (SFU reciprocal and
+    # exponential) and of the final product
+    bound = 0.5 * x64.abs() * (1.5e-7 + 4e-7) + 1.2e-7 * exact.abs() + 1e-12
+    print(f"GELU: max |err| {err.max().item():.2e}, max err / bound {(err / bound).max().item():.2f}")
+    assert (err <= bound).all()
+    cuda_erf = torch.nn.functional.gelu(x)  # FP32, CUDA's erff
+    assert ((out[0] - cuda_erf).abs() <= 2 * bound[0:N].float() + 1e-7).all()
 
 
 def test_gemm_rejects_bad_shapes():
