@@ -391,8 +391,17 @@ def main():
                 m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
             a1.record(stream)
             torch.cuda.synchronize()
-            tf = 2.0 * Mg * Ng * Kg * 20 / (a0.elapsed_time(a1) / 1e3) / 1e12
-            gemm["shapes"][name] = {"N": Ng, "K": Kg, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"]}
+            sec = a0.elapsed_time(a1) / 1e3 / 20
+            tf = 2.0 * Mg * Ng * Kg / sec / 1e12
+            # bytes a launch must move: A, Bt, C (and the residual R)
+            nbytes = Mg * Kg * 2 + Ng * Kg * 2 + Mg * Ng * (2 if epi < 2 else 4) + (Mg * Ng * 4 if epi == 2 else 0)
+            gbs = nbytes / sec / 1e9
+            t_tensor = 2.0 * Mg * Ng * Kg / (pk["bf16_tflops_burst"] * 1e12)
+            t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
+            gemm["shapes"][name] = {"N": Ng, "K": Kg, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"],
+                                    "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
+                                    "roofline_bound": "tensor" if t_tensor >= t_hbm else "hbm",
+                                    "roofline_frac": max(t_tensor, t_hbm) / sec}
             del A, Bt, Rg, Cg
 
     # roofline of the dominant stage, from the live CUDA-event stage times

@@ -3,16 +3,16 @@
 //
 //   C[M, N] = A[M, K] @ Bt[N, K]^T + bias (+ epilogue),  A and Bt K-major BF16.
 //
-// Persistent kernel, one CTA per SM, 10 warps:
+// Persistent kernel, one CTA per SM, 18 warps:
 //   warp 0      one thread issues TMA tile loads (128-byte swizzle) into a ring
 //               of STAGES shared-memory slots, completion tracked by mbarriers;
 //   warp 1      one thread issues tcgen05.mma (M = 128, N = BN, K = 16) into a
 //               double-buffered TMEM accumulator and commits slot releases;
 //               the warp also owns the TMEM allocation;
-//   warps 2-9   epilogue (two warps per 32-lane TMEM quarter, alternate
-//               32-column chunks): tcgen05.ld, bias / activation / residual in
-//               FP32, stores to global memory, then release the accumulator
-//               buffer so the next tile's MMAs overlap.
+//   warps 2-17  epilogue (four warps per 32-lane TMEM quarter, every fourth
+//               32-column chunk): tcgen05.ld, bias / activation / residual in
+//               FP32, TMA stores of 32 x 32 chunks, then release the
+//               accumulator buffer so the next tile's MMAs overlap.
 // The row count M is read from device memory (unique rows are only known on
 // the device).  Every wait is bounded; on timeout the kernel sets
 // VQNQS_DEV_TIMEOUT, drains its own in-flight copies and frees its TMEM.
@@ -23,18 +23,24 @@
 
 namespace vq {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 320;
+constexpr int TC_BM = 128, TC_BK = 64;
 
-constexpr int EPI_WARPS = 8, SLOT_BYTES = 4096;  // per epilogue warp: one 32 x 32 output chunk
+// 16 epilogue warps, four per TMEM lane quarter; per epilogue warp one 32 x 32 output chunk slot
+constexpr int EPI_WARPS = 16, SLOT_BYTES = 4096, TC_THREADS = 64 + 32 * EPI_WARPS;
 
 template <int BN>
 struct TcCfg {
-    static constexpr int STAGES = BN >= 192 ? 4 : 6;
+    // as many ring stages (up to 6) as fit beside the output slots
+    static constexpr int STAGES_FIT = (227 * 1024 - 1024 - 512 - EPI_WARPS * SLOT_BYTES) / (TC_BM * TC_BK * 2 + BN * TC_BK * 2);
+    static constexpr int STAGES = STAGES_FIT < 6 ? STAGES_FIT : 6;
     static constexpr int A_BYTES = TC_BM * TC_BK * 2;
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BN <= 128 ? 128 : (2 * BN <= 256 ? 256 : 512);
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * SLOT_BYTES + 256;
+    // barriers (2 STAGES + 5 + EPI_WARPS words) and the TMEM address after the slots
+    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE_BYTES + (size_t)EPI_WARPS * SLOT_BYTES + 512;
+    static_assert((2 * STAGES + 5 + EPI_WARPS) * 8 + 4 <= 512, "barrier block");
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
 // erf by Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7 for all real x):
@@ -94,7 +100,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 256); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&accf[a], 1); tc::mbar_init(&acce[a], 32 * EPI_WARPS); }
         tc::mbar_init(done, 1);
         for (int w = 0; w < EPI_WARPS; ++w) tc::mbar_init(&rbar[w], 1);
         tc::fence_barrier_init();
@@ -158,7 +164,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             tc::mbar_wait(done, 0, status, 100000000LL);
         }
     } else {
-        // warps 2..9: two warps per TMEM lane quarter, each taking alternate 32-column chunks.
+        // warps 2..17: four warps per TMEM lane quarter, each taking every fourth 32-column chunk.
         // A chunk of 32 rows x 32 columns whose rows all exist goes out through the warp's
         // shared-memory slot and a TMA store (rows 128 bytes apart for FP32 with the 128-byte
         // swizzle, 64 bytes apart for BF16 with the 64-byte swizzle: conflict-free writes);
@@ -182,7 +188,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int row = rb + lane;
             const bool boxed = rb + 32 <= M;  // warp-uniform
 #pragma unroll 1
-            for (int c = part * 32; c < BN && ok; c += 64) {
+            for (int c = part * 32; c < BN && ok; c += 128) {
                 const int n = n0 + c;
                 if (boxed) {  // the slot is free once the previous store has read it
                     if (lane == 0) {
