@@ -238,6 +238,44 @@ def config_dict(w, path):
             "l2": "flushed between timed steps (256 MiB write); the step's working set is also far above L2"}
 
 
+def gemm_probe(m, dm: int, stream=None) -> dict:
+    """The QKV, MLP-up and MLP-down tensor-core GEMMs at M = 131072 (d_model dm):
+    3 untimed then 20 timed launches per shape, with the tensor and HBM fractions."""
+    import torch
+    pk = measured_peaks()
+    Mg = 131072
+    gemm = {"M": Mg, "peak_tflops": pk["bf16_tflops_burst"], "peak_source": f"bf16 dense, burst ({pk['src']})",
+            "shapes": {}}
+    for name, Ng, Kg, epi in (("qkv_bias_bf16", 3 * dm, dm, 0), ("mlp_up_bias_gelu_bf16", 4 * dm, dm, 1),
+                              ("mlp_down_bias_residual_f32", dm, 4 * dm, 2)):
+        A = torch.randn(Mg, Kg, device="cuda").to(torch.bfloat16)
+        Bt = (0.05 * torch.randn(Ng, Kg, device="cuda")).to(torch.bfloat16)
+        bias = torch.zeros(Ng, device="cuda")
+        Rg = torch.zeros(Mg, Ng, device="cuda") if epi == 2 else None
+        Cg = torch.empty(Mg, Ng, dtype=torch.bfloat16 if epi < 2 else torch.float32, device="cuda")
+        for _ in range(3):
+            m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(20):
+            m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        sec = a0.elapsed_time(a1) / 1e3 / 20
+        tf = 2.0 * Mg * Ng * Kg / sec / 1e12
+        # bytes a launch must move: A, Bt, C (and the residual R)
+        nbytes = Mg * Kg * 2 + Ng * Kg * 2 + Mg * Ng * (2 if epi < 2 else 4) + (Mg * Ng * 4 if epi == 2 else 0)
+        gbs = nbytes / sec / 1e9
+        t_tensor = 2.0 * Mg * Ng * Kg / (pk["bf16_tflops_burst"] * 1e12)
+        t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
+        gemm["shapes"][name] = {"N": Ng, "K": Kg, "us": sec * 1e6, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"],
+                                "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
+                                "roofline_bound": "tensor" if t_tensor >= t_hbm else "hbm",
+                                "roofline_frac": max(t_tensor, t_hbm) / sec}
+        del A, Bt, Rg, Cg
+    return gemm
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +287,8 @@ def main():
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
+    ap.add_argument("--gemm-only", action="store_true",
+                    help="run only the tensor-core GEMM probe (three shapes at M = 131072) and print it")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -260,6 +300,12 @@ def main():
     import torch.distributed as dist
     import synthetic_inputs as si
     from paper_2212_11296_gb300 import BF16, INCREMENTAL, REUSE, VQNQS
+
+    if args.gemm_only:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        m = VQNQS(4, True, 1.0, 1, 64, 2, 4, si.make_weights(16, 1, 64, 4))
+        print(json.dumps({"gemm_tc": gemm_probe(m, w["d_model"])}))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -369,40 +415,7 @@ def main():
 
     # the three per-location tensor-core GEMM shapes on a large M (the reuse
     # path only feeds them the few unique rows), each with its fused epilogue
-    gemm = None
-    if flags & BF16:
-        pk = measured_peaks()
-        dm = w["d_model"]
-        Mg = 131072
-        gemm = {"M": Mg, "peak_tflops": pk["bf16_tflops_burst"], "peak_source": f"bf16 dense, burst ({pk['src']})",
-                "shapes": {}}
-        for name, Ng, Kg, epi in (("qkv_bias_bf16", 3 * dm, dm, 0), ("mlp_up_bias_gelu_bf16", 4 * dm, dm, 1),
-                                  ("mlp_down_bias_residual_f32", dm, 4 * dm, 2)):
-            A = torch.randn(Mg, Kg, device="cuda").to(torch.bfloat16)
-            Bt = (0.05 * torch.randn(Ng, Kg, device="cuda")).to(torch.bfloat16)
-            bias = torch.zeros(Ng, device="cuda")
-            Rg = torch.zeros(Mg, Ng, device="cuda") if epi == 2 else None
-            Cg = torch.empty(Mg, Ng, dtype=torch.bfloat16 if epi < 2 else torch.float32, device="cuda")
-            for _ in range(3):
-                m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg)
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            for _ in range(20):
-                m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            sec = a0.elapsed_time(a1) / 1e3 / 20
-            tf = 2.0 * Mg * Ng * Kg / sec / 1e12
-            # bytes a launch must move: A, Bt, C (and the residual R)
-            nbytes = Mg * Kg * 2 + Ng * Kg * 2 + Mg * Ng * (2 if epi < 2 else 4) + (Mg * Ng * 4 if epi == 2 else 0)
-            gbs = nbytes / sec / 1e9
-            t_tensor = 2.0 * Mg * Ng * Kg / (pk["bf16_tflops_burst"] * 1e12)
-            t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
-            gemm["shapes"][name] = {"N": Ng, "K": Kg, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"],
-                                    "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
-                                    "roofline_bound": "tensor" if t_tensor >= t_hbm else "hbm",
-                                    "roofline_frac": max(t_tensor, t_hbm) / sec}
-            del A, Bt, Rg, Cg
+    gemm = gemm_probe(m, w["d_model"], stream) if flags & BF16 else None
 
     # roofline of the dominant stage, from the live CUDA-event stage times
     per_step = {k: v for k, v in prof.items() if v[1] > 0}
