@@ -22,10 +22,14 @@ so the output at p is the conditional of s_p.  Each block is pre-LayerNorm:
 and the head is log_softmax(LN_f(x) W_head + b_head) over the two spin values.
 LayerNorm uses eps = 1e-5 and the biased variance; GELU is the erf form.
 
+Multi-head VQ (Eq. vq with H heads): o is split into H segments of d/H
+values, segment h is quantized with its own codebook W_h of K vectors (the
+codebook block of the blob is W in R^{H x K x d/H}), and the quantized vector
+is the concatenation of the chosen W_h rows; H = 1 is the single-head case.
+
 Readings of the paper used here (it leaves block internals to prior work):
-pre-LN, erf-GELU, biases everywhere, one quantizer head (H = 1), and the
-argmax in Eq. vq read as the argmax of D = -||x - W_j||, i.e. the nearest
-codeword.  The squared distance is expanded as ||o||^2 - 2 o.W_j + ||W_j||^2 in
+pre-LN, erf-GELU, biases everywhere, and the argmax in Eq. vq read as the
+argmax of D = -||x_h - W_h,j||, i.e. the nearest codeword of each segment.  The squared distance is expanded as ||o||^2 - 2 o.W_j + ||W_j||^2 in
 float64; its argmin equals the direct one unless two distances agree to ~1e-15
 relative.
 """
@@ -49,14 +53,19 @@ class Params:
     layers: int
     n_max: int
     t: dict  # name -> float64 tensor
+    vq_heads: int = 1
 
 
-def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int) -> Params:
+def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_heads: int = 1) -> Params:
     """Split a flat float32 weight blob into named float64 tensors.
 
     The order is the documented blob order: token and position embeddings,
     then per layer LN1, W_qkv, codebook, W_o, LN2, W_1, W_2 (each matrix
-    followed by its bias), then LN_f and the head."""
+    followed by its bias), then LN_f and the head.  The codebook block holds
+    K * d values: [K, d] for one quantizer head, [vq_heads, K, d / vq_heads]
+    for several."""
+    if d % vq_heads:
+        raise ValueError("d must be a multiple of vq_heads")
     blob = torch.as_tensor(np.asarray(blob, dtype=np.float32)).double()
     pos = 0
     t = {}
@@ -72,7 +81,10 @@ def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int) -> Par
     for l in range(layers):
         take(f"{l}.ln1_g", d); take(f"{l}.ln1_b", d)
         take(f"{l}.w_qkv", d, 3 * d); take(f"{l}.b_qkv", 3 * d)
-        take(f"{l}.codebook", K, d)
+        if vq_heads == 1:
+            take(f"{l}.codebook", K, d)
+        else:
+            take(f"{l}.codebook", vq_heads, K, d // vq_heads)
         take(f"{l}.w_o", d, d); take(f"{l}.b_o", d)
         take(f"{l}.ln2_g", d); take(f"{l}.ln2_b", d)
         take(f"{l}.w_1", d, 4 * d); take(f"{l}.b_1", 4 * d)
@@ -81,7 +93,7 @@ def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int) -> Par
     take("w_head", d, 2); take("b_head", 2)
     if pos != blob.numel():
         raise ValueError(f"blob has {blob.numel()} values, layout needs {pos}")
-    return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t)
+    return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t, vq_heads=vq_heads)
 
 
 def layer_norm(x, g, b):
@@ -123,6 +135,32 @@ def nearest_code(o, codebook):
     return torch.argmin(sq_distances(o, codebook), dim=-1)
 
 
+def quantize(o, codebook):
+    """Eq. vq with H heads.  codebook [K, d] (H = 1) or [H, K, d / H].
+
+    Returns (V, codes): V the concatenation over h of W_h[c_h], codes [..., H]
+    with c_h the nearest codeword of segment h (lowest index on exact ties)."""
+    if codebook.dim() == 2:
+        c = nearest_code(o, codebook)
+        return codebook[c], c[..., None]
+    H, K, dq = codebook.shape
+    parts, codes = [], []
+    for h in range(H):
+        seg = o[..., h * dq:(h + 1) * dq]
+        c = nearest_code(seg, codebook[h])
+        parts.append(codebook[h][c])
+        codes.append(c)
+    return torch.cat(parts, dim=-1), torch.stack(codes, dim=-1)
+
+
+def segment_gap(o, codebook):
+    """Smallest relative_gap over the quantizer's segments."""
+    if codebook.dim() == 2:
+        return relative_gap(o, codebook)
+    H, K, dq = codebook.shape
+    return torch.stack([relative_gap(o[..., h * dq:(h + 1) * dq], codebook[h]) for h in range(H)]).min(0).values
+
+
 def tokens(spins: torch.Tensor) -> torch.Tensor:
     """Shift right: token at p is s_{p-1}, begin-of-sequence at p = 0."""
     C, N = spins.shape
@@ -156,14 +194,17 @@ def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
         a = layer_norm(x, t[f"{l}.ln1_g"], t[f"{l}.ln1_b"])
         o = causal_attention(a, t[f"{l}.w_qkv"], t[f"{l}.b_qkv"], P.heads)
         if quantizer is None:
-            c = nearest_code(o, t[f"{l}.codebook"])
-            vq = t[f"{l}.codebook"][c]
+            vq, c = quantize(o, t[f"{l}.codebook"])
+            if P.vq_heads == 1:
+                c = c[..., 0]
         else:
+            if P.vq_heads != 1:
+                raise ValueError("a replacement quantizer is defined for one quantizer head only")
             vq, c = quantizer(l, o)
         if record is not None:
             record.append(c)
         if gaps is not None:
-            gaps.append(relative_gap(o, t[f"{l}.codebook"]))
+            gaps.append(segment_gap(o, t[f"{l}.codebook"]))
         y = x + vq @ t[f"{l}.w_o"] + t[f"{l}.b_o"]
         h = gelu(layer_norm(y, t[f"{l}.ln2_g"], t[f"{l}.ln2_b"]) @ t[f"{l}.w_1"] + t[f"{l}.b_1"])
         x = y + h @ t[f"{l}.w_2"] + t[f"{l}.b_2"]

@@ -1,0 +1,80 @@
+"""Pins of the oracle's multi-head quantizer (Sec. 3.1, Eq. vq with H heads).
+
+* Brute force: the quantized vector is the joint nearest point over all K^H
+  concatenations of one codeword per segment (the squared distance splits into
+  one term per segment), found here by enumerating every tuple.
+* Scalar segments (H = d): each coordinate goes to its nearest codebook value
+  (closed form).
+* With K = 1 the codebook block [H, 1, d/H] is the same memory as a single
+  codeword [1, d]: the model read with H heads equals the one-head model.
+* The multi-head model is a normalised autoregressive distribution.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic_inputs as si
+from oracle import model
+
+
+@pytest.mark.parametrize("H,K,dq", [(2, 4, 4), (3, 3, 2), (4, 2, 3)])
+def test_quantize_is_joint_nearest_by_brute_force(H, K, dq):
+    g = torch.Generator().manual_seed(H * 100 + K * 10 + dq)
+    cb = torch.randn(H, K, dq, generator=g, dtype=torch.float64)
+    o = torch.randn(7, H * dq, generator=g, dtype=torch.float64)
+    V, codes = model.quantize(o, cb)
+    for r in range(o.shape[0]):
+        best, arg = None, None
+        for tup in itertools.product(range(K), repeat=H):
+            v = torch.cat([cb[h, tup[h]] for h in range(H)])
+            dist = float(((o[r] - v) ** 2).sum())
+            if best is None or dist < best:
+                best, arg = dist, tup
+        assert tuple(int(c) for c in codes[r]) == arg
+        assert torch.equal(V[r], torch.cat([cb[h, arg[h]] for h in range(H)]))
+
+
+def test_scalar_segments_closed_form():
+    d, K = 6, 5
+    rng = np.random.default_rng(3)
+    cb = rng.standard_normal((d, K, 1))
+    o = rng.standard_normal((9, d))
+    V, codes = model.quantize(torch.as_tensor(o), torch.as_tensor(cb))
+    want_idx = np.argmin(np.abs(o[:, :, None] - cb[None, :, :, 0]), axis=-1)
+    assert np.array_equal(codes.numpy(), want_idx)
+    assert np.allclose(V.numpy(), np.take_along_axis(cb[None, :, :, 0].repeat(9, 0), want_idx[..., None], -1)[..., 0],
+                       rtol=0, atol=0)
+
+
+def test_single_head_path_unchanged():
+    g = torch.Generator().manual_seed(5)
+    cb = torch.randn(6, 8, generator=g, dtype=torch.float64)
+    o = torch.randn(11, 8, generator=g, dtype=torch.float64)
+    V, codes = model.quantize(o, cb)
+    c = model.nearest_code(o, cb)
+    assert torch.equal(codes[:, 0], c) and torch.equal(V, cb[c])
+
+
+@pytest.mark.parametrize("H", [2, 4])
+def test_one_code_per_head_equals_single_head_model(H):
+    L, layers, d, heads = 4, 2, 16, 2
+    N = L * L
+    w = si.make_weights(N, layers, d, 1, seed=4, std=0.3)
+    P1 = model.parse_blob(w, N, layers, d, heads, 1)
+    PH = model.parse_blob(w, N, layers, d, heads, 1, vq_heads=H)
+    spins = si.make_samples(L, 12, seed=2)
+    assert np.array_equal(model.log_psi(P1, spins), model.log_psi(PH, spins))
+
+
+def test_multi_head_model_is_normalised():
+    N, layers, d, heads, K, H = 4, 2, 16, 2, 4, 4
+    w = si.make_weights(N, layers, d, K, seed=6, std=0.4)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H)
+    states = np.array(list(itertools.product([0, 1], repeat=N)))
+    lp = model.log_psi(P, states)
+    assert abs(np.exp(2.0 * lp).sum() - 1.0) < 1e-12
+    # several heads do change the model when K > 1
+    P1 = model.parse_blob(w, N, layers, d, heads, K)
+    assert not np.allclose(lp, model.log_psi(P1, states))
