@@ -37,20 +37,26 @@ def _check_dev(t: torch.Tensor, dtype, name):
 
 
 class VQNQS:
-    """One model on one lattice: vqnqs_create(L, periodic, J, layers, d_model, heads, K, weights)."""
+    """One model on one lattice: vqnqs_create(L, periodic, J, layers, d_model, heads, K, weights), or
+    vqnqs_create_vq(..., K, vq_heads, weights) for quantizers with vq_heads heads of K codes each."""
 
     def __init__(self, L: int, periodic: bool, J: float, layers: int, d_model: int, heads: int, K: int,
-                 weights: np.ndarray):
+                 weights: np.ndarray, vq_heads: int = 1):
         self.L, self.N = L, L * L
         self.periodic, self.J = bool(periodic), float(J)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
+        self.vq_heads = int(vq_heads)
         w = np.ascontiguousarray(weights, dtype=np.float32)
         n = lib().vqnqs_num_params(self.N, layers, d_model, K)
         if w.size != n:
             raise ValueError(f"weight blob has {w.size} floats, layout needs {n}")
         h = ctypes.c_void_p()
-        rc = lib().vqnqs_create(L, int(periodic), float(J), layers, d_model, heads, K,
-                                w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        if self.vq_heads == 1:
+            rc = lib().vqnqs_create(L, int(periodic), float(J), layers, d_model, heads, K,
+                                    w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+        else:
+            rc = lib().vqnqs_create_vq(L, int(periodic), float(J), layers, d_model, heads, K, self.vq_heads,
+                                       w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         if rc != 0:
             raise VQNQSError(f"vqnqs_create failed: {_lib.STATUS_NAMES.get(rc, rc)}")
         self._h = h
@@ -64,6 +70,7 @@ class VQNQS:
         self.L, self.N = None, N
         self.periodic, self.J, self.Gamma = bool(periodic), float(J), float(Gamma)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
+        self.vq_heads = 1
         w = np.ascontiguousarray(weights, dtype=np.float32)
         n = lib().vqnqs_num_params(N, layers, d_model, K)
         if w.size != n:

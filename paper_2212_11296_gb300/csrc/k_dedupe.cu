@@ -26,7 +26,8 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 }
 
 __device__ __forceinline__ unsigned long long make_key(int uid, int code) {
-    return ((((unsigned long long)(unsigned)uid) << 16) | (unsigned)code) + 1ULL;  // 0 = empty slot
+    // row id in the high word, the (packed) code in the low one; 0 = empty slot
+    return ((((unsigned long long)(unsigned)uid) << 32) | (unsigned)code) + 1ULL;
 }
 
 __global__ void k_hash_clear(unsigned long long* __restrict__ keys, size_t H, int* __restrict__ counters,

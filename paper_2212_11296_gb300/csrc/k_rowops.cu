@@ -44,20 +44,32 @@ __global__ void k_layernorm(const float* __restrict__ X, const int* __restrict__
 }
 
 // y = x[rep_uid] + T[rep_code]  (T = codebook @ W_o + b_o), then A = LN2(y).
+// With H quantizer heads the code packs c_h in bits [h * bits, (h + 1) * bits)
+// and T holds one table per head (b_o in head 0's): y = x + sum_h T_h[c_h].
 template <int PER>
 __global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restrict__ rep_uid,
                                  const int* __restrict__ rep_code, const float* __restrict__ T,
                                  const int* __restrict__ counters, int u_slot, const float* __restrict__ g,
                                  const float* __restrict__ b, int d, float* __restrict__ Y,
-                                 float* __restrict__ A_f32, __nv_bfloat16* __restrict__ A_bf16) {
+                                 float* __restrict__ A_f32, __nv_bfloat16* __restrict__ A_bf16, int vq_heads, int K,
+                                 int bits) {
     const int U = counters[u_slot];
+    const int mask = vq_heads == 1 ? -1 : (1 << bits) - 1;
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
         const float* x = X + (size_t)rep_uid[u] * d;
-        const float* t = T + (size_t)rep_code[u] * d;
+        const int code = rep_code[u];
+        const float* t = T + (size_t)(code & mask) * d;
         float y[PER], a[PER];
 #pragma unroll
-        for (int i = 0; i < PER; ++i) y[i] = x[lane + 32 * i] + t[lane + 32 * i];
+        for (int i = 0; i < PER; ++i) y[i] = t[lane + 32 * i];
+        for (int h = 1; h < vq_heads; ++h) {
+            const float* th = T + ((size_t)h * K + ((code >> (h * bits)) & mask)) * d;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) y[i] += th[lane + 32 * i];
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) y[i] = x[lane + 32 * i] + y[i];
         ln_row<PER>(y, lane, d, g, b, a);
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
@@ -69,22 +81,26 @@ __global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restr
     }
 }
 
-// T[j] = W_j @ w_o + b_o and cnorm[j] = ||W_j||^2, one block per codeword.
+// Per quantizer head h and codeword j (codebook [H][K][d / H]):
+// T_h[j] = W_h,j @ w_o[rows h * d / H ..] (+ b_o for h = 0) and cnorm_h[j] = ||W_h,j||^2,
+// one block per (h, j).  With one head: T[j] = W_j @ w_o + b_o.
 __global__ void k_table_T(const float* __restrict__ cb, const float* __restrict__ wo, const float* __restrict__ bo,
-                          int K, int d, float* __restrict__ T, float* __restrict__ cnorm) {
+                          int K, int d, int vq_heads, float* __restrict__ T, float* __restrict__ cnorm) {
     extern __shared__ float s_w[];
-    for (int j = blockIdx.x; j < K; j += gridDim.x) {
-        for (int k = threadIdx.x; k < d; k += blockDim.x) s_w[k] = cb[(size_t)j * d + k];
+    const int dq = d / vq_heads;
+    for (int hj = blockIdx.x; hj < vq_heads * K; hj += gridDim.x) {
+        const int h = hj / K;
+        for (int k = threadIdx.x; k < dq; k += blockDim.x) s_w[k] = cb[(size_t)hj * dq + k];
         __syncthreads();
         for (int n = threadIdx.x; n < d; n += blockDim.x) {
             float acc = 0.f;
-            for (int k = 0; k < d; ++k) acc = fmaf(s_w[k], wo[(size_t)k * d + n], acc);
-            T[(size_t)j * d + n] = acc + bo[n];
+            for (int k = 0; k < dq; ++k) acc = fmaf(s_w[k], wo[((size_t)h * dq + k) * d + n], acc);
+            T[(size_t)hj * d + n] = h == 0 ? acc + bo[n] : acc;
         }
         if (threadIdx.x == 0) {
             float s = 0.f;
-            for (int k = 0; k < d; ++k) s = fmaf(s_w[k], s_w[k], s);
-            cnorm[j] = s;
+            for (int k = 0; k < dq; ++k) s = fmaf(s_w[k], s_w[k], s);
+            cnorm[hj] = s;
         }
         __syncthreads();
     }
@@ -150,15 +166,18 @@ cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, co
 
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
-                                  float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid) {
-    VQ_DISPATCH_PER(d, k_residual_vq_ln, X, rep_uid, rep_code, T, counters, u_slot, g, b, d, Y, A_f32, A_bf16);
+                                  float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads, int K,
+                                  int bits) {
+    VQ_DISPATCH_PER(d, k_residual_vq_ln, X, rep_uid, rep_code, T, counters, u_slot, g, b, d, Y, A_f32, A_bf16,
+                    vq_heads, K, bits);
     return cudaGetLastError();
 }
 
-cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, float* T,
-                           float* cnorm, cudaStream_t st) {
-    int grid = K < 1024 ? K : 1024;
-    k_table_T<<<grid, 256, d * sizeof(float), st>>>(codebook, w_o, b_o, K, d, T, cnorm);
+cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, int vq_heads,
+                           float* T, float* cnorm, cudaStream_t st) {
+    if (vq_heads < 1 || d % vq_heads) return cudaErrorInvalidValue;
+    int grid = vq_heads * K < 1024 ? vq_heads * K : 1024;
+    k_table_T<<<grid, 256, d * sizeof(float), st>>>(codebook, w_o, b_o, K, d, vq_heads, T, cnorm);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,10 @@
 //
 //   code(o) = argmin_j ||o - W_j||^2 = argmin_j (||W_j||^2 - 2 o . W_j),  lowest j on ties.
 //
+// With H quantizer heads each segment o_h (d / H values, row stride d) is
+// assigned against its own codebook by one launch, and the packed code holds
+// c_h in bits [h * bits, (h + 1) * bits).
+//
 // The o . W_j products are a [rows x d] x [d x K] contraction tiled like the
 // FP32 GEMM (128 rows x 128 codewords per pass, 8x8 per thread); the epilogue
 // keeps (best, index, second best) per row in registers and merges across the
@@ -32,9 +36,9 @@ __device__ __forceinline__ void best_merge(Best& a, float c1, int j1, float c2) 
 }
 
 __global__ void __launch_bounds__(VQ_THREADS, 2)
-k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
+k_vq_argmin(const float* __restrict__ O, int ldo, const int* __restrict__ counters, const int* __restrict__ act_rows,
             const float* __restrict__ W, const float* __restrict__ cnorm, int K, int d, int* __restrict__ code,
-            long long* __restrict__ near_ties, int a_slot) {
+            int shift, int accumulate, long long* __restrict__ near_ties, int a_slot) {
     __shared__ __align__(16) float As[2][VQ_BK][VQ_BM];
     __shared__ __align__(16) float Bs[2][VQ_BK][VQ_BN];  // Bs[k][j] = W[j][k]
     __shared__ int s_ties;
@@ -51,7 +55,7 @@ k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const
         for (int i = 0; i < 8; ++i) { best[i].v1 = INFINITY; best[i].i1 = 0x7fffffff; best[i].v2 = INFINITY; osq[i] = 0.f; }
         const bool a_ok = (m0 + a_row) < R;
         const int a_src = a_ok ? (act_rows ? act_rows[m0 + a_row] : m0 + a_row) : 0;
-        const float* a_ptr = O + (size_t)a_src * d + a_k;
+        const float* a_ptr = O + (size_t)a_src * ldo + a_k;
 
         for (int n0 = 0; n0 < K; n0 += VQ_BN) {
             float acc[8][8];
@@ -133,7 +137,8 @@ k_vq_argmin(const float* __restrict__ O, const int* __restrict__ counters, const
             for (int i = 0; i < 8; ++i) {
                 const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
                 if (m < R) {
-                    code[act_rows ? act_rows[m] : m] = best[i].i1;
+                    const int r = act_rows ? act_rows[m] : m;
+                    code[r] = (accumulate ? code[r] : 0) | (best[i].i1 << shift);
                     const float l1 = best[i].v1 + osq[i], l2 = best[i].v2 + osq[i];
                     if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
                 }
@@ -163,8 +168,27 @@ cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act
     int tiles = (Rmax + VQ_BM - 1) / VQ_BM;
     int grid = tiles < 2 * num_sms ? tiles : 2 * num_sms;
     if (grid < 1) grid = 1;
-    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, counters, act_rows, codebook, cnorm, K, d, code, near_ties, a_slot);
+    k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O, d, counters, act_rows, codebook, cnorm, K, d, code, 0, 0, near_ties,
+                                             a_slot);
     return cudaGetLastError();
+}
+
+cudaError_t launch_vq_argmin_heads(const float* O, const int* counters, const int* act_rows, const float* codebook,
+                                   const float* cnorm, int K, int d, int vq_heads, int bits, int* code,
+                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot) {
+    const int dq = d / vq_heads;
+    if (d % vq_heads || dq % VQ_BK) return cudaErrorInvalidValue;
+    int tiles = (Rmax + VQ_BM - 1) / VQ_BM;
+    int grid = tiles < 2 * num_sms ? tiles : 2 * num_sms;
+    if (grid < 1) grid = 1;
+    for (int h = 0; h < vq_heads; ++h) {  // segment h: its own codebook, its bits of the packed code
+        k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O + (size_t)h * dq, d, counters, act_rows,
+                                                 codebook + (size_t)h * K * dq, cnorm + (size_t)h * K, K, dq, code,
+                                                 h * bits, h > 0 ? 1 : 0, near_ties, a_slot);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace vq

@@ -14,6 +14,7 @@ using namespace vq;
 
 struct vqnqs_ctx {
     int L = 0, N = 0, periodic = 0, layers = 0, d = 0, heads = 0, K = 0, nb = 0;
+    int vq_heads = 1, vq_bits = 0;  // quantizer heads; bits of one head's field in a packed code
     int model = MODEL_HEISENBERG;
     int max_conn = 0;  // connected configurations per sample at most (bonds, or sites for the Ising chain)
     double J = 1.0, Gamma = 0.0;
@@ -231,12 +232,14 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
     const int d = ctx->d, K = ctx->K;
     for (int l = 0; l < ctx->layers; ++l) {
         LayerW& w = ctx->lw[l];
-        VQ_CK(launch_table_T(w.codebook, w.w_o, w.b_o, K, d, w.T, w.cnorm, st));
+        VQ_CK(launch_table_T(w.codebook, w.w_o, w.b_o, K, d, ctx->vq_heads, w.T, w.cnorm, st));
         VQ_CK(launch_transpose_bf16(w.w_qkv, d, 3 * d, w.wqkv_t, st));
         VQ_CK(launch_transpose_bf16(w.w_1, d, 4 * d, w.w1_t, st));
         VQ_CK(launch_transpose_bf16(w.w_2, 4 * d, d, w.w2_t, st));
-        VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
-        VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
+        if (ctx->vq_heads == 1) {  // the tensor-core search and the incremental certificate: one head
+            VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
+            VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
+        }
     }
     return VQNQS_OK;
 }
@@ -424,7 +427,12 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         }
         const int* vq_list = inc ? vq_rows : act_rows;
         const int vq_slot = inc ? CNT_V : CNT_A;
-        if (bf16 && vq_tc_supported(K, d))
+        if (ctx->vq_heads > 1)  // one search per quantizer head, FP32 on the CUDA cores
+            VQ_STAGE(S_VQ, ctx->vq_heads,
+                     launch_vq_argmin_heads(O, counters, vq_list, w.codebook, w.cnorm, K, d, ctx->vq_heads,
+                                            ctx->vq_bits, code, ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms,
+                                            vq_slot));
+        else if (bf16 && vq_tc_supported(K, d))
             VQ_STAGE(S_VQ, 1, launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, vq_list, w.cnorm, K, d, code,
                                            ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, Rmax, vq_slot));
         else
@@ -440,14 +448,16 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
                                ctx->num_sms));
         if (bf16) {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
-                                                        d, Y, nullptr, A16, st, g_urows));
+                                                        d, Y, nullptr, A16, st, g_urows, ctx->vq_heads, K,
+                                                        ctx->vq_bits));
             VQ_STAGE(S_MLP1, 1, launch_gemm_tc(A16, Umax, w.tm_w1, w.b_1, nullptr, Hid16, counters, un, 4 * d, d, 1,
                                                ctx->status, st, ctx->num_sms, ctx->bn[1]));
             VQ_STAGE(S_MLP2, 1, launch_gemm_tc(Hid16, Umax, w.tm_w2, w.b_2, Y, X_next, counters, un, d, 4 * d, 2,
                                                ctx->status, st, ctx->num_sms, ctx->bn[2]));
         } else {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
-                                                        d, Y, A, nullptr, st, g_urows));
+                                                        d, Y, A, nullptr, st, g_urows, ctx->vq_heads, K,
+                                                        ctx->vq_bits));
             VQ_STAGE(S_MLP1, 1, launch_sgemm(A, w.w_1, w.b_1, nullptr, Hid, counters, un, Umax, 4 * d, d,
                                              EPI_BIAS_GELU, st, ctx->num_sms));
             VQ_STAGE(S_MLP2, 1, launch_sgemm(Hid, w.w_2, w.b_2, Y, X_next, counters, un, Umax, d, 4 * d,
@@ -479,6 +489,7 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -736,11 +747,16 @@ size_t vqnqs_num_params(int n_max, int layers, int d_model, int K) {
 namespace {
 // Shared by vqnqs_create (L x L Heisenberg lattice) and vqnqs_create_tfim (N-site chain).
 int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, int layers, int d_model, int heads,
-               int K, const float* weights, vqnqs_ctx** out) {
+               int K, const float* weights, vqnqs_ctx** out, int vq_heads = 1) {
     if (!out) return VQNQS_ERR_ARG;
     *out = nullptr;
     if (N < 2 || N > 512 || layers < 1 || layers > VQNQS_MAX_LAYERS || d_model < 32 || d_model % 32 ||
         d_model > 1024 || heads < 1 || d_model % heads || K < 1 || K > 65535 || !weights)
+        return VQNQS_ERR_ARG;
+    int vq_bits = 1;
+    while ((1 << vq_bits) < K) ++vq_bits;
+    if (vq_heads < 1 || vq_heads > 8 || d_model % vq_heads || (d_model / vq_heads) % 8 ||
+        (vq_heads > 1 && vq_heads * vq_bits > 31))
         return VQNQS_ERR_ARG;
     const int dh = d_model / heads;
     if (!(dh == 8 || dh == 16 || dh == 32)) return VQNQS_ERR_ARG;
@@ -748,6 +764,7 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     ctx->model = model;
     ctx->L = L; ctx->N = N; ctx->periodic = periodic ? 1 : 0; ctx->J = J; ctx->Gamma = Gamma;
     ctx->layers = layers; ctx->d = d_model; ctx->heads = heads; ctx->K = K;
+    ctx->vq_heads = vq_heads; ctx->vq_bits = vq_heads > 1 ? vq_bits : 0;
     auto bail = [&](int code) { vqnqs_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(VQNQS_ERR_CUDA);
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
@@ -788,8 +805,8 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     const size_t d = d_model;
     for (int l = 0; l < layers; ++l) {
         LayerW& w = ctx->lw[l];
-        w.T = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
-        w.cnorm = static_cast<float*>(dalloc((size_t)K * sizeof(float)));
+        w.T = static_cast<float*>(dalloc((size_t)vq_heads * K * d * sizeof(float)));
+        w.cnorm = static_cast<float*>(dalloc((size_t)vq_heads * K * sizeof(float)));
         w.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * sizeof(__nv_bfloat16)));
         w.w1_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
         w.w2_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
@@ -814,7 +831,7 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     bind_weights(ctx);
     int rc = vqnqs_set_weights(ctx, weights, 0, nullptr);
     if (rc != VQNQS_OK) return bail(rc);
-    if (vq_tc_supported(K, d_model)) {
+    if (vq_heads == 1 && vq_tc_supported(K, d_model)) {
         for (int l = 0; l < layers; ++l) {
             LayerW& w = ctx->lw[l];
             if (make_tmap_codebook(&w.tm_cb_hi, w.cb_hi, K, d_model) != cudaSuccess ||
@@ -848,6 +865,16 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
     return create_ctx(MODEL_TFIM_CHAIN, 0, N, periodic, J, Gamma, layers, d_model, heads, K, weights, out);
 }
 
+int vqnqs_create_vq(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
+                    const float* weights, vqnqs_ctx** out) {
+    if (L < 2 || L * L > 512) {
+        if (out) *out = nullptr;
+        return VQNQS_ERR_ARG;
+    }
+    return create_ctx(MODEL_HEISENBERG, L, L * L, periodic, J, 0.0, layers, d_model, heads, K, weights, out,
+                      vq_heads);
+}
+
 int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream) {
     if (!ctx || !weights) return VQNQS_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -879,6 +906,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1037,10 +1065,12 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
                        float* grad, int flags, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
+    if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: one quantizer head only");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
+        if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1098,6 +1128,7 @@ int vqnqs_vq_assign(vqnqs_ctx* ctx, int layer, int R, const float* O, int* code,
                     void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
+    if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: one quantizer head only");
     if (layer < 0 || layer >= ctx->layers || R < 0) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: bad layer or R");
     if (R > 0 && (!O || !code)) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: null pointer");
     if ((reinterpret_cast<uintptr_t>(O) & 15)) return fail(ctx, VQNQS_ERR_ARG, "vq_assign: O must be 16-byte aligned");
@@ -1240,6 +1271,7 @@ int vqnqs_sample(vqnqs_ctx* ctx, int B, const float* uniforms, uint8_t* spins, f
                  size_t ws_bytes, void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
+    if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "sample: one quantizer head only");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     const bool bf16 = (flags & VQNQS_BF16) != 0;
@@ -1352,6 +1384,7 @@ int vqnqs_vmc_step(vqnqs_ctx* ctx, int B, const float* uniforms, float lr, uint8
                    double* mean_var, int flags, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
+    if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: one quantizer head only");
     if (B <= 0 || !uniforms || !spins || !e_loc || !grad || !mean_var)
         return fail(ctx, VQNQS_ERR_ARG, "vmc step: B > 0 and every buffer are required");
     // e_loc holds the drawn configurations' log psi until the local energies overwrite it

@@ -172,11 +172,15 @@ cudaError_t launch_accumulate_stats(const int* counters, int layers, int S, long
 // LayerNorm and per-location helpers (k_rowops.cu)
 cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, const float* g, const float* b, int d,
                              float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid);
+// residual with the quantized vector's projection, then LN2; with vq_heads > 1 the
+// code packs one bits-wide field per head and T holds vq_heads tables of K rows
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
-                                  float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid);
-cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, float* T,
-                           float* cnorm, cudaStream_t st);
+                                  float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads = 1,
+                                  int K = 0, int bits = 0);
+// T and cnorm of a layer's codebook ([vq_heads][K][d / vq_heads])
+cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, int vq_heads,
+                           float* T, float* cnorm, cudaStream_t st);
 cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st);
 
 // FP32 SIMT GEMM (k_gemm_f32.cu): C[M,N] = A[M,K] @ B[K,N] + bias (+GELU) (+R); M = counters[u_slot]
@@ -220,6 +224,10 @@ cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream
 cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
                              const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
                              cudaStream_t st, int num_sms, int a_slot = CNT_A);
+// the same per quantizer head: segment h of every row against codebook h, packed codes
+cudaError_t launch_vq_argmin_heads(const float* O, const int* counters, const int* act_rows, const float* codebook,
+                                   const float* cnorm, int K, int d, int vq_heads, int bits, int* code,
+                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot = CNT_A);
 
 cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st);
 

@@ -1,0 +1,123 @@
+"""Multi-head vector quantizers (Sec. 3.1, Eq. vq with H heads) through the C ABI.
+
+* FP32, plain and reuse paths, H = 2 and 4: local energies and log psi within
+  1e-5 of the FP64 oracle (near-tie rule of test_gpu_parity), reuse bitwise
+  equal to plain, and the packed codes (c_h in bits [h b, (h + 1) b)) equal
+  to the oracle's codes on rows without a near tie.
+* BF16 GEMMs with H = 2 at 8x8, d_model 128: as close to FP32 as the
+  one-head BF16 path.
+* Table 1's bandwidths at 16x16 (three blocks, d_model 256, 8 attention heads,
+  64 codes per head; H = 1, 2, 4 = 6, 12, 24 bits): oracle parity on sampled
+  configurations and the unique-row fraction and FLOP reduction per bandwidth.
+* The entry points defined for one head refuse several.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic_inputs as si
+from oracle import hamiltonian, model
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def rel_err(got, want, N):
+    return np.abs(np.asarray(got, np.float64) - want) / np.maximum(np.abs(want), 1e-3 * N)
+
+
+def check(P, spins, got, L, tol=FP32_TOL, max_miss=0.25):
+    N = L * L
+    gap = np.empty(len(spins))
+    want = hamiltonian.local_energy(P, spins, L, True, 1.0, min_gap=gap)
+    err = rel_err(got, want, N)
+    miss = err > tol
+    for i in np.argsort(-err)[:4]:
+        print(f"sample {i}: rel err {err[i]:.3e}  min gap {gap[i]:.3e}")
+    assert not np.any(miss & (gap >= 1e-6))
+    assert miss.mean() <= max_miss
+
+
+@pytest.mark.parametrize("H", [2, 4])
+def test_fp32_plain_and_reuse_match_oracle_4x4(H):
+    from paper_2212_11296_gb300 import REUSE, VQNQS
+    L, layers, d, heads, K, B = 4, 2, 32, 4, 16, 64
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H)
+    e_plain = m.local_energy(s, 0)
+    e_reuse = m.local_energy(s, REUSE)
+    assert torch.equal(e_plain, e_reuse)
+    check(P, spins, e_reuse.cpu().numpy(), L)
+    # log psi and the packed codes of the samples themselves
+    rec = []
+    gap = np.empty(B)
+    lp_or = model.log_psi(P, spins, record=rec, min_gap=gap)
+    codes, lp = m.codes(s)
+    assert np.max(np.abs(lp.cpu().numpy() - lp_or) / np.abs(lp_or)) <= FP32_TOL
+    bits = int(np.ceil(np.log2(K)))
+    want = np.concatenate([np.stack([sum(c[..., h].numpy().astype(np.int64) << (h * bits) for h in range(H))
+                                     for c in batch], axis=1) for batch in rec])  # [B, layers, N]
+    got = codes.cpu().numpy()
+    ok = gap >= 1e-6
+    assert np.array_equal(got[ok], want[ok])
+    assert m.stats()["device_status"] == 0
+
+
+def test_bf16_two_heads_close_to_fp32():
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B = 8, 2, 128, 4, 64, 128
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m1 = VQNQS(L, True, 1.0, layers, d, heads, K, w)
+    m2 = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=2)
+    d1 = rel_err(m1.local_energy(s, REUSE | BF16).cpu().numpy(), m1.local_energy(s, REUSE).cpu().numpy(), N)
+    d2 = rel_err(m2.local_energy(s, REUSE | BF16).cpu().numpy(), m2.local_energy(s, REUSE).cpu().numpy(), N)
+    print(f"BF16 vs FP32: one head median {np.median(d1):.2e}, two heads median {np.median(d2):.2e}")
+    assert np.median(d2) <= 2 * np.median(d1) + 1e-4
+    assert d2.max() <= 0.1
+    assert torch.equal(m2.local_energy(s, REUSE | BF16), m2.local_energy(s, BF16))
+
+
+def test_table1_bandwidths_16x16():
+    from paper_2212_11296_gb300 import REUSE, VQNQS
+    L, layers, d, heads, K, B = 16, 3, 256, 8, 64, 32
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    for H in (1, 2, 4):
+        m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H)
+        m.reset_stats()
+        e = m.local_energy(s, REUSE).cpu().numpy()
+        st = m.stats()
+        rows = st["rows"]
+        uniq = [u / rows for u in st["unique_rows"][1:]]
+        print(f"H = {H} ({H * 6} bits): unique-row fraction per layer {', '.join(f'{u:.4f}' for u in uniq)}; "
+              f"FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
+        P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H)
+        check(P, spins[:2], e[:2], L, max_miss=0.5)
+        assert st["device_status"] == 0
+
+
+def test_one_head_entry_points_refuse_several():
+    from paper_2212_11296_gb300 import INCREMENTAL, REUSE, VQNQS, VQNQSError
+    L, layers, d, heads, K = 4, 2, 32, 4, 16
+    w = si.make_weights(L * L, layers, d, K, seed=0)
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=2)
+    s = torch.as_tensor(si.make_samples(L, 4, seed=1)).cuda()
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.local_energy(s, REUSE | INCREMENTAL)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.grad_log_psi(s)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.sample(torch.rand(4, L * L, device="cuda"))
+    with pytest.raises(VQNQSError):  # 8 heads of 64 codes: 48 bits do not fit a packed code
+        VQNQS(4, True, 1.0, 1, 64, 2, 64, si.make_weights(16, 1, 64, 64), vq_heads=8)
+    with pytest.raises(VQNQSError):  # d_model not a multiple of the heads
+        VQNQS(4, True, 1.0, layers, d, heads, K, w, vq_heads=3)
