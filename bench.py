@@ -276,6 +276,49 @@ def gemm_probe(m, dm: int, stream=None) -> dict:
     return gemm
 
 
+def vq_sweep(args) -> dict:
+    """Table 1's protocol with seeded random weights: the same 16x16 network (three
+    blocks, d_model 256, 8 attention heads, 64 codes per quantizer head) with 1, 2 and
+    4 quantizer heads (6, 12, 24 bits); per bandwidth the unique-row fraction per
+    layer, the FLOP reduction and the timed local energies per second (FP32 reuse
+    path, the search runs per head on the CUDA cores; L2 flushed between steps)."""
+    import torch
+    import synthetic_inputs as si
+    from paper_2212_11296_gb300 import REUSE, VQNQS
+    L, layers, d, heads, K, B = 16, 3, 256, 8, 64, 512
+    N = L * L
+    blob = si.make_weights(N, layers, d, K, seed=0)
+    spins = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"16x16 periodic Heisenberg, {layers} blocks d_model {d} heads {heads}, "
+                       f"{K} codes per quantizer head, {B} uniform S_z=0 samples", "flags": "reuse (FP32)",
+           "data": "synthetic, seeded random weights", "bandwidths": {}}
+    for H in (1, 2, 4):
+        m = VQNQS(L, True, 1.0, layers, d, heads, K, blob, vq_heads=H)
+        ws = m.workspace(REUSE)
+        e = torch.empty(B, device="cuda")
+        for _ in range(2):
+            m.local_energy(spins, REUSE, out=e, workspace=ws)
+        m.reset_stats()
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            m.local_energy(spins, REUSE, out=e, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        st = m.stats()
+        out["bandwidths"][f"{6 * H} bits"] = {
+            "vq_heads": H, "unique_row_fraction": [u / st["rows"] for u in st["unique_rows"][1:]],
+            "flop_reduction": st["flops_full"] / st["flops_done"], "ms_per_step": min(ms),
+            "local_energies_per_s": B / (min(ms) / 1e3), "near_ties": st["near_ties"],
+            "device_status": st["device_status"]}
+        m.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -289,6 +332,9 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--gemm-only", action="store_true",
                     help="run only the tensor-core GEMM probe (three shapes at M = 131072) and print it")
+    ap.add_argument("--vq-sweep", action="store_true",
+                    help="quantization bandwidth sweep (Table 1 protocol, random weights): 16x16, three blocks, "
+                         "64 codes per head, 1, 2 and 4 quantizer heads")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -305,6 +351,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         m = VQNQS(4, True, 1.0, 1, 64, 2, 4, si.make_weights(16, 1, 64, 4))
         print(json.dumps({"gemm_tc": gemm_probe(m, w["d_model"])}))
+        return 0
+    if args.vq_sweep:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(vq_sweep(args)))
         return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
