@@ -22,6 +22,9 @@ so the output at p is the conditional of s_p.  Each block is pre-LayerNorm:
 and the head is log_softmax(LN_f(x) W_head + b_head) over the two spin values.
 LayerNorm uses eps = 1e-5 and the biased variance; GELU is the erf form.
 
+Optional final half-block (Table 1's networks): after the blocks,
+x <- x + W_o attention(LN(x)) + b_o with its own weights and no quantizer.
+
 Multi-head VQ (Eq. vq with H heads): o is split into H segments of d/H
 values, segment h is quantized with its own codebook W_h of K vectors (the
 codebook block of the blob is W in R^{H x K x d/H}), and the quantized vector
@@ -54,16 +57,19 @@ class Params:
     n_max: int
     t: dict  # name -> float64 tensor
     vq_heads: int = 1
+    half_block: bool = False
 
 
-def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_heads: int = 1) -> Params:
+def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_heads: int = 1,
+               half_block: bool = False) -> Params:
     """Split a flat float32 weight blob into named float64 tensors.
 
     The order is the documented blob order: token and position embeddings,
     then per layer LN1, W_qkv, codebook, W_o, LN2, W_1, W_2 (each matrix
     followed by its bias), then LN_f and the head.  The codebook block holds
     K * d values: [K, d] for one quantizer head, [vq_heads, K, d / vq_heads]
-    for several."""
+    for several.  With half_block, LN, W_qkv and W_o of the final
+    attention-only half-block follow the blocks."""
     if d % vq_heads:
         raise ValueError("d must be a multiple of vq_heads")
     blob = torch.as_tensor(np.asarray(blob, dtype=np.float32)).double()
@@ -89,11 +95,16 @@ def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_hea
         take(f"{l}.ln2_g", d); take(f"{l}.ln2_b", d)
         take(f"{l}.w_1", d, 4 * d); take(f"{l}.b_1", 4 * d)
         take(f"{l}.w_2", 4 * d, d); take(f"{l}.b_2", d)
+    if half_block:
+        take("h.ln_g", d); take("h.ln_b", d)
+        take("h.w_qkv", d, 3 * d); take("h.b_qkv", 3 * d)
+        take("h.w_o", d, d); take("h.b_o", d)
     take("lnf_g", d); take("lnf_b", d)
     take("w_head", d, 2); take("b_head", 2)
     if pos != blob.numel():
         raise ValueError(f"blob has {blob.numel()} values, layout needs {pos}")
-    return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t, vq_heads=vq_heads)
+    return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t, vq_heads=vq_heads,
+                  half_block=half_block)
 
 
 def layer_norm(x, g, b):
@@ -208,6 +219,10 @@ def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
         y = x + vq @ t[f"{l}.w_o"] + t[f"{l}.b_o"]
         h = gelu(layer_norm(y, t[f"{l}.ln2_g"], t[f"{l}.ln2_b"]) @ t[f"{l}.w_1"] + t[f"{l}.b_1"])
         x = y + h @ t[f"{l}.w_2"] + t[f"{l}.b_2"]
+    if P.half_block:  # Table 1's final half-block: attention and W_o, no quantizer, no MLP
+        a = layer_norm(x, t["h.ln_g"], t["h.ln_b"])
+        o = causal_attention(a, t["h.w_qkv"], t["h.b_qkv"], P.heads)
+        x = x + o @ t["h.w_o"] + t["h.b_o"]
     logits = layer_norm(x, t["lnf_g"], t["lnf_b"]) @ t["w_head"] + t["b_head"]
     return torch.log_softmax(logits, dim=-1)
 

@@ -75,10 +75,12 @@ def normals(seed: int, n: int) -> np.ndarray:
     return out[:n]
 
 
-def blob_segments(n_max: int, layers: int, d: int, K: int):
+def blob_segments(n_max: int, layers: int, d: int, K: int, half_block: bool = False):
     """(name, shape, kind) for every tensor of the blob, in order.
 
-    kind is 'w' (random), 'zero' (bias / LayerNorm shift) or 'one' (gain)."""
+    kind is 'w' (random), 'zero' (bias / LayerNorm shift) or 'one' (gain).  With
+    half_block the final attention-only half-block (LN, W_qkv, W_o and their
+    biases) follows the quantized blocks."""
     seg = [("tok_emb", (3, d), "w"), ("pos_emb", (n_max, d), "w")]
     for l in range(layers):
         p = f"l{l}."
@@ -91,22 +93,26 @@ def blob_segments(n_max: int, layers: int, d: int, K: int):
             (p + "w_1", (d, 4 * d), "w"), (p + "b_1", (4 * d,), "zero"),
             (p + "w_2", (4 * d, d), "w"), (p + "b_2", (d,), "zero"),
         ]
+    if half_block:
+        seg += [("h.ln_g", (d,), "one"), ("h.ln_b", (d,), "zero"),
+                ("h.w_qkv", (d, 3 * d), "w"), ("h.b_qkv", (3 * d,), "zero"),
+                ("h.w_o", (d, d), "w"), ("h.b_o", (d,), "zero")]
     seg += [("lnf_g", (d,), "one"), ("lnf_b", (d,), "zero"),
             ("w_head", (d, 2), "w"), ("b_head", (2,), "zero")]
     return seg
 
 
-def num_params(n_max: int, layers: int, d: int, K: int) -> int:
-    return int(sum(int(np.prod(s)) for _, s, _ in blob_segments(n_max, layers, d, K)))
+def num_params(n_max: int, layers: int, d: int, K: int, half_block: bool = False) -> int:
+    return int(sum(int(np.prod(s)) for _, s, _ in blob_segments(n_max, layers, d, K, half_block)))
 
 
 def make_weights(n_max: int, layers: int, d: int, K: int, seed: int = 0,
-                 std: float = 0.02) -> np.ndarray:
+                 std: float = 0.02, half_block: bool = False) -> np.ndarray:
     """Seeded float32 weight blob in the layout documented above."""
-    n = num_params(n_max, layers, d, K)
+    n = num_params(n_max, layers, d, K, half_block)
     blob = (std * normals(seed, n)).astype(np.float32)
     off = 0
-    for _, shape, kind in blob_segments(n_max, layers, d, K):
+    for _, shape, kind in blob_segments(n_max, layers, d, K, half_block):
         sz = int(np.prod(shape))
         if kind == "zero":
             blob[off:off + sz] = 0.0

@@ -78,3 +78,44 @@ def test_multi_head_model_is_normalised():
     # several heads do change the model when K > 1
     P1 = model.parse_blob(w, N, layers, d, heads, K)
     assert not np.allclose(lp, model.log_psi(P1, states))
+
+
+def _zero_half_block_blob(N, layers, d, K, seed, std=0.3):
+    """The blob of a half-block model whose W_o and b_o are zero, and the blob of the
+    same network without the half-block."""
+    w_h = si.make_weights(N, layers, d, K, seed=seed, std=std, half_block=True)
+    off = 0
+    for name, shape, _ in si.blob_segments(N, layers, d, K, half_block=True):
+        sz = int(np.prod(shape))
+        if name in ("h.w_o", "h.b_o"):
+            w_h[off:off + sz] = 0.0
+        off += sz
+    keep = []
+    off = 0
+    for name, shape, _ in si.blob_segments(N, layers, d, K, half_block=True):
+        sz = int(np.prod(shape))
+        if not name.startswith("h."):
+            keep.append(w_h[off:off + sz])
+        off += sz
+    return w_h, np.concatenate(keep)
+
+
+def test_half_block_with_zero_projection_is_the_plain_model():
+    L, layers, d, heads, K = 4, 2, 16, 2, 4
+    N = L * L
+    w_h, w = _zero_half_block_blob(N, layers, d, K, seed=8)
+    Ph = model.parse_blob(w_h, N, layers, d, heads, K, half_block=True)
+    P = model.parse_blob(w, N, layers, d, heads, K)
+    spins = si.make_samples(L, 10, seed=3)
+    assert np.array_equal(model.log_psi(Ph, spins), model.log_psi(P, spins))
+
+
+def test_half_block_model_is_normalised_and_differs():
+    N, layers, d, heads, K = 4, 2, 16, 2, 4
+    w = si.make_weights(N, layers, d, K, seed=9, std=0.4, half_block=True)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=2, half_block=True)
+    states = np.array(list(itertools.product([0, 1], repeat=N)))
+    lp = model.log_psi(P, states)
+    assert abs(np.exp(2.0 * lp).sum() - 1.0) < 1e-12
+    w_h, w0 = _zero_half_block_blob(N, layers, d, K, seed=9, std=0.4)  # the same network, W_o = 0
+    assert not np.allclose(lp, model.log_psi(model.parse_blob(w0, N, layers, d, heads, K, vq_heads=2), states))
