@@ -278,23 +278,25 @@ def gemm_probe(m, dm: int, stream=None) -> dict:
 
 def vq_sweep(args) -> dict:
     """Table 1's protocol with seeded random weights: the same 16x16 network (three
-    blocks, d_model 256, 8 attention heads, 64 codes per quantizer head) with 1, 2 and
-    4 quantizer heads (6, 12, 24 bits); per bandwidth the unique-row fraction per
-    layer, the FLOP reduction and the timed local energies per second (FP32 reuse
-    path, the search runs per head on the CUDA cores; L2 flushed between steps)."""
+    blocks and the final attention-only half-block, d_model 256, 8 attention heads,
+    64 codes per quantizer head) with 1, 2 and 4 quantizer heads (6, 12, 24 bits);
+    per bandwidth the unique-row fraction per layer, the FLOP reduction of the
+    quantized blocks (Table 1's quantized-ops savings) and the timed local energies
+    per second (FP32 reuse path; L2 flushed between steps)."""
     import torch
     import synthetic_inputs as si
     from paper_2212_11296_gb300 import REUSE, VQNQS
     L, layers, d, heads, K, B = 16, 3, 256, 8, 64, 512
     N = L * L
-    blob = si.make_weights(N, layers, d, K, seed=0)
+    blob = si.make_weights(N, layers, d, K, seed=0, half_block=True)
     spins = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    out = {"workload": f"16x16 periodic Heisenberg, {layers} blocks d_model {d} heads {heads}, "
-                       f"{K} codes per quantizer head, {B} uniform S_z=0 samples", "flags": "reuse (FP32)",
+    out = {"workload": f"16x16 periodic Heisenberg, {layers} blocks + attention-only half-block, d_model {d} "
+                       f"heads {heads}, {K} codes per quantizer head, {B} uniform S_z=0 samples",
+           "flags": "reuse (FP32)",
            "data": "synthetic, seeded random weights", "bandwidths": {}}
     for H in (1, 2, 4):
-        m = VQNQS(L, True, 1.0, layers, d, heads, K, blob, vq_heads=H)
+        m = VQNQS(L, True, 1.0, layers, d, heads, K, blob, vq_heads=H, half_block=True)
         ws = m.workspace(REUSE)
         e = torch.empty(B, device="cuda")
         for _ in range(2):
@@ -312,7 +314,7 @@ def vq_sweep(args) -> dict:
         st = m.stats()
         out["bandwidths"][f"{6 * H} bits"] = {
             "vq_heads": H, "unique_row_fraction": [u / st["rows"] for u in st["unique_rows"][1:]],
-            "flop_reduction": st["flops_full"] / st["flops_done"], "ms_per_step": min(ms),
+            "quantized_ops_flop_reduction": st["flops_full"] / st["flops_done"], "ms_per_step": min(ms),
             "local_energies_per_s": B / (min(ms) / 1e3), "near_ties": st["near_ties"],
             "device_status": st["device_status"]}
         m.close()

@@ -136,24 +136,39 @@ int vqnqs_create(int L, int periodic, double J, int layers, int d_model, int hea
 int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, int d_model, int heads, int K,
                       const float* weights, vqnqs_ctx** out);
 
-/* Create an L x L Heisenberg context whose vector quantizers have vq_heads
- * heads (Sec. 3.1, Eq. vq with H heads; Table 1 uses H in {1, 2, 4, 8} with
- * 64 codes each): the attention output o is split into vq_heads segments of
- * d_model / vq_heads values, segment h goes to its nearest codeword among the
- * K of its own codebook, and the quantized vector is the concatenation.
- *   K         codewords per head;  vq_heads in 1..8, d_model / vq_heads a
- *             multiple of 8, vq_heads * ceil(log2 K) <= 31 (the code of a row
- *             packs c_h in bits [h * b, (h + 1) * b), b = ceil(log2 K));
- *             so 64 codes allow up to 5 heads
- *   weights   as vqnqs_create; each layer's codebook block (K * d_model
- *             floats) is read as [vq_heads][K][d_model / vq_heads]
- * vq_heads = 1 is vqnqs_create.  With several heads the quantizer search runs
- * per head on the CUDA cores (FP32 distances, lowest index on ties) in every
- * flag combination of vqnqs_local_energy / vqnqs_log_psi except
- * VQNQS_INCREMENTAL; vqnqs_grad_log_psi, vqnqs_vq_assign, vqnqs_sample and
- * vqnqs_vmc_step return VQNQS_ERR_ARG; vqnqs_codes returns packed codes. */
-int vqnqs_create_vq(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
-                    const float* weights, vqnqs_ctx** out);
+/* Create an L x L Heisenberg context with the paper's architecture variants
+ * (Sec. 3.1 and Table 1):
+ *   vq_heads    the vector quantizers have vq_heads heads (Eq. vq with H
+ *               heads; Table 1 uses H in {1, 2, 4, 8} with 64 codes each): the
+ *               attention output o is split into vq_heads segments of
+ *               d_model / vq_heads values, segment h goes to its nearest
+ *               codeword among the K of its own codebook, and the quantized
+ *               vector is the concatenation.  K is the codewords per head;
+ *               vq_heads in 1..8, d_model / vq_heads a multiple of 8,
+ *               vq_heads * ceil(log2 K) <= 31 (a row's code packs c_h in bits
+ *               [h * b, (h + 1) * b), b = ceil(log2 K)), so 64 codes allow up
+ *               to 5 heads.  Each layer's codebook block (K * d_model floats)
+ *               is read as [vq_heads][K][d_model / vq_heads].
+ *   half_block  nonzero: Table 1's final half-block follows the blocks,
+ *               x <- x + attention(LN(x)) W_o + b_o with its own LN, W_qkv and
+ *               W_o and no quantizer or MLP; its weights (LN gain and shift,
+ *               W_qkv [d][3d], b_qkv, W_o [d][d], b_o) sit between the last
+ *               block and LN_f in the blob, which then has
+ *               vqnqs_num_params_arch(L*L, layers, d_model, K, 1) values.  Its
+ *               outputs are not quantized: the output projection and the head
+ *               run per active row.
+ * vq_heads = 1, half_block = 0 is vqnqs_create.  With several heads the
+ * quantizer search runs per head on the CUDA cores (FP32 distances, lowest
+ * index on ties).  Local energies and log psi accept every flag combination
+ * except VQNQS_INCREMENTAL; vqnqs_grad_log_psi, vqnqs_sample and
+ * vqnqs_vmc_step return VQNQS_ERR_ARG for either variant, vqnqs_vq_assign for
+ * several heads; vqnqs_codes returns packed codes.  The FLOP counters of
+ * vqnqs_get_stats cover the quantized blocks only. */
+int vqnqs_create_arch(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
+                      int half_block, const float* weights, vqnqs_ctx** out);
+
+/* Weight blob size of a model with the final half-block (half_block != 0) or without. */
+size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block);
 
 /* Replace the weights (HOST blob when is_device == 0, DEVICE blob otherwise) and
  * rebuild the derived tables on `stream`. */

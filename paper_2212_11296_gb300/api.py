@@ -38,25 +38,26 @@ def _check_dev(t: torch.Tensor, dtype, name):
 
 class VQNQS:
     """One model on one lattice: vqnqs_create(L, periodic, J, layers, d_model, heads, K, weights), or
-    vqnqs_create_vq(..., K, vq_heads, weights) for quantizers with vq_heads heads of K codes each."""
+    vqnqs_create_arch(..., K, vq_heads, half_block, weights) for quantizers with vq_heads heads of K
+    codes each and/or the final attention-only half-block."""
 
     def __init__(self, L: int, periodic: bool, J: float, layers: int, d_model: int, heads: int, K: int,
-                 weights: np.ndarray, vq_heads: int = 1):
+                 weights: np.ndarray, vq_heads: int = 1, half_block: bool = False):
         self.L, self.N = L, L * L
         self.periodic, self.J = bool(periodic), float(J)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
-        self.vq_heads = int(vq_heads)
+        self.vq_heads, self.half_block = int(vq_heads), bool(half_block)
         w = np.ascontiguousarray(weights, dtype=np.float32)
-        n = lib().vqnqs_num_params(self.N, layers, d_model, K)
+        n = lib().vqnqs_num_params_arch(self.N, layers, d_model, K, int(self.half_block))
         if w.size != n:
             raise ValueError(f"weight blob has {w.size} floats, layout needs {n}")
         h = ctypes.c_void_p()
-        if self.vq_heads == 1:
+        if self.vq_heads == 1 and not self.half_block:
             rc = lib().vqnqs_create(L, int(periodic), float(J), layers, d_model, heads, K,
                                     w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         else:
-            rc = lib().vqnqs_create_vq(L, int(periodic), float(J), layers, d_model, heads, K, self.vq_heads,
-                                       w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+            rc = lib().vqnqs_create_arch(L, int(periodic), float(J), layers, d_model, heads, K, self.vq_heads,
+                                         int(self.half_block), w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         if rc != 0:
             raise VQNQSError(f"vqnqs_create failed: {_lib.STATUS_NAMES.get(rc, rc)}")
         self._h = h
@@ -70,7 +71,7 @@ class VQNQS:
         self.L, self.N = None, N
         self.periodic, self.J, self.Gamma = bool(periodic), float(J), float(Gamma)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
-        self.vq_heads = 1
+        self.vq_heads, self.half_block = 1, False
         w = np.ascontiguousarray(weights, dtype=np.float32)
         n = lib().vqnqs_num_params(N, layers, d_model, K)
         if w.size != n:
@@ -323,7 +324,7 @@ class VQNQS:
 
     @property
     def num_params(self) -> int:
-        return int(lib().vqnqs_num_params(self.N, self.layers, self.d, self.K))
+        return int(lib().vqnqs_num_params_arch(self.N, self.layers, self.d, self.K, int(self.half_block)))
 
     def grad_log_psi(self, spins: torch.Tensor, seeds: torch.Tensor | None = None,
                      e_loc: torch.Tensor | None = None, want_O: bool = False, want_grad: bool = True,

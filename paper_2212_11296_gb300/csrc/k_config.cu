@@ -394,6 +394,60 @@ cudaError_t launch_head(const float* X, const int* counters, int u_slot, const f
     k_head<<<grid, 256, 0, st>>>(X, counters, u_slot, g, b, w_head, b_head, d, logp);
     return cudaGetLastError();
 }
+// ---- final half-block (Table 1's networks): attention and W_o, no quantizer ------------
+// Its outputs are not quantized, so every active row is its own row from here on.
+__global__ void k_half_gather(const int* __restrict__ counters, const int* __restrict__ act_rows,
+                              const int* __restrict__ uid, const float* __restrict__ O, const float* __restrict__ X,
+                              int d, float* __restrict__ G_o, __nv_bfloat16* __restrict__ G_o16,
+                              float* __restrict__ G_x) {
+    const int A = counters[CNT_A];
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int a = blockIdx.x * wpb + (threadIdx.x >> 5); a < A; a += gridDim.x * wpb) {
+        const int row = act_rows[a];
+        const float* o = O + (size_t)row * d;
+        const float* x = X + (size_t)uid[row] * d;
+        for (int k = lane * 4; k < d; k += 128) {
+            const float4 ov = *reinterpret_cast<const float4*>(o + k);
+            *reinterpret_cast<float4*>(G_x + (size_t)a * d + k) = *reinterpret_cast<const float4*>(x + k);
+            if (G_o) *reinterpret_cast<float4*>(G_o + (size_t)a * d + k) = ov;
+            if (G_o16) {
+                const __nv_bfloat162 h0 = __floats2bfloat162_rn(ov.x, ov.y), h1 = __floats2bfloat162_rn(ov.z, ov.w);
+                uint2 u;
+                u.x = *reinterpret_cast<const uint32_t*>(&h0);
+                u.y = *reinterpret_cast<const uint32_t*>(&h1);
+                *reinterpret_cast<uint2*>(G_o16 + (size_t)a * d + k) = u;
+            }
+        }
+    }
+}
+
+// Row ids after the half-block: position p of configuration c is its active row
+// act_off[c] + p - p0, or the sample's active row act_off[cfg_off[b]] + p before p0.
+__global__ void k_half_ids(Chunk ch, int prefix_reuse, const int* __restrict__ act_off, int* __restrict__ uid_out) {
+    const int C = ch.counters[CNT_C];
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
+        const int b = ch.cfg_sample[c];
+        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int N = cfg_N(ch, c), r0 = ch.cfg_row[c];
+        const int own = act_off[c], base = act_off[ch.cfg_off[b]];
+        for (int p = lane; p < N; p += 32) uid_out[r0 + p] = p >= p0 ? own + p - p0 : base + p;
+    }
+}
+
+cudaError_t launch_half_gather(const int* counters, const int* act_rows, const int* uid, const float* O,
+                               const float* X, int d, float* G_o, __nv_bfloat16* G_o16, float* G_x, cudaStream_t st,
+                               int grid) {
+    if (d % 4) return cudaErrorInvalidValue;
+    k_half_gather<<<grid, 256, 0, st>>>(counters, act_rows, uid, O, X, d, G_o, G_o16, G_x);
+    return cudaGetLastError();
+}
+cudaError_t launch_half_ids(const Chunk& ch, int prefix_reuse, const int* act_off, int* uid_out, cudaStream_t st,
+                            int grid) {
+    k_half_ids<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_off, uid_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eloc(const Chunk& ch, const int* uid, const float* logp, float* ratio, float* log_psi_out,
                         cudaStream_t st, int grid) {
     k_eloc_ratio<<<grid, 256, 0, st>>>(ch, uid, logp, ratio, log_psi_out);

@@ -15,6 +15,7 @@ using namespace vq;
 struct vqnqs_ctx {
     int L = 0, N = 0, periodic = 0, layers = 0, d = 0, heads = 0, K = 0, nb = 0;
     int vq_heads = 1, vq_bits = 0;  // quantizer heads; bits of one head's field in a packed code
+    int half_block = 0;             // final attention-only half-block (its weights in hw)
     int model = MODEL_HEISENBERG;
     int max_conn = 0;  // connected configurations per sample at most (bonds, or sites for the Ising chain)
     double J = 1.0, Gamma = 0.0;
@@ -24,6 +25,7 @@ struct vqnqs_ctx {
     const float *tok_emb = nullptr, *pos_emb = nullptr, *lnf_g = nullptr, *lnf_b = nullptr, *w_head = nullptr,
                 *b_head = nullptr;
     std::vector<LayerW> lw;
+    LayerW hw{};  // the final half-block: ln1, w_qkv, w_o and their biases, transposes and maps
     int* bonds = nullptr;          // [nb][2] bonds of the context's lattice (side L)
     int* bonds_all = nullptr;      // bond tables of every side 2 .. L, concatenated
     std::vector<int> side_bond_off, side_nb;  // per side: first bond in bonds_all, count
@@ -65,11 +67,11 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_COUNT };
+             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_HALF, S_COUNT };
 const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
                                     "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward",
                                     "inc_certificate", "inc_classify", "inc_patch", "inc_recompute",
-                                    "inc_recompute_whole"};
+                                    "inc_recompute_whole", "half_block"};
 static_assert(S_COUNT <= VQNQS_MAX_STAGES, "stage table larger than the ABI's VQNQS_MAX_STAGES");
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
@@ -241,6 +243,10 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
             VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
         }
     }
+    if (ctx->half_block) {
+        VQ_CK(launch_transpose_bf16(ctx->hw.w_qkv, d, 3 * d, ctx->hw.wqkv_t, st));
+        VQ_CK(launch_transpose_bf16(ctx->hw.w_o, d, d, ctx->hw.wo_t, st));
+    }
     return VQNQS_OK;
 }
 
@@ -251,6 +257,10 @@ int build_weight_tmaps(vqnqs_ctx* ctx) {
         VQ_CK(make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
         VQ_CK(make_tmap_bf16(&w.tm_w1, w.w1_t, 4 * d, (int)d, ctx->bn[1]));
         VQ_CK(make_tmap_bf16(&w.tm_w2, w.w2_t, d, 4 * (int)d, ctx->bn[2]));
+    }
+    if (ctx->half_block) {
+        VQ_CK(make_tmap_bf16(&ctx->hw.tm_wqkv, ctx->hw.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
+        VQ_CK(make_tmap_bf16(&ctx->hw.tm_wo, ctx->hw.wo_t, d, (int)d, ctx->bn[2]));
     }
     return VQNQS_OK;
 }
@@ -270,6 +280,12 @@ void bind_weights(vqnqs_ctx* c) {
         w.ln2_g = take(d); w.ln2_b = take(d);
         w.w_1 = take(d * 4 * d); w.b_1 = take(4 * d);
         w.w_2 = take(4 * d * d); w.b_2 = take(d);
+    }
+    if (c->half_block) {
+        LayerW& w = c->hw;
+        w.ln1_g = take(d); w.ln1_b = take(d);
+        w.w_qkv = take(d * 3 * d); w.b_qkv = take(3 * d);
+        w.w_o = take(d * d); w.b_o = take(d);
     }
     c->lnf_g = take(d); c->lnf_b = take(d);
     c->w_head = take(2 * d); c->b_head = take(2);
@@ -466,13 +482,53 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         std::swap(uid_cur, uid_next);
         std::swap(X_cur, X_next);
     }
+    const int* uid_final = uid_cur;
+    const float* X_head = X_cur;
+    int head_slot = CNT_U0 + ctx->layers;
+    if (ctx->half_block) {
+        // Table 1's final half-block: LN and QKV on the unique rows, attention over the active
+        // rows, then W_o and the residual per active row.  Without a quantizer the rows stay
+        // distinct from here on: each active row is its own row for the head and the ratios.
+        const LayerW& w = ctx->hw;
+        const int us = CNT_U0 + ctx->layers;
+        if (bf16) {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows));
+            VQ_STAGE(S_QKV, 1, launch_gemm_tc(A16, Umax, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, us, 3 * d, d, 0,
+                                              ctx->status, st, ctx->num_sms, ctx->bn[0]));
+            if (attention_tc_supported(N, d / ctx->heads))
+                VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, reuse ? 1 : 0, ctx->status, st,
+                                                        grid_for(ctx, P.Cmax * ctx->heads, 1, 4)));
+            else
+                VQ_STAGE(S_ATTN, 1, launch_attention_bf16in(ch, uid_cur, qkv16, O, reuse ? 1 : 0, st,
+                                                            grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
+        } else {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, A, nullptr, st, g_urows));
+            VQ_STAGE(S_QKV, 1, launch_sgemm(A, w.w_qkv, w.b_qkv, nullptr, qkv, counters, us, Umax, 3 * d, d, EPI_BIAS,
+                                            st, ctx->num_sms));
+            VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid_cur, qkv, O, reuse ? 1 : 0, st,
+                                                     grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
+        }
+        StageScope scope_(ctx, S_HALF, 3, st);
+        VQ_CK(launch_half_gather(counters, act_rows, uid_cur, O, X_cur, d, bf16 ? nullptr : A, bf16 ? A16 : nullptr, Y,
+                                 st, g_rows));
+        if (bf16)
+            VQ_CK(launch_gemm_tc(A16, Umax, w.tm_wo, w.b_o, Y, X_next, counters, CNT_A, d, d, 2, ctx->status, st,
+                                 ctx->num_sms, ctx->bn[2]));
+        else
+            VQ_CK(launch_sgemm(A, w.w_o, w.b_o, Y, X_next, counters, CNT_A, Umax, d, d, EPI_BIAS_RESID, st,
+                               ctx->num_sms));
+        VQ_CK(launch_half_ids(ch, reuse ? 1 : 0, act_off, uid_next, st, grid_for(ctx, P.Cmax, 8, 16)));
+        uid_final = uid_next;
+        X_head = X_next;
+        head_slot = CNT_A;
+    }
     float* logp = at<float>(ws, P.logp);
-    VQ_STAGE(S_HEAD, 1, launch_head(X_cur, counters, CNT_U0 + ctx->layers, ctx->lnf_g, ctx->lnf_b, ctx->w_head,
-                                    ctx->b_head, d, logp, st, g_urows));
+    VQ_STAGE(S_HEAD, 1, launch_head(X_head, counters, head_slot, ctx->lnf_g, ctx->lnf_b, ctx->w_head, ctx->b_head, d,
+                                    logp, st, g_urows));
     float* ratio = at<float>(ws, P.ratio);
     {
         StageScope scope_(ctx, S_ELOC, e_loc_out ? 2 : 1, st);
-        VQ_CK(launch_eloc(ch, uid_cur, logp, ratio, log_psi_out, st, grid_for(ctx, P.Cmax, 8, 16)));
+        VQ_CK(launch_eloc(ch, uid_final, logp, ratio, log_psi_out, st, grid_for(ctx, P.Cmax, 8, 16)));
         if (e_loc_out)
             VQ_CK(launch_eloc_reduce(ch, diag, ratio, offdiag, e_loc_out, st, grid_for(ctx, S, 8, 16)));
     }
@@ -490,6 +546,7 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
+        if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -744,10 +801,16 @@ size_t vqnqs_num_params(int n_max, int layers, int d_model, int K) {
     return 3 * d + (size_t)n_max * d + (size_t)layers * per + 2 * d + 2 * d + 2;
 }
 
+size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block) {
+    const size_t base = vqnqs_num_params(n_max, layers, d_model, K);
+    const size_t d = d_model;
+    return base && half_block ? base + 2 * d + 3 * d * d + 3 * d + d * d + d : base;
+}
+
 namespace {
 // Shared by vqnqs_create (L x L Heisenberg lattice) and vqnqs_create_tfim (N-site chain).
 int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, int layers, int d_model, int heads,
-               int K, const float* weights, vqnqs_ctx** out, int vq_heads = 1) {
+               int K, const float* weights, vqnqs_ctx** out, int vq_heads = 1, int half_block = 0) {
     if (!out) return VQNQS_ERR_ARG;
     *out = nullptr;
     if (N < 2 || N > 512 || layers < 1 || layers > VQNQS_MAX_LAYERS || d_model < 32 || d_model % 32 ||
@@ -765,11 +828,12 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     ctx->L = L; ctx->N = N; ctx->periodic = periodic ? 1 : 0; ctx->J = J; ctx->Gamma = Gamma;
     ctx->layers = layers; ctx->d = d_model; ctx->heads = heads; ctx->K = K;
     ctx->vq_heads = vq_heads; ctx->vq_bits = vq_heads > 1 ? vq_bits : 0;
+    ctx->half_block = half_block ? 1 : 0;
     auto bail = [&](int code) { vqnqs_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(VQNQS_ERR_CUDA);
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
         return bail(VQNQS_ERR_CUDA);
-    ctx->nparams = vqnqs_num_params(ctx->N, layers, d_model, K);
+    ctx->nparams = vqnqs_num_params_arch(ctx->N, layers, d_model, K, ctx->half_block);
     auto dalloc = [&](size_t bytes) -> void* {
         void* p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
@@ -815,6 +879,11 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
         w.wd = static_cast<float*>(dalloc((size_t)K * K * sizeof(float)));
         if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo || !w.wd)
             return bail(VQNQS_ERR_OOM);
+    }
+    if (ctx->half_block) {
+        ctx->hw.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * sizeof(__nv_bfloat16)));
+        ctx->hw.wo_t = static_cast<__nv_bfloat16*>(dalloc(d * d * sizeof(__nv_bfloat16)));
+        if (!ctx->hw.wqkv_t || !ctx->hw.wo_t) return bail(VQNQS_ERR_OOM);
     }
     if (!ctx->blob || !ctx->bonds || !ctx->status || !ctx->stats) return bail(VQNQS_ERR_OOM);
     if (!ctx->bonds_all ||
@@ -865,14 +934,14 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
     return create_ctx(MODEL_TFIM_CHAIN, 0, N, periodic, J, Gamma, layers, d_model, heads, K, weights, out);
 }
 
-int vqnqs_create_vq(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
-                    const float* weights, vqnqs_ctx** out) {
+int vqnqs_create_arch(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
+                      int half_block, const float* weights, vqnqs_ctx** out) {
     if (L < 2 || L * L > 512) {
         if (out) *out = nullptr;
         return VQNQS_ERR_ARG;
     }
     return create_ctx(MODEL_HEISENBERG, L, L * L, periodic, J, 0.0, layers, d_model, heads, K, weights, out,
-                      vq_heads);
+                      vq_heads, half_block);
 }
 
 int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream) {
@@ -907,6 +976,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
+        if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1066,11 +1136,13 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: one quantizer head only");
+    if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: no final half-block");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
+        if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1272,6 +1344,7 @@ int vqnqs_sample(vqnqs_ctx* ctx, int B, const float* uniforms, uint8_t* spins, f
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "sample: one quantizer head only");
+    if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "sample: no final half-block");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     const bool bf16 = (flags & VQNQS_BF16) != 0;
@@ -1385,6 +1458,7 @@ int vqnqs_vmc_step(vqnqs_ctx* ctx, int B, const float* uniforms, float lr, uint8
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: one quantizer head only");
+    if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: no final half-block");
     if (B <= 0 || !uniforms || !spins || !e_loc || !grad || !mean_var)
         return fail(ctx, VQNQS_ERR_ARG, "vmc step: B > 0 and every buffer are required");
     // e_loc holds the drawn configurations' log psi until the local energies overwrite it

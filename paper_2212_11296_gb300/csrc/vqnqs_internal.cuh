@@ -69,6 +69,8 @@ struct LayerW {
     float* wd;                            // [K][K] ||W_a - W_c|| (incremental path's certificates)
     float *cb_hi, *cb_lo;                 // codebook split into TF32 hi / lo parts
     CUtensorMap tm_cb_hi, tm_cb_lo;       // their TMA maps (valid when vq_tc_supported)
+    __nv_bfloat16* wo_t = nullptr;        // final half-block only: BF16 transpose of W_o
+    CUtensorMap tm_wo;                    //   and its TMA map
 };
 
 // Lattice groups of a batch (one group for a single lattice, up to MAX_GROUPS
@@ -159,6 +161,14 @@ cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos
                          int* uid0, cudaStream_t st, int grid);
 cudaError_t launch_head(const float* X, const int* counters, int u_slot, const float* g, const float* b,
                         const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid);
+// final half-block (no quantizer): active row a (counters[CNT_A] of them, row act_rows[a])
+// gets G_o[a] = O[row] (FP32 or BF16) and G_x[a] = X[uid[row]]; then every chunk row
+// gets the index of its active row (of the sample's row before the first changed site)
+cudaError_t launch_half_gather(const int* counters, const int* act_rows, const int* uid, const float* O,
+                               const float* X, int d, float* G_o, __nv_bfloat16* G_o16, float* G_x, cudaStream_t st,
+                               int grid);
+cudaError_t launch_half_ids(const Chunk& ch, int prefix_reuse, const int* act_off, int* uid_out, cudaStream_t st,
+                            int grid);
 cudaError_t launch_eloc(const Chunk& ch, const int* uid, const float* logp, float* ratio, float* log_psi_out,
                         cudaStream_t st, int grid);
 // e_loc = diag + offdiag * sum over connected configurations of psi(s') / psi(s)

@@ -1,4 +1,6 @@
-"""Multi-head vector quantizers (Sec. 3.1, Eq. vq with H heads) through the C ABI.
+"""The paper's architecture variants through the C ABI: multi-head vector
+quantizers (Sec. 3.1, Eq. vq with H heads) and the final attention-only
+half-block of Table 1's networks.
 
 * FP32, plain and reuse paths, H = 2 and 4: local energies and log psi within
   1e-5 of the FP64 oracle (near-tie rule of test_gpu_parity), reuse bitwise
@@ -9,7 +11,10 @@
 * Table 1's bandwidths at 16x16 (three blocks, d_model 256, 8 attention heads,
   64 codes per head; H = 1, 2, 4 = 6, 12, 24 bits): oracle parity on sampled
   configurations and the unique-row fraction and FLOP reduction per bandwidth.
-* The entry points defined for one head refuse several.
+* The final half-block, FP32 plain and reuse (one and two quantizer heads)
+  against the oracle, BF16 against FP32, and Table 1's network (three blocks,
+  half-block, two heads of 64 codes) at 16x16 on sampled configurations.
+* The entry points defined for one head and no half-block refuse the variants.
 """
 import numpy as np
 import pytest
@@ -121,3 +126,72 @@ def test_one_head_entry_points_refuse_several():
         VQNQS(4, True, 1.0, 1, 64, 2, 64, si.make_weights(16, 1, 64, 64), vq_heads=8)
     with pytest.raises(VQNQSError):  # d_model not a multiple of the heads
         VQNQS(4, True, 1.0, layers, d, heads, K, w, vq_heads=3)
+
+
+@pytest.mark.parametrize("H", [1, 2])
+def test_half_block_fp32_matches_oracle_4x4(H):
+    from paper_2212_11296_gb300 import REUSE, VQNQS
+    L, layers, d, heads, K, B = 4, 2, 32, 4, 16, 64
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, half_block=True)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H, half_block=True)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True)
+    e_plain = m.local_energy(s, 0)
+    e_reuse = m.local_energy(s, REUSE)
+    assert torch.equal(e_plain, e_reuse)
+    check(P, spins, e_reuse.cpu().numpy(), L)
+    lp = m.log_psi(s, REUSE).cpu().numpy()
+    lp_or = model.log_psi(P, spins)
+    assert np.max(np.abs(lp - lp_or) / np.abs(lp_or)) <= FP32_TOL
+    assert m.stats()["device_status"] == 0
+
+
+def test_half_block_bf16_close_to_fp32():
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B = 8, 2, 128, 4, 64, 128
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, half_block=True)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, half_block=True)
+    e16 = m.local_energy(s, REUSE | BF16)
+    dd = rel_err(e16.cpu().numpy(), m.local_energy(s, REUSE).cpu().numpy(), N)
+    print(f"half-block BF16 vs FP32: median {np.median(dd):.2e} max {dd.max():.2e}")
+    assert np.median(dd) <= 5e-3 and dd.max() <= 0.1
+    assert torch.equal(e16, m.local_energy(s, BF16))
+
+
+def test_table1_network_16x16_sampled():
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B, H = 16, 3, 256, 8, 64, 16, 2
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, half_block=True)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H, half_block=True)
+    m.reset_stats()
+    e = m.local_energy(s, REUSE).cpu().numpy()
+    st = m.stats()
+    print(f"Table 1 network, 12 bits: quantized-ops FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True)
+    check(P, spins[:2], e[:2], L, max_miss=0.5)
+    e16 = m.local_energy(s, REUSE | BF16).cpu().numpy()
+    assert np.median(rel_err(e16, e, N)) <= 1e-2
+    assert m.stats()["device_status"] == 0
+
+
+def test_half_block_refusals():
+    from paper_2212_11296_gb300 import INCREMENTAL, REUSE, VQNQS, VQNQSError
+    L, layers, d, heads, K = 4, 2, 32, 4, 16
+    w = si.make_weights(L * L, layers, d, K, seed=0, half_block=True)
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, half_block=True)
+    s = torch.as_tensor(si.make_samples(L, 4, seed=1)).cuda()
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.local_energy(s, REUSE | INCREMENTAL)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.grad_log_psi(s)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.sample(torch.rand(4, L * L, device="cuda"))
+    with pytest.raises(ValueError):  # a blob without the half-block's weights
+        VQNQS(L, True, 1.0, layers, d, heads, K, si.make_weights(L * L, layers, d, K), half_block=True)
