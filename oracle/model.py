@@ -22,6 +22,11 @@ so the output at p is the conditional of s_p.  Each block is pre-LayerNorm:
 and the head is log_softmax(LN_f(x) W_head + b_head) over the two spin values.
 LayerNorm uses eps = 1e-5 and the biased variance; GELU is the erf form.
 
+Tokens as particle groups (Sec. 3.1): with token_group G each token is a group
+of G consecutive spins with value sum_k s[tG + k] 2^k, the input at position t
+is the value of group t - 1 (begin-of-sequence 2^G at t = 0), the head is a
+2^G-way log-softmax and log psi = 1/2 sum_t log P(group t | earlier groups).
+
 Optional final half-block (Table 1's networks): after the blocks,
 x <- x + W_o attention(LN(x)) + b_o with its own weights and no quantizer.
 
@@ -58,10 +63,11 @@ class Params:
     t: dict  # name -> float64 tensor
     vq_heads: int = 1
     half_block: bool = False
+    token_group: int = 1  # G spins per token (Sec. 3.1 tokens as particle groups)
 
 
 def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_heads: int = 1,
-               half_block: bool = False) -> Params:
+               half_block: bool = False, token_group: int = 1) -> Params:
     """Split a flat float32 weight blob into named float64 tensors.
 
     The order is the documented blob order: token and position embeddings,
@@ -82,8 +88,11 @@ def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_hea
         t[name] = blob[pos:pos + n].reshape(shape).clone()
         pos += n
 
-    take("tok_emb", 3, d)
-    take("pos_emb", n_max, d)
+    G = token_group
+    if n_max % G:
+        raise ValueError("n_max must be a multiple of token_group")
+    take("tok_emb", (1 << G) + 1, d)
+    take("pos_emb", n_max // G, d)
     for l in range(layers):
         take(f"{l}.ln1_g", d); take(f"{l}.ln1_b", d)
         take(f"{l}.w_qkv", d, 3 * d); take(f"{l}.b_qkv", 3 * d)
@@ -100,11 +109,11 @@ def parse_blob(blob, n_max: int, layers: int, d: int, heads: int, K: int, vq_hea
         take("h.w_qkv", d, 3 * d); take("h.b_qkv", 3 * d)
         take("h.w_o", d, d); take("h.b_o", d)
     take("lnf_g", d); take("lnf_b", d)
-    take("w_head", d, 2); take("b_head", 2)
+    take("w_head", d, 1 << G); take("b_head", 1 << G)
     if pos != blob.numel():
         raise ValueError(f"blob has {blob.numel()} values, layout needs {pos}")
     return Params(d=d, heads=heads, K=K, layers=layers, n_max=n_max, t=t, vq_heads=vq_heads,
-                  half_block=half_block)
+                  half_block=half_block, token_group=G)
 
 
 def layer_norm(x, g, b):
@@ -172,12 +181,20 @@ def segment_gap(o, codebook):
     return torch.stack([relative_gap(o[..., h * dq:(h + 1) * dq], codebook[h]) for h in range(H)]).min(0).values
 
 
-def tokens(spins: torch.Tensor) -> torch.Tensor:
-    """Shift right: token at p is s_{p-1}, begin-of-sequence at p = 0."""
+def group_values(spins: torch.Tensor, G: int = 1) -> torch.Tensor:
+    """Value of each group of G consecutive spins, sum_k s[t G + k] 2^k: [C, N / G]."""
     C, N = spins.shape
-    tok = torch.empty(C, N, dtype=torch.long)
-    tok[:, 0] = BOS
-    tok[:, 1:] = spins[:, :-1].long()
+    g = spins.long().reshape(C, N // G, G)
+    return (g * (1 << torch.arange(G))).sum(-1)
+
+
+def tokens(spins: torch.Tensor, G: int = 1) -> torch.Tensor:
+    """Shift right: the token at position t is the value of group t - 1, the
+    begin-of-sequence token 2^G at t = 0 (for G = 1: s_{p-1}, BOS = 2)."""
+    v = group_values(spins, G)
+    tok = torch.empty_like(v)
+    tok[:, 0] = 1 << G
+    tok[:, 1:] = v[:, :-1]
     return tok
 
 
@@ -191,7 +208,7 @@ def relative_gap(o, codebook):
 
 
 def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
-    """Conditional log-probabilities log P(. | s_<p), shape [C, N, 2].
+    """Conditional log-probabilities log P(. | earlier groups), shape [C, N / G, 2^G].
 
     ``quantizer(l, o) -> (V, codes)`` replaces the plain nearest-codeword
     lookup (used by the gradient module for the straight-through form);
@@ -200,7 +217,8 @@ def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
     spins = torch.as_tensor(np.asarray(spins)).long()
     C, N = spins.shape
     t = P.t
-    x = t["tok_emb"][tokens(spins)] + t["pos_emb"][:N]
+    T = N // P.token_group
+    x = t["tok_emb"][tokens(spins, P.token_group)] + t["pos_emb"][:T]
     for l in range(P.layers):
         a = layer_norm(x, t[f"{l}.ln1_g"], t[f"{l}.ln1_b"])
         o = causal_attention(a, t[f"{l}.w_qkv"], t[f"{l}.b_qkv"], P.heads)
@@ -240,7 +258,8 @@ def log_psi(P: Params, spins, batch: int = 64, record=None, min_gap=None) -> np.
             rec = [] if record is not None else None
             gp = [] if min_gap is not None else None
             lp = forward(P, s, record=rec, gaps=gp)
-            out[i:i + batch] = 0.5 * lp.gather(-1, s[..., None])[..., 0].sum(-1).numpy()
+            v = group_values(s, P.token_group)
+            out[i:i + batch] = 0.5 * lp.gather(-1, v[..., None])[..., 0].sum(-1).numpy()
             if record is not None:
                 record.append(rec)
             if min_gap is not None:

@@ -75,13 +75,16 @@ def normals(seed: int, n: int) -> np.ndarray:
     return out[:n]
 
 
-def blob_segments(n_max: int, layers: int, d: int, K: int, half_block: bool = False):
+def blob_segments(n_max: int, layers: int, d: int, K: int, half_block: bool = False, token_group: int = 1):
     """(name, shape, kind) for every tensor of the blob, in order.
 
     kind is 'w' (random), 'zero' (bias / LayerNorm shift) or 'one' (gain).  With
     half_block the final attention-only half-block (LN, W_qkv, W_o and their
-    biases) follows the quantized blocks."""
-    seg = [("tok_emb", (3, d), "w"), ("pos_emb", (n_max, d), "w")]
+    biases) follows the quantized blocks.  With token_group G each token is a
+    group of G spins: 2^G + 1 token embeddings (the last one begin-of-sequence),
+    n_max / G positions and a 2^G-way head."""
+    G = token_group
+    seg = [("tok_emb", ((1 << G) + 1, d), "w"), ("pos_emb", (n_max // G, d), "w")]
     for l in range(layers):
         p = f"l{l}."
         seg += [
@@ -98,21 +101,21 @@ def blob_segments(n_max: int, layers: int, d: int, K: int, half_block: bool = Fa
                 ("h.w_qkv", (d, 3 * d), "w"), ("h.b_qkv", (3 * d,), "zero"),
                 ("h.w_o", (d, d), "w"), ("h.b_o", (d,), "zero")]
     seg += [("lnf_g", (d,), "one"), ("lnf_b", (d,), "zero"),
-            ("w_head", (d, 2), "w"), ("b_head", (2,), "zero")]
+            ("w_head", (d, 1 << G), "w"), ("b_head", (1 << G,), "zero")]
     return seg
 
 
-def num_params(n_max: int, layers: int, d: int, K: int, half_block: bool = False) -> int:
-    return int(sum(int(np.prod(s)) for _, s, _ in blob_segments(n_max, layers, d, K, half_block)))
+def num_params(n_max: int, layers: int, d: int, K: int, half_block: bool = False, token_group: int = 1) -> int:
+    return int(sum(int(np.prod(s)) for _, s, _ in blob_segments(n_max, layers, d, K, half_block, token_group)))
 
 
 def make_weights(n_max: int, layers: int, d: int, K: int, seed: int = 0,
-                 std: float = 0.02, half_block: bool = False) -> np.ndarray:
+                 std: float = 0.02, half_block: bool = False, token_group: int = 1) -> np.ndarray:
     """Seeded float32 weight blob in the layout documented above."""
-    n = num_params(n_max, layers, d, K, half_block)
+    n = num_params(n_max, layers, d, K, half_block, token_group)
     blob = (std * normals(seed, n)).astype(np.float32)
     off = 0
-    for _, shape, kind in blob_segments(n_max, layers, d, K, half_block):
+    for _, shape, kind in blob_segments(n_max, layers, d, K, half_block, token_group):
         sz = int(np.prod(shape))
         if kind == "zero":
             blob[off:off + sz] = 0.0

@@ -1,4 +1,6 @@
-"""Pins of the oracle's multi-head quantizer (Sec. 3.1, Eq. vq with H heads).
+"""Pins of the oracle's architecture variants (Sec. 3.1 and Table 1): the
+multi-head quantizer (Eq. vq with H heads), the final half-block and tokens
+of G spins.
 
 * Brute force: the quantized vector is the joint nearest point over all K^H
   concatenations of one codeword per segment (the squared distance splits into
@@ -119,3 +121,54 @@ def test_half_block_model_is_normalised_and_differs():
     assert abs(np.exp(2.0 * lp).sum() - 1.0) < 1e-12
     w_h, w0 = _zero_half_block_blob(N, layers, d, K, seed=9, std=0.4)  # the same network, W_o = 0
     assert not np.allclose(lp, model.log_psi(model.parse_blob(w0, N, layers, d, heads, K, vq_heads=2), states))
+
+
+def _passthrough_blob(N, layers, d, K, G, seed):
+    """A G-token blob whose blocks leave x unchanged (W_o, b_o, W_2, b_2 zero)."""
+    w = si.make_weights(N, layers, d, K, seed=seed, std=0.5, token_group=G)
+    off = 0
+    for name, shape, _ in si.blob_segments(N, layers, d, K, token_group=G):
+        sz = int(np.prod(shape))
+        if name.endswith((".w_o", ".b_o", ".w_2", ".b_2")):
+            w[off:off + sz] = 0.0
+        off += sz
+    return w
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_token_groups_closed_form_without_blocks(G):
+    """With blocks that pass x through, P(group t | earlier) is the head applied to
+    tok_emb[value of group t-1 (BOS 2^G at t = 0)] + pos_emb[t], computed here in numpy."""
+    N, layers, d, heads, K = 8, 2, 16, 2, 4
+    w = _passthrough_blob(N, layers, d, K, G, seed=11)
+    P = model.parse_blob(w, N, layers, d, heads, K, token_group=G)
+    seg = {name: shape for name, shape, _ in si.blob_segments(N, layers, d, K, token_group=G)}
+    off, arr = 0, {}
+    for name, shape, _ in si.blob_segments(N, layers, d, K, token_group=G):
+        sz = int(np.prod(shape))
+        arr[name] = w[off:off + sz].astype(np.float64).reshape(shape)
+        off += sz
+    rng = np.random.default_rng(G)
+    spins = rng.integers(0, 2, size=(6, N)).astype(np.uint8)
+    T = N // G
+    want = np.zeros(len(spins))
+    for b, s in enumerate(spins):
+        vals = [sum(int(s[t * G + k]) << k for k in range(G)) for t in range(T)]
+        for t in range(T):
+            tok = (1 << G) if t == 0 else vals[t - 1]
+            x = arr["tok_emb"][tok] + arr["pos_emb"][t]
+            a = (x - x.mean()) / np.sqrt(x.var() + 1e-5) * arr["lnf_g"] + arr["lnf_b"]
+            z = a @ arr["w_head"] + arr["b_head"]
+            lse = z.max() + np.log(np.exp(z - z.max()).sum())
+            want[b] += 0.5 * (z[vals[t]] - lse)
+    assert seg["w_head"] == (d, 1 << G)
+    assert np.allclose(model.log_psi(P, spins), want, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_token_group_model_is_normalised(G):
+    N, layers, d, heads, K = 4, 2, 16, 2, 4
+    w = si.make_weights(N, layers, d, K, seed=12, std=0.4, token_group=G)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=2, token_group=G)
+    states = np.array(list(itertools.product([0, 1], repeat=N)))
+    assert abs(np.exp(2.0 * model.log_psi(P, states)).sum() - 1.0) < 1e-12
