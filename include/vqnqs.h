@@ -149,26 +149,36 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
  *               [h * b, (h + 1) * b), b = ceil(log2 K)), so 64 codes allow up
  *               to 5 heads.  Each layer's codebook block (K * d_model floats)
  *               is read as [vq_heads][K][d_model / vq_heads].
+ *   token_group G in {1, 2, 4}: each token is a group of G consecutive spins
+ *               (Sec. 3.1 tokens as particle groups): the token at position t
+ *               is the value of group t - 1, sum_k s[(t-1) G + k] 2^k, with
+ *               begin-of-sequence 2^G at t = 0; the blob holds 2^G + 1 token
+ *               embeddings, N / G position embeddings and a 2^G-way head
+ *               (W_head [d][2^G], b_head [2^G]); log psi = 1/2 sum_t log
+ *               P(group t | earlier groups); rows per configuration are N / G
+ *               and vqnqs_codes returns [B][layers][N / G].  N % G == 0.
  *   half_block  nonzero: Table 1's final half-block follows the blocks,
  *               x <- x + attention(LN(x)) W_o + b_o with its own LN, W_qkv and
  *               W_o and no quantizer or MLP; its weights (LN gain and shift,
  *               W_qkv [d][3d], b_qkv, W_o [d][d], b_o) sit between the last
  *               block and LN_f in the blob, which then has
- *               vqnqs_num_params_arch(L*L, layers, d_model, K, 1) values.  Its
+ *               vqnqs_num_params_arch(L*L, layers, d_model, K, 1, G) values.  Its
  *               outputs are not quantized: the output projection and the head
  *               run per active row.
- * vq_heads = 1, half_block = 0 is vqnqs_create.  With several heads the
+ * vq_heads = 1, half_block = 0, token_group = 1 is vqnqs_create.  With several heads the
  * quantizer search runs per head on the CUDA cores (FP32 distances, lowest
  * index on ties).  Local energies and log psi accept every flag combination
  * except VQNQS_INCREMENTAL; vqnqs_grad_log_psi, vqnqs_sample and
- * vqnqs_vmc_step return VQNQS_ERR_ARG for either variant, vqnqs_vq_assign for
- * several heads; vqnqs_codes returns packed codes.  The FLOP counters of
+ * vqnqs_vmc_step return VQNQS_ERR_ARG for any variant, vqnqs_vq_assign for
+ * several heads, vqnqs_local_energy_ragged for G > 1; vqnqs_codes returns
+ * packed codes.  The FLOP counters of
  * vqnqs_get_stats cover the quantized blocks only. */
 int vqnqs_create_arch(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
-                      int half_block, const float* weights, vqnqs_ctx** out);
+                      int half_block, int token_group, const float* weights, vqnqs_ctx** out);
 
-/* Weight blob size of a model with the final half-block (half_block != 0) or without. */
-size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block);
+/* Weight blob size of a model with the final half-block (half_block != 0) or
+ * without, and tokens of token_group spins (0 for an invalid group size). */
+size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block, int token_group);
 
 /* Replace the weights (HOST blob when is_device == 0, DEVICE blob otherwise) and
  * rebuild the derived tables on `stream`. */

@@ -38,26 +38,27 @@ def _check_dev(t: torch.Tensor, dtype, name):
 
 class VQNQS:
     """One model on one lattice: vqnqs_create(L, periodic, J, layers, d_model, heads, K, weights), or
-    vqnqs_create_arch(..., K, vq_heads, half_block, weights) for quantizers with vq_heads heads of K
-    codes each and/or the final attention-only half-block."""
+    vqnqs_create_arch(..., K, vq_heads, half_block, token_group, weights) for quantizers with vq_heads
+    heads of K codes each, the final attention-only half-block and/or tokens of token_group spins."""
 
     def __init__(self, L: int, periodic: bool, J: float, layers: int, d_model: int, heads: int, K: int,
-                 weights: np.ndarray, vq_heads: int = 1, half_block: bool = False):
+                 weights: np.ndarray, vq_heads: int = 1, half_block: bool = False, token_group: int = 1):
         self.L, self.N = L, L * L
         self.periodic, self.J = bool(periodic), float(J)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
-        self.vq_heads, self.half_block = int(vq_heads), bool(half_block)
+        self.vq_heads, self.half_block, self.token_group = int(vq_heads), bool(half_block), int(token_group)
         w = np.ascontiguousarray(weights, dtype=np.float32)
-        n = lib().vqnqs_num_params_arch(self.N, layers, d_model, K, int(self.half_block))
+        n = lib().vqnqs_num_params_arch(self.N, layers, d_model, K, int(self.half_block), self.token_group)
         if w.size != n:
             raise ValueError(f"weight blob has {w.size} floats, layout needs {n}")
         h = ctypes.c_void_p()
-        if self.vq_heads == 1 and not self.half_block:
+        if self.vq_heads == 1 and not self.half_block and self.token_group == 1:
             rc = lib().vqnqs_create(L, int(periodic), float(J), layers, d_model, heads, K,
                                     w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
         else:
             rc = lib().vqnqs_create_arch(L, int(periodic), float(J), layers, d_model, heads, K, self.vq_heads,
-                                         int(self.half_block), w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h))
+                                         int(self.half_block), self.token_group, w.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(h))
         if rc != 0:
             raise VQNQSError(f"vqnqs_create failed: {_lib.STATUS_NAMES.get(rc, rc)}")
         self._h = h
@@ -71,7 +72,7 @@ class VQNQS:
         self.L, self.N = None, N
         self.periodic, self.J, self.Gamma = bool(periodic), float(J), float(Gamma)
         self.layers, self.d, self.heads, self.K = layers, d_model, heads, K
-        self.vq_heads, self.half_block = 1, False
+        self.vq_heads, self.half_block, self.token_group = 1, False, 1
         w = np.ascontiguousarray(weights, dtype=np.float32)
         n = lib().vqnqs_num_params(N, layers, d_model, K)
         if w.size != n:
@@ -180,7 +181,7 @@ class VQNQS:
         """(codes [B, layers, N] int32, log psi [B]) of the configurations as given (see vqnqs_codes)."""
         _check_dev(spins, torch.uint8, "spins")
         B = spins.shape[0]
-        codes = torch.empty(B, self.layers, self.N, dtype=torch.int32, device=spins.device)
+        codes = torch.empty(B, self.layers, self.N // self.token_group, dtype=torch.int32, device=spins.device)
         lp = torch.empty(B, dtype=torch.float32, device=spins.device)
         ws = self.workspace(flags) if workspace is None else workspace
         self._check(lib().vqnqs_codes(self._h, B, ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(codes.data_ptr()),
@@ -324,7 +325,8 @@ class VQNQS:
 
     @property
     def num_params(self) -> int:
-        return int(lib().vqnqs_num_params_arch(self.N, self.layers, self.d, self.K, int(self.half_block)))
+        return int(lib().vqnqs_num_params_arch(self.N, self.layers, self.d, self.K, int(self.half_block),
+                                               self.token_group))
 
     def grad_log_psi(self, spins: torch.Tensor, seeds: torch.Tensor | None = None,
                      e_loc: torch.Tensor | None = None, want_O: bool = False, want_grad: bool = True,

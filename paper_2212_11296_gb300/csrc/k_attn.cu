@@ -48,7 +48,7 @@ __global__ void k_attention_f32(Chunk ch, const int* __restrict__ uid, const T* 
         }
         __syncthreads();
         const int p = threadIdx.x;
-        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         const bool active = p < N && p >= p0;
         float q[DH], acc[DH];
         if (active) {

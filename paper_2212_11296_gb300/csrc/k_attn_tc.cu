@@ -95,7 +95,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
         const int c = cfg_list ? cfg_list[ci] : ci;
         const int N = cfg_N(ch, c);
         const int* urow = uid + ch.cfg_row[c];
-        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         // keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
         for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
             const int j = u % Npad, kb = u / Npad;

@@ -159,7 +159,7 @@ __global__ void k_active_count(Chunk ch, int prefix_reuse, int* __restrict__ act
     long long rows = 0, pairs = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
         const int N = cfg_N(ch, c);
-        const long long p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const long long p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         act_cnt[c] = N - (int)p0;
         rows += N - p0;
         pairs += ((long long)N * (N + 1) - p0 * (p0 + 1)) / 2;  // sum over active rows p of (p + 1) keys
@@ -185,46 +185,55 @@ __global__ void k_active_fill(Chunk ch, int prefix_reuse, const int* __restrict_
     const int C = ch.counters[CNT_C];
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
-        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         const int off = act_off[c], r0 = ch.cfg_row[c], N = cfg_N(ch, c);
         for (int p = p0 + lane; p < N; p += 32) act_rows[off + p - p0] = r0 + p;
     }
 }
 
 // ---- embedding: x0 = tok_emb[token] + pos_emb[p], token = s_{p-1} (BOS at p = 0) --------
-// reuse: rows are keyed by (p, token) -> uid p * 3 + token, table of 3N rows.
+// With tokens of G spins the token at position p is the value of group p - 1,
+// sum_k s[(p-1) G + k] 2^k, and BOS = 2^G: V = 2^G + 1 token values (3 for G = 1).
+// reuse: rows are keyed by (p, token) -> uid p * V + token, table of V N rows.
 // full:  every (config, position) row gets its own copy.
 __global__ void k_embed_table(const float* __restrict__ tok_emb, const float* __restrict__ pos_emb, int N, int d,
-                              float* __restrict__ X0) {
-    size_t total = (size_t)3 * N * d;
+                              int V, float* __restrict__ X0) {
+    size_t total = (size_t)V * N * d;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         int k = (int)(e % d);
         int u = (int)(e / d);
-        int p = u / 3, t = u % 3;
+        int p = u / V, t = u % V;
         X0[e] = tok_emb[(size_t)t * d + k] + pos_emb[(size_t)p * d + k];
     }
 }
 
+// value of the spin group at position p of configuration c (G spins, bit k = spin k)
+__device__ __forceinline__ int cfg_group(const Chunk& ch, const uint8_t* s, int c, int p) {
+    int v = 0;
+    for (int k = 0; k < ch.G; ++k) v |= cfg_spin(s, ch.cfg_i[c], ch.cfg_j[c], p * ch.G + k) << k;
+    return v;
+}
+
 __global__ void k_embed_rows(Chunk ch, const float* __restrict__ tok_emb, const float* __restrict__ pos_emb,
                              int reuse, float* __restrict__ X0, int* __restrict__ uid0) {
-    const int N = ch.N, d = ch.d;
+    const int N = ch.N, d = ch.d, V = (1 << ch.G) + 1;
     const int R = ch.counters[CNT_R];
     // one warp per row
     int lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
     for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < R; r += gridDim.x * wpb) {
         const int c = ch.row_cfg[r], p = r - ch.cfg_row[c];
-        int t = BOS;
-        if (p > 0) t = cfg_spin(sample_spins(ch, ch.cfg_sample[c]), ch.cfg_i[c], ch.cfg_j[c], p - 1);
+        int t = ch.G == 1 ? BOS : (1 << ch.G);
+        if (p > 0) t = cfg_group(ch, sample_spins(ch, ch.cfg_sample[c]), c, p - 1);
         if (reuse) {
-            if (lane == 0) uid0[r] = p * 3 + t;
+            if (lane == 0) uid0[r] = p * V + t;
         } else {
             if (lane == 0) uid0[r] = r;
             for (int k = lane; k < d; k += 32)
                 X0[(size_t)r * d + k] = tok_emb[(size_t)t * d + k] + pos_emb[(size_t)p * d + k];
         }
     }
-    if (reuse && blockIdx.x == 0 && threadIdx.x == 0) ch.counters[CNT_U0] = 3 * N;
+    if (reuse && blockIdx.x == 0 && threadIdx.x == 0) ch.counters[CNT_U0] = V * N;
     if (!reuse && blockIdx.x == 0 && threadIdx.x == 0) ch.counters[CNT_U0] = R;
 }
 
@@ -259,12 +268,55 @@ __global__ void k_head(const float* __restrict__ X, const int* __restrict__ coun
     }
 }
 
+// The head of tokens of G spins: V = 2^G logits (W_head [d][V]), log-softmax.
+template <int V>
+__global__ void k_head_groups(const float* __restrict__ X, const int* __restrict__ counters, int u_slot,
+                              const float* __restrict__ g, const float* __restrict__ bta, const float* __restrict__ w,
+                              const float* __restrict__ bh, int d, float* __restrict__ logp) {
+    const int U = counters[u_slot];
+    int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
+        const float* x = X + (size_t)u * d;
+        float s = 0.f;
+        for (int k = lane; k < d; k += 32) s += x[k];
+        float mu = warp_sum(s) / d;
+        float v = 0.f;
+        for (int k = lane; k < d; k += 32) { float t = x[k] - mu; v += t * t; }
+        float rstd = rsqrtf(warp_sum(v) / d + LN_EPS);
+        float z[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) z[j] = 0.f;
+        for (int k = lane; k < d; k += 32) {
+            const float a = (x[k] - mu) * rstd * g[k] + bta[k];
+#pragma unroll
+            for (int j = 0; j < V; ++j) z[j] += a * w[(size_t)V * k + j];
+        }
+        float m = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            z[j] = warp_sum(z[j]) + bh[j];
+            m = fmaxf(m, z[j]);
+        }
+        float se = 0.f;
+#pragma unroll
+        for (int j = 0; j < V; ++j) se += expf(z[j] - m);
+        const float lse = m + logf(se);
+        if (lane < V) {
+            float zl = 0.f;
+#pragma unroll
+            for (int j = 0; j < V; ++j) zl = j == lane ? z[j] : zl;
+            logp[(size_t)V * u + lane] = zl - lse;
+        }
+    }
+}
+
 // ---- log-ratio per configuration ------------------------------------------------
 // Delta_c = 1/2 sum_p [log P(s'_p | row of c at p) - log P(s_p | row of the sample at p)],
 // summed term by term so that positions whose rows agree contribute exact zeros.
 __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float* __restrict__ logp,
                              float* __restrict__ ratio, float* __restrict__ log_psi_out) {
     const int C = ch.counters[CNT_C];
+    const int V = 1 << ch.G;  // values of a token's spin group (2 for single spins)
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
         const int b = ch.cfg_sample[c], ci = ch.cfg_i[c], cj = ch.cfg_j[c];
@@ -274,17 +326,17 @@ __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float*
         const uint8_t* s = sample_spins(ch, b);
         float acc = 0.f;
         if (ci < 0) {
-            for (int p = lane; p < N; p += 32) acc += logp[2 * (size_t)urow[p] + (s[p] & 1)];
+            for (int p = lane; p < N; p += 32) acc += logp[(size_t)V * urow[p] + cfg_group(ch, s, c, p)];
             acc = warp_sum(acc);
             if (lane == 0) {
                 ratio[c] = 0.f;
                 if (log_psi_out) log_psi_out[b] = 0.5f * acc;
             }
         } else {
+            const int cs = ch.cfg_off[b];  // the sample's own configuration
             for (int p = lane; p < N; p += 32) {
-                const int sp = s[p] & 1;
-                const int spc = cfg_spin(s, ci, cj, p);
-                acc += logp[2 * (size_t)urow[p] + spc] - logp[2 * (size_t)ubase[p] + sp];
+                const int vc = cfg_group(ch, s, c, p), vs = cfg_group(ch, s, cs, p);
+                acc += logp[(size_t)V * urow[p] + vc] - logp[(size_t)V * ubase[p] + vs];
             }
             acc = warp_sum(acc);
             if (lane == 0) ratio[c] = expf(0.5f * acc);
@@ -359,7 +411,7 @@ cudaError_t launch_configs(const Chunk& ch, float diag_coef, int with_bonds, int
 cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos_emb, int reuse, float* X0,
                          int* uid0, cudaStream_t st, int grid) {
     if (reuse) {
-        k_embed_table<<<grid, 256, 0, st>>>(tok_emb, pos_emb, ch.N, ch.d, X0);
+        k_embed_table<<<grid, 256, 0, st>>>(tok_emb, pos_emb, ch.N, ch.d, (1 << ch.G) + 1, X0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -390,8 +442,14 @@ cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, 
     return cudaGetLastError();
 }
 cudaError_t launch_head(const float* X, const int* counters, int u_slot, const float* g, const float* b,
-                        const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid) {
-    k_head<<<grid, 256, 0, st>>>(X, counters, u_slot, g, b, w_head, b_head, d, logp);
+                        const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid,
+                        int G) {
+    switch (G) {
+        case 1: k_head<<<grid, 256, 0, st>>>(X, counters, u_slot, g, b, w_head, b_head, d, logp); break;
+        case 2: k_head_groups<4><<<grid, 256, 0, st>>>(X, counters, u_slot, g, b, w_head, b_head, d, logp); break;
+        case 4: k_head_groups<16><<<grid, 256, 0, st>>>(X, counters, u_slot, g, b, w_head, b_head, d, logp); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 // ---- final half-block (Table 1's networks): attention and W_o, no quantizer ------------
@@ -428,7 +486,7 @@ __global__ void k_half_ids(Chunk ch, int prefix_reuse, const int* __restrict__ a
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
         const int b = ch.cfg_sample[c];
-        const int p0 = prefix_reuse ? cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]) : 0;
+        const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         const int N = cfg_N(ch, c), r0 = ch.cfg_row[c];
         const int own = act_off[c], base = act_off[ch.cfg_off[b]];
         for (int p = lane; p < N; p += 32) uid_out[r0 + p] = p >= p0 ? own + p - p0 : base + p;

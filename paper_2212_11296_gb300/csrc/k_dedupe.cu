@@ -42,7 +42,7 @@ __global__ void k_hash_clear(unsigned long long* __restrict__ keys, size_t H, in
 // the same computation on the same inputs.
 __device__ __forceinline__ int row_code(const Chunk& ch, const int* __restrict__ code, int r) {
     const int c = ch.row_cfg[r], p = r - ch.cfg_row[c];
-    if (p < cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c])) return code[ch.cfg_row[ch.cfg_off[ch.cfg_sample[c]]] + p];
+    if (p < cfg_p0(ch, c)) return code[ch.cfg_row[ch.cfg_off[ch.cfg_sample[c]]] + p];
     return code[r];
 }
 

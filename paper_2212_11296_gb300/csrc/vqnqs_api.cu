@@ -16,6 +16,7 @@ struct vqnqs_ctx {
     int L = 0, N = 0, periodic = 0, layers = 0, d = 0, heads = 0, K = 0, nb = 0;
     int vq_heads = 1, vq_bits = 0;  // quantizer heads; bits of one head's field in a packed code
     int half_block = 0;             // final attention-only half-block (its weights in hw)
+    int G = 1, P = 0;               // spins per token; positions (rows) per sample = N / G
     int model = MODEL_HEISENBERG;
     int max_conn = 0;  // connected configurations per sample at most (bonds, or sites for the Ising chain)
     double J = 1.0, Gamma = 0.0;
@@ -142,7 +143,8 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.S = S;
     p.Cmax = C;
     p.Rmax = R;
-    p.Umax = p.Rmax > 3LL * c->N ? p.Rmax : 3LL * c->N;
+    const long long emb_rows = (long long)((1 << c->G) + 1) * c->P;  // the reuse path's embedding table
+    p.Umax = p.Rmax > emb_rows ? p.Rmax : emb_rows;
     int hb = 1;
     while ((1LL << hb) < 2 * p.Rmax) ++hb;
     p.hash_bits = hb;
@@ -175,7 +177,7 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.vals = take(((size_t)1 << hb) * sizeof(int));
     p.rep_uid = take((size_t)p.Umax * sizeof(int));
     p.rep_code = take((size_t)p.Umax * sizeof(int));
-    p.logp = take((size_t)p.Umax * 2 * sizeof(float));
+    p.logp = take((size_t)p.Umax * (1 << c->G) * sizeof(float));
     p.ratio = take((size_t)p.Cmax * sizeof(float));
     // incremental path: samples' softmax statistics and certificates, search and recompute lists
     p.bstat = take((size_t)S * c->N * c->heads * sizeof(float2));
@@ -194,12 +196,12 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
 // Uniform chunks of S samples of the context's lattice (worst case: every bond anti-aligned).
 Plan make_plan(const vqnqs_ctx* c, int S, bool with_bonds) {
     const long long C = (long long)S * (with_bonds ? (1 + c->max_conn) : 1);
-    return make_plan_budget(c, S, C, C * c->N);
+    return make_plan_budget(c, S, C, C * c->P);
 }
 
 int default_chunk(const vqnqs_ctx* c, bool with_bonds) {
     // aim for about 2M token rows per chunk in the worst case
-    long long per = (long long)(with_bonds ? (1 + c->max_conn) : 1) * c->N;
+    long long per = (long long)(with_bonds ? (1 + c->max_conn) : 1) * c->P;
     long long s = (2LL << 20) / per;
     if (s < 1) s = 1;
     if (s > 65536) s = 65536;
@@ -269,8 +271,8 @@ void bind_weights(vqnqs_ctx* c) {
     const size_t d = c->d, K = c->K;
     const float* p = c->blob;
     auto take = [&](size_t n) { const float* r = p; p += n; return r; };
-    c->tok_emb = take(3 * d);
-    c->pos_emb = take((size_t)c->N * d);
+    c->tok_emb = take((size_t)((1 << c->G) + 1) * d);
+    c->pos_emb = take((size_t)c->P * d);
     for (int l = 0; l < c->layers; ++l) {
         LayerW& w = c->lw[l];
         w.ln1_g = take(d); w.ln1_b = take(d);
@@ -288,7 +290,7 @@ void bind_weights(vqnqs_ctx* c) {
         w.w_o = take(d * d); w.b_o = take(d);
     }
     c->lnf_g = take(d); c->lnf_b = take(d);
-    c->w_head = take(2 * d); c->b_head = take(2);
+    c->w_head = take((size_t)(1 << c->G) * d); c->b_head = take((size_t)1 << c->G);
 }
 
 // Lattice groups of a single-lattice batch.
@@ -308,7 +310,7 @@ Groups uniform_groups(const vqnqs_ctx* c, int B) {
 Chunk make_chunk(const vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& g, int s0, int S) {
     Chunk ch;
     ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = g; ch.s0 = s0; ch.S = S;
-    ch.N = ctx->N; ch.d = ctx->d; ch.heads = ctx->heads; ch.K = ctx->K; ch.model = ctx->model;
+    ch.N = ctx->P; ch.G = ctx->G; ch.d = ctx->d; ch.heads = ctx->heads; ch.K = ctx->K; ch.model = ctx->model;
     ch.cfg_sample = at<int>(ws, P.cfg_sample);
     ch.cfg_i = at<int>(ws, P.cfg_i);
     ch.cfg_j = at<int>(ws, P.cfg_j);
@@ -323,7 +325,7 @@ Chunk make_chunk(const vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* s
 int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& grp, int s0, int S,
               bool with_bonds, int flags, float* e_loc_out, float* log_psi_out, cudaStream_t st,
               int* codes_out = nullptr) {
-    const int N = ctx->N, d = ctx->d, K = ctx->K;
+    const int N = ctx->P, d = ctx->d, K = ctx->K;  // N: positions (rows) per sample
     const bool reuse = (flags & VQNQS_REUSE) != 0;
     int* counters = at<int>(ws, P.counters);
     Chunk ch = make_chunk(ctx, P, ws, spins, grp, s0, S);
@@ -524,7 +526,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
     }
     float* logp = at<float>(ws, P.logp);
     VQ_STAGE(S_HEAD, 1, launch_head(X_head, counters, head_slot, ctx->lnf_g, ctx->lnf_b, ctx->w_head, ctx->b_head, d,
-                                    logp, st, g_urows));
+                                    logp, st, g_urows, ctx->G));
     float* ratio = at<float>(ws, P.ratio);
     {
         StageScope scope_(ctx, S_ELOC, e_loc_out ? 2 : 1, st);
@@ -547,6 +549,7 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
+        if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: one spin per token");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -572,7 +575,7 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
         const int Sc = (B - s0) < S ? (B - s0) : S;
         int rc = run_chunk(ctx, P, ws, spins, g, s0, Sc, with_bonds, flags, e_loc ? e_loc + s0 : nullptr,
                            log_psi ? log_psi + s0 : nullptr, st,
-                           codes ? codes + (size_t)s0 * ctx->layers * ctx->N : nullptr);
+                           codes ? codes + (size_t)s0 * ctx->layers * ctx->P : nullptr);
         if (rc != VQNQS_OK) return rc;
     }
     if (mean_var) VQ_STAGE(S_MEANVAR, 1, launch_mean_var(e_loc, B, mean_var, st));
@@ -801,16 +804,21 @@ size_t vqnqs_num_params(int n_max, int layers, int d_model, int K) {
     return 3 * d + (size_t)n_max * d + (size_t)layers * per + 2 * d + 2 * d + 2;
 }
 
-size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block) {
+size_t vqnqs_num_params_arch(int n_max, int layers, int d_model, int K, int half_block, int token_group) {
+    if (!(token_group == 1 || token_group == 2 || token_group == 4) || n_max % token_group) return 0;
     const size_t base = vqnqs_num_params(n_max, layers, d_model, K);
-    const size_t d = d_model;
-    return base && half_block ? base + 2 * d + 3 * d * d + 3 * d + d * d + d : base;
+    if (!base) return 0;
+    const size_t d = d_model, V = (size_t)1 << token_group;
+    // token embeddings V + 1 rows (3 for single spins), n_max / G positions, a V-way head
+    size_t n = base - 3 * d - (size_t)n_max * d - 2 * d - 2 + (V + 1) * d + (size_t)(n_max / token_group) * d + V * d + V;
+    return half_block ? n + 2 * d + 3 * d * d + 3 * d + d * d + d : n;
 }
 
 namespace {
 // Shared by vqnqs_create (L x L Heisenberg lattice) and vqnqs_create_tfim (N-site chain).
 int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, int layers, int d_model, int heads,
-               int K, const float* weights, vqnqs_ctx** out, int vq_heads = 1, int half_block = 0) {
+               int K, const float* weights, vqnqs_ctx** out, int vq_heads = 1, int half_block = 0,
+               int token_group = 1) {
     if (!out) return VQNQS_ERR_ARG;
     *out = nullptr;
     if (N < 2 || N > 512 || layers < 1 || layers > VQNQS_MAX_LAYERS || d_model < 32 || d_model % 32 ||
@@ -821,6 +829,7 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     if (vq_heads < 1 || vq_heads > 8 || d_model % vq_heads || (d_model / vq_heads) % 8 ||
         (vq_heads > 1 && vq_heads * vq_bits > 31))
         return VQNQS_ERR_ARG;
+    if (!(token_group == 1 || token_group == 2 || token_group == 4) || N % token_group) return VQNQS_ERR_ARG;
     const int dh = d_model / heads;
     if (!(dh == 8 || dh == 16 || dh == 32)) return VQNQS_ERR_ARG;
     vqnqs_ctx* ctx = new vqnqs_ctx();
@@ -829,11 +838,13 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     ctx->layers = layers; ctx->d = d_model; ctx->heads = heads; ctx->K = K;
     ctx->vq_heads = vq_heads; ctx->vq_bits = vq_heads > 1 ? vq_bits : 0;
     ctx->half_block = half_block ? 1 : 0;
+    ctx->G = token_group;
+    ctx->P = N / token_group;
     auto bail = [&](int code) { vqnqs_destroy(ctx); return code; };
     if (cudaGetDevice(&ctx->device) != cudaSuccess) return bail(VQNQS_ERR_CUDA);
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
         return bail(VQNQS_ERR_CUDA);
-    ctx->nparams = vqnqs_num_params_arch(ctx->N, layers, d_model, K, ctx->half_block);
+    ctx->nparams = vqnqs_num_params_arch(ctx->N, layers, d_model, K, ctx->half_block, ctx->G);
     auto dalloc = [&](size_t bytes) -> void* {
         void* p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
@@ -935,13 +946,13 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
 }
 
 int vqnqs_create_arch(int L, int periodic, double J, int layers, int d_model, int heads, int K, int vq_heads,
-                      int half_block, const float* weights, vqnqs_ctx** out) {
+                      int half_block, int token_group, const float* weights, vqnqs_ctx** out) {
     if (L < 2 || L * L > 512) {
         if (out) *out = nullptr;
         return VQNQS_ERR_ARG;
     }
     return create_ctx(MODEL_HEISENBERG, L, L * L, periodic, J, 0.0, layers, d_model, heads, K, weights, out,
-                      vq_heads, half_block);
+                      vq_heads, half_block, token_group);
 }
 
 int vqnqs_set_weights(vqnqs_ctx* ctx, const float* weights, int is_device, void* stream) {
@@ -970,6 +981,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (ctx->model != MODEL_HEISENBERG) return fail(ctx, VQNQS_ERR_ARG, "ragged: square-lattice contexts only");
+    if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "ragged: one spin per token");
     if (n_groups < 1 || n_groups > MAX_GROUPS || !L_g || !B_g)
         return fail(ctx, VQNQS_ERR_ARG, "ragged: need 1..8 groups and host arrays L_g, B_g");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
@@ -977,6 +989,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
+        if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: one spin per token");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1081,7 +1094,7 @@ int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out) {
     out->inc_patch_pairs = st[ST_INC_PPAIRS];
     out->inc_full_pairs = st[ST_INC_FPAIRS];
     // analytic FLOPs, 2 per multiply-add
-    const double d = ctx->d, K = ctx->K, N = ctx->N, Ly = ctx->layers;
+    const double d = ctx->d, K = ctx->K, N = ctx->P, Ly = ctx->layers;
     const double rows = (double)out->rows, cfgs = (double)out->configs;
     const double attn = cfgs * Ly * 2.0 * d * N * (N + 1);
     const double vq = rows * Ly * 2.0 * K * d;
@@ -1137,12 +1150,14 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: one quantizer head only");
     if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: no final half-block");
+    if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: one spin per token");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
         if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
+        if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: one spin per token");
         if (!incremental_supported(ctx->d, ctx->heads))
             return fail(ctx, VQNQS_ERR_ARG,
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
@@ -1345,6 +1360,7 @@ int vqnqs_sample(vqnqs_ctx* ctx, int B, const float* uniforms, uint8_t* spins, f
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "sample: one quantizer head only");
     if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "sample: no final half-block");
+    if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "sample: one spin per token");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     const bool bf16 = (flags & VQNQS_BF16) != 0;
@@ -1459,6 +1475,7 @@ int vqnqs_vmc_step(vqnqs_ctx* ctx, int B, const float* uniforms, float lr, uint8
     ctx->err.clear();
     if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: one quantizer head only");
     if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: no final half-block");
+    if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "vmc_step: one spin per token");
     if (B <= 0 || !uniforms || !spins || !e_loc || !grad || !mean_var)
         return fail(ctx, VQNQS_ERR_ARG, "vmc step: B > 0 and every buffer are required");
     // e_loc holds the drawn configurations' log psi until the local energies overwrite it

@@ -100,7 +100,8 @@ struct Chunk {
     const int* bonds;       // bond table of all groups, [.][2]
     Groups g;
     int s0, S;              // this chunk holds global samples s0 .. s0+S-1 (local index b)
-    int N, d, heads, K;     // N: largest number of sites (position-embedding rows)
+    int N, d, heads, K;     // N: largest number of positions (position-embedding rows)
+    int G = 1;              // spins per token: a sample of n sites has n / G positions
     int model;              // MODEL_*
     const int* cfg_sample;  // [C] local sample of each configuration
     const int* cfg_i;       // [C] exchanged site pair (-1 for the sample itself)
@@ -117,7 +118,8 @@ __device__ __forceinline__ int sample_group(const Chunk& ch, int b) {
     while (g + 1 < ch.g.n && gb >= ch.g.first[g + 1]) ++g;
     return g;
 }
-__device__ __forceinline__ int sample_N(const Chunk& ch, int b) { return ch.g.N[sample_group(ch, b)]; }
+// positions (rows) of sample b: its sites over the token group size
+__device__ __forceinline__ int sample_N(const Chunk& ch, int b) { return ch.g.N[sample_group(ch, b)] / ch.G; }
 __device__ __forceinline__ const uint8_t* sample_spins(const Chunk& ch, int b) {
     const int g = sample_group(ch, b);
     return ch.spins + ch.g.spin_off[g] + (long long)(ch.s0 + b - ch.g.first[g]) * ch.g.N[g];
@@ -129,6 +131,12 @@ __device__ __forceinline__ int cfg_N(const Chunk& ch, int c) { return sample_N(c
 // p = j+1, and a causal network's rows at p <= min(i, j) see none of them
 // (Sec. 2: conditionals before the changed site are unchanged).
 __device__ __forceinline__ int cfg_first_changed(int ci, int cj) { return ci < 0 ? 0 : min(ci, cj) + 1; }
+// The same for tokens of G spins: the group of the first changed site is the first
+// changed token input one position later.
+__device__ __forceinline__ int cfg_p0(const Chunk& ch, int c) {
+    const int ci = ch.cfg_i[c], cj = ch.cfg_j[c];
+    return ci < 0 ? 0 : min(ci, cj) / ch.G + 1;
+}
 
 // Spin at site q of the configuration whose sample spins are s and whose exchanged
 // pair is (ci, cj), or whose site ci is flipped when cj == CFG_FLIP.
@@ -159,8 +167,10 @@ cudaError_t launch_configs(const Chunk& ch, float diag_coef, int with_bonds, int
                            cudaStream_t st, int grid);
 cudaError_t launch_embed(const Chunk& ch, const float* tok_emb, const float* pos_emb, int reuse, float* X0,
                          int* uid0, cudaStream_t st, int grid);
+// V = 2^G outputs (log-softmax over the values of a token's spin group)
 cudaError_t launch_head(const float* X, const int* counters, int u_slot, const float* g, const float* b,
-                        const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid);
+                        const float* w_head, const float* b_head, int d, float* logp, cudaStream_t st, int grid,
+                        int G = 1);
 // final half-block (no quantizer): active row a (counters[CNT_A] of them, row act_rows[a])
 // gets G_o[a] = O[row] (FP32 or BF16) and G_x[a] = X[uid[row]]; then every chunk row
 // gets the index of its active row (of the sample's row before the first changed site)

@@ -195,3 +195,77 @@ def test_half_block_refusals():
         m.sample(torch.rand(4, L * L, device="cuda"))
     with pytest.raises(ValueError):  # a blob without the half-block's weights
         VQNQS(L, True, 1.0, layers, d, heads, K, si.make_weights(L * L, layers, d, K), half_block=True)
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_token_groups_fp32_match_oracle_4x4(G):
+    from paper_2212_11296_gb300 import REUSE, VQNQS
+    L, layers, d, heads, K, B = 4, 2, 32, 4, 16, 64
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, token_group=G)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, token_group=G)
+    P = model.parse_blob(w, N, layers, d, heads, K, token_group=G)
+    e_plain = m.local_energy(s, 0)
+    e_reuse = m.local_energy(s, REUSE)
+    assert torch.equal(e_plain, e_reuse)
+    check(P, spins, e_reuse.cpu().numpy(), L)
+    codes, lp = m.codes(s)
+    assert codes.shape == (B, layers, N // G)
+    lp_or = model.log_psi(P, spins)
+    assert np.max(np.abs(lp.cpu().numpy() - lp_or) / np.abs(lp_or)) <= FP32_TOL
+    assert m.stats()["device_status"] == 0
+
+
+def test_token_groups_bf16_close_to_fp32():
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B, G = 8, 2, 128, 4, 64, 128, 4
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, token_group=G)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, token_group=G)
+    e16 = m.local_energy(s, REUSE | BF16)
+    dd = rel_err(e16.cpu().numpy(), m.local_energy(s, REUSE).cpu().numpy(), N)
+    print(f"G = 4 BF16 vs FP32: median {np.median(dd):.2e} max {dd.max():.2e}")
+    assert np.median(dd) <= 5e-3 and dd.max() <= 0.1
+    assert torch.equal(e16, m.local_energy(s, BF16))
+
+
+def test_all_variants_16x16_sampled():
+    """Tokens of 4 spins with a 16-way head, two quantizer heads of 64 codes and the
+    final half-block at 16x16: sampled configurations against the oracle."""
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B, H, G = 16, 3, 256, 8, 64, 16, 2, 4
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, half_block=True, token_group=G)
+    spins = si.make_samples(L, B, seed=1)
+    s = torch.as_tensor(spins).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H, half_block=True, token_group=G)
+    m.reset_stats()
+    e = m.local_energy(s, REUSE).cpu().numpy()
+    st = m.stats()
+    print(f"G = 4, 12 bits, half-block: quantized-ops FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True, token_group=G)
+    check(P, spins[:2], e[:2], L, max_miss=0.5)
+    e16 = m.local_energy(s, REUSE | BF16).cpu().numpy()
+    assert np.median(rel_err(e16, e, N)) <= 1e-2
+    assert m.stats()["device_status"] == 0
+
+
+def test_token_group_refusals():
+    from paper_2212_11296_gb300 import INCREMENTAL, REUSE, VQNQS, VQNQSError
+    L, layers, d, heads, K, G = 4, 2, 32, 4, 16, 4
+    w = si.make_weights(L * L, layers, d, K, seed=0, token_group=G)
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, token_group=G)
+    s = torch.as_tensor(si.make_samples(L, 4, seed=1)).cuda()
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.local_energy(s, REUSE | INCREMENTAL)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.grad_log_psi(s)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.sample(torch.rand(4, L * L, device="cuda"))
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.local_energy_ragged([(4, s)])
+    with pytest.raises((VQNQSError, ValueError)):  # three spins per token: not a supported group
+        VQNQS(L, True, 1.0, layers, d, heads, K, w, token_group=3)
