@@ -269,3 +269,37 @@ def test_token_group_refusals():
         m.local_energy_ragged([(4, s)])
     with pytest.raises((VQNQSError, ValueError)):  # three spins per token: not a supported group
         VQNQS(L, True, 1.0, layers, d, heads, K, w, token_group=3)
+
+
+@pytest.mark.parametrize("flags", [1, 3])
+def test_ragged_with_variants_equals_separate_lattices(flags):
+    """Two quantizer heads and the final half-block in a ragged batch (6x6, 8x8,
+    12x12): bitwise equal to separate single-lattice contexts whose blob holds the
+    first L^2 position-embedding rows."""
+    from paper_2212_11296_gb300 import VQNQS
+    layers, d, heads, K, Lmax = 2, 128, 4, 64, 12
+    groups_spec = [(6, 12), (8, 8), (12, 4)]
+    blob = si.make_weights(Lmax * Lmax, layers, d, K, seed=0, half_block=True)
+    big = VQNQS(Lmax, True, 1.0, layers, d, heads, K, blob, vq_heads=2, half_block=True)
+    groups = [(L, torch.as_tensor(si.make_samples(L, B, seed=1 + L)).cuda()) for L, B in groups_spec]
+    e = big.local_energy_ragged(groups, flags)
+    assert big.stats()["device_status"] == 0
+    off = 0
+    for L, s in groups:
+        head = 3 * d
+        sliced = np.concatenate([blob[:head], blob[head:head + L * L * d], blob[head + Lmax * Lmax * d:]])
+        small = VQNQS(L, True, 1.0, layers, d, heads, K, sliced.astype(np.float32), vq_heads=2, half_block=True)
+        assert torch.equal(e[off:off + s.shape[0]], small.local_energy(s, flags)), L
+        off += s.shape[0]
+
+
+def test_graph_replay_with_variants():
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS, LocalEnergyGraph
+    L, layers, d, heads, K, B = 8, 2, 128, 4, 64, 32
+    w = si.make_weights(L * L, layers, d, K, seed=0, half_block=True, token_group=2)
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=2, half_block=True, token_group=2)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    for flags in (REUSE, REUSE | BF16):
+        direct = m.local_energy(s, flags)
+        g = LocalEnergyGraph(m, [(L, B)], flags)
+        assert torch.equal(g(s).clone(), direct)
