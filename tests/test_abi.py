@@ -53,3 +53,51 @@ def test_create_rejects_bad_shapes_without_touching_a_gpu(lib):
                  (24, 1, 1.0, 2, 32, 4, 16)]:
         assert lib.vqnqs_create(*args, ctypes.cast(w, ctypes.c_void_p), ctypes.byref(h)) == 1
         assert not h.value
+
+
+def declared_prototypes():
+    """{name: number of parameters} of every function include/vqnqs.h declares."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(vqnqs_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_header():
+    from paper_2212_11296_gb300 import _lib
+    protos = declared_prototypes()
+    assert set(protos) == set(declared_functions())
+    for name, _, args in _lib.SIGNATURES:
+        assert name in protos, name
+        assert len(args) == protos[name], f"{name}: header {protos[name]} parameters, binding {len(args)}"
+
+
+def test_num_params_arch_matches_generator_layout(lib):
+    for n, layers, d, K in [(16, 2, 32, 16), (64, 3, 128, 64), (256, 3, 256, 64)]:
+        for half in (0, 1):
+            for G in (1, 2, 4):
+                assert lib.vqnqs_num_params_arch(n, layers, d, K, half, G) == \
+                    si.num_params(n, layers, d, K, bool(half), G), (n, half, G)
+    assert lib.vqnqs_num_params_arch(16, 2, 32, 16, 0, 3) == 0  # three spins per token: not supported
+    assert lib.vqnqs_num_params_arch(18, 2, 32, 16, 0, 4) == 0  # sites not a multiple of the group
+
+
+def test_create_arch_rejects_bad_variants_without_touching_a_gpu(lib):
+    h = ctypes.c_void_p()
+    w = (ctypes.c_float * 4)()
+    # (L, layers, d, heads, K, vq_heads, half_block, token_group)
+    for L, layers, d, heads, K, H, half, G in [
+            (4, 2, 32, 4, 16, 3, 0, 1),    # d_model not a multiple of the quantizer heads
+            (4, 1, 64, 2, 64, 8, 0, 1),    # 8 heads x 6 bits = 48 bits: over the 31-bit packed code
+            (4, 2, 32, 4, 16, 1, 0, 3),    # three spins per token
+            (3, 2, 32, 4, 16, 1, 0, 2),    # 9 sites: not a multiple of two
+            (4, 2, 32, 4, 16, 9, 0, 1)]:   # more than 8 quantizer heads
+        rc = lib.vqnqs_create_arch(L, 1, 1.0, layers, d, heads, K, H, half, G, ctypes.cast(w, ctypes.c_void_p),
+                                   ctypes.byref(h))
+        assert rc == 1 and not h.value, (L, d, K, H, G)
