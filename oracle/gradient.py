@@ -9,8 +9,9 @@ D_j = -||o - W_j||_2 and
 
 so the forward value is the nearest codeword and the backward pass flows
 through softmax(D) (straight-through, temperature 1, no noise: the paper's
-"variant of Gumbel-Softmax" is read as this noiseless form).  The gradient is
-taken by torch autograd on exactly that expression.
+"variant of Gumbel-Softmax" is read as this noiseless form).  With H quantizer
+heads the expression is applied per head, V_h = g(D_h)^T W_h, as Eq. st is
+written.  The gradient is taken by torch autograd on exactly that expression.
 
 Sec. 2 gradient estimator: dE/dtheta ~ sum_i (E_loc(s_i) - E)^* d log Psi(s_i)/dtheta.
 Read with the 1/B normalisation and the factor 2 that the derivative of the
@@ -31,49 +32,67 @@ from . import model
 
 def _leaf_params(P: model.Params) -> model.Params:
     t = {k: v.detach().clone().requires_grad_(True) for k, v in P.t.items()}
-    return model.Params(d=P.d, heads=P.heads, K=P.K, layers=P.layers, n_max=P.n_max, t=t)
+    return model.Params(d=P.d, heads=P.heads, K=P.K, layers=P.layers, n_max=P.n_max, t=t, vq_heads=P.vq_heads,
+                        half_block=P.half_block, token_group=P.token_group)
+
+
+def _heads(W, o):
+    """(segments of o, codebooks): one pair per quantizer head (one for a [K, d] codebook)."""
+    if W.dim() == 2:
+        return [o], [W]
+    H, K, dq = W.shape
+    return [o[..., h * dq:(h + 1) * dq] for h in range(H)], [W[h] for h in range(H)]
+
+
+def _soft_D(seg, Wh):
+    """softmax over j of D_j = -||seg - W_h,j||_2."""
+    D = -torch.sqrt(torch.clamp(((seg[..., None, :] - Wh) ** 2).sum(-1), min=0.0))
+    return torch.softmax(D, dim=-1)
 
 
 def st_quantizer(P: model.Params):
-    """Eq. st with SG = detach."""
+    """Eq. st with SG = detach, per quantizer head."""
     def q(l, o):
-        W = P.t[f"{l}.codebook"]
-        dist2 = model.sq_distances(o, W)
-        c = torch.argmin(dist2, dim=-1)
-        D = -torch.sqrt(torch.clamp(((o[..., None, :] - W) ** 2).sum(-1), min=0.0))
-        soft = torch.softmax(D, dim=-1)
-        onehot = torch.nn.functional.one_hot(c, W.shape[0]).to(o.dtype)
-        g = onehot.detach() + soft - soft.detach()
-        return g @ W, c
+        parts, codes = [], []
+        for seg, Wh in zip(*_heads(P.t[f"{l}.codebook"], o)):
+            c = torch.argmin(model.sq_distances(seg, Wh), dim=-1)
+            soft = _soft_D(seg, Wh)
+            onehot = torch.nn.functional.one_hot(c, Wh.shape[0]).to(o.dtype)
+            parts.append((onehot.detach() + soft - soft.detach()) @ Wh)
+            codes.append(c)
+        return torch.cat(parts, dim=-1), codes[0] if len(codes) == 1 else torch.stack(codes, -1)
     return q
 
 
 def frozen_quantizer(P: model.Params, frozen):
     """The straight-through surrogate with every stop-gradient term frozen at theta_0.
 
-    ``frozen[l] = (codes, softmax(D_0))``.  Its value is onehot(c_0)^T W +
-    (softmax(D(theta)) - softmax(D_0))^T W, whose derivative at theta_0 equals
-    the straight-through gradient; finite differences of it check Eq. st."""
+    ``frozen[l] = [(codes, softmax(D_0)) per head]``.  Its value is
+    onehot(c_0)^T W + (softmax(D(theta)) - softmax(D_0))^T W per head, whose
+    derivative at theta_0 equals the straight-through gradient; finite
+    differences of it check Eq. st."""
     def q(l, o):
-        W = P.t[f"{l}.codebook"]
-        c0, soft0 = frozen[l]
-        D = -torch.sqrt(torch.clamp(((o[..., None, :] - W) ** 2).sum(-1), min=0.0))
-        soft = torch.softmax(D, dim=-1)
-        onehot = torch.nn.functional.one_hot(c0, W.shape[0]).to(o.dtype)
-        return (onehot + soft - soft0) @ W, c0
+        parts, codes = [], []
+        for (seg, Wh), (c0, soft0) in zip(zip(*_heads(P.t[f"{l}.codebook"], o)), frozen[l]):
+            onehot = torch.nn.functional.one_hot(c0, Wh.shape[0]).to(o.dtype)
+            parts.append((onehot + _soft_D(seg, Wh) - soft0) @ Wh)
+            codes.append(c0)
+        return torch.cat(parts, dim=-1), codes[0] if len(codes) == 1 else torch.stack(codes, -1)
     return q
 
 
 def record_frozen(P: model.Params, spins):
-    """Codes and softmax(D) of every layer at the current parameters, for ``frozen_quantizer``."""
+    """Codes and softmax(D) of every layer and head at the current parameters, for ``frozen_quantizer``."""
     frozen = []
 
     def q(l, o):
-        W = P.t[f"{l}.codebook"]
-        c = model.nearest_code(o, W)
-        D = -torch.sqrt(torch.clamp(((o[..., None, :] - W) ** 2).sum(-1), min=0.0))
-        frozen.append((c, torch.softmax(D, dim=-1)))
-        return W[c], c
+        per_head, parts = [], []
+        for seg, Wh in zip(*_heads(P.t[f"{l}.codebook"], o)):
+            c = model.nearest_code(seg, Wh)
+            per_head.append((c, _soft_D(seg, Wh)))
+            parts.append(Wh[c])
+        frozen.append(per_head)
+        return torch.cat(parts, dim=-1), per_head[0][0]
 
     with torch.no_grad():
         model.forward(P, spins, quantizer=q)
@@ -83,7 +102,8 @@ def record_frozen(P: model.Params, spins):
 def log_psi_with(P: model.Params, spins, quantizer) -> torch.Tensor:
     s = torch.as_tensor(np.asarray(spins)).long()
     lp = model.forward(P, s, quantizer=quantizer)
-    return 0.5 * lp.gather(-1, s[..., None])[..., 0].sum(-1)
+    v = model.group_values(s, P.token_group)
+    return 0.5 * lp.gather(-1, v[..., None])[..., 0].sum(-1)
 
 
 def flatten(P: model.Params, grads: dict) -> np.ndarray:

@@ -227,8 +227,6 @@ def forward(P: Params, spins, quantizer=None, record=None, gaps=None):
             if P.vq_heads == 1:
                 c = c[..., 0]
         else:
-            if P.vq_heads != 1:
-                raise ValueError("a replacement quantizer is defined for one quantizer head only")
             vq, c = quantizer(l, o)
         if record is not None:
             record.append(c)

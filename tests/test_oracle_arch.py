@@ -172,3 +172,41 @@ def test_token_group_model_is_normalised(G):
     P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=2, token_group=G)
     states = np.array(list(itertools.product([0, 1], repeat=N)))
     assert abs(np.exp(2.0 * model.log_psi(P, states)).sum() - 1.0) < 1e-12
+
+
+def test_st_gradient_of_the_variants_matches_finite_differences():
+    """Eq. st per quantizer head, with the half-block and tokens of two spins:
+    central differences (h = 1e-6) of the straight-through surrogate, its
+    stop-gradient terms frozen at theta_0, equal the autograd O_k."""
+    import dataclasses
+    from oracle import gradient
+    L, layers, d, heads, K, H, G = 4, 2, 16, 2, 4, 2, 2
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=13, std=0.3, half_block=True, token_group=G)
+    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True, token_group=G)
+    s = si.make_samples(L, 1, seed=9)
+    O = gradient.per_sample_O(P, s)[0]
+    frozen = gradient.record_frozen(P, s)
+    names = list(P.t)
+    sizes = [P.t[n].numel() for n in names]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(5)
+    picks = list(rng.choice(len(O), 120, replace=False))
+    for n in ("0.codebook", "1.codebook", "h.w_o", "h.w_qkv", "w_head", "tok_emb"):
+        k = names.index(n)
+        picks += list(range(offs[k], min(offs[k] + 8, offs[k + 1])))
+    h = 1e-6
+    for g in picks:
+        k = int(np.searchsorted(offs, g, side="right") - 1)
+        name, j = names[k], int(g - offs[k])
+        vals = []
+        for sgn in (+1, -1):
+            Q = dataclasses.replace(P, t={a: b.clone() for a, b in P.t.items()})
+            Q.t[name].view(-1)[j] += sgn * h
+            with torch.no_grad():
+                vals.append(float(gradient.log_psi_with(Q, s, gradient.frozen_quantizer(Q, frozen))[0]))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - O[g]) <= 1e-7 * max(1.0, abs(O[g])), (name, j, fd, O[g])
+    # the codebooks do receive a gradient through softmax(D_h) of each head
+    k = names.index("0.codebook")
+    assert np.abs(O[offs[k]:offs[k + 1]]).max() > 0
