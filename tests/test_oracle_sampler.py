@@ -65,3 +65,24 @@ def test_recorded_conditionals_give_log_psi():
     s, pup = sampler.sample(P, u)
     logp = np.where(s == 1, np.log(pup), np.log1p(-pup)).sum(1)
     assert np.allclose(logp, 2.0 * model.log_psi(P, s), rtol=0, atol=1e-10)
+
+
+def test_group_tokens_draws_follow_psi_squared():
+    """Tokens of 2 spins (16-way over 4 sites: two 4-way draws): the empirical
+    distribution matches P(s) over the basis, and the recorded conditionals give
+    2 log psi of the drawn configurations."""
+    G = 2
+    w = si.make_weights(N, LAYERS, D, K, seed=6, std=0.3, token_group=G)
+    P = model.parse_blob(w, N, LAYERS, D, HEADS, K, token_group=G)
+    n = 40000
+    u = si.uniforms(10, n * (N // G)).reshape(n, N // G)
+    s, probs = sampler.sample_groups(P, u)
+    p = exact(P)
+    assert abs(p.sum() - 1.0) < 1e-12 and p.max() / p.min() > 3.0
+    assert np.max(np.abs(z_scores(frequencies(s), p, n))) < 5.0
+    v = (s.reshape(n, N // G, G) * (1 << np.arange(G))).sum(-1)
+    logp = np.log(np.take_along_axis(probs, v[..., None], -1)[..., 0]).sum(1)
+    assert np.allclose(logp[:64], 2.0 * model.log_psi(P, s[:64]), rtol=0, atol=1e-10)
+    # a plausible mistake, the bits of a group in the opposite order, is caught
+    s_rev = s.reshape(n, N // G, G)[..., ::-1].reshape(n, N)
+    assert np.max(np.abs(z_scores(frequencies(s_rev), p, n))) > 5.0
