@@ -47,31 +47,12 @@ namespace vq {
 namespace {
 
 constexpr float CERT_ETA_REL = 1.52587890625e-05f;  // 2^-16
-constexpr int PATCH_KB = 16;                        // changed keys staged per block in k_inc_patch
-
-template <typename T>
-__device__ __forceinline__ float ldf(const T* p);
-template <>
-__device__ __forceinline__ float ldf<float>(const float* p) { return *p; }
-template <>
-__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
 
 // 2^x with the SFU's approximate exponential (relative error ~2^-22; flushes denormals)
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// Appends `take` rows to the list behind counters[slot]; one atomic per warp.
-__device__ __forceinline__ void warp_append(bool take, int row, int* counters, int slot, int* list) {
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (!m) return;
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(&counters[slot], __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (take) list[base + __popc(m & ((1u << lane) - 1))] = row;
 }
 
 // Ascending list of the positions p in [lo, hi) with pred(p), written to out
