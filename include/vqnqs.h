@@ -197,10 +197,12 @@ size_t vqnqs_workspace_bytes(const vqnqs_ctx* ctx, int chunk_samples, int flags)
 int vqnqs_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_log_psi, int flags,
                   void* dev_ws, size_t ws_bytes, void* stream);
 
-/* Local energies of a ragged batch: n_groups (1..8) groups of samples of
- * different lattice sizes evaluated with the context's model, all groups
- * sharing one pipeline (chunks mix lattice sizes; deduplication of
- * per-location work spans the groups of a chunk).
+/* Local energies (Sec. 2, Eq. local-energy; per-location reuse of Sec. 3.2)
+ * of a ragged batch: n_groups (1..8) groups of samples of different lattice
+ * sizes (Sec. 4 evaluates 4x4 to 12x12 lattices with one architecture)
+ * evaluated with the context's model, all groups sharing one pipeline (chunks
+ * mix lattice sizes; deduplication of per-location work spans the groups of a
+ * chunk).
  *   L_g, B_g     HOST int [n_groups]: lattice side (2 .. L of the context) and sample
  *                count of each group; boundary conditions and J are the context's
  *   dev_spins    DEVICE uint8: the groups' samples concatenated, group after group,
@@ -345,7 +347,10 @@ int vqnqs_compress_rows(vqnqs_ctx* ctx, int R, const int* dev_uid, const int* de
  * call on a device looks up the array's address with cudaGetSymbolAddress
  * (VQNQS_ERR_CUDA if that fails): make it before any stream capture.  All
  * calls on a device share the array; each call clears what it uses first, but
- * calls whose kernels overlap on the GPU race and give wrong results.
+ * calls whose kernels overlap on the GPU race and give wrong results.  A
+ * probe-bound overrun (which a table of twice the rows does not reach) sets
+ * *dev_count to -1 instead of U.  After cudaDeviceReset the cached address is
+ * stale: do not call this again in that process.
  * Asynchronous on `stream`. */
 #define VQNQS_NOALLOC_MAX_ROWS (1 << 18)
 int vqnqs_compress_rows_noalloc(int R, const int* dev_uid, const int* dev_code, int* dev_new_id,

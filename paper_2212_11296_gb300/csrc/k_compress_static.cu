@@ -18,7 +18,12 @@
 //    host threads on one device) race on the table and give wrong results;
 //  - the first call on each device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current) and caches it; make that
-//    first call before capturing a stream into a graph.
+//    first call before capturing a stream into a graph.  cudaDeviceReset
+//    destroys the module copy the cached address points into: after a reset
+//    this entry point must not be called again in the same process;
+//  - a probe that runs past its bound (the table holds at least twice the
+//    rows, so a probe finds a free slot before that) is reported to the caller
+//    by *count = -1 once the call's work has run, in place of the row count.
 #include <mutex>
 
 #include "vqnqs_internal.cuh"
@@ -33,6 +38,13 @@ constexpr size_t kNoallocBytes = kNoallocKeyBytes + kNoallocValBytes + 256;  // 
 
 // 6 MiB + 256 B: hash keys, then hash values, then a status word.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// The status word of this array is cleared by each call before its hash kernels
+// run; afterwards a raised overflow bit turns the returned count into -1.
+__global__ void k_noalloc_status_clear(int* status) { *status = 0; }
+__global__ void k_noalloc_report(const int* __restrict__ status, int* __restrict__ count) {
+    if (*status & VQNQS_DEV_HASH_OVERFLOW) *count = -1;
+}
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -49,6 +61,7 @@ extern "C" int vqnqs_compress_rows_noalloc(int R, const int* uid, const int* cod
                                            int* rep_code, int* count, void* stream) {
     if (R < 0 || R > kNoallocMaxRows) return VQNQS_ERR_ARG;
     if (!count || (R > 0 && (!uid || !code || !new_id || !rep_uid || !rep_code))) return VQNQS_ERR_ARG;
+    (void)cudaGetLastError();  // an error left by earlier, unrelated work is not this call's
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VQNQS_ERR_CUDA;
     void* base = nullptr;
@@ -71,8 +84,12 @@ extern "C" int vqnqs_compress_rows_noalloc(int R, const int* uid, const int* cod
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(b);
     int* vals = reinterpret_cast<int*>(b + kNoallocKeyBytes);
     int* status = reinterpret_cast<int*>(b + kNoallocKeyBytes + kNoallocValBytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    k_noalloc_status_clear<<<1, 1, 0, st>>>(status);
     // the clear step zeroes the keys this call uses and *count
-    const cudaError_t e = launch_compress_pairs(R, uid, code, new_id, rep_uid, rep_code, count, keys, vals,
-                                                compress_hash_bits(R), status, static_cast<cudaStream_t>(stream), sms);
-    return e == cudaSuccess ? VQNQS_OK : VQNQS_ERR_CUDA;
+    cudaError_t e = launch_compress_pairs(R, uid, code, new_id, rep_uid, rep_code, count, keys, vals,
+                                          compress_hash_bits(R), status, st, sms);
+    if (e != cudaSuccess) return VQNQS_ERR_CUDA;
+    k_noalloc_report<<<1, 1, 0, st>>>(status, count);
+    return cudaGetLastError() == cudaSuccess ? VQNQS_OK : VQNQS_ERR_CUDA;
 }
