@@ -73,10 +73,10 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
     the attention stage covers the samples' own rows only; the certificate is a
     2 K d distance pass per sample row; a patch costs 8 d per (row, changed
     key) pair (two scores and two value updates per head); a recomputed row 4 d
-    per query-key pair.  The BF16 patch runs its few products on the tensor
-    cores and is bound by the rows' data instead: bytes, 6 d per patched row
-    (its BF16 query and the sample's FP32 output) and 4 d per searched row (its
-    FP32 output written)."""
+    per query-key pair.  On the BF16 path the patch and the recompute run these
+    products on the tensor cores and are rated against the BF16 tensor peak
+    (algorithmic FLOPs: split operands take three MMAs per product, which are
+    not counted); their DRAM bytes are reported beside the rate."""
     d, K, Ly = w["d_model"], w["K"], w["layers"]
     U = st["unique_rows"]
     tc = "tensor" if bf16 else "alu"
@@ -90,12 +90,10 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
         return st["attn_pairs"] * Ly * 4.0 * d, tc
     if stage == "inc_certificate":
         return st["inc_base_rows"] * 2.0 * K * d, "alu"
-    if stage == "inc_patch":
-        if bf16:  # tensor-core scores and sums are negligible: the bound is the rows' data (bytes)
-            return st["inc_patched_rows"] * 6.0 * d + st["inc_searched_rows"] * 4.0 * d, "hbm"
-        return st["inc_patch_pairs"] * 8.0 * d, "alu"
+    if stage == "inc_patch":  # its scores and value sums run on the tensor cores on the BF16 path
+        return st["inc_patch_pairs"] * 8.0 * d, tc
     if stage == "inc_recompute":
-        return st["inc_full_pairs"] * 4.0 * d, "alu"
+        return st["inc_full_pairs"] * 4.0 * d, tc
     if stage == "qkv_gemm":
         return sum(U[:Ly]) * 6.0 * d * d, tc
     if stage in ("mlp_up", "mlp_down"):
@@ -239,40 +237,48 @@ def config_dict(w, path):
 
 
 def gemm_probe(m, dm: int, stream=None) -> dict:
-    """The QKV, MLP-up and MLP-down tensor-core GEMMs at M = 131072 (d_model dm):
-    3 untimed then 20 timed launches per shape, with the tensor and HBM fractions."""
+    """The QKV, MLP-up and MLP-down tensor-core GEMMs at M = 131072 (d_model dm), with single
+    and with split (hi + lo, three MMA passes) operands: 3 untimed then 20 timed launches per
+    shape, with the tensor fraction (of the MMAs issued) and the HBM fraction."""
     import torch
     pk = measured_peaks()
     Mg = 131072
     gemm = {"M": Mg, "peak_tflops": pk["bf16_tflops_burst"], "peak_source": f"bf16 dense, burst ({pk['src']})",
             "shapes": {}}
-    for name, Ng, Kg, epi in (("qkv_bias_bf16", 3 * dm, dm, 0), ("mlp_up_bias_gelu_bf16", 4 * dm, dm, 1),
-                              ("mlp_down_bias_residual_f32", dm, 4 * dm, 2)):
-        A = torch.randn(Mg, Kg, device="cuda").to(torch.bfloat16)
-        Bt = (0.05 * torch.randn(Ng, Kg, device="cuda")).to(torch.bfloat16)
-        bias = torch.zeros(Ng, device="cuda")
-        Rg = torch.zeros(Mg, Ng, device="cuda") if epi == 2 else None
-        Cg = torch.empty(Mg, Ng, dtype=torch.bfloat16 if epi < 2 else torch.float32, device="cuda")
-        for _ in range(3):
-            m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(20):
-            m.gemm_bf16(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        sec = a0.elapsed_time(a1) / 1e3 / 20
-        tf = 2.0 * Mg * Ng * Kg / sec / 1e12
-        # bytes a launch must move: A, Bt, C (and the residual R)
-        nbytes = Mg * Kg * 2 + Ng * Kg * 2 + Mg * Ng * (2 if epi < 2 else 4) + (Mg * Ng * 4 if epi == 2 else 0)
-        gbs = nbytes / sec / 1e9
-        t_tensor = 2.0 * Mg * Ng * Kg / (pk["bf16_tflops_burst"] * 1e12)
-        t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
-        gemm["shapes"][name] = {"N": Ng, "K": Kg, "us": sec * 1e6, "tflops": tf, "frac": tf / pk["bf16_tflops_burst"],
-                                "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
-                                "roofline_bound": "tensor" if t_tensor >= t_hbm else "hbm",
-                                "roofline_frac": max(t_tensor, t_hbm) / sec}
-        del A, Bt, Rg, Cg
+    for split in (False, True):
+        for name, Ng, Kg, epi in (("qkv_bias_bf16", 3 * dm, dm, 0), ("mlp_up_bias_gelu_bf16", 4 * dm, dm, 1),
+                                  ("mlp_down_bias_residual_f32", dm, 4 * dm, 2)):
+            npl = 2 if split else 1  # operand planes (hi, lo)
+            A = torch.randn(npl * Mg, Kg, device="cuda").to(torch.bfloat16)
+            Bt = (0.05 * torch.randn(npl * Ng, Kg, device="cuda")).to(torch.bfloat16)
+            bias = torch.zeros(Ng, device="cuda")
+            Rg = torch.zeros(Mg, Ng, device="cuda") if epi == 2 else None
+            Cg = torch.empty((npl if epi < 2 else 1) * Mg, Ng, dtype=torch.bfloat16 if epi < 2 else torch.float32,
+                             device="cuda")
+            fn = m.gemm_bf16_split if split else m.gemm_bf16
+            for _ in range(3):
+                fn(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(20):
+                fn(A, Bt, bias, epilogue=epi, R=Rg, out=Cg, stream=stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            sec = a0.elapsed_time(a1) / 1e3 / 20
+            mma = 3 if split else 1  # BF16 MMA passes per product
+            tf = 2.0 * Mg * Ng * Kg / sec / 1e12
+            # bytes a launch must move: A, Bt, C (and the residual R), every plane
+            nbytes = (npl * (Mg * Kg * 2 + Ng * Kg * 2) + Mg * Ng * (2 * npl if epi < 2 else 4) +
+                      (Mg * Ng * 4 if epi == 2 else 0))
+            gbs = nbytes / sec / 1e9
+            t_tensor = mma * 2.0 * Mg * Ng * Kg / (pk["bf16_tflops_burst"] * 1e12)
+            t_hbm = nbytes / (pk["hbm_gbs"] * 1e9)
+            gemm["shapes"][name + ("_split" if split else "")] = {
+                "N": Ng, "K": Kg, "us": sec * 1e6, "tflops": tf, "mma_tflops": mma * tf,
+                "frac": mma * tf / pk["bf16_tflops_burst"], "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"],
+                "roofline_bound": "tensor" if t_tensor >= t_hbm else "hbm",
+                "roofline_frac": max(t_tensor, t_hbm) / sec}
+            del A, Bt, Rg, Cg
     return gemm
 
 
@@ -321,19 +327,79 @@ def vq_sweep(args) -> dict:
     return out
 
 
+def grad_bench(args) -> dict:
+    """The differentiation workload: 20x20 periodic Heisenberg (N = 400, 800 bonds), 12 layers,
+    d_model 384, 12 heads, codebook 512, 512 uniform S_z = 0 samples (seeded weights).  One step:
+    the samples' local energies (VQ reuse, BF16 tensor-core GEMMs and attention) and the
+    hand-written backward with activation recomputation giving the energy gradient
+    2 mean[(E - mean E) O_k] (vqnqs_grad_log_psi).  Timed with CUDA events, L2 flushed between
+    steps; reported as gradient samples per second with the two parts' times and the backward's
+    per-stage times."""
+    import torch
+    import synthetic_inputs as si
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    L, layers, d, heads, K, B = 20, 12, 384, 12, 512, 512
+    N = L * L
+    blob = si.make_weights(N, layers, d, K, seed=0)
+    spins = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, blob)
+    flags = REUSE | BF16
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ws = m.workspace(flags)
+    for _ in range(args.warmup):
+        e = m.local_energy(spins, flags, workspace=ws)
+        _, g = m.grad_log_psi(spins, e_loc=e)
+    torch.cuda.synchronize()
+    te, tg = [], []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            e = m.local_energy(spins, flags, workspace=ws)
+            ev[1].record(stream)
+            _, g = m.grad_log_psi(spins, e_loc=e)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            te.append(ev[0].elapsed_time(ev[1]))
+            tg.append(ev[1].elapsed_time(ev[2]))
+    m.profile(True)
+    m.profile_read()
+    m.grad_log_psi(spins, e_loc=e)
+    prof = m.profile_read()
+    m.profile(False)
+    st = m.stats()
+    ms = sum(te) + sum(tg)
+    return {"metric": "energy-gradient samples/sec at 20x20 (E_loc + backward)", "unit": "samples/s",
+            "value": B * args.steps / (ms / 1e3), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "eloc_ms_per_step": sum(te) / args.steps,
+            "backward_ms_per_step": sum(tg) / args.steps,
+            "config": {"workload": f"{L}x{L} periodic Heisenberg J=1, {layers} layers d_model {d} heads {heads} "
+                                   f"codebook {K}, {B} uniform S_z=0 samples", "eloc_path": "VQ-reuse BF16",
+                       "backward": "FP32 hand-written, activation recomputation"},
+            "backward_stages": {k: {"ms": v[2], "launches": v[1]} for k, v in prof.items() if v[1] > 0},
+            "grad_norm": float(g.norm().item()), "device_status": st["device_status"], "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--flags", default="reuse,bf16,incremental",
-                    help="comma list of reuse,bf16,incremental for the timed path")
+    ap.add_argument("--flags", default="reuse,bf16,incremental,split",
+                    help="comma list of reuse,bf16,incremental,split for the timed path (split: BF16 tensor-core "
+                         "products from hi + lo operand pairs, FP32-grade)")
+    ap.add_argument("--plain-runs", type=int, default=5, help="timed runs of the plain FP32 leg (median)")
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
     ap.add_argument("--gemm-only", action="store_true",
                     help="run only the tensor-core GEMM probe (three shapes at M = 131072) and print it")
+    ap.add_argument("--grad", action="store_true",
+                    help="the differentiation workload (20x20, 12 layers, d_model 384, 512 samples): E_loc plus the "
+                         "energy gradient per step, printed as its own line")
     ap.add_argument("--vq-sweep", action="store_true",
                     help="quantization bandwidth sweep (Table 1 protocol, random weights): 16x16, three blocks, "
                          "64 codes per head, 1, 2 and 4 quantizer heads")
@@ -347,7 +413,7 @@ def main():
     import torch
     import torch.distributed as dist
     import synthetic_inputs as si
-    from paper_2212_11296_gb300 import BF16, INCREMENTAL, REUSE, VQNQS
+    from paper_2212_11296_gb300 import BF16, BF16_SPLIT, INCREMENTAL, REUSE, VQNQS
 
     if args.gemm_only:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -358,6 +424,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(vq_sweep(args)))
         return 0
+    if args.grad:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(grad_bench(args)))
+        return 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -367,7 +437,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     flags = 0
     for f in args.flags.split(","):
-        flags |= {"reuse": REUSE, "bf16": BF16, "incremental": INCREMENTAL, "": 0}[f.strip()]
+        flags |= {"reuse": REUSE, "bf16": BF16, "incremental": INCREMENTAL, "split": BF16_SPLIT, "": 0}[f.strip()]
     B, L, N = w["samples_per_gpu"], w["L"], w["L"] ** 2
     blob = si.make_weights(N, w["layers"], w["d_model"], w["K"], seed=0)
     all_spins = si.make_samples(L, B * world, seed=1)
@@ -459,18 +529,41 @@ def main():
             raise RuntimeError("graph replay differs from the eager step")
         del g
 
-    # the plain full-recompute FP32 path on a subset of the same samples
+    # the plain full-recompute FP32 path on a subset of the same samples (median of several runs)
     n_plain = min(64, B)
     sub = spins[:n_plain].contiguous()
     ws0 = m.workspace(0)
     m.local_energy(sub, 0, workspace=ws0)
     torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    m.local_energy(sub, 0, workspace=ws0)
-    b.record(stream)
-    torch.cuda.synchronize()
-    plain_value = n_plain / (a.elapsed_time(b) / 1e3)
+    plain_ms = []
+    for k in range(max(1, args.plain_runs)):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.local_energy(sub, 0, workspace=ws0)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    plain_value = n_plain / (statistics.median(plain_ms) / 1e3)
+
+    # accuracy: the first 64 samples of the workload against the stored FP64 oracle values
+    # (tests/golden/eloc_16x16_64.txt, written by a script that calls the oracle only),
+    # raw: no sample exempted; the single-BF16 path beside it for context
+    accuracy = None
+    gold = os.path.join(ROOT, "tests", "golden", "eloc_16x16_64.txt")
+    if w["L"] == 16 and B >= 64 and os.path.exists(gold):
+        ref = np.loadtxt(gold, comments="#")[:, 1]
+        n_acc = len(ref)
+        e_acc = m.local_energy(spins[:n_acc].contiguous(), flags).cpu().numpy().astype(np.float64)
+        rel = np.abs(e_acc - ref) / np.maximum(np.abs(ref), 1e-3 * N)
+        bar = 2e-3 if flags & BF16 else 1e-5
+        accuracy = {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)), "samples": n_acc,
+                    "bar": bar, "pass": bool(rel.max() <= bar),
+                    "reference": "stored FP64 oracle values of the first 64 samples (no sample exempted)"}
+        if flags & BF16_SPLIT:
+            e1 = m.local_energy(spins[:n_acc].contiguous(), flags & ~BF16_SPLIT).cpu().numpy().astype(np.float64)
+            r1 = np.abs(e1 - ref) / np.maximum(np.abs(ref), 1e-3 * N)
+            accuracy["single_bf16_operands"] = {"max_rel": float(r1.max()), "median_rel": float(np.median(r1))}
 
     # the three per-location tensor-core GEMM shapes on a large M (the reuse
     # path only feeds them the few unique rows), each with its fused epilogue
@@ -500,6 +593,12 @@ def main():
                 ("bytes_per_launch" if bound == "hbm" else "flops_per_launch"): fl / max(1, nl)}
     stages = {k: {"ms_per_step": v[2] / args.steps, "launches_per_step": v[1] / args.steps,
                   "share": v[2] / max(1e-9, sum(x[2] for x in per_step.values()))} for k, v in per_step.items()}
+    for k, v in per_step.items():  # each stage's algorithmic rate against its own bound
+        fl_k, bound_k = stage_flops(k, st, w, bool(flags & BF16), bool(flags & INCREMENTAL))
+        if fl_k > 0 and v[2] > 0:
+            rate = fl_k / (v[2] / 1e3) / 1e12
+            pk_k = pk["bf16_tflops"] if bound_k == "tensor" else FP32_FFMA_PEAK_TFLOPS
+            stages[k].update({"tflops": rate, "bound": bound_k, "frac": rate / pk_k})
 
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
@@ -510,14 +609,18 @@ def main():
         "vs_baseline": None, "dtype": "bf16" if flags & BF16 else "f32", "data": "synthetic",
         "config": config_dict(w, ("VQ-reuse" if flags & REUSE else "full recompute") +
                               (" incremental" if flags & INCREMENTAL else "") +
-                              (" BF16 GEMMs, FP32 VQ" if flags & BF16 else " FP32")),
+                              ((" BF16 tensor-core products from hi + lo operand pairs (three MMAs each, FP32 "
+                                "accumulation), FP32-grade VQ" if flags & BF16_SPLIT else
+                                " BF16 GEMMs, FP32 VQ") if flags & BF16 else " FP32")),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * N),
                 "d2h_bytes_per_step": int(B * 4)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "graph_replay": {"value": graph_value, "unit": UNIT} if graph_value else None,
-        "plain_fp32": {"value": plain_value, "unit": UNIT, "samples": n_plain},
+        "plain_fp32": {"value": plain_value, "unit": UNIT, "samples": n_plain, "runs": len(plain_ms),
+                       "ms_runs": plain_ms},
+        "err_vs_fp64": accuracy,
         "speedup_vs_plain_fp32": value / plain_value,
         "unique_row_fraction": [u / max(1, st["rows"]) for u in st["unique_rows"]],
         "flop_reduction": st["flops_full"] / max(1.0, st["flops_done"]),
@@ -535,8 +638,8 @@ def main():
         n = len(vals)
         rel = np.abs(e_gpu[:n] - vals) / np.maximum(np.abs(vals), 1e-3 * N)
         res["cpu_baseline"] = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"first {n} samples of the workload, FP64 full recompute"}
-        res["err_vs_fp64"] = {"max_rel": float(rel.max()), "samples": n}
+                               "sample": f"first {n} samples of the workload, FP64 full recompute",
+                               "max_rel_vs_gpu": float(rel.max())}
     print(json.dumps(res))
     if world > 1:
         dist.destroy_process_group()

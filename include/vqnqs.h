@@ -65,13 +65,23 @@ typedef enum {
 enum {
     VQNQS_REUSE = 1,       /* deduplicate per-location work by (row, code) keys (Sec. 3.2) */
     VQNQS_BF16 = 2,        /* BF16 tensor-core GEMMs with FP32 accumulation */
-    VQNQS_INCREMENTAL = 4  /* with VQNQS_REUSE, local energies only: a connected configuration's
+    VQNQS_INCREMENTAL = 4, /* with VQNQS_REUSE, local energies only: a connected configuration's
                               attention rows whose query is the sample's are corrected for the
                               changed keys only, and their codeword is taken from the sample's row
                               when a distance bound proves it unchanged (else searched).  Exact up
                               to rounding; the paper leaves attention dense (Sec. 3.2).  Needs
                               d_model in {32, 64, 128, 256, 512} and d_model / heads in {16, 32},
                               a multiple of d_model / 32. */
+    VQNQS_BF16_SPLIT = 8   /* with VQNQS_BF16: every tensor-core product takes its operands as BF16
+                              pairs x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and sums
+                              hi.hi + hi.lo + lo.hi in FP32, three BF16 MMAs per product: the pair
+                              holds x to 2^-17 relative (one BF16 value: 2^-9), so the GEMMs and
+                              the attention carry FP32-grade error and the Eq. vq codeword choices
+                              follow the exact ones except on rows whose relative distance gap is
+                              within that error.  Local energies, log psi and codes; needs
+                              d_model / heads in {16, 32}, at most 256 positions and no final
+                              half-block (with VQNQS_INCREMENTAL: d_model / heads = 32 and
+                              d_model in {128, 256}).  The sampler and the gradient ignore it. */
 };
 
 /* bits of the device status word */
@@ -271,6 +281,21 @@ int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* d
                        double* dev_mean_var, float* dev_log_psi, int flags,
                        void* dev_ws, size_t ws_bytes, void* stream);
 
+/* vqnqs_local_energy that also returns the codeword chosen (Sec. 3.1, Eq. vq)
+ * at every layer and position of every configuration it evaluated: the
+ * sample (configuration 0) and its connected configurations (1, 2, ... in
+ * bond order: site p = y L + x contributes its bond to ((x+1) mod L, y), then
+ * to (x, (y+1) mod L), wrapped bonds only when periodic; a bond enters when its
+ * two spins differ), or the N single flips in site order for the Ising chain.
+ *   dev_codes  DEVICE int32 [B][1 + max_conn][layers][N], max_conn = the number of
+ *              bonds (sites for the chain); slots of configurations a sample does
+ *              not have are left as they were
+ * A row before its configuration's first changed position reports the sample's
+ * code there (causality: the same inputs).  Same flags, workspace and stream
+ * rules as vqnqs_local_energy; each layer adds one copy kernel. */
+int vqnqs_local_energy_codes(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, float* dev_e_loc, int* dev_codes,
+                             int flags, void* dev_ws, size_t ws_bytes, void* stream);
+
 /* Gradient of log psi through the straight-through quantizer (Sec. 3.1,
  * Eq. st: the forward uses the nearest codeword, the backward flows through
  * softmax(-||o - W_j||)), and the VMC energy gradient (Sec. 2):
@@ -291,6 +316,32 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, const fl
                        const float* dev_e_loc, float* dev_O, float* dev_grad, int flags, void* dev_ws,
                        size_t ws_bytes, void* stream);
 
+/* The energy gradient of samples sharded over ranks (one GPU each), with one
+ * exchange step (Sec. 2 gradient estimator: grad_k = 2 mean[(E - mean E) O_k]).
+ * Since sum_b (E_b - Ebar) O_b = sum_b E_b O_b - Ebar sum_b O_b, each rank sums
+ * over its own samples
+ *     partials[0 .. P)      sum_b E_b O_b[k]
+ *     partials[P .. 2P)     sum_b O_b[k]
+ *     partials[2P], [2P+1]  sum_b E_b, sum_b E_b^2
+ *     partials[2P+2]        its sample count
+ * (FP64, P = vqnqs_num_params floats of the blob), the ranks add these 2P + 3
+ * values with one all-reduce (the caller's collective, e.g. NCCL), and
+ * vqnqs_energy_grad_combine turns the sums into grad (FP32 [P]) and the FP64
+ * mean and variance of E_loc over all ranks' samples.
+ *   dev_e_loc   DEVICE float [B]: the rank's local energies
+ *   dev_partials DEVICE double [2P + 3] (output; zeros when B = 0)
+ *   dev_ws      DEVICE workspace of vqnqs_energy_grad_partials_workspace_bytes(ctx, B, chunk)
+ * The two sums take two backward passes (vqnqs_grad_log_psi with seeds E and 1),
+ * each summed in FP32.  Same model restrictions as vqnqs_grad_log_psi. */
+size_t vqnqs_energy_grad_partials_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples);
+int vqnqs_energy_grad_partials(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, const float* dev_e_loc,
+                               double* dev_partials, int flags, void* dev_ws, size_t ws_bytes, void* stream);
+/*   dev_partials  DEVICE double [2P + 3]: the all-reduced partials (any number of ranks)
+ *   dev_grad      DEVICE float [P] (output): 2 (sum E O - Ebar sum O) / n
+ *   dev_mean_var  DEVICE double [2] (output, may be NULL): Ebar and sum E^2 / n - Ebar^2 */
+int vqnqs_energy_grad_combine(vqnqs_ctx* ctx, const double* dev_partials, float* dev_grad, double* dev_mean_var,
+                              void* stream);
+
 /* The per-location tensor-core GEMM on its own (the kernel behind the QKV and
  * MLP steps of the BF16 path, Sec. 3.2 per-location operations):
  *     C[M][N] = A[M][K] @ Bt[N][K]^T + bias[N]   (+ epilogue)
@@ -308,6 +359,18 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, const fl
  * `stream`; a stalled pipeline sets VQNQS_DEV_TIMEOUT in the status word. */
 int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* dev_A, const void* dev_Bt,
                     const float* dev_bias, const float* dev_R, void* dev_C, int epilogue, void* stream);
+
+/* vqnqs_gemm_bf16 with split operands (the GEMMs of VQNQS_BF16_SPLIT, Sec. 3.2
+ * per-location operations in FP32-grade arithmetic on the BF16 tensor cores):
+ *   A2   DEVICE bfloat16 [2M][K]: rows 0..M-1 hold hi = bf16(a), rows M..2M-1 lo = bf16(a - hi)
+ *   Bt2  DEVICE bfloat16 [2N][K]: the same for the weight stored [out][in]
+ *   C    epilogues 0, 1: bfloat16 [2M][N], hi rows then lo rows of the result;
+ *        epilogues 2, 3, 4: float [M][N] as in vqnqs_gemm_bf16
+ * C = A_hi Bt_hi^T + A_hi Bt_lo^T + A_lo Bt_hi^T + bias (+ epilogue), three BF16
+ * MMA passes into one FP32 accumulator.  Same limits and errors as vqnqs_gemm_bf16,
+ * and M <= 2^29. */
+int vqnqs_gemm_bf16_split(vqnqs_ctx* ctx, int M, int N, int K, const void* dev_A2, const void* dev_Bt2,
+                          const float* dev_bias, const float* dev_R, void* dev_C, int epilogue, void* stream);
 
 /* Nearest codeword of R vectors under layer `layer`'s codebook (Sec. 3.1, Eq. vq):
  * code[r] = argmin_j ||W_j||^2 - 2 O[r] . W_j, lowest j on exact ties.

@@ -17,6 +17,7 @@ VQNQS_OK, VQNQS_ERR_ARG, VQNQS_ERR_CUDA, VQNQS_ERR_OOM, VQNQS_ERR_WORKSPACE, VQN
 REUSE = 1
 BF16 = 2
 INCREMENTAL = 4
+BF16_SPLIT = 8
 DEV_BAD_SPIN, DEV_HASH_OVERFLOW, DEV_TIMEOUT = 1, 2, 4
 MAX_LAYERS = 64
 NOALLOC_MAX_ROWS = 1 << 18
@@ -90,10 +91,19 @@ SIGNATURES = [
     ("vqnqs_local_energy", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_local_energy_codes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3 +
+     [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("vqnqs_gemm_bf16", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_int, ctypes.c_void_p]),
+    ("vqnqs_gemm_bf16_split", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("vqnqs_grad_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("vqnqs_energy_grad_partials_workspace_bytes", ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("vqnqs_energy_grad_partials", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3 +
+     [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_energy_grad_combine", ctypes.c_int, [ctypes.c_void_p] * 5),
     ("vqnqs_grad_log_psi", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 5 +
      [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     ("vqnqs_vq_assign", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,

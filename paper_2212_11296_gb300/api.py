@@ -11,6 +11,7 @@ from . import _lib
 REUSE = _lib.REUSE
 BF16 = _lib.BF16
 INCREMENTAL = _lib.INCREMENTAL
+BF16_SPLIT = _lib.BF16_SPLIT
 
 _LIB = None
 
@@ -215,6 +216,28 @@ class VQNQS:
             res.append(lp)
         return res[0] if len(res) == 1 else tuple(res)
 
+    def local_energy_codes(self, spins: torch.Tensor, flags: int = 0, workspace: torch.Tensor | None = None,
+                           stream=None):
+        """Returns (e_loc [B], codes int32 [B, 1 + max_conn, layers, N]): the codeword of every row and
+        layer of the sample (index 0) and of its connected configurations in bond order
+        (vqnqs_local_energy_codes); slots of configurations a sample does not have hold -1."""
+        _check_dev(spins, torch.uint8, "spins")
+        if spins.dim() != 2 or spins.shape[1] != self.N:
+            raise ValueError(f"spins must be [B, {self.N}]")
+        B = spins.shape[0]
+        n_b = 2 * self.N if self.periodic else 2 * self.L * (self.L - 1)
+        if self.L is None:  # the Ising chain: one flip per site
+            n_b = self.N
+        e = torch.empty(B, dtype=torch.float32, device=spins.device)
+        codes = torch.full((B, 1 + n_b, self.layers, self.N // self.token_group), -1, dtype=torch.int32,
+                           device=spins.device)
+        ws = self.workspace(flags) if workspace is None else workspace
+        self._check(lib().vqnqs_local_energy_codes(
+            self._h, B, ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+            ctypes.c_void_p(codes.data_ptr()), int(flags), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+            ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_local_energy_codes")
+        return e, codes
+
     def _ragged_flat(self, Ls, Bs, spins, e, mv, flags, ws, stream=None):
         arr = lambda v: (ctypes.c_int * len(v))(*v)
         self._check(lib().vqnqs_local_energy_ragged(
@@ -304,6 +327,27 @@ class VQNQS:
                                           ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_gemm_bf16")
         return out
 
+    def gemm_bf16_split(self, A2: torch.Tensor, Bt2: torch.Tensor, bias: torch.Tensor, epilogue: int = 3,
+                        R: torch.Tensor | None = None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """C = A @ Bt^T + bias from split operands A2 = [A_hi; A_lo] [2M, K], Bt2 = [Bt_hi; Bt_lo]
+        [2N, K] (see vqnqs_gemm_bf16_split); BF16 outputs come back as [2M, N] (hi rows, then lo rows)."""
+        _check_dev(A2, torch.bfloat16, "A2")
+        _check_dev(Bt2, torch.bfloat16, "Bt2")
+        _check_dev(bias, torch.float32, "bias")
+        M, K = A2.shape[0] // 2, A2.shape[1]
+        N = Bt2.shape[0] // 2
+        if out is None:
+            out = (torch.empty(2 * M, N, dtype=torch.bfloat16, device=A2.device) if epilogue in (0, 1) else
+                   torch.empty(M, N, dtype=torch.float32, device=A2.device))
+        if R is not None:
+            _check_dev(R, torch.float32, "R")
+        self._check(lib().vqnqs_gemm_bf16_split(self._h, M, N, K, ctypes.c_void_p(A2.data_ptr()),
+                                                ctypes.c_void_p(Bt2.data_ptr()), ctypes.c_void_p(bias.data_ptr()),
+                                                ctypes.c_void_p(R.data_ptr() if R is not None else 0),
+                                                ctypes.c_void_p(out.data_ptr()), int(epilogue),
+                                                ctypes.c_void_p(_stream_ptr(stream))), "vqnqs_gemm_bf16_split")
+        return out
+
     def compress_rows(self, uid: torch.Tensor, code: torch.Tensor, stream=None):
         """Dense new ids of the distinct (uid, code) pairs (see vqnqs_compress_rows).
 
@@ -348,6 +392,36 @@ class VQNQS:
                                              ptr(ws), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
                     "vqnqs_grad_log_psi")
         return O, grad
+
+    def energy_grad_partials(self, spins: torch.Tensor, e_loc: torch.Tensor, chunk_samples: int = 0,
+                             stream=None) -> torch.Tensor:
+        """This rank's FP64 partial sums [2P + 3] of the sharded energy gradient
+        (sum E O, sum O, sum E, sum E^2, n; see vqnqs_energy_grad_partials)."""
+        _check_dev(spins, torch.uint8, "spins")
+        _check_dev(e_loc, torch.float32, "e_loc")
+        B = spins.shape[0]
+        P = self.num_params
+        part = torch.empty(2 * P + 3, dtype=torch.float64, device=spins.device)
+        ws = torch.empty(int(lib().vqnqs_energy_grad_partials_workspace_bytes(self._h, B, int(chunk_samples))),
+                         dtype=torch.uint8, device=spins.device)
+        self._check(lib().vqnqs_energy_grad_partials(self._h, B, ctypes.c_void_p(spins.data_ptr()),
+                                                     ctypes.c_void_p(e_loc.data_ptr()), ctypes.c_void_p(part.data_ptr()),
+                                                     0, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                     ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_energy_grad_partials")
+        return part
+
+    def energy_grad_combine(self, partials: torch.Tensor, stream=None):
+        """(grad [P] float32, [mean, var] float64) from the all-reduced partials
+        (see vqnqs_energy_grad_combine)."""
+        _check_dev(partials, torch.float64, "partials")
+        grad = torch.empty(self.num_params, dtype=torch.float32, device=partials.device)
+        mv = torch.empty(2, dtype=torch.float64, device=partials.device)
+        self._check(lib().vqnqs_energy_grad_combine(self._h, ctypes.c_void_p(partials.data_ptr()),
+                                                    ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(mv.data_ptr()),
+                                                    ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_energy_grad_combine")
+        return grad, mv
 
     def vq_assign(self, layer: int, O: torch.Tensor, tensor_cores: bool = False, stream=None) -> torch.Tensor:
         """Nearest codeword of each row of O under layer `layer`'s codebook (see vqnqs_vq_assign)."""

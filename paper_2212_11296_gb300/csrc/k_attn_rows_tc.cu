@@ -17,6 +17,11 @@
 // against m').  One work item = (sample, head, slice): s's K and V of the head
 // are staged once for all the item's tiles.
 //
+// Split operands (SPLIT, as in k_attn_tc.cu): Q, K and V arrive as BF16 hi and
+// lo planes (lo_off elements apart) and P is split the same way, three MMAs per
+// product; the changed keys' corrections read hi + lo in FP32, and the removed
+// weight is the one the split P carried (hi + lo of e).
+//
 // Rows come from a per-sample list of (row, position) pairs laid out like the
 // active rows (sample b's entries start at act_off[first configuration of b];
 // count[b] of them, or the whole region when count is NULL).  Each
@@ -50,9 +55,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// n consecutive BF16 values (n a multiple of 8, 16-byte aligned) as floats
-template <int NV>
-__device__ __forceinline__ void ld_bf16(const __nv_bfloat16* p, float (&out)[NV]) {
+// n consecutive BF16 values (n a multiple of 8, 16-byte aligned) as floats; with
+// SPLIT the value is hi + lo, the lo plane lo_off elements further on
+template <int NV, bool SPLIT>
+__device__ __forceinline__ void ld_bf16(const __nv_bfloat16* p, size_t lo_off, float (&out)[NV]) {
 #pragma unroll
     for (int i = 0; i < NV; i += 8) {
         const uint4 u = *reinterpret_cast<const uint4*>(p + i);
@@ -63,25 +69,62 @@ __device__ __forceinline__ void ld_bf16(const __nv_bfloat16* p, float (&out)[NV]
             out[i + 2 * k] = f.x;
             out[i + 2 * k + 1] = f.y;
         }
+        if (SPLIT) {
+            const uint4 ul = *reinterpret_cast<const uint4*>(p + lo_off + i);
+            const __nv_bfloat162* l = reinterpret_cast<const __nv_bfloat162*>(&ul);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = __bfloat1622float2(l[k]);
+                out[i + 2 * k] += f.x;
+                out[i + 2 * k + 1] += f.y;
+            }
+        }
     }
+}
+
+__device__ __forceinline__ void split_pack2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// the value a BF16 operand (pair, with SPLIT) carries for x
+template <bool SPLIT>
+__device__ __forceinline__ float operand_value(float x) {
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    return SPLIT ? h + __bfloat162float(__float2bfloat16_rn(x - h)) : h;
+}
+
+__host__ __device__ constexpr size_t rows_tile_bytes(int Npad) { return (size_t)Npad * DH * 2; }
+__host__ __device__ constexpr size_t rows_p_bytes(int Npad) {
+    return (size_t)128 * Npad * 2 > (size_t)Npad * (2 * DH + 16) ? (size_t)128 * Npad * 2
+                                                                  : (size_t)Npad * (2 * DH + 16);
+}
+__host__ __device__ constexpr size_t rows_smem_bytes(int Npad, bool split) {
+    return 1024 + (split ? 2 : 1) * (2 * rows_tile_bytes(Npad) + (size_t)128 * DH * 2 + rows_p_bytes(Npad)) + 64;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(AR_THREADS, 2)
-k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
+template <bool SPLIT>
+__global__ void __launch_bounds__(AR_THREADS, SPLIT ? 1 : 2)
+k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
                     float* __restrict__ O, const int2* __restrict__ list, const int* __restrict__ act_off,
                     const int* __restrict__ count, const short* __restrict__ dpos, const int* __restrict__ dcnt,
                     int slices, int Npad, uint32_t tmem_cols, int* __restrict__ status, long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int VS = 2 * DH + 16;               // row stride of the V staging rows (bank-conflict free)
+    constexpr int NP = SPLIT ? 2 : 1;             // operand planes: hi (and lo)
     const int d = ch.d, H = ch.heads;
-    uint8_t* sK = smem;                           // [Npad x DH] K-major
-    uint8_t* sVt = sK + (size_t)Npad * DH * 2;    // [DH x Npad]
-    uint8_t* sQ = sVt + (size_t)Npad * DH * 2;    // [128 x DH]
-    uint8_t* sP = sQ + 128 * DH * 2;              // [128 x Npad]; V staging rows alias it
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + (size_t)128 * Npad * 2);
+    const size_t tb = rows_tile_bytes(Npad), pb = rows_p_bytes(Npad);
+    uint8_t* sK = smem;                           // [NP][Npad x DH] K-major
+    uint8_t* sVt = sK + NP * tb;                  // [NP][DH x Npad]
+    uint8_t* sQ = sVt + NP * tb;                  // [NP][128 x DH]
+    uint8_t* sP = sQ + NP * 128 * DH * 2;         // [NP][128 x Npad]; V staging rows alias it
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + NP * pb);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
     __shared__ float s_red[2][128];
     __shared__ int s_pw[4];
@@ -128,27 +171,31 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
         const int* ub = uid + rb;
         __syncthreads();  // the previous item's readers of the shared tiles are done
         // s's keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
-        for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
-            const int j = u % Npad, kb = u / Npad;
-            uint4 kv = make_uint4(0, 0, 0, 0);
-            if (j < N) kv = *reinterpret_cast<const uint4*>(qkv + (size_t)ub[j] * ld + d + h * DH + kb * 8);
-            *reinterpret_cast<uint4*>(sK + tc::core_off(j, kb * 8, DH)) = kv;
-        }
-        // s's values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
-        for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
-            const int j = u / (DH / 8), kb = u - j * (DH / 8);
-            uint4 vv = make_uint4(0, 0, 0, 0);
-            if (j < N) vv = *reinterpret_cast<const uint4*>(qkv + (size_t)ub[j] * ld + 2 * d + h * DH + kb * 8);
-            *reinterpret_cast<uint4*>(sP + j * VS + kb * 16) = vv;
+        for (int pl = 0; pl < NP; ++pl) {
+            const __nv_bfloat16* src = qkv + pl * lo_off;
+            for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
+                const int j = u % Npad, kb = u / Npad;
+                uint4 kv = make_uint4(0, 0, 0, 0);
+                if (j < N) kv = *reinterpret_cast<const uint4*>(src + (size_t)ub[j] * ld + d + h * DH + kb * 8);
+                *reinterpret_cast<uint4*>(sK + pl * tb + tc::core_off(j, kb * 8, DH)) = kv;
+            }
+            // s's values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
+            for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
+                const int j = u / (DH / 8), kb = u - j * (DH / 8);
+                uint4 vv = make_uint4(0, 0, 0, 0);
+                if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)ub[j] * ld + 2 * d + h * DH + kb * 8);
+                *reinterpret_cast<uint4*>(sP + pl * pb + j * VS + kb * 16) = vv;
+            }
         }
         __syncthreads();
-        for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AR_THREADS / 32) {
-            const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
-            const int m = lane >> 3, r = lane & 7;
-            uint32_t f[4];
-            tc::ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
-            tc::stsm_x4(tc::smem_u32(sVt + tc::core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
-        }
+        for (int pl = 0; pl < NP; ++pl)
+            for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AR_THREADS / 32) {
+                const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
+                const int m = lane >> 3, r = lane & 7;
+                uint32_t f[4];
+                tc::ldsm_x4_trans(tc::smem_u32(sP + pl * pb + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
+                tc::stsm_x4(tc::smem_u32(sVt + pl * tb + tc::core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
+            }
         __syncthreads();
         for (int t0 = z * 128; t0 < n && ok; t0 += slices * 128) {
             // this thread's row: (row index, position), or none
@@ -158,15 +205,17 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                 rrow = e.x;
                 p = e.y;
             }
-            for (int u = tid; u < 128 * (DH / 8); u += AR_THREADS) {
-                const int r = u & 127, kb = u >> 7;
-                uint4 qv = make_uint4(0, 0, 0, 0);
-                if (t0 + r < n) {
-                    const int2 e = lst[t0 + r];
-                    qv = *reinterpret_cast<const uint4*>(qkv + (size_t)uid[e.x] * ld + h * DH + kb * 8);
+            for (int pl = 0; pl < NP; ++pl)
+                for (int u = tid; u < 128 * (DH / 8); u += AR_THREADS) {
+                    const int r = u & 127, kb = u >> 7;
+                    uint4 qv = make_uint4(0, 0, 0, 0);
+                    if (t0 + r < n) {
+                        const int2 e = lst[t0 + r];
+                        qv = *reinterpret_cast<const uint4*>(qkv + pl * lo_off + (size_t)uid[e.x] * ld + h * DH +
+                                                             kb * 8);
+                    }
+                    *reinterpret_cast<uint4*>(sQ + pl * 128 * DH * 2 + tc::core_off(r, kb * 8, DH)) = qv;
                 }
-                *reinterpret_cast<uint4*>(sQ + tc::core_off(r, kb * 8, DH)) = qv;
-            }
             // the tile's key range: up to its largest position (warp maxima for uniform TMEM reads)
             const int pw = __reduce_max_sync(0xffffffffu, p);
             if (lane == 0 && half == 0) s_pw[warp] = pw;
@@ -184,15 +233,21 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
             }
             if (tid == 0) {
                 tc::tc_fence_after();
-                const uint64_t dq = tc::desc_kmajor_none(tc::smem_u32(sQ), 128, (DH / 8) * 128);
-                const uint64_t dk = tc::desc_kmajor_none(tc::smem_u32(sK), 128, (DH / 8) * 128);
+                constexpr int NPROD = SPLIT ? 3 : 1;  // (Q plane, K plane): hi.hi, hi.lo, lo.hi
                 for (int n0 = 0; n0 < nk16; n0 += 256) {
                     const int nn = min(256, nk16 - n0);
-                    const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
 #pragma unroll
-                    for (int ks = 0; ks < DH / 16; ++ks)
-                        tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16),
-                                     tc::idesc_bf16_f32(128, nn), ks > 0 ? 1u : 0u);
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int qp = pr == 2 ? 1 : 0, kp = pr == 1 ? 1 : 0;
+                        const uint64_t dq =
+                            tc::desc_kmajor_none(tc::smem_u32(sQ + qp * 128 * DH * 2), 128, (DH / 8) * 128);
+                        const uint64_t dk = tc::desc_kmajor_none(tc::smem_u32(sK + kp * tb), 128, (DH / 8) * 128);
+                        const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
+#pragma unroll
+                        for (int ks = 0; ks < DH / 16; ++ks)
+                            tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16),
+                                         tc::idesc_bf16_f32(128, nn), (pr | ks) > 0 ? 1u : 0u);
+                    }
                 }
                 tc::mma_commit(bar);
             }
@@ -227,10 +282,10 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
             const float mb = (p >= 0) ? mx * sl2 : 0.f;
             float sum = 0.f;
             for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
-                uint32_t pk[16];
+                uint32_t pk[16], plo[16];
                 if (c0 > plim_w) {  // invisible to every row of the warp: P = 0
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = 0u;
+                    for (int j = 0; j < 16; ++j) pk[j] = plo[j] = 0u;
                 } else {
                     uint32_t r[32];
                     tc::tmem_ld32(tmem + lane_base + c0, r);
@@ -244,15 +299,23 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                             e1 = (c0 + j + 1 <= plim) ? e1 : 0.f;
                         }
                         sum += e0 + e1;
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
-                        pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                        if (SPLIT) {
+                            split_pack2(e0, e1, pk[j / 2], plo[j / 2]);
+                        } else {
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
+                            pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                        }
                     }
                 }
 #pragma unroll
                 for (int j8 = 0; j8 < 4; ++j8)
-                    if (c0 + j8 * 8 < nk16)
+                    if (c0 + j8 * 8 < nk16) {
                         *reinterpret_cast<uint4*>(sP + tc::core_off(row, c0 + j8 * 8, Npad)) =
                             make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+                        if (SPLIT)
+                            *reinterpret_cast<uint4*>(sP + pb + tc::core_off(row, c0 + j8 * 8, Npad)) =
+                                make_uint4(plo[4 * j8], plo[4 * j8 + 1], plo[4 * j8 + 2], plo[4 * j8 + 3]);
+                    }
             }
             __syncthreads();  // both halves read s_red (max) before it is reused for sums
             s_red[half][row] = sum;
@@ -263,10 +326,16 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
             if (tid == 0) {
                 tc::tc_fence_after();
                 const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
-                const uint64_t dp = tc::desc_kmajor_none(tc::smem_u32(sP), 128, (Npad / 8) * 128);
-                const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt), 128, (Npad / 8) * 128);
-                for (int ks = 0; ks < nk16 / 16; ++ks)
-                    tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc, ks > 0 ? 1u : 0u);
+                constexpr int NPROD = SPLIT ? 3 : 1;  // (P plane, V plane): hi.hi, hi.lo, lo.hi
+#pragma unroll
+                for (int pr = 0; pr < NPROD; ++pr) {
+                    const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
+                    const uint64_t dp = tc::desc_kmajor_none(tc::smem_u32(sP + pp * pb), 128, (Npad / 8) * 128);
+                    const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128);
+                    for (int ks = 0; ks < nk16 / 16; ++ks)
+                        tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
+                                     (pr | ks) > 0 ? 1u : 0u);
+                }
                 tc::mma_commit(bar);
             }
             ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
@@ -286,14 +355,14 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                     const int* uc = uid + (rrow - p);
                     const short* dp = dpos + (size_t)c * INC_MAX_KEYS;
                     float q[DH];
-                    ld_bf16<DH>(qkv + (size_t)uid[rrow] * ld + h * DH, q);
+                    ld_bf16<DH, SPLIT>(qkv + (size_t)uid[rrow] * ld + h * DH, lo_off, q);
                     float m2 = mb, lsub = 0.f;  // log2-unit maximum; removed weight
                     // the new maximum first
                     for (int i = 0; i < nd; ++i) {
                         const int k = dp[i];
                         if (k > p) break;  // ascending
                         float kc[DH];
-                        ld_bf16<DH>(qkv + (size_t)uc[k] * ld + d + h * DH, kc);
+                        ld_bf16<DH, SPLIT>(qkv + (size_t)uc[k] * ld + d + h * DH, lo_off, kc);
                         float sc = 0.f;
 #pragma unroll
                         for (int t = 0; t < DH; ++t) sc = fmaf(q[t], kc[t], sc);
@@ -308,8 +377,8 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                         const int k = dp[i];
                         if (k > p) break;
                         float kb[DH], kc[DH];
-                        ld_bf16<DH>(qkv + (size_t)ub[k] * ld + d + h * DH, kb);
-                        ld_bf16<DH>(qkv + (size_t)uc[k] * ld + d + h * DH, kc);
+                        ld_bf16<DH, SPLIT>(qkv + (size_t)ub[k] * ld + d + h * DH, lo_off, kb);
+                        ld_bf16<DH, SPLIT>(qkv + (size_t)uc[k] * ld + d + h * DH, lo_off, kc);
                         float sb = 0.f, sc = 0.f;
 #pragma unroll
                         for (int t = 0; t < DH; ++t) {
@@ -317,11 +386,11 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                             sc = fmaf(q[t], kc[t], sc);
                         }
                         const float eb = ex2_approx(fmaf(sb, sl2, -mb));  // as s's softmax added it
-                        const float ebq = __bfloat162float(__float2bfloat16_rn(eb));
+                        const float ebq = operand_value<SPLIT>(eb);
                         const float ec = ex2_approx(fmaf(sc, sl2, -m2));
                         float vb[16], vc[16];
-                        ld_bf16<16>(qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, vb);
-                        ld_bf16<16>(qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, vc);
+                        ld_bf16<16, SPLIT>(qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, lo_off, vb);
+                        ld_bf16<16, SPLIT>(qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, lo_off, vc);
 #pragma unroll
                         for (int t = 0; t < 16; ++t) {
                             a[t] = fmaf(-ebq, vb[t], a[t]);
@@ -354,32 +423,42 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
     if (tid == 0 && s_pairs && stats) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_FPAIRS]), s_pairs);
 }
 
-bool attention_rows_tc_supported(int N, int d, int heads) { return d / heads == DH && N <= 256; }
+bool attention_rows_tc_supported(int N, int d, int heads) {
+    return d / heads == DH && N <= 256 && rows_smem_bytes((N + 31) & ~31, true) <= 227 * 1024;
+}
 
 cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                      const int2* list, const int* act_off, const int* count, const short* dpos,
-                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms) {
+                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms,
+                                     size_t lo_off) {
     if (!attention_rows_tc_supported(ch.N, ch.d, ch.heads)) return cudaErrorInvalidValue;
+    const bool split = lo_off != 0;
     const int Npad = (ch.N + 31) & ~31;
     uint32_t cols = 32;
     while ((int)cols < Npad) cols <<= 1;
-    const size_t smem = 1024 + (size_t)Npad * DH * 2 * 2 + 128 * DH * 2 +
-                        std::max((size_t)128 * Npad * 2, (size_t)Npad * (2 * DH + 16)) + 64;
+    const size_t smem = rows_smem_bytes(Npad, split);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const size_t max_ctas = 512 / cols;  // TMEM columns of the CTAs resident on one SM
     size_t smem_req = smem;
     if ((228 * 1024) / smem_req > max_ctas) smem_req = (228 * 1024) / (max_ctas + 1) + 1024;
-    static size_t granted = 0;
-    if (smem_req > granted) {
-        cudaFuncSetAttribute(k_attention_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
-        granted = smem_req;
-    }
     const int sh = ch.S * ch.heads;
-    int slices = (2 * num_sms + sh - 1) / sh;
+    int slices = ((split ? 1 : 2) * num_sms + sh - 1) / sh;
     if (slices < 1) slices = 1;
     if (slices > 64) slices = 64;
-    k_attention_rows_tc<<<sh * slices, AR_THREADS, smem_req, st>>>(ch, uid, qkv, O, list, act_off, count, dpos,
-                                                                   dcnt, slices, Npad, cols, status, stats);
+#define VQ_ROWS(SP, SLOT)                                                                                         \
+    {                                                                                                             \
+        static size_t granted = 0;                                                                                \
+        if (smem_req > granted) {                                                                                 \
+            cudaFuncSetAttribute(k_attention_rows_tc<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                 (int)smem_req);                                                                  \
+            granted = smem_req;                                                                                   \
+        }                                                                                                         \
+        k_attention_rows_tc<SP><<<sh * slices, AR_THREADS, smem_req, st>>>(ch, uid, qkv, lo_off, O, list, act_off, \
+                                                                           count, dpos, dcnt, slices, Npad, cols, \
+                                                                           status, stats);                        \
+    }
+    if (split) VQ_ROWS(true, 1) else VQ_ROWS(false, 0)
+#undef VQ_ROWS
     return cudaGetLastError();
 }
 

@@ -18,6 +18,13 @@
 // With prefix reuse, query tiles start at the configuration's first changed
 // position: rows before it are neither computed nor stored.
 // Waits on the MMA barrier are bounded (VQNQS_DEV_TIMEOUT on expiry).
+//
+// Split operands (SPLIT): Q, K and V arrive as two BF16 planes, x = hi + lo
+// (hi = bf16(x), lo = bf16(x - hi), the lo plane lo_off elements after the hi
+// one), and P is written the same way; each product is hi.hi + hi.lo + lo.hi,
+// three MMAs into the same FP32 accumulator.  An operand pair represents x to
+// 2^-17 relative (one BF16 value: 2^-9), the dropped lo.lo term is below
+// 2^-18 of the product, so scores and outputs carry FP32-grade error.
 #include <algorithm>
 
 #include "tc_common.cuh"
@@ -54,21 +61,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int DH>
+// BF16 hi and lo parts of two floats, packed as bf16x2 words
+__device__ __forceinline__ void split_pack2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Shared-memory plan of one CTA: K, V^T, Q and P tiles (each twice with SPLIT).
+__host__ __device__ constexpr size_t attn_tile_bytes(int Npad, int DH) { return (size_t)Npad * DH * 2; }
+__host__ __device__ constexpr size_t attn_p_bytes(int Npad, int DH) {
+    return (size_t)128 * Npad * 2 > (size_t)Npad * (2 * DH + 16) ? (size_t)128 * Npad * 2
+                                                                  : (size_t)Npad * (2 * DH + 16);
+}
+__host__ __device__ constexpr size_t attn_smem_bytes(int Npad, int DH, bool split) {
+    return 1024 + (split ? 2 : 1) * (2 * attn_tile_bytes(Npad, DH) + (size_t)128 * DH * 2 + attn_p_bytes(Npad, DH)) +
+           64;
+}
+
+template <int DH, bool SPLIT>
 __global__ void __launch_bounds__(AT_THREADS)
-k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, float* __restrict__ O,
-               int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
+k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
+               float* __restrict__ O, int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
                const int* __restrict__ cfg_list, int n_list, const int* __restrict__ n_list_dev,
                float2* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int d = ch.d, H = ch.heads;
     constexpr int VS = 2 * DH + 16;                // row stride of the V staging rows (bank-conflict free)
-    uint8_t* sK = smem;                            // [Npad x DH] K-major core layout
-    uint8_t* sVt = sK + (size_t)Npad * DH * 2;     // [DH x Npad]
-    uint8_t* sQ = sVt + (size_t)Npad * DH * 2;     // [128 x DH]
-    uint8_t* sP = sQ + 128 * DH * 2;               // [128 x Npad]; V staging rows alias it
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + (size_t)128 * Npad * 2);
+    constexpr int NP = SPLIT ? 2 : 1;              // operand planes: hi (and lo)
+    const size_t tb = attn_tile_bytes(Npad, DH), pb = attn_p_bytes(Npad, DH);
+    uint8_t* sK = smem;                            // [NP][Npad x DH] K-major core layout
+    uint8_t* sVt = sK + NP * tb;                   // [NP][DH x Npad]
+    uint8_t* sQ = sVt + NP * tb;                   // [NP][128 x DH]
+    uint8_t* sP = sQ + NP * 128 * DH * 2;          // [NP][128 x Npad]; V staging rows alias it
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + NP * pb);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
     __shared__ float s_red[2][128];
 
@@ -97,35 +126,42 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
         const int* urow = uid + ch.cfg_row[c];
         const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
         // keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
-        for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
-            const int j = u % Npad, kb = u / Npad;
-            uint4 kv = make_uint4(0, 0, 0, 0);
-            if (j < N) kv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[j] * ld + d + h * DH + kb * 8);
-            *reinterpret_cast<uint4*>(sK + core_off(j, kb * 8, DH)) = kv;
-        }
-        // values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
-        for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
-            const int j = u / (DH / 8), kb = u - j * (DH / 8);
-            uint4 vv = make_uint4(0, 0, 0, 0);
-            if (j < N) vv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[j] * ld + 2 * d + h * DH + kb * 8);
-            *reinterpret_cast<uint4*>(sP + j * VS + kb * 16) = vv;
+        for (int pl = 0; pl < NP; ++pl) {
+            const __nv_bfloat16* src = qkv + pl * lo_off;
+            for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
+                const int j = u % Npad, kb = u / Npad;
+                uint4 kv = make_uint4(0, 0, 0, 0);
+                if (j < N) kv = *reinterpret_cast<const uint4*>(src + (size_t)urow[j] * ld + d + h * DH + kb * 8);
+                *reinterpret_cast<uint4*>(sK + pl * tb + core_off(j, kb * 8, DH)) = kv;
+            }
+            // values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
+            for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
+                const int j = u / (DH / 8), kb = u - j * (DH / 8);
+                uint4 vv = make_uint4(0, 0, 0, 0);
+                if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)urow[j] * ld + 2 * d + h * DH + kb * 8);
+                *reinterpret_cast<uint4*>(sP + pl * pb + j * VS + kb * 16) = vv;
+            }
         }
         __syncthreads();
-        for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AT_THREADS / 32) {
-            // four 8x8 matrices: key block jb, dh blocks kq*4 .. kq*4+3
-            const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
-            const int m = lane >> 3, r = lane & 7;
-            uint32_t f[4];
-            ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
-            stsm_x4(tc::smem_u32(sVt + core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
-        }
-        if (DH == 16) {  // the two dh blocks of a key block in one x4 with two key blocks
-            for (int blk = warp; blk < Npad / 16; blk += AT_THREADS / 32) {
+        for (int pl = 0; pl < NP; ++pl) {
+            uint8_t* stg = sP + pl * pb;
+            uint8_t* vt = sVt + pl * tb;
+            for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AT_THREADS / 32) {
+                // four 8x8 matrices: key block jb, dh blocks kq*4 .. kq*4+3
+                const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
                 const int m = lane >> 3, r = lane & 7;
-                const int jb = blk * 2 + (m >> 1), kb = m & 1;
                 uint32_t f[4];
-                ldsm_x4_trans(tc::smem_u32(sP + (jb * 8 + r) * VS + kb * 16), f);
-                stsm_x4(tc::smem_u32(sVt + core_off(kb * 8 + r, jb * 8, Npad)), f);
+                ldsm_x4_trans(tc::smem_u32(stg + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
+                stsm_x4(tc::smem_u32(vt + core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
+            }
+            if (DH == 16) {  // the two dh blocks of a key block in one x4 with two key blocks
+                for (int blk = warp; blk < Npad / 16; blk += AT_THREADS / 32) {
+                    const int m = lane >> 3, r = lane & 7;
+                    const int jb = blk * 2 + (m >> 1), kb = m & 1;
+                    uint32_t f[4];
+                    ldsm_x4_trans(tc::smem_u32(stg + (jb * 8 + r) * VS + kb * 16), f);
+                    stsm_x4(tc::smem_u32(vt + core_off(kb * 8 + r, jb * 8, Npad)), f);
+                }
             }
         }
         __syncthreads();
@@ -134,27 +170,36 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             const int nk = min(N, q0 + 128);             // keys this tile can see
             const int nk16 = (nk + 15) & ~15;            // MMA N (multiple of 16)
             const int nk32 = (nk + 31) & ~31;            // columns read back
-            for (int u = tid; u < 128 * (DH / 8); u += AT_THREADS) {
-                const int r = u & 127, kb = u >> 7;
-                uint4 qv = make_uint4(0, 0, 0, 0);
-                if (q0 + r < N) qv = *reinterpret_cast<const uint4*>(qkv + (size_t)urow[q0 + r] * ld + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sQ + core_off(r, kb * 8, DH)) = qv;
-            }
+            for (int pl = 0; pl < NP; ++pl)
+                for (int u = tid; u < 128 * (DH / 8); u += AT_THREADS) {
+                    const int r = u & 127, kb = u >> 7;
+                    uint4 qv = make_uint4(0, 0, 0, 0);
+                    if (q0 + r < N)
+                        qv = *reinterpret_cast<const uint4*>(qkv + pl * lo_off + (size_t)urow[q0 + r] * ld + h * DH +
+                                                             kb * 8);
+                    *reinterpret_cast<uint4*>(sQ + pl * 128 * DH * 2 + core_off(r, kb * 8, DH)) = qv;
+                }
             fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
             if (tid == 0) {
                 tc::tc_fence_after();
-                const uint64_t dq = desc_kmajor_none(tc::smem_u32(sQ), 128, (DH / 8) * 128);
-                const uint64_t dk = desc_kmajor_none(tc::smem_u32(sK), 128, (DH / 8) * 128);
+                // (Q plane, K plane) pairs: hi.hi, then hi.lo and lo.hi with split operands
+                constexpr int NPROD = SPLIT ? 3 : 1;
                 for (int n0 = 0; n0 < nk16; n0 += 256) {
                     const int nn = min(256, nk16 - n0);
                     const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
-                    const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
 #pragma unroll
-                    for (int ks = 0; ks < DH / 16; ++ks)
-                        tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16), idesc,
-                                     ks > 0 ? 1u : 0u);
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int qp = pr == 2 ? 1 : 0, kp = pr == 1 ? 1 : 0;
+                        const uint64_t dq = desc_kmajor_none(tc::smem_u32(sQ + qp * 128 * DH * 2), 128, (DH / 8) * 128);
+                        const uint64_t dk = desc_kmajor_none(tc::smem_u32(sK + kp * tb), 128, (DH / 8) * 128);
+                        const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
+#pragma unroll
+                        for (int ks = 0; ks < DH / 16; ++ks)
+                            tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16), idesc,
+                                         (pr | ks) > 0 ? 1u : 0u);
+                    }
                 }
                 tc::mma_commit(bar);
             }
@@ -194,10 +239,10 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             const float mb = mx * sl2;
             float sum = 0.f;
             for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
-                uint32_t pk[16];
+                uint32_t pk[16], pl[16];
                 if (c0 > plim_w) {  // invisible chunk: P = 0 (still read by the PV MMA up to nk16)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = 0u;
+                    for (int j = 0; j < 16; ++j) pk[j] = pl[j] = 0u;
                 } else {
                     uint32_t r[32];
                     tc::tmem_ld32(tmem + lane_base + c0, r);
@@ -211,15 +256,23 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                             e1 = (c0 + j + 1 <= plim) ? e1 : 0.f;
                         }
                         sum += e0 + e1;
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
-                        pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                        if (SPLIT) {
+                            split_pack2(e0, e1, pk[j / 2], pl[j / 2]);
+                        } else {
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
+                            pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                        }
                     }
                 }
 #pragma unroll
                 for (int j8 = 0; j8 < 4; ++j8)
-                    if (c0 + j8 * 8 < nk16)
+                    if (c0 + j8 * 8 < nk16) {
                         *reinterpret_cast<uint4*>(sP + core_off(row, c0 + j8 * 8, Npad)) =
                             make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+                        if (SPLIT)
+                            *reinterpret_cast<uint4*>(sP + pb + core_off(row, c0 + j8 * 8, Npad)) =
+                                make_uint4(pl[4 * j8], pl[4 * j8 + 1], pl[4 * j8 + 2], pl[4 * j8 + 3]);
+                    }
             }
             __syncthreads();  // both halves read s_red (max) before it is reused for sums
             s_red[half][row] = sum;
@@ -230,10 +283,16 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             if (tid == 0) {
                 tc::tc_fence_after();
                 const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
-                const uint64_t dp = desc_kmajor_none(tc::smem_u32(sP), 128, (Npad / 8) * 128);
-                const uint64_t dv = desc_kmajor_none(tc::smem_u32(sVt), 128, (Npad / 8) * 128);
-                for (int ks = 0; ks < nk16 / 16; ++ks)
-                    tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc, ks > 0 ? 1u : 0u);
+                constexpr int NPROD = SPLIT ? 3 : 1;  // (P plane, V plane): hi.hi, hi.lo, lo.hi
+#pragma unroll
+                for (int pr = 0; pr < NPROD; ++pr) {
+                    const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
+                    const uint64_t dp = desc_kmajor_none(tc::smem_u32(sP + pp * pb), 128, (Npad / 8) * 128);
+                    const uint64_t dv = desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128);
+                    for (int ks = 0; ks < nk16 / 16; ++ks)
+                        tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
+                                     (pr | ks) > 0 ? 1u : 0u);
+                }
                 tc::mma_commit(bar);
             }
             ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
@@ -269,18 +328,21 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     }
 }
 
-bool attention_tc_supported(int N, int dh) { return (dh == 16 || dh == 32) && N <= AT_MAX_N; }
+bool attention_tc_supported(int N, int dh, bool split) {
+    if (!(dh == 16 || dh == 32) || N > AT_MAX_N) return false;
+    return attn_smem_bytes((N + 31) & ~31, dh, split) <= 227 * 1024;
+}
 
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list, int n_list,
-                                float2* stats, const int* n_list_dev) {
+                                float2* stats, const int* n_list_dev, size_t lo_off) {
     const int DH = ch.d / ch.heads;
-    if (!attention_tc_supported(ch.N, DH)) return cudaErrorInvalidValue;
+    const bool split = lo_off != 0;
+    if (!attention_tc_supported(ch.N, DH, split)) return cudaErrorInvalidValue;
     const int Npad = (ch.N + 31) & ~31;
     uint32_t cols = 32;
     while ((int)cols < Npad) cols <<= 1;
-    const size_t smem = 1024 + (size_t)Npad * DH * 2 * 2 + 128 * DH * 2 +
-                        std::max((size_t)128 * Npad * 2, (size_t)Npad * (2 * DH + 16)) + 64;
+    const size_t smem = attn_smem_bytes(Npad, DH, split);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     // the TMEM columns of all CTAs resident on one SM must fit in its 512: cap the
     // residency through the shared-memory request
@@ -288,20 +350,22 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const size_t max_ctas = 512 / cols;
     size_t smem_req = smem;
     if (smem_sm / smem_req > max_ctas) smem_req = smem_sm / (max_ctas + 1) + 1024;
-    static size_t granted[2] = {};  // attribute set once per instantiation and size, outside captures
-#define VQ_ATC(D, SLOT)                                                                                        \
+    static size_t granted[4] = {};  // attribute set once per instantiation and size, outside captures
+#define VQ_ATC(D, SP, SLOT)                                                                                    \
     {                                                                                                          \
         if (smem_req > granted[SLOT]) {                                                                        \
-            cudaFuncSetAttribute(k_attention_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req); \
+            cudaFuncSetAttribute(k_attention_tc<D, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                 (int)smem_req);                                                               \
             granted[SLOT] = smem_req;                                                                          \
         }                                                                                                      \
-        k_attention_tc<D><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, O, prefix_reuse, Npad, cols, status,   \
-                                                              cfg_list, n_list, n_list_dev, stats);          \
+        k_attention_tc<D, SP><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, lo_off, O, prefix_reuse, Npad,    \
+                                                                  cols, status, cfg_list, n_list, n_list_dev, \
+                                                                  stats);                                     \
     }
     if (DH == 16) {
-        VQ_ATC(16, 0)
+        if (split) VQ_ATC(16, true, 2) else VQ_ATC(16, false, 0)
     } else if (DH == 32) {
-        VQ_ATC(32, 1)
+        if (split) VQ_ATC(32, true, 3) else VQ_ATC(32, false, 1)
     } else {
         return cudaErrorInvalidValue;
     }

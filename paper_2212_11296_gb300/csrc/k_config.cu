@@ -434,6 +434,27 @@ cudaError_t launch_copy_codes(const Chunk& ch, const int* code, int l, int layer
     return cudaGetLastError();
 }
 
+// out[((b * per_sample + k) * layers + l) * N + p] = code of position p of configuration k of
+// chunk sample b (k = 0: the sample, k >= 1: its connected configurations in enumeration
+// order); a row before its configuration's first changed position takes the sample's code
+// at that position (the same computation on the same inputs, not recomputed).
+__global__ void k_copy_cfg_codes(Chunk ch, const int* __restrict__ code, int l, int layers, int per_sample,
+                                 int* __restrict__ out) {
+    const int R = ch.counters[CNT_R], N = ch.N;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        const int c = ch.row_cfg[r], p = r - ch.cfg_row[c];
+        const int b = ch.cfg_sample[c], k = c - ch.cfg_off[b];
+        const int v = p < cfg_p0(ch, c) ? code[ch.cfg_row[ch.cfg_off[b]] + p] : code[r];
+        out[(((size_t)b * per_sample + k) * layers + l) * N + p] = v;
+    }
+}
+
+cudaError_t launch_copy_cfg_codes(const Chunk& ch, const int* code, int l, int layers, int per_sample, int* out,
+                                  cudaStream_t st, int grid) {
+    k_copy_cfg_codes<<<grid, 256, 0, st>>>(ch, code, l, layers, per_sample, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_active_rows(const Chunk& ch, int prefix_reuse, int* act_cnt, int* act_off, int* act_rows,
                                long long* stats, cudaStream_t st, int grid) {
     k_active_count<<<grid, 256, 0, st>>>(ch, prefix_reuse, act_cnt, stats);

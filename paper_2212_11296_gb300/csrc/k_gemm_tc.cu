@@ -17,6 +17,14 @@
 // the device).  Every wait is bounded; on timeout the kernel sets
 // VQNQS_DEV_TIMEOUT, drains its own in-flight copies and frees its TMEM.
 // A row's result depends only on that row: the K loop order is fixed.
+//
+// Split operands (a_lo_row > 0): A and Bt each hold a BF16 lo plane after the
+// hi one (A's at row a_lo_row, Bt's at row N), x = hi + lo with hi = bf16(x),
+// lo = bf16(x - hi), and the K loop runs three passes into one accumulator:
+// A_hi Bt_hi, A_hi Bt_lo, A_lo Bt_hi (the lo.lo term, below 2^-18 of a
+// product, is dropped): FP32-grade products from BF16 MMAs.  BF16 outputs
+// (epilogues 0 and 1) are then written the same way, the lo plane at row
+// c_lo_row.
 #include <cstdio>
 
 #include "tc_common.cuh"
@@ -78,7 +86,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
           const float* __restrict__ bias, const float* __restrict__ R, void* __restrict__ Cout,
-          const int* __restrict__ counters, int u_slot, int N, int K, int* __restrict__ status) {
+          const int* __restrict__ counters, int u_slot, int N, int K, int a_lo_row, int c_lo_row,
+          int* __restrict__ status) {
     using C = TcCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -97,6 +106,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = N / BN, m_tiles = (M + TC_BM - 1) / TC_BM, total = m_tiles * n_tiles;
     const int KB = K / TC_BK;
+    const int KBT = a_lo_row > 0 ? 3 * KB : KB;  // K blocks over all passes
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -119,13 +129,15 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             int it = 0;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
                 const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
-                for (int kb = 0; kb < KB; ++kb, ++it) {
+                for (int kbt = 0; kbt < KBT; ++kbt, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (it / C::STAGES) & 1;
+                    // pass 0: A_hi Bt_hi, pass 1: A_hi Bt_lo, pass 2: A_lo Bt_hi
+                    const int pass = kbt / KB, kb = kbt - pass * KB;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
-                    tc::tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * TC_BK, m0, &full[s]);
-                    tc::tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * TC_BK, n0, &full[s]);
+                    tc::tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * TC_BK, m0 + (pass == 2 ? a_lo_row : 0), &full[s]);
+                    tc::tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * TC_BK, n0 + (pass == 1 ? N : 0), &full[s]);
                 }
             }
             if (!ok) {  // wait (bounded) for the copies this thread still has in flight
@@ -144,7 +156,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (!tc::mbar_wait(&acce[a], aph ^ 1, status)) { ok = false; break; }
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem + a * BN;
-                for (int kb = 0; kb < KB; ++kb, ++it) {
+                for (int kbt = 0; kbt < KBT; ++kbt, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (it / C::STAGES) & 1;
                     if (!tc::mbar_wait(&full[s], ph, status)) { ok = false; break; }
@@ -153,7 +165,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     const uint64_t db = tc::desc_kmajor_sw128(tc::smem_u32(sB + s * C::B_BYTES));
 #pragma unroll
                     for (int k = 0; k < TC_BK / 16; ++k)
-                        tc::mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+                        tc::mma_bf16(d_tmem, da + 2 * k, db + 2 * k, idesc, (kbt | k) != 0 ? 1u : 0u);
                     tc::mma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -228,21 +240,39 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         for (int k = 0; k < 8; ++k)
                             srow[k ^ (lane & 7)] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     } else {  // row `lane` at lane * 64 bytes, 16-byte chunk k at k ^ ((lane >> 1) & 3)
+                        // (split outputs: the lo box in the slot's second half, same pattern)
                         uint4* srow = reinterpret_cast<uint4*>(slot + lane * 64);
+                        uint4* srow_lo = reinterpret_cast<uint4*>(slot + 2048 + lane * 64);
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            uint32_t p[4];
+                            uint32_t p[4], pl[4];
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * k + 2 * j], v[8 * k + 2 * j + 1]);
+                                const float a = v[8 * k + 2 * j], b = v[8 * k + 2 * j + 1];
+                                __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
                                 p[j] = *reinterpret_cast<uint32_t*>(&h);
+                                const float2 hf = __bfloat1622float2(h);
+                                __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+                                pl[j] = *reinterpret_cast<uint32_t*>(&l);
                             }
                             srow[k ^ ((lane >> 1) & 3)] = make_uint4(p[0], p[1], p[2], p[3]);
+                            if (c_lo_row > 0) srow_lo[k ^ ((lane >> 1) & 3)] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
                         }
                     }
                     tc::fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0 && ok) tma_store_2d(&tmC, slot, n, rb);
+                    if (lane == 0 && ok) {
+                        if (!F32OUT && c_lo_row > 0) {  // both boxes in one bulk group
+                            asm volatile(
+                                "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                    reinterpret_cast<uint64_t>(&tmC)),
+                                "r"(n), "r"(rb), "r"(tc::smem_u32(slot))
+                                : "memory");
+                            tma_store_2d(&tmC, slot + 2048, n, rb + c_lo_row);
+                        } else {
+                            tma_store_2d(&tmC, slot, n, rb);
+                        }
+                    }
                 } else if (row < M) {
                     if (EPI == 2) {  // FP32 out + residual
                         const float4* rr = reinterpret_cast<const float4*>(R + (size_t)row * N + n);
@@ -257,15 +287,25 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
                         for (int j = 0; j < 8; ++j) out[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     } else {
-                        uint32_t p[16];
+                        uint32_t p[16], pl[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
                             p[j] = *reinterpret_cast<uint32_t*>(&h);
+                            const float2 hf = __bfloat1622float2(h);
+                            __nv_bfloat162 l = __floats2bfloat162_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                            pl[j] = *reinterpret_cast<uint32_t*>(&l);
                         }
                         uint4* out = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + (size_t)row * N + n);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) out[j] = make_uint4(p[4 * j], p[4 * j + 1], p[4 * j + 2], p[4 * j + 3]);
+                        if (c_lo_row > 0) {
+                            uint4* lo = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) +
+                                                                 ((size_t)row + c_lo_row) * N + n);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                lo[j] = make_uint4(pl[4 * j], pl[4 * j + 1], pl[4 * j + 2], pl[4 * j + 3]);
+                        }
                     }
                 }
             }
@@ -328,8 +368,8 @@ EncodeTiledFn encode_fn() {
 template <int BN, int EPI>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm, const CUtensorMap& trm,
                       const float* bias, const float* R, void* Cout,
-                      const int* counters, int u_slot, int Mmax, int N, int K, int* status, cudaStream_t st,
-                      int num_sms) {
+                      const int* counters, int u_slot, int Mmax, int N, int K, int a_lo_row, int c_lo_row,
+                      int* status, cudaStream_t st, int num_sms) {
     using C = TcCfg<BN>;
     static bool attr = false;
     if (!attr) {
@@ -342,15 +382,18 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const CUtens
     int grid = (int)(tiles < num_sms ? tiles : num_sms);
     if (grid < 1) grid = 1;
     k_gemm_tc<BN, EPI><<<grid, TC_THREADS, C::SMEM, st>>>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, N, K,
-                                                          status);
+                                                          a_lo_row, c_lo_row, status);
     return cudaGetLastError();
 }
 
 template <int EPI>
 cudaError_t launch_epi(int BN, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm,
                        const CUtensorMap& trm, const float* bias, const float* R, void* Cout, const int* counters,
-                       int u_slot, int Mmax, int N, int K, int* status, cudaStream_t st, int num_sms) {
-#define VQ_BN(B) launch_bn<B, EPI>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms)
+                       int u_slot, int Mmax, int N, int K, int a_lo_row, int c_lo_row, int* status, cudaStream_t st,
+                       int num_sms) {
+#define VQ_BN(B)                                                                                                   \
+    launch_bn<B, EPI>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, a_lo_row, c_lo_row, status, st, \
+                      num_sms)
     switch (BN) {
         case 64: return VQ_BN(64);
         case 128: return VQ_BN(128);
@@ -410,14 +453,18 @@ cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, i
 
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms, int BN) {
+                           int* status, cudaStream_t st, int num_sms, int BN, bool split) {
     if (BN <= 0) BN = tc_pick_bn(N);
     if (!BN || N % BN || K % TC_BK || K <= 0 || epi < 0 || epi > 4 || (epi == 2 && !R)) return cudaErrorInvalidValue;
     if (Arows < 1) return cudaSuccess;  // no rows to compute
+    if (split && Arows > (1LL << 30)) return cudaErrorInvalidValue;
+    // split: A (and a BF16 C) hold their lo plane Arows rows after the hi one
+    const int a_lo_row = split ? (int)Arows : 0;
+    const int c_lo_row = split && epi < 2 ? (int)Arows : 0;
     CUtensorMap ta, tcm, trm;
-    cudaError_t e = make_tmap_bf16(&ta, A, Arows, K, TC_BM);
+    cudaError_t e = make_tmap_bf16(&ta, A, split ? 2 * Arows : Arows, K, TC_BM);
     if (e != cudaSuccess) return e;
-    e = make_tmap_out(&tcm, Cout, Arows, N, epi >= 2);
+    e = make_tmap_out(&tcm, Cout, c_lo_row ? 2 * Arows : Arows, N, epi >= 2);
     if (e != cudaSuccess) return e;
     if (epi == 2) {
         e = make_tmap_out(&trm, R, Arows, N, true);
@@ -426,7 +473,9 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
         trm = tcm;  // not read
     }
     const int Mmax = (int)Arows;
-#define VQ_EPI(E) launch_epi<E>(BN, ta, tmB, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, status, st, num_sms)
+#define VQ_EPI(E) \
+    launch_epi<E>(BN, ta, tmB, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, a_lo_row, c_lo_row, status, st, \
+                  num_sms)
     switch (epi) {
         case 0: return VQ_EPI(0);
         case 1: return VQ_EPI(1);

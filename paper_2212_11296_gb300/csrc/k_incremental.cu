@@ -339,26 +339,61 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 //   5. per row: delta = (acc - (sum e_c - sum e_s) o) / l' with the sample's
 //      outputs o read by the row's own threads; delta goes back to TMEM, the two
 //      threads' partial norms are added, and the certificate is checked as in
-//      k_inc_patch with the norm enlarged by 2% for the rounding of the BF16
-//      weights (the listed candidates' projections also in two halves);
+//      k_inc_patch with ||delta|| replaced by ||delta|| + B, B a bound on the
+//      error of the BF16 computation (below), and each listed candidate's
+//      projection by |delta . (W_j - W_c)| + B ||W_j - W_c||;
 //   6. only a row that is searched (certificate not met) has o + delta written
 //      to O; a certified row keeps the sample's codeword and writes nothing else.
+//      With split operands (the path whose Q/K/V carry a BF16 lo plane) a row
+//      that the certificate does not settle is recomputed over all keys from the
+//      split operands instead, so every output that reaches the search carries
+//      FP32-grade error.
+//
+// The bound B.  The kernel reads only the hi planes: q~ = bf16(q), k~, v~ (each
+// within 2^-9 relative of the exact value, or equal to it on the plain BF16
+// path), e~ = exp2(s~ sl2 - m) with s~ = q~ . k~ accumulated in FP32, and the
+// MMA takes e^ = bf16(e~).  Per head, |s~ - s| <= 2^-8 (1 + 2^-7) ||q~|| ||k~||
+// (two relative 2^-9 perturbations plus the 32-term FP32 sum), so
+// |e~ / e - 1| <= tau = 2^dx - 1 + 2^-20 with dx = 2^-8 1.01 sl2 ||q~|| ||k~||
+// (the 2^-20 covers ex2.approx and the rounding of its argument; 2^dx - 1 is
+// bounded by y + y^2, y = dx ln 2, which holds for y <= 1), and
+// e^ v~ - e v = (e^ - e) v~ + e (v~ - v) has norm <= e (tau + 2^-8) ||v~||.
+// With A = sum_k e~ (tau + 2^-8) ||v~|| and T = sum_k e~ tau over the row's
+// changed keys (the sample's and the configuration's), the numerator and the
+// weight sum w differ from exact by at most 1.1 (A + T ||o||) and the
+// normaliser by at most 1.1 T (e <= 1.1 e~ while tau <= 0.1), so
+//   ||delta~_h - delta_h|| <= B_h = 1.1 (A + T (||o_h|| + ||delta~_h||)) / (l~' - 1.1 T)
+// per head and B = sqrt(sum_h B_h^2).  A row with tau > 0.1 for some key, or
+// l~' - 1.1 T <= l~' / 2, is recomputed over all keys.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 size_t patch_tc_smem(int d, int heads, int N) {
-    return 128 + (size_t)128 * d * 2 + (size_t)heads * 4096 + (size_t)2 * 128 * (1 + CERT_T) * 4 + 256 * 4 + 64 +
-           (size_t)4 * N * 4 + (size_t)((N + 15) & ~15);
+    return 128 + (size_t)128 * d * 2 + (size_t)heads * 4096 + (size_t)2 * 128 * (2 + CERT_T) * 4 + 64 +
+           (size_t)4 * N * 4 + (size_t)((N + 15) & ~15) + (size_t)2 * heads * 32 * 4;
+}
+
+// e~ (tau + 2^-8) ||v~|| and e~ tau of one changed key (see the bound B above), with
+// 2^dx - 1 = e^y - 1 <= y + y^2 for y = dx ln 2 <= 1; sets guard when tau would exceed 0.1
+__device__ __forceinline__ void patch_err_terms(float e, float dx, float vn, float& acc_a, float& acc_t, bool& guard) {
+    const float y = dx * 0.69314718f * 1.0001f;
+    const float tau = fmaf(y, y, y) + 9.5367431640625e-07f;  // + 2^-20
+    if (y > 0.09f) guard = true;
+    acc_a = fmaf(e * (tau + 3.90625e-3f), vn, acc_a);
+    acc_t = fmaf(e, tau, acc_t);
 }
 
 // The BF16 weights of one head for a row with nk changed keys before it (nk <= NKB):
 // e_s = exp(s_s / sqrt(dh) - m) negated in slots 0..15, e_c in 16..31, zeros beyond
 // nk; seb, sec their sums; guard set when a new score overflows the sample's max.
+// Also the error bound's sums over the row's changed keys: aa += e (tau + 2^-8) ||v~||,
+// at += e tau (patch_err_terms), with dx = qn ||k~|| per key (qn = 2^-8 1.01 sl2 ||q~||).
 template <int NKB>
 __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float sl2, float m2, bool& guard, float& seb,
-                                              float& sec, uint32_t (&e16)[16]) {
+                                              float& sec, uint32_t (&e16)[16], float qn, const float* __restrict__ kn,
+                                              const float* __restrict__ vn, float& aa, float& at) {
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         float eb = 0.f, ec = 0.f;
@@ -367,6 +402,8 @@ __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float s
             if (xc > 115.f) guard = true;
             eb = ex2_approx(__uint_as_float(s[kk]) * sl2 - m2);
             ec = ex2_approx(fminf(xc, 115.f));
+            patch_err_terms(eb, qn * kn[kk], vn[kk], aa, at, guard);
+            patch_err_terms(ec, qn * kn[16 + kk], vn[16 + kk], aa, at, guard);
         }
         seb += eb;
         sec += ec;
@@ -383,10 +420,11 @@ __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float s
 __global__ void __launch_bounds__(256, 2)
 k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
                float* __restrict__ O, const float2* __restrict__ bstat, const CertRow* __restrict__ cert,
-               const float* __restrict__ codebook, int* __restrict__ code, int* __restrict__ vq_rows,
-               const int* __restrict__ act_off, int2* __restrict__ rc_rows, int* __restrict__ rc_cnt,
-               const int* __restrict__ list_tc, const short* __restrict__ dpos, const int* __restrict__ dcnt,
-               uint32_t tmem_cols, int* __restrict__ status, long long* __restrict__ stats) {
+               const float* __restrict__ codebook, const float* __restrict__ wd, int* __restrict__ code,
+               int* __restrict__ vq_rows, const int* __restrict__ act_off, int2* __restrict__ rc_rows,
+               int* __restrict__ rc_cnt, const int* __restrict__ list_tc, const short* __restrict__ dpos,
+               const int* __restrict__ dcnt, int split, uint32_t tmem_cols, int* __restrict__ status,
+               long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     constexpr int DH = 32;
@@ -395,16 +433,18 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint8_t* sQE = smem;                          // [128 x d] queries, then [128 x d] weights
     uint8_t* sK = sQE + 128 * d * 2;              // per head [32 keys x 32 dims]
     uint8_t* sVt = sK + H * 2048;                 // per head [32 dims x 32 keys]
-    float* sN2 = reinterpret_cast<float*>(sVt + H * 2048);  // [2 halves][128]: partial norms
-    float* sP = sN2 + 256;                                  // [2 halves][128][CERT_T]: partial projections
-    int* sGd = reinterpret_cast<int*>(sP + 256 * CERT_T);   // [2 halves][128]: guard flags
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sGd + 256);
+    // [2 halves][128]: partial ||delta~||^2 and B^2 (B^2 = -1: the thread's heads need a recompute)
+    float2* sN2 = reinterpret_cast<float2*>(sVt + H * 2048);
+    float* sP = reinterpret_cast<float*>(sN2 + 256);        // [2 halves][128][CERT_T]: partial projections
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + 256 * CERT_T);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
     int* sD = reinterpret_cast<int*>(tmem_holder + 4);  // [PATCH_TC_KEYS]
     int* sRows = sD + PATCH_TC_KEYS;                    // [NM]
     int* sVq = sRows + NM;                              // [NM]
     int* sFull = sVq + NM;                              // [NM]
     uint8_t* sFlag = reinterpret_cast<uint8_t*>(sFull + NM);  // [NM]
+    float* sKn = reinterpret_cast<float*>(sFlag + ((NM + 15) & ~15));  // [H][32]: ||k~|| of the key slots
+    float* sVn = sKn + H * 32;                                         // [H][32]: ||v~||
     __shared__ int s_warp[32];
     __shared__ int sNvq, sNfull, sBase[2], s_item;
     __shared__ long long sCnt[4];
@@ -498,6 +538,23 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
+            // norms of the staged key and value slots (zero-filled slots give 0); read after the
+            // next block-wide barrier
+            for (int u = tid; u < H * 32; u += blockDim.x) {
+                const int h = u >> 5, n = u & 31;
+                float kk2 = 0.f, vv2 = 0.f;
+#pragma unroll
+                for (int t = 0; t < DH; ++t) {
+                    const float kx = __bfloat162float(
+                        *reinterpret_cast<const __nv_bfloat16*>(sK + h * 2048 + tc::core_off(n, t, DH)));
+                    const float vx = __bfloat162float(
+                        *reinterpret_cast<const __nv_bfloat16*>(sVt + h * 2048 + tc::core_off(t, n, 32)));
+                    kk2 = fmaf(kx, kx, kk2);
+                    vv2 = fmaf(vx, vx, vv2);
+                }
+                sKn[u] = sqrtf(kk2);
+                sVn[u] = sqrtf(vv2);
+            }
             if (tid == 0) {
                 tc::tc_fence_after();
                 const uint64_t dq = tc::desc_kmajor_none(tc::smem_u32(sQE), 128, (d / 8) * 128);
@@ -515,6 +572,7 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             tc::tc_fence_after();
             if (!ok) break;
             float w[4], inv[4];  // per own head: sum e_c - sum e_s, 1 / l'
+            float ea[4], et[4];  // per own head: the bound's sums A and T, times 1.1 / (l~' - 1.1 T)
             bool guard = false;
             int nk = 0;  // changed keys before this row
             while (p >= 0 && nk < nd && sD[nk] < p) ++nk;
@@ -526,29 +584,51 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 const float2* bs = bstat + ((size_t)b * NM + (p >= 0 ? p : 0)) * H + h0;
 #pragma unroll
                 for (int hh = 0; hh < 4; ++hh) mls[hh] = (hh < HH && p >= 0) ? bs[hh] : make_float2(0.f, 1.f);
+                const float cdx = 3.90625e-3f * 1.01f * sl2;  // 2^-8 (1 + 2^-7), log2 units
 #pragma unroll
                 for (int hh = 0; hh < 4; ++hh) {
                     if (hh >= HH) break;
                     const int h = h0 + hh;
+                    // ||q~|| of this head, from the staged query before its columns take the weights
+                    float qn = 0.f;
+#pragma unroll
+                    for (int c8 = 0; c8 < 4; ++c8) {
+                        const uint4 u = *reinterpret_cast<const uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d));
+                        const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float2 f = __bfloat1622float2(b2[k]);
+                            qn = fmaf(f.x, f.x, fmaf(f.y, f.y, qn));
+                        }
+                    }
+                    qn = cdx * sqrtf(qn);
                     uint32_t s[32];
                     tc::tmem_ld32(tmem + lane_base + h * 32, s);
                     const float2 ml = mls[hh];
                     const float m2 = ml.x * 1.4426950408889634f;
                     float seb = 0.f, sec = 0.f;
                     uint32_t e16[16];  // the 32 weights as packed BF16 pairs
+                    float aa = 0.f, at = 0.f;  // the error bound's sums A and T
+                    const float* kn = sKn + h * 32;
+                    const float* vn = sVn + h * 32;
                     if (nkw <= 4)
-                        patch_weights<4>(s, nk, sl2, m2, guard, seb, sec, e16);
+                        patch_weights<4>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
                     else if (nkw <= 8)
-                        patch_weights<8>(s, nk, sl2, m2, guard, seb, sec, e16);
+                        patch_weights<8>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
                     else
-                        patch_weights<16>(s, nk, sl2, m2, guard, seb, sec, e16);
+                        patch_weights<16>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
 #pragma unroll
                     for (int c8 = 0; c8 < 4; ++c8)
                         *reinterpret_cast<uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d)) =
                             make_uint4(e16[4 * c8], e16[4 * c8 + 1], e16[4 * c8 + 2], e16[4 * c8 + 3]);
                     if (!(seb <= 0.5f * ml.y)) guard = true;  // cancellation
                     w[hh] = sec - seb;
-                    inv[hh] = 1.f / (ml.y - seb + sec);
+                    const float lp = ml.y - seb + sec;
+                    if (!(lp - 1.1f * at > 0.5f * lp)) guard = true;
+                    inv[hh] = 1.f / lp;
+                    const float f = 1.1f / (lp - 1.1f * at);
+                    ea[hh] = aa * f;
+                    et[hh] = at * f;
                 }
             }
             tc::fence_proxy_async_smem();
@@ -572,7 +652,7 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             if (!ok) break;
             // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm
             const float* orow = O + (size_t)(rb + (p >= 0 ? p : 0)) * d;
-            float n2 = 0.f;
+            float n2 = 0.f, b2 = 0.f;
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
                 if (hh >= HH || !wact) break;
@@ -583,33 +663,42 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                     o4[t] = p >= 0 ? *reinterpret_cast<const float4*>(orow + h * 32 + 4 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
                 uint32_t a[32];
                 tc::tmem_ld32(tmem + lane_base + h * 32, a);
+                float hn2 = 0.f, on2 = 0.f;
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const float d0 = (__uint_as_float(a[4 * t]) - w[hh] * o4[t].x) * inv[hh];
                     const float d1 = (__uint_as_float(a[4 * t + 1]) - w[hh] * o4[t].y) * inv[hh];
                     const float d2 = (__uint_as_float(a[4 * t + 2]) - w[hh] * o4[t].z) * inv[hh];
                     const float d3 = (__uint_as_float(a[4 * t + 3]) - w[hh] * o4[t].w) * inv[hh];
-                    n2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, n2))));
+                    hn2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, hn2))));
+                    on2 = fmaf(o4[t].x, o4[t].x, fmaf(o4[t].y, o4[t].y, fmaf(o4[t].z, o4[t].z, fmaf(o4[t].w, o4[t].w, on2))));
                     a[4 * t] = __float_as_uint(d0);
                     a[4 * t + 1] = __float_as_uint(d1);
                     a[4 * t + 2] = __float_as_uint(d2);
                     a[4 * t + 3] = __float_as_uint(d3);
                 }
+                n2 += hn2;
+                // B_h = 1.1 (A + T (||o_h|| + ||delta~_h||)) / (l~' - 1.1 T)
+                const float bh = ea[hh] + et[hh] * (sqrtf(on2) + sqrtf(hn2));
+                b2 = fmaf(bh, bh, b2);
                 tc::tmem_st32(tmem + lane_base + h * 32, a);
             }
-            sN2[tid] = n2;
-            sGd[tid] = guard ? 1 : 0;
+            sN2[tid] = make_float2(n2, guard ? -1.f : b2);
             __syncthreads();
-            n2 = sN2[r] + sN2[128 + r];  // the same sum, in the same order, for both threads of the row
-            guard = (sGd[r] | sGd[128 + r]) != 0;
+            {  // the same sums, in the same order, for both threads of the row
+                const float2 a0 = sN2[r], a1 = sN2[128 + r];
+                n2 = a0.x + a1.x;
+                guard = a0.y < 0.f || a1.y < 0.f;
+            }
+            const float bnd = guard ? 0.f : sqrtf(sN2[r].y + sN2[128 + r].y);
             const CertRow* cr = cert + ((size_t)b * NM + (p >= 0 ? p : 0));
             int md = -1, nc = 0;
             if (p >= 0) {
                 if (guard) {
                     md = 2;
                 } else {
-                    // weights are BF16 here: 2% more than the computed norm covers their rounding
-                    const float dn = sqrtf(n2) * 1.02f;
+                    // ||delta|| <= ||delta~|| + B for the exact correction of these inputs
+                    const float dn = sqrtf(n2) + bnd;
                     if (!(dn < cr->next)) {
                         md = 1;
                     } else {
@@ -654,9 +743,14 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             __syncthreads();
             if (md == 3) {
                 md = 0;
-                for (int i = 0; i < nc; ++i)
-                    if (!(cr->gap[i] - 2.f * (sP[r * CERT_T + i] + sP[(128 + r) * CERT_T + i]) > cr->eta)) md = 1;
+                for (int i = 0; i < nc; ++i) {
+                    const float wj = wd[(size_t)cr->code * ch.K + cr->j[i]];  // ||W_j - W_c||
+                    if (!(cr->gap[i] - 2.f * (sP[r * CERT_T + i] + sP[(128 + r) * CERT_T + i] + bnd * wj) > cr->eta))
+                        md = 1;
+                }
             }
+            // split operands: a row the certificate does not settle is recomputed from them
+            if (split && md == 1) md = 2;
             // a searched row: o + delta goes to O for the vector quantizer
             if (__any_sync(0xffffffffu, md == 1)) {
                 float* xo = O + (size_t)(rc + (p >= 0 ? p : 0)) * d;
@@ -1244,10 +1338,10 @@ size_t inc_patch_smem(int d, int N) {
 
 template <typename T>
 cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, float* O, const float2* bstat,
-                               const CertRow* cert, const float* codebook, int* code, int* vq_rows,
+                               const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
                                const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
-                               const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int* status,
-                               long long* stats, cudaStream_t st, int grid) {
+                               const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int split,
+                               int* status, long long* stats, cudaStream_t st, int grid) {
     if (!incremental_supported(ch.d, ch.heads)) return cudaErrorInvalidValue;
     const int kb = inc_patch_keys(ch.d);
     const size_t smem = inc_patch_smem(ch.d, ch.N);
@@ -1275,8 +1369,9 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                 cudaFuncSetAttribute(k_inc_patch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
                 granted_tc = smem_tc;
             }
-            k_inc_patch_tc<<<grid, 256, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, code, vq_rows, act_off,
-                                                      rc_rows, rc_cnt, list_tc, dpos, dcnt, cols, status, stats);
+            k_inc_patch_tc<<<grid, 256, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows,
+                                                      act_off, rc_rows, rc_cnt, list_tc, dpos, dcnt, split, cols,
+                                                      status, stats);
             return cudaGetLastError();
         }
     }
@@ -1325,20 +1420,21 @@ cudaError_t launch_inc_attention_t(const Chunk& ch, const int* uid, const T* qkv
 }
 
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, float* O, const float2* bstat,
-                             const CertRow* cert, const float* codebook, int* code, int* vq_rows,
-                             const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
-                             const int* dcnt, int use_tc, int* status, long long* stats, cudaStream_t st,
-                             int grid) {
-    return launch_inc_patch_t<float>(ch, uid, qkv, O, bstat, cert, codebook, code, vq_rows, act_off, rc_rows,
-                                     rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, status, stats, st, grid);
+                             const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
+                             const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
+                             const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int* status,
+                             long long* stats, cudaStream_t st, int grid) {
+    return launch_inc_patch_t<float>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off, rc_rows,
+                                     rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, 0, status, stats, st, grid);
 }
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                             const float2* bstat, const CertRow* cert, const float* codebook, int* code,
-                             int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
-                             const int* dcnt, int use_tc, int* status, long long* stats,
-                             cudaStream_t st, int grid) {
-    return launch_inc_patch_t<__nv_bfloat16>(ch, uid, qkv, O, bstat, cert, codebook, code, vq_rows, act_off,
-                                             rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, status, stats, st, grid);
+                             const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
+                             int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
+                             const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
+                             int split, int* status, long long* stats, cudaStream_t st, int grid) {
+    return launch_inc_patch_t<__nv_bfloat16>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off,
+                                             rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, split, status,
+                                             stats, st, grid);
 }
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
                                  const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,

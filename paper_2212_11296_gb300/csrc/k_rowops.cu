@@ -23,10 +23,18 @@ __device__ __forceinline__ void ln_row(const float (&x)[PER], int lane, int d, c
     }
 }
 
+// BF16 value of y at out[o] and, when lo_off > 0, the BF16 rounding of its
+// remainder y - bf16(y) at out[lo_off + o] (the split-operand lo plane).
+__device__ __forceinline__ void store_bf16_split(__nv_bfloat16* __restrict__ out, size_t o, size_t lo_off, float y) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(y);
+    out[o] = h;
+    if (lo_off) out[lo_off + o] = __float2bfloat16_rn(y - __bfloat162float(h));
+}
+
 template <int PER>
 __global__ void k_layernorm(const float* __restrict__ X, const int* __restrict__ counters, int u_slot,
                             const float* __restrict__ g, const float* __restrict__ b, int d,
-                            float* __restrict__ out_f32, __nv_bfloat16* __restrict__ out_bf16) {
+                            float* __restrict__ out_f32, __nv_bfloat16* __restrict__ out_bf16, size_t lo_off) {
     const int U = counters[u_slot];
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
@@ -38,7 +46,7 @@ __global__ void k_layernorm(const float* __restrict__ X, const int* __restrict__
         for (int i = 0; i < PER; ++i) {
             size_t o = (size_t)u * d + lane + 32 * i;
             if (out_f32) out_f32[o] = y[i];
-            if (out_bf16) out_bf16[o] = __float2bfloat16_rn(y[i]);
+            if (out_bf16) store_bf16_split(out_bf16, o, lo_off, y[i]);
         }
     }
 }
@@ -52,7 +60,7 @@ __global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restr
                                  const int* __restrict__ counters, int u_slot, const float* __restrict__ g,
                                  const float* __restrict__ b, int d, float* __restrict__ Y,
                                  float* __restrict__ A_f32, __nv_bfloat16* __restrict__ A_bf16, int vq_heads, int K,
-                                 int bits) {
+                                 int bits, size_t lo_off) {
     const int U = counters[u_slot];
     const int mask = vq_heads == 1 ? -1 : (1 << bits) - 1;
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -76,7 +84,7 @@ __global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restr
             size_t o = (size_t)u * d + lane + 32 * i;
             Y[o] = y[i];
             if (A_f32) A_f32[o] = a[i];
-            if (A_bf16) A_bf16[o] = __float2bfloat16_rn(a[i]);
+            if (A_bf16) store_bf16_split(A_bf16, o, lo_off, a[i]);
         }
     }
 }
@@ -106,8 +114,9 @@ __global__ void k_table_T(const float* __restrict__ cb, const float* __restrict_
     }
 }
 
-// WT[c][r] = bf16(W[r][c])
-__global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols, __nv_bfloat16* __restrict__ WT) {
+// WT[c][r] = bf16(W[r][c]); with lo, also the split lo plane WT[cols + c][r] = bf16(W[r][c] - WT[c][r])
+__global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols, __nv_bfloat16* __restrict__ WT,
+                                 int lo) {
     __shared__ float tile[32][33];
     for (int by = blockIdx.y; by * 32 < rows; by += gridDim.y)
         for (int bx = blockIdx.x; bx * 32 < cols; bx += gridDim.x) {
@@ -115,7 +124,12 @@ __global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols
             tile[threadIdx.y][threadIdx.x] = (r < rows && c < cols) ? W[(size_t)r * cols + c] : 0.f;
             __syncthreads();
             int r2 = by * 32 + threadIdx.x, c2 = bx * 32 + threadIdx.y;
-            if (r2 < rows && c2 < cols) WT[(size_t)c2 * rows + r2] = __float2bfloat16_rn(tile[threadIdx.x][threadIdx.y]);
+            if (r2 < rows && c2 < cols) {
+                const float x = tile[threadIdx.x][threadIdx.y];
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                WT[(size_t)c2 * rows + r2] = h;
+                if (lo) WT[((size_t)cols + c2) * rows + r2] = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
             __syncthreads();
         }
 }
@@ -159,17 +173,17 @@ __global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols
     }
 
 cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, const float* g, const float* b, int d,
-                             float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid) {
-    VQ_DISPATCH_PER(d, k_layernorm, X, counters, u_slot, g, b, d, out_f32, out_bf16);
+                             float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid, size_t lo_off) {
+    VQ_DISPATCH_PER(d, k_layernorm, X, counters, u_slot, g, b, d, out_f32, out_bf16, lo_off);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
                                   float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads, int K,
-                                  int bits) {
+                                  int bits, size_t lo_off) {
     VQ_DISPATCH_PER(d, k_residual_vq_ln, X, rep_uid, rep_code, T, counters, u_slot, g, b, d, Y, A_f32, A_bf16,
-                    vq_heads, K, bits);
+                    vq_heads, K, bits, lo_off);
     return cudaGetLastError();
 }
 
@@ -181,9 +195,9 @@ cudaError_t launch_table_T(const float* codebook, const float* w_o, const float*
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st) {
+cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st, bool lo) {
     dim3 grid((cols + 31) / 32 < 1024 ? (cols + 31) / 32 : 1024, (rows + 31) / 32 < 1024 ? (rows + 31) / 32 : 1024);
-    k_transpose_bf16<<<grid, dim3(32, 32), 0, st>>>(W, rows, cols, WT);
+    k_transpose_bf16<<<grid, dim3(32, 32), 0, st>>>(W, rows, cols, WT, lo ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -237,9 +237,9 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
     for (int l = 0; l < ctx->layers; ++l) {
         LayerW& w = ctx->lw[l];
         VQ_CK(launch_table_T(w.codebook, w.w_o, w.b_o, K, d, ctx->vq_heads, w.T, w.cnorm, st));
-        VQ_CK(launch_transpose_bf16(w.w_qkv, d, 3 * d, w.wqkv_t, st));
-        VQ_CK(launch_transpose_bf16(w.w_1, d, 4 * d, w.w1_t, st));
-        VQ_CK(launch_transpose_bf16(w.w_2, 4 * d, d, w.w2_t, st));
+        VQ_CK(launch_transpose_bf16(w.w_qkv, d, 3 * d, w.wqkv_t, st, true));
+        VQ_CK(launch_transpose_bf16(w.w_1, d, 4 * d, w.w1_t, st, true));
+        VQ_CK(launch_transpose_bf16(w.w_2, 4 * d, d, w.w2_t, st, true));
         if (ctx->vq_heads == 1) {  // the tensor-core search and the incremental certificate: one head
             VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
             VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
@@ -256,9 +256,10 @@ int build_weight_tmaps(vqnqs_ctx* ctx) {
     const long long d = ctx->d;
     for (int l = 0; l < ctx->layers; ++l) {
         LayerW& w = ctx->lw[l];
-        VQ_CK(make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
-        VQ_CK(make_tmap_bf16(&w.tm_w1, w.w1_t, 4 * d, (int)d, ctx->bn[1]));
-        VQ_CK(make_tmap_bf16(&w.tm_w2, w.w2_t, d, 4 * (int)d, ctx->bn[2]));
+        // the maps cover the hi rows and the split lo rows after them
+        VQ_CK(make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 2 * 3 * d, (int)d, ctx->bn[0]));
+        VQ_CK(make_tmap_bf16(&w.tm_w1, w.w1_t, 2 * 4 * d, (int)d, ctx->bn[1]));
+        VQ_CK(make_tmap_bf16(&w.tm_w2, w.w2_t, 2 * d, 4 * (int)d, ctx->bn[2]));
     }
     if (ctx->half_block) {
         VQ_CK(make_tmap_bf16(&ctx->hw.tm_wqkv, ctx->hw.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
@@ -324,7 +325,7 @@ Chunk make_chunk(const vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* s
 // One chunk of samples (global s0 .. s0+S-1 of the batch described by g) through the whole path.
 int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, const Groups& grp, int s0, int S,
               bool with_bonds, int flags, float* e_loc_out, float* log_psi_out, cudaStream_t st,
-              int* codes_out = nullptr) {
+              int* codes_out = nullptr, int* cfg_codes_out = nullptr) {
     const int N = ctx->P, d = ctx->d, K = ctx->K;  // N: positions (rows) per sample
     const bool reuse = (flags & VQNQS_REUSE) != 0;
     int* counters = at<int>(ws, P.counters);
@@ -356,6 +357,10 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
 
     const bool bf16 = (flags & VQNQS_BF16) != 0;
     const bool inc = with_bonds && (flags & VQNQS_INCREMENTAL) != 0;
+    // split operands: BF16 lo planes after the hi ones (elements) of the LN outputs, Q/K/V and MLP hidden rows
+    const bool split = bf16 && (flags & VQNQS_BF16_SPLIT) != 0;
+    const size_t a_lo = split ? (size_t)P.Umax * d : 0;
+    const size_t qkv_lo = split ? (size_t)P.Umax * 3 * d : 0;
     int* act_rows = at<int>(ws, P.act_rows);
     const int* cfg_off = at<int>(ws, P.cfg_off);
     float2* bstat = at<float2>(ws, P.bstat);
@@ -378,21 +383,23 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         const LayerW& w = ctx->lw[l];
         const int us = CNT_U0 + l, un = CNT_U0 + l + 1;
         if (bf16) {
-            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows));
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X_cur, counters, us, w.ln1_g, w.ln1_b, d, nullptr, A16, st, g_urows,
+                                                a_lo));
             VQ_STAGE(S_QKV, 1, launch_gemm_tc(A16, Umax, w.tm_wqkv, w.b_qkv, nullptr, qkv16, counters, us, 3 * d, d, 0,
-                                              ctx->status, st, ctx->num_sms, ctx->bn[0]));
+                                              ctx->status, st, ctx->num_sms, ctx->bn[0], split));
             if (inc) {  // the samples' own configurations only, with their softmax statistics
-                if (attention_tc_supported(N, d / ctx->heads))
+                if (attention_tc_supported(N, d / ctx->heads, split))
                     VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
                                                             grid_for(ctx, (long long)S * ctx->heads, 1, 4), cfg_off, S,
-                                                            bstat));
+                                                            bstat, nullptr, qkv_lo));
                 else
                     VQ_STAGE(S_ATTN, 1, launch_attention_bf16in(ch, uid_cur, qkv16, O, 1, st,
                                                                 grid_for(ctx, (long long)S * ctx->heads, 1, 8), cfg_off,
                                                                 S, bstat));
-            } else if (attention_tc_supported(N, d / ctx->heads))
+            } else if (attention_tc_supported(N, d / ctx->heads, split))
                 VQ_STAGE(S_ATTN, 1, launch_attention_tc(ch, uid_cur, qkv16, O, reuse ? 1 : 0, ctx->status, st,
-                                                        grid_for(ctx, P.Cmax * ctx->heads, 1, 4)));
+                                                        grid_for(ctx, P.Cmax * ctx->heads, 1, 4), nullptr, 0,
+                                                        nullptr, nullptr, qkv_lo));
             else
                 VQ_STAGE(S_ATTN, 1, launch_attention_bf16in(ch, uid_cur, qkv16, O, reuse ? 1 : 0, st,
                                                             grid_for(ctx, P.Cmax * ctx->heads, 1, 8)));
@@ -413,32 +420,34 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             VQ_STAGE(S_CERT, 1, launch_base_cert(ch, O, w.codebook, w.cnorm, w.wd, K, d, code, cert, ctx->stats,
                                                  counters, rc_cnt, st));
             const int g_cfg = grid_for(ctx, P.Cmax, 1, 3);
-            const bool tc_inc = bf16 && patch_tc_supported(d, ctx->heads) && attention_tc_supported(N, d / ctx->heads) &&
+            const bool tc_inc = bf16 && patch_tc_supported(d, ctx->heads) &&
+                                attention_tc_supported(N, d / ctx->heads, split) &&
                                 attention_rows_tc_supported(N, d, ctx->heads);
             VQ_STAGE(S_CLASSIFY, 1, launch_inc_classify(ch, uid_cur, tc_inc ? 1 : 0, list_tc, list_simt, dpos, dcnt,
                                                         vq_rows, ctx->stats, st, grid_for(ctx, P.Cmax, 8, 8)));
             if (tc_inc) {
                 // tensor cores: rows patched, their changed rows recomputed against the sample's keys,
                 // configurations with many changes recomputed whole
-                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
-                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 1,
-                                                      ctx->status, ctx->stats, st, g_cfg));
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
+                                                      vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
+                                                      dcnt, 1, split ? 1 : 0, ctx->status, ctx->stats, st, g_cfg));
                 VQ_STAGE(S_RECOMP, 1, launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos,
-                                                               dcnt, ctx->status, ctx->stats, st, ctx->num_sms));
+                                                               dcnt, ctx->status, ctx->stats, st, ctx->num_sms,
+                                                               qkv_lo));
                 VQ_STAGE(S_RECOMP_WHOLE, 1,
                          launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
                                              grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
-                                             counters + CNT_SCL));
+                                             counters + CNT_SCL, qkv_lo));
             } else if (bf16) {
-                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, code, vq_rows,
-                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 0,
-                                                      ctx->status, ctx->stats, st, g_cfg));
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
+                                                      vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
+                                                      dcnt, 0, 0, ctx->status, ctx->stats, st, g_cfg));
                 VQ_STAGE(S_RECOMP, 1, launch_inc_attention(ch, uid_cur, qkv16, O, act_off, rc_rows, rc_cnt, 0,
                                                            ctx->stats, st, ctx->num_sms));
             } else {
-                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv, O, bstat, cert, w.codebook, code, vq_rows,
-                                                      act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, 0,
-                                                      ctx->status, ctx->stats, st, g_cfg));
+                VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv, O, bstat, cert, w.codebook, w.wd, code,
+                                                      vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
+                                                      dcnt, 0, ctx->status, ctx->stats, st, g_cfg));
                 VQ_STAGE(S_RECOMP, 1, launch_inc_attention(ch, uid_cur, qkv, O, act_off, rc_rows, rc_cnt, 0, ctx->stats,
                                                            st, ctx->num_sms));
             }
@@ -460,6 +469,10 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             ctx->launches += 1;
             VQ_CK(launch_copy_codes(ch, code, l, ctx->layers, codes_out, st, g_rows));
         }
+        if (cfg_codes_out) {  // codes of every configuration: [sample][configuration][layer][position]
+            ctx->launches += 1;
+            VQ_CK(launch_copy_cfg_codes(ch, code, l, ctx->layers, 1 + ctx->max_conn, cfg_codes_out, st, g_rows));
+        }
         VQ_STAGE(S_DEDUPE, reuse ? 3 : 1,
                  launch_dedupe(ch, uid_cur, code, un, Rmax, at<unsigned long long>(ws, P.keys),
                                at<int>(ws, P.vals), P.hash_bits, uid_next, rep_uid, rep_code, reuse, ctx->status, st,
@@ -467,11 +480,12 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         if (bf16) {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, nullptr, A16, st, g_urows, ctx->vq_heads, K,
-                                                        ctx->vq_bits));
+                                                        ctx->vq_bits, a_lo));
+            // split: the hidden rows' lo plane follows the hi one (Umax rows of 4d, over the dead attention output)
             VQ_STAGE(S_MLP1, 1, launch_gemm_tc(A16, Umax, w.tm_w1, w.b_1, nullptr, Hid16, counters, un, 4 * d, d, 1,
-                                               ctx->status, st, ctx->num_sms, ctx->bn[1]));
+                                               ctx->status, st, ctx->num_sms, ctx->bn[1], split));
             VQ_STAGE(S_MLP2, 1, launch_gemm_tc(Hid16, Umax, w.tm_w2, w.b_2, Y, X_next, counters, un, d, 4 * d, 2,
-                                               ctx->status, st, ctx->num_sms, ctx->bn[2]));
+                                               ctx->status, st, ctx->num_sms, ctx->bn[2], split));
         } else {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, A, nullptr, st, g_urows, ctx->vq_heads, K,
@@ -539,12 +553,10 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
     return VQNQS_OK;
 }
 
-int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_var, float* log_psi, int flags,
-        void* ws, size_t ws_bytes, void* stream, bool with_bonds, int* codes = nullptr) {
-    if (!ctx) return VQNQS_ERR_ARG;
-    ctx->err.clear();
-    if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+// Flags of the local-energy, log psi and codes paths for this context's model.
+int check_flags(vqnqs_ctx* ctx, int flags) {
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL | VQNQS_BF16_SPLIT))
+        return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
@@ -555,8 +567,26 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
                         "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
                         "a multiple of d_model/32");
     }
-    if ((flags & VQNQS_BF16) && ctx->d % 64)
-        return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
+    if ((flags & VQNQS_BF16) && ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
+    if (flags & VQNQS_BF16_SPLIT) {
+        if (!(flags & VQNQS_BF16)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16_SPLIT needs VQNQS_BF16");
+        if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16_SPLIT: no final half-block");
+        if (!attention_tc_supported(ctx->P, ctx->d / ctx->heads, true))
+            return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16_SPLIT needs d_model/heads in {16, 32} and at most 256 positions");
+        if ((flags & VQNQS_INCREMENTAL) &&
+            !(patch_tc_supported(ctx->d, ctx->heads) && attention_rows_tc_supported(ctx->P, ctx->d, ctx->heads)))
+            return fail(ctx, VQNQS_ERR_ARG,
+                        "VQNQS_BF16_SPLIT with VQNQS_INCREMENTAL needs d_model/heads = 32 and d_model in {128, 256}");
+    }
+    return VQNQS_OK;
+}
+
+int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_var, float* log_psi, int flags,
+        void* ws, size_t ws_bytes, void* stream, bool with_bonds, int* codes = nullptr, int* cfg_codes = nullptr) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
+    if (int rc = check_flags(ctx, flags)) return rc;
     if (B == 0) return VQNQS_OK;
     if (!spins) return fail(ctx, VQNQS_ERR_ARG, "spins is NULL");
     if (with_bonds && !e_loc) return fail(ctx, VQNQS_ERR_ARG, "e_loc is NULL");
@@ -575,7 +605,8 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
         const int Sc = (B - s0) < S ? (B - s0) : S;
         int rc = run_chunk(ctx, P, ws, spins, g, s0, Sc, with_bonds, flags, e_loc ? e_loc + s0 : nullptr,
                            log_psi ? log_psi + s0 : nullptr, st,
-                           codes ? codes + (size_t)s0 * ctx->layers * ctx->P : nullptr);
+                           codes ? codes + (size_t)s0 * ctx->layers * ctx->P : nullptr,
+                           cfg_codes ? cfg_codes + (size_t)s0 * (1 + ctx->max_conn) * ctx->layers * ctx->P : nullptr);
         if (rc != VQNQS_OK) return rc;
     }
     if (mean_var) VQ_STAGE(S_MEANVAR, 1, launch_mean_var(e_loc, B, mean_var, st));
@@ -882,9 +913,10 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
         LayerW& w = ctx->lw[l];
         w.T = static_cast<float*>(dalloc((size_t)vq_heads * K * d * sizeof(float)));
         w.cnorm = static_cast<float*>(dalloc((size_t)vq_heads * K * sizeof(float)));
-        w.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * sizeof(__nv_bfloat16)));
-        w.w1_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
-        w.w2_t = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * sizeof(__nv_bfloat16)));
+        // BF16 transposes with their split lo planes: [2 out][in]
+        w.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(2 * 3 * d * d * sizeof(__nv_bfloat16)));
+        w.w1_t = static_cast<__nv_bfloat16*>(dalloc(2 * 4 * d * d * sizeof(__nv_bfloat16)));
+        w.w2_t = static_cast<__nv_bfloat16*>(dalloc(2 * 4 * d * d * sizeof(__nv_bfloat16)));
         w.cb_hi = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
         w.cb_lo = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
         w.wd = static_cast<float*>(dalloc((size_t)K * K * sizeof(float)));
@@ -984,18 +1016,7 @@ int vqnqs_local_energy_ragged(vqnqs_ctx* ctx, int n_groups, const int* L_g, cons
     if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "ragged: one spin per token");
     if (n_groups < 1 || n_groups > MAX_GROUPS || !L_g || !B_g)
         return fail(ctx, VQNQS_ERR_ARG, "ragged: need 1..8 groups and host arrays L_g, B_g");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
-    if (flags & VQNQS_INCREMENTAL) {
-        if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
-        if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
-        if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
-        if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: one spin per token");
-        if (!incremental_supported(ctx->d, ctx->heads))
-            return fail(ctx, VQNQS_ERR_ARG,
-                        "VQNQS_INCREMENTAL needs d_model in {32, 64, 128, 256, 512} and d_model/heads in {16, 32}, "
-                        "a multiple of d_model/32");
-    }
-    if ((flags & VQNQS_BF16) && ctx->d % 64) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_BF16 needs d_model % 64 == 0");
+    if (int rc = check_flags(ctx, flags)) return rc;
     Groups g;
     std::memset(&g, 0, sizeof(g));
     g.n = n_groups;
@@ -1070,6 +1091,12 @@ int vqnqs_local_energy(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc
     return run(ctx, B, spins, e_loc, mean_var, log_psi, flags, ws, ws_bytes, stream, true);
 }
 
+int vqnqs_local_energy_codes(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, int* codes, int flags,
+                             void* ws, size_t ws_bytes, void* stream) {
+    if (ctx && B > 0 && !codes) return fail(ctx, VQNQS_ERR_ARG, "codes is NULL");
+    return run(ctx, B, spins, e_loc, nullptr, nullptr, flags, ws, ws_bytes, stream, true, nullptr, codes);
+}
+
 int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out) {
     if (!ctx || !out) return VQNQS_ERR_ARG;
     VQ_CK(cudaDeviceSynchronize());
@@ -1116,8 +1143,10 @@ int vqnqs_reset_stats(vqnqs_ctx* ctx) {
     return VQNQS_OK;
 }
 
-int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const void* Bt, const float* bias,
-                    const float* R, void* C, int epilogue, void* stream) {
+namespace {
+// The tensor-core GEMM on its own; split: A [2M][K], Bt [2N][K] and a BF16 C [2M][N] hold lo planes.
+int gemm_entry(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const void* Bt, const float* bias, const float* R,
+               void* C, int epilogue, void* stream, bool split) {
     if (!ctx) return VQNQS_ERR_ARG;
     ctx->err.clear();
     if (M < 0 || N <= 0 || K <= 0 || K % 64 || !tc_pick_bn(N) || epilogue < 0 || epilogue > 4)
@@ -1128,13 +1157,25 @@ int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const vo
         return fail(ctx, VQNQS_ERR_ARG, "gemm: pointers must be 16-byte aligned");
     if (M == 0) return VQNQS_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (split && M > (1 << 29)) return fail(ctx, VQNQS_ERR_ARG, "gemm: M too large for split planes");
     CUtensorMap tb;
-    VQ_CK(make_tmap_bf16(&tb, Bt, N, K, tc_pick_bn(N)));
+    VQ_CK(make_tmap_bf16(&tb, Bt, split ? 2LL * N : N, K, tc_pick_bn(N)));
     VQ_CK(launch_set_int(ctx->gemm_m, M, st));
     ctx->launches += 2;
     VQ_CK(launch_gemm_tc(static_cast<const __nv_bfloat16*>(A), M, tb, bias, R, C, ctx->gemm_m, 0, N, K, epilogue,
-                         ctx->status, st, ctx->num_sms));
+                         ctx->status, st, ctx->num_sms, 0, split));
     return VQNQS_OK;
+}
+}  // namespace
+
+int vqnqs_gemm_bf16(vqnqs_ctx* ctx, int M, int N, int K, const void* A, const void* Bt, const float* bias,
+                    const float* R, void* C, int epilogue, void* stream) {
+    return gemm_entry(ctx, M, N, K, A, Bt, bias, R, C, epilogue, stream, false);
+}
+
+int vqnqs_gemm_bf16_split(vqnqs_ctx* ctx, int M, int N, int K, const void* A2, const void* Bt2, const float* bias,
+                          const float* R, void* C, int epilogue, void* stream) {
+    return gemm_entry(ctx, M, N, K, A2, Bt2, bias, R, C, epilogue, stream, true);
 }
 
 size_t vqnqs_grad_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples) {
@@ -1208,6 +1249,49 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
             VQ_CK(launch_colsum(O, B, B, (int)Pn, grad, 0, 0, st, ctx->num_sms * 16));
         }
     }
+    return VQNQS_OK;
+}
+
+size_t vqnqs_energy_grad_partials_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples) {
+    if (!ctx || B < 0) return 0;
+    return align256(2 * ctx->nparams * sizeof(float)) + vqnqs_grad_workspace_bytes(ctx, B, chunk_samples);
+}
+
+int vqnqs_energy_grad_partials(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float* e_loc, double* partials,
+                               int flags, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B < 0 || !partials) return fail(ctx, VQNQS_ERR_ARG, "energy_grad_partials: need B >= 0 and partials");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long Pn = (long long)ctx->nparams;
+    if (B == 0) {  // a rank without samples contributes zeros
+        VQ_CK(cudaMemsetAsync(partials, 0, (size_t)(2 * Pn + 3) * sizeof(double), st));
+        return VQNQS_OK;
+    }
+    if (!spins || !e_loc || !ws) return fail(ctx, VQNQS_ERR_ARG, "energy_grad_partials: null pointer");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(ctx, VQNQS_ERR_ARG, "workspace must be 256-byte aligned");
+    const size_t head = align256(2 * ctx->nparams * sizeof(float));
+    if (ws_bytes <= head) return fail(ctx, VQNQS_ERR_WORKSPACE, "energy_grad_partials: workspace too small");
+    float* s_eo = static_cast<float*>(ws);
+    float* s_o = s_eo + Pn;
+    void* gws = static_cast<char*>(ws) + head;
+    // sum_b E_b O_b (seeds E) and sum_b O_b (unit seeds): two backward passes
+    int rc = vqnqs_grad_log_psi(ctx, B, spins, e_loc, nullptr, nullptr, s_eo, flags, gws, ws_bytes - head, stream);
+    if (rc != VQNQS_OK) return rc;
+    rc = vqnqs_grad_log_psi(ctx, B, spins, nullptr, nullptr, nullptr, s_o, flags, gws, ws_bytes - head, stream);
+    if (rc != VQNQS_OK) return rc;
+    ctx->launches += 2;
+    VQ_CK(launch_grad_partials(s_eo, s_o, Pn, e_loc, B, partials, st, ctx->num_sms * 8));
+    return VQNQS_OK;
+}
+
+int vqnqs_energy_grad_combine(vqnqs_ctx* ctx, const double* partials, float* grad, double* mean_var, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (!partials || !grad) return fail(ctx, VQNQS_ERR_ARG, "energy_grad_combine: null pointer");
+    ctx->launches += 1;
+    VQ_CK(launch_energy_grad_combine(partials, (long long)ctx->nparams, grad, mean_var,
+                                     static_cast<cudaStream_t>(stream), ctx->num_sms * 8));
     return VQNQS_OK;
 }
 

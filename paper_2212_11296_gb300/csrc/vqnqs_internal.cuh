@@ -186,22 +186,28 @@ cudaError_t launch_eloc_reduce(const Chunk& ch, const float* diag, const float* 
                                float* e_loc_out, cudaStream_t st, int grid);
 cudaError_t launch_copy_codes(const Chunk& ch, const int* code, int l, int layers, int* out, cudaStream_t st,
                               int grid);
+// codes of every configuration's rows: out [S][per_sample][layers][N] of the chunk's samples
+cudaError_t launch_copy_cfg_codes(const Chunk& ch, const int* code, int l, int layers, int per_sample, int* out,
+                                  cudaStream_t st, int grid);
 cudaError_t launch_mean_var(const float* e_loc, int B, double* mean_var, cudaStream_t st);
 cudaError_t launch_accumulate_stats(const int* counters, int layers, int S, long long* stats, cudaStream_t st);
 
 // LayerNorm and per-location helpers (k_rowops.cu)
+// lo_off > 0: out_bf16 also gets the split lo plane lo_off elements after the hi one
 cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, const float* g, const float* b, int d,
-                             float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid);
+                             float* out_f32, __nv_bfloat16* out_bf16, cudaStream_t st, int grid, size_t lo_off = 0);
 // residual with the quantized vector's projection, then LN2; with vq_heads > 1 the
 // code packs one bits-wide field per head and T holds vq_heads tables of K rows
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
                                   float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads = 1,
-                                  int K = 0, int bits = 0);
+                                  int K = 0, int bits = 0, size_t lo_off = 0);
 // T and cnorm of a layer's codebook ([vq_heads][K][d / vq_heads])
 cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, int vq_heads,
                            float* T, float* cnorm, cudaStream_t st);
-cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st);
+// WT [cols][rows] = bf16(W^T); with lo, WT holds [2 cols][rows]: the split lo plane follows
+cudaError_t launch_transpose_bf16(const float* W, int rows, int cols, __nv_bfloat16* WT, cudaStream_t st,
+                                  bool lo = false);
 
 // FP32 SIMT GEMM (k_gemm_f32.cu): C[M,N] = A[M,K] @ B[K,N] + bias (+GELU) (+R); M = counters[u_slot]
 enum { EPI_BIAS = 0, EPI_BIAS_GELU = 1, EPI_BIAS_RESID = 2 };
@@ -223,20 +229,25 @@ cudaError_t launch_attention_f32(const Chunk& ch, const int* uid, const float* q
 cudaError_t launch_attention_bf16in(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                    int prefix_reuse, cudaStream_t st, int grid, const int* cfg_list = nullptr,
                                    int n_list = 0, float2* stats = nullptr);
-// tensor-core attention (k_attn_tc.cu): dh in {16, 32}, N <= 448; cfg_list and stats as above
-bool attention_tc_supported(int N, int dh);
+// tensor-core attention (k_attn_tc.cu): dh in {16, 32}, N <= 448 (<= 256 with split operands, whose
+// shared-memory tiles are twice as large); cfg_list and stats as above.  lo_off != 0: split operands,
+// the BF16 lo plane of Q/K/V lo_off elements after the hi plane qkv.
+bool attention_tc_supported(int N, int dh, bool split = false);
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list = nullptr,
-                                int n_list = 0, float2* stats = nullptr, const int* n_list_dev = nullptr);
+                                int n_list = 0, float2* stats = nullptr, const int* n_list_dev = nullptr,
+                                size_t lo_off = 0);
 
 // BF16 tensor-core GEMM (k_gemm_tc.cu): C[M,N] = A[M,K] @ Bt[N,K]^T + bias, M = counters[u_slot]
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
 int tc_pick_bn(int N);
 cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows);
-// BN = output tile width (64, 128, 192 or 256 dividing N; 0 picks the widest); tmB's box must be [BN x 64]
+// BN = output tile width (64, 128, 192 or 256 dividing N; 0 picks the widest); tmB's box must be [BN x 64].
+// split: A is [2 Arows][K] (hi plane, then lo plane), tmB covers [2N][K] (hi rows, then lo rows), three
+// passes per K block; BF16 outputs (epi 0, 1) are [2 Arows][N] (hi, then lo plane).
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms, int BN = 0);
+                           int* status, cudaStream_t st, int num_sms, int BN = 0, bool split = false);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream_t st);
 
@@ -276,7 +287,8 @@ bool patch_tc_supported(int d, int heads);  // BF16 path: rows patched on the te
 bool attention_rows_tc_supported(int N, int d, int heads);
 cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                      const int2* list, const int* act_off, const int* count, const short* dpos,
-                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms);
+                                     const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms,
+                                     size_t lo_off = 0);
 // per connected configuration: changed positions (first INC_MAX_KEYS), their count, and the work list it joins
 // (BF16 path: tensor-core patch, or recomputed whole with its rows searched; FP32 path: CUDA-core patch)
 cudaError_t launch_inc_classify(const Chunk& ch, const int* uid, int tc_ok, int* list_tc, int* list_simt, short* dpos,
@@ -285,16 +297,18 @@ cudaError_t launch_codeword_dist(const float* W, int K, int d, float* wd, cudaSt
 cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
                              const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
                              int* counters, int* rc_cnt, cudaStream_t st);
+// wd: the layer's ||W_a - W_c|| table; split (BF16 qkv only): the Q/K/V in qkv are the hi plane of split
+// operands, and rows the certificate does not settle are recomputed instead of searched with o + delta
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, float* O, const float2* bstat,
-                             const CertRow* cert, const float* codebook, int* code, int* vq_rows,
-                             const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
-                             const int* dcnt, int use_tc, int* status, long long* stats, cudaStream_t st,
-                             int grid);
+                             const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
+                             const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
+                             const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int* status,
+                             long long* stats, cudaStream_t st, int grid);
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
-                             const float2* bstat, const CertRow* cert, const float* codebook, int* code,
-                             int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc, const int* list_simt, const short* dpos,
-                             const int* dcnt, int use_tc, int* status, long long* stats,
-                             cudaStream_t st, int grid);
+                             const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
+                             int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
+                             const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
+                             int split, int* status, long long* stats, cudaStream_t st, int grid);
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
                                  const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,
                                  int num_sms);
@@ -338,6 +352,11 @@ cudaError_t launch_embed_bwd(const float* dX0, const uint8_t* spins, int S, int 
 cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N, int d, int H, float* dQKV,
                                  float* stat, cudaStream_t st, int cap);
 cudaError_t launch_seeds_from_eloc(const float* e_loc, int B, float* seeds, cudaStream_t st);
+// sharded energy gradient: partials [2P + 3] = (sum E O, sum O, sum E, sum E^2, n), and their combination
+cudaError_t launch_grad_partials(const float* s_eo, const float* s_o, long long P, const float* e_loc, int B,
+                                 double* out, cudaStream_t st, int cap);
+cudaError_t launch_energy_grad_combine(const double* part, long long P, float* grad, double* mean_var, cudaStream_t st,
+                                       int cap);
 cudaError_t launch_sub_scaled_rows(float* out, const float* csum, const float* W, int K, int d, int groups,
                                    long long stride, cudaStream_t st, int cap);
 
