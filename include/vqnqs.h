@@ -450,7 +450,9 @@ int vqnqs_reset_stats(vqnqs_ctx* ctx);
  * synchronises the device and returns, per stage, the number of kernel
  * launches and the summed event time since the last read (then clears them).
  * Stage names: config, active_rows, embed, ln1, qkv_gemm, attention, vq_argmin, dedupe,
- * post_ln, mlp_up, mlp_down, head, eloc, mean_var, backward. */
+ * post_ln, mlp_up, mlp_down, head, eloc, mean_var, backward, inc_certificate,
+ * inc_classify, inc_patch, inc_recompute, inc_recompute_whole, half_block,
+ * inc_exact_delta. */
 typedef struct vqnqs_stage_time {
     char name[24];
     int64_t calls;     /* times the stage ran */

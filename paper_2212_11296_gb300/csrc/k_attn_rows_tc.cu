@@ -55,30 +55,51 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// n consecutive BF16 values (n a multiple of 8, 16-byte aligned) as floats; with
-// SPLIT the value is hi + lo, the lo plane lo_off elements further on
-template <int NV, bool SPLIT>
-__device__ __forceinline__ void ld_bf16(const __nv_bfloat16* p, size_t lo_off, float (&out)[NV]) {
+// 8 consecutive BF16 values (16-byte aligned) as floats; with SPLIT the value is hi + lo,
+// the lo plane lo_off elements further on
+template <bool SPLIT>
+__device__ __forceinline__ void ld8(const __nv_bfloat16* p, size_t lo_off, float (&out)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-    for (int i = 0; i < NV; i += 8) {
-        const uint4 u = *reinterpret_cast<const uint4*>(p + i);
-        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(h[k]);
+        out[2 * k] = f.x;
+        out[2 * k + 1] = f.y;
+    }
+    if (SPLIT) {
+        const uint4 ul = *reinterpret_cast<const uint4*>(p + lo_off);
+        const __nv_bfloat162* l = reinterpret_cast<const __nv_bfloat162*>(&ul);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const float2 f = __bfloat1622float2(h[k]);
-            out[i + 2 * k] = f.x;
-            out[i + 2 * k + 1] = f.y;
+            const float2 f = __bfloat1622float2(l[k]);
+            out[2 * k] += f.x;
+            out[2 * k + 1] += f.y;
         }
-        if (SPLIT) {
-            const uint4 ul = *reinterpret_cast<const uint4*>(p + lo_off + i);
-            const __nv_bfloat162* l = reinterpret_cast<const __nv_bfloat162*>(&ul);
+    }
+}
+// q . x over DH values read eight at a time
+template <bool SPLIT>
+__device__ __forceinline__ float dot_dh(const float (&q)[DH], const __nv_bfloat16* p, size_t lo_off) {
+    float s = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 f = __bfloat1622float2(l[k]);
-                out[i + 2 * k] += f.x;
-                out[i + 2 * k + 1] += f.y;
-            }
-        }
+    for (int t8 = 0; t8 < DH; t8 += 8) {
+        float x[8];
+        ld8<SPLIT>(p + t8, lo_off, x);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) s = fmaf(q[t8 + t], x[t], s);
+    }
+    return s;
+}
+// a += w x over 16 values
+template <bool SPLIT>
+__device__ __forceinline__ void axpy16(float w, const __nv_bfloat16* p, size_t lo_off, float (&a)[16]) {
+#pragma unroll
+    for (int t8 = 0; t8 < 16; t8 += 8) {
+        float x[8];
+        ld8<SPLIT>(p + t8, lo_off, x);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t8 + t] = fmaf(w, x[t], a[t8 + t]);
     }
 }
 
@@ -97,36 +118,44 @@ __device__ __forceinline__ float operand_value(float x) {
     return SPLIT ? h + __bfloat162float(__float2bfloat16_rn(x - h)) : h;
 }
 
+// Shared-memory plan (as in k_attn_tc.cu): K and V^T tiles, then a region holding the Q
+// tile and two P chunk tiles of PCH keys (each with NP planes), aliased by the V staging rows.
+constexpr int PCH = 32;
+constexpr size_t PCB = (size_t)128 * PCH * 2;
 __host__ __device__ constexpr size_t rows_tile_bytes(int Npad) { return (size_t)Npad * DH * 2; }
-__host__ __device__ constexpr size_t rows_p_bytes(int Npad) {
-    return (size_t)128 * Npad * 2 > (size_t)Npad * (2 * DH + 16) ? (size_t)128 * Npad * 2
-                                                                  : (size_t)Npad * (2 * DH + 16);
+__host__ __device__ constexpr size_t rows_region_bytes(int Npad, int NP) {
+    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16)
+               ? (size_t)NP * 128 * DH * 2 + 2 * NP * PCB
+               : (size_t)NP * Npad * (2 * DH + 16);
 }
 __host__ __device__ constexpr size_t rows_smem_bytes(int Npad, bool split) {
-    return 1024 + (split ? 2 : 1) * (2 * rows_tile_bytes(Npad) + (size_t)128 * DH * 2 + rows_p_bytes(Npad)) + 64;
+    return 128 + (split ? 2 : 1) * 2 * rows_tile_bytes(Npad) + rows_region_bytes(Npad, split ? 2 : 1) + 64;
 }
 
 }  // namespace
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(AR_THREADS, SPLIT ? 1 : 2)
+__global__ void __launch_bounds__(AR_THREADS, 2)
 k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
                     float* __restrict__ O, const int2* __restrict__ list, const int* __restrict__ act_off,
                     const int* __restrict__ count, const short* __restrict__ dpos, const int* __restrict__ dcnt,
                     int slices, int Npad, uint32_t tmem_cols, int* __restrict__ status, long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     constexpr int VS = 2 * DH + 16;               // row stride of the V staging rows (bank-conflict free)
     constexpr int NP = SPLIT ? 2 : 1;             // operand planes: hi (and lo)
     const int d = ch.d, H = ch.heads;
-    const size_t tb = rows_tile_bytes(Npad), pb = rows_p_bytes(Npad);
+    const size_t tb = rows_tile_bytes(Npad);
+    const size_t pb = (size_t)Npad * VS;          // one V staging plane
     uint8_t* sK = smem;                           // [NP][Npad x DH] K-major
     uint8_t* sVt = sK + NP * tb;                  // [NP][DH x Npad]
-    uint8_t* sQ = sVt + NP * tb;                  // [NP][128 x DH]
-    uint8_t* sP = sQ + NP * 128 * DH * 2;         // [NP][128 x Npad]; V staging rows alias it
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + NP * pb);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
-    __shared__ float s_red[2][128];
+    uint8_t* sQ = sVt + NP * tb;                  // [NP][128 x DH]; V staging rows alias Q and P
+    uint8_t* sP = sQ + NP * 128 * DH * 2;         // [2 tiles][NP][128 x PCH]
+    uint8_t* sStage = sQ;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + rows_region_bytes(Npad, NP));  // S MMAs
+    uint64_t* pbar = bar + 1;                     // [2]: MMAs reading P tile 0 / 1
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pbar + 2);
+    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(sQ);  // [2][128], used once Q has been read
     __shared__ int s_pw[4];
     __shared__ unsigned long long s_pairs;
 
@@ -134,9 +163,12 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
     const int row = tid & 127, half = tid >> 7;  // two threads per query row
     if (tid == 0) {
         tc::mbar_init(bar, 1);
+        tc::mbar_init(&pbar[0], 1);
+        tc::mbar_init(&pbar[1], 1);
         tc::fence_barrier_init();
         s_pairs = 0;
     }
+    uint32_t pph[2] = {0u, 0u};  // phases of pbar
     unsigned long long pairs = 0;  // query-key pairs of this thread's rows (head 0, first half)
     if (blockIdx.x == 0 && tid == 0 && stats)  // the layer's search list is complete: count it
         atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_VQ]), (unsigned long long)ch.counters[CNT_V]);
@@ -184,7 +216,7 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                 const int j = u / (DH / 8), kb = u - j * (DH / 8);
                 uint4 vv = make_uint4(0, 0, 0, 0);
                 if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)ub[j] * ld + 2 * d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sP + pl * pb + j * VS + kb * 16) = vv;
+                *reinterpret_cast<uint4*>(sStage + pl * pb + j * VS + kb * 16) = vv;
             }
         }
         __syncthreads();
@@ -193,7 +225,7 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                 const int jb = blk / (DH / 32), kq = blk - jb * (DH / 32);
                 const int m = lane >> 3, r = lane & 7;
                 uint32_t f[4];
-                tc::ldsm_x4_trans(tc::smem_u32(sP + pl * pb + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
+                tc::ldsm_x4_trans(tc::smem_u32(sStage + pl * pb + (jb * 8 + r) * VS + (kq * 4 + m) * 16), f);
                 tc::stsm_x4(tc::smem_u32(sVt + pl * tb + tc::core_off((kq * 4 + m) * 8 + r, jb * 8, Npad)), f);
             }
         __syncthreads();
@@ -281,17 +313,30 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
             mx = fmaxf(s_red[0][row], s_red[1][row]);
             const float mb = (p >= 0) ? mx * sl2 : 0.f;
             float sum = 0.f;
-            for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
-                uint32_t pk[16], plo[16];
-                if (c0 > plim_w) {  // invisible to every row of the warp: P = 0
+            // P V in chunks of PCH keys, double-buffered P tiles (pend: MMAs of this tile still reading them)
+            const int nch = (nk16 + PCH - 1) / PCH;
+            int pend[2] = {0, 0};
+            for (int jc = 0; jc < nch && ok; ++jc) {
+                const int u = jc & 1;
+                uint8_t* pt = sP + (size_t)u * NP * PCB;
+                if (pend[u]) {  // chunk jc - 2's MMAs read this tile
+                    ok = __syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0;
+                    pph[u] ^= 1;
+                    pend[u] = 0;
+                    tc::tc_fence_after();
+                    if (!ok) break;
+                }
+                const int c0 = jc * PCH + half * 16;  // this thread's 16 keys of the chunk
+                uint32_t pk[8], plo[8];
+                if (c0 > plim_w || c0 >= nk16) {  // invisible to the warp's rows, or past the MMA's keys: P = 0
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = plo[j] = 0u;
+                    for (int j = 0; j < 8; ++j) pk[j] = plo[j] = 0u;
                 } else {
-                    uint32_t r[32];
-                    tc::tmem_ld32(tmem + lane_base + c0, r);
-                    const bool full = c0 + 31 <= plim;
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + c0, r);
+                    const bool full = c0 + 15 <= plim;
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
+                    for (int j = 0; j < 16; j += 2) {
                         float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
                         float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
                         if (!full) {
@@ -308,40 +353,46 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                     }
                 }
 #pragma unroll
-                for (int j8 = 0; j8 < 4; ++j8)
-                    if (c0 + j8 * 8 < nk16) {
-                        *reinterpret_cast<uint4*>(sP + tc::core_off(row, c0 + j8 * 8, Npad)) =
-                            make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
-                        if (SPLIT)
-                            *reinterpret_cast<uint4*>(sP + pb + tc::core_off(row, c0 + j8 * 8, Npad)) =
-                                make_uint4(plo[4 * j8], plo[4 * j8 + 1], plo[4 * j8 + 2], plo[4 * j8 + 3]);
-                    }
-            }
-            __syncthreads();  // both halves read s_red (max) before it is reused for sums
-            s_red[half][row] = sum;
-            tc::tc_fence_before();
-            tc::fence_proxy_async_smem();
-            __syncthreads();
-            sum = s_red[0][row] + s_red[1][row];
-            if (tid == 0) {
-                tc::tc_fence_after();
-                const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
-                constexpr int NPROD = SPLIT ? 3 : 1;  // (P plane, V plane): hi.hi, hi.lo, lo.hi
-#pragma unroll
-                for (int pr = 0; pr < NPROD; ++pr) {
-                    const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
-                    const uint64_t dp = tc::desc_kmajor_none(tc::smem_u32(sP + pp * pb), 128, (Npad / 8) * 128);
-                    const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128);
-                    for (int ks = 0; ks < nk16 / 16; ++ks)
-                        tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
-                                     (pr | ks) > 0 ? 1u : 0u);
+                for (int j8 = 0; j8 < 2; ++j8) {
+                    const uint32_t off = tc::core_off(row, half * 16 + j8 * 8, PCH);
+                    *reinterpret_cast<uint4*>(pt + off) = make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+                    if (SPLIT)
+                        *reinterpret_cast<uint4*>(pt + PCB + off) =
+                            make_uint4(plo[4 * j8], plo[4 * j8 + 1], plo[4 * j8 + 2], plo[4 * j8 + 3]);
                 }
-                tc::mma_commit(bar);
+                tc::fence_proxy_async_smem();
+                tc::tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::tc_fence_after();
+                    const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
+                    const int kk = min(PCH, nk16 - jc * PCH);  // keys of this chunk the MMA covers
+                    constexpr int NPROD = SPLIT ? 3 : 1;     // (P plane, V plane): hi.hi, hi.lo, lo.hi
+#pragma unroll
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
+                        const uint64_t dp = tc::desc_kmajor_none(tc::smem_u32(pt + pp * PCB), 128, (PCH / 8) * 128);
+                        const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128) +
+                                            (uint64_t)(((jc * PCH / 8) * 128) >> 4);
+                        for (int ks = 0; ks < kk / 16; ++ks)
+                            tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
+                                         (jc | pr | ks) > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&pbar[u]);
+                }
+                pend[u] = 1;
             }
-            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
-            phase ^= 1;
+            // the last chunk's MMAs (and every earlier one) have completed
+            for (int u = 0; u < 2; ++u)
+                if (pend[u]) {
+                    ok = (__syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0) && ok;
+                    pph[u] ^= 1;
+                }
             tc::tc_fence_after();
             if (!ok) break;
+            s_red[half][row] = sum;
+            __syncthreads();
+            sum = s_red[0][row] + s_red[1][row];
             {
                 uint32_t r[16];
                 tmem_ld16(tmem + lane_base + half * (DH / 2), r);  // this thread's half of the dims
@@ -355,17 +406,19 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                     const int* uc = uid + (rrow - p);
                     const short* dp = dpos + (size_t)c * INC_MAX_KEYS;
                     float q[DH];
-                    ld_bf16<DH, SPLIT>(qkv + (size_t)uid[rrow] * ld + h * DH, lo_off, q);
+#pragma unroll
+                    for (int t8 = 0; t8 < DH; t8 += 8) {
+                        float x[8];
+                        ld8<SPLIT>(qkv + (size_t)uid[rrow] * ld + h * DH + t8, lo_off, x);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) q[t8 + t] = x[t];
+                    }
                     float m2 = mb, lsub = 0.f;  // log2-unit maximum; removed weight
                     // the new maximum first
                     for (int i = 0; i < nd; ++i) {
                         const int k = dp[i];
                         if (k > p) break;  // ascending
-                        float kc[DH];
-                        ld_bf16<DH, SPLIT>(qkv + (size_t)uc[k] * ld + d + h * DH, lo_off, kc);
-                        float sc = 0.f;
-#pragma unroll
-                        for (int t = 0; t < DH; ++t) sc = fmaf(q[t], kc[t], sc);
+                        const float sc = dot_dh<SPLIT>(q, qkv + (size_t)uc[k] * ld + d + h * DH, lo_off);
                         m2 = fmaxf(m2, sc * sl2);
                     }
                     const float rs = ex2_approx(mb - m2);  // rescale of s's part (1 if no new maximum)
@@ -376,26 +429,13 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                     for (int i = 0; i < nd; ++i) {
                         const int k = dp[i];
                         if (k > p) break;
-                        float kb[DH], kc[DH];
-                        ld_bf16<DH, SPLIT>(qkv + (size_t)ub[k] * ld + d + h * DH, lo_off, kb);
-                        ld_bf16<DH, SPLIT>(qkv + (size_t)uc[k] * ld + d + h * DH, lo_off, kc);
-                        float sb = 0.f, sc = 0.f;
-#pragma unroll
-                        for (int t = 0; t < DH; ++t) {
-                            sb = fmaf(q[t], kb[t], sb);
-                            sc = fmaf(q[t], kc[t], sc);
-                        }
+                        const float sb = dot_dh<SPLIT>(q, qkv + (size_t)ub[k] * ld + d + h * DH, lo_off);
+                        const float sc = dot_dh<SPLIT>(q, qkv + (size_t)uc[k] * ld + d + h * DH, lo_off);
                         const float eb = ex2_approx(fmaf(sb, sl2, -mb));  // as s's softmax added it
                         const float ebq = operand_value<SPLIT>(eb);
                         const float ec = ex2_approx(fmaf(sc, sl2, -m2));
-                        float vb[16], vc[16];
-                        ld_bf16<16, SPLIT>(qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, lo_off, vb);
-                        ld_bf16<16, SPLIT>(qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, lo_off, vc);
-#pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            a[t] = fmaf(-ebq, vb[t], a[t]);
-                            add[t] = fmaf(ec, vc[t], add[t]);
-                        }
+                        axpy16<SPLIT>(-ebq, qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, lo_off, a);
+                        axpy16<SPLIT>(ec, qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, lo_off, add);
                         lsub += eb;
                         ladd += ec;
                     }
@@ -426,6 +466,7 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
 bool attention_rows_tc_supported(int N, int d, int heads) {
     return d / heads == DH && N <= 256 && rows_smem_bytes((N + 31) & ~31, true) <= 227 * 1024;
 }
+// (two CTAs per SM need rows_smem_bytes(256, true) plus the static words within half of the SM's 228 KB)
 
 cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                      const int2* list, const int* act_off, const int* count, const short* dpos,
@@ -442,7 +483,7 @@ cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv
     size_t smem_req = smem;
     if ((228 * 1024) / smem_req > max_ctas) smem_req = (228 * 1024) / (max_ctas + 1) + 1024;
     const int sh = ch.S * ch.heads;
-    int slices = ((split ? 1 : 2) * num_sms + sh - 1) / sh;
+    int slices = (2 * num_sms + sh - 1) / sh;
     if (slices < 1) slices = 1;
     if (slices > 64) slices = 64;
 #define VQ_ROWS(SP, SLOT)                                                                                         \

@@ -13,8 +13,12 @@
 //      lane): two passes (causal max, then exp2 / sum) combined through shared
 //      memory, writing P as BF16 into shared memory; chunks wholly left of the
 //      diagonal take a compare-free path, chunks right of it are skipped;
-//   4. thread 0 issues O = P V (M = 128, N = dh, K = keys) into TMEM columns
-//      already read; each thread scales half of its row by 1/sum and stores it.
+//   4. P V in 32-key chunks through two P tiles in shared memory: while thread 0's
+//      MMAs of chunk j (O += P_j V_j, M = 128, N = dh) run, the threads write
+//      chunk j + 1 into the other tile; O accumulates in TMEM columns whose scores
+//      were consumed by chunk 0; each thread scales half of its row by 1/sum and
+//      stores it.  The chunked P keeps the shared memory of a CTA near 113 KB
+//      even with split operands, so two CTAs share an SM.
 // With prefix reuse, query tiles start at the configuration's first changed
 // position: rows before it are neither computed nor stored.
 // Waits on the MMA barrier are bounded (VQNQS_DEV_TIMEOUT on expiry).
@@ -70,43 +74,52 @@ __device__ __forceinline__ void split_pack2(float a, float b, uint32_t& hi, uint
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// Shared-memory plan of one CTA: K, V^T, Q and P tiles (each twice with SPLIT).
+// Shared-memory plan of one CTA: K and V^T tiles, then a region holding the Q tile and
+// two P chunk tiles (each with NP planes), which the V staging rows alias; barriers last.
+constexpr int PCH = 32;                      // keys per P chunk
+constexpr size_t PCB = (size_t)128 * PCH * 2;  // one plane of one P chunk tile
 __host__ __device__ constexpr size_t attn_tile_bytes(int Npad, int DH) { return (size_t)Npad * DH * 2; }
-__host__ __device__ constexpr size_t attn_p_bytes(int Npad, int DH) {
-    return (size_t)128 * Npad * 2 > (size_t)Npad * (2 * DH + 16) ? (size_t)128 * Npad * 2
-                                                                  : (size_t)Npad * (2 * DH + 16);
+__host__ __device__ constexpr size_t attn_region_bytes(int Npad, int DH, int NP) {
+    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16)
+               ? (size_t)NP * 128 * DH * 2 + 2 * NP * PCB
+               : (size_t)NP * Npad * (2 * DH + 16);
 }
 __host__ __device__ constexpr size_t attn_smem_bytes(int Npad, int DH, bool split) {
-    return 1024 + (split ? 2 : 1) * (2 * attn_tile_bytes(Npad, DH) + (size_t)128 * DH * 2 + attn_p_bytes(Npad, DH)) +
-           64;
+    return 128 + (split ? 2 : 1) * 2 * attn_tile_bytes(Npad, DH) + attn_region_bytes(Npad, DH, split ? 2 : 1) + 64;
 }
 
 template <int DH, bool SPLIT>
-__global__ void __launch_bounds__(AT_THREADS)
+__global__ void __launch_bounds__(AT_THREADS, 2)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
                float* __restrict__ O, int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
                const int* __restrict__ cfg_list, int n_list, const int* __restrict__ n_list_dev,
                float2* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const int d = ch.d, H = ch.heads;
     constexpr int VS = 2 * DH + 16;                // row stride of the V staging rows (bank-conflict free)
     constexpr int NP = SPLIT ? 2 : 1;              // operand planes: hi (and lo)
-    const size_t tb = attn_tile_bytes(Npad, DH), pb = attn_p_bytes(Npad, DH);
+    const size_t tb = attn_tile_bytes(Npad, DH);
     uint8_t* sK = smem;                            // [NP][Npad x DH] K-major core layout
     uint8_t* sVt = sK + NP * tb;                   // [NP][DH x Npad]
-    uint8_t* sQ = sVt + NP * tb;                   // [NP][128 x DH]
-    uint8_t* sP = sQ + NP * 128 * DH * 2;          // [NP][128 x Npad]; V staging rows alias it
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + NP * pb);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
-    __shared__ float s_red[2][128];
+    uint8_t* sQ = sVt + NP * tb;                   // [NP][128 x DH]; V staging rows alias Q and P
+    uint8_t* sP = sQ + NP * 128 * DH * 2;          // [2 tiles][NP][128 x PCH]
+    uint8_t* sStage = sQ;                          // [NP][Npad x VS]
+    const size_t pb = (size_t)Npad * VS;           // one staging plane
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + attn_region_bytes(Npad, DH, NP));  // S MMAs
+    uint64_t* pbar = bar + 1;                      // [2]: MMAs reading P tile 0 / 1
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pbar + 2);
+    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(sQ);  // [2][128], used once Q has been read
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & 127, half = tid >> 7;  // two threads per query row
     if (tid == 0) {
         tc::mbar_init(bar, 1);
+        tc::mbar_init(&pbar[0], 1);
+        tc::mbar_init(&pbar[1], 1);
         tc::fence_barrier_init();
     }
+    uint32_t pph[2] = {0u, 0u};  // phases of pbar
     if (warp == 0) tc::tmem_alloc(tmem_holder, tmem_cols);
     tc::tc_fence_before();
     __syncthreads();
@@ -139,12 +152,12 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 const int j = u / (DH / 8), kb = u - j * (DH / 8);
                 uint4 vv = make_uint4(0, 0, 0, 0);
                 if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)urow[j] * ld + 2 * d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sP + pl * pb + j * VS + kb * 16) = vv;
+                *reinterpret_cast<uint4*>(sStage + pl * pb + j * VS + kb * 16) = vv;
             }
         }
         __syncthreads();
         for (int pl = 0; pl < NP; ++pl) {
-            uint8_t* stg = sP + pl * pb;
+            uint8_t* stg = sStage + pl * pb;
             uint8_t* vt = sVt + pl * tb;
             for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AT_THREADS / 32) {
                 // four 8x8 matrices: key block jb, dh blocks kq*4 .. kq*4+3
@@ -238,17 +251,30 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             mx = fmaxf(s_red[0][row], s_red[1][row]);
             const float mb = mx * sl2;
             float sum = 0.f;
-            for (int c0 = half * 32; c0 < nk32 && c0 < nk16; c0 += 64) {
-                uint32_t pk[16], pl[16];
-                if (c0 > plim_w) {  // invisible chunk: P = 0 (still read by the PV MMA up to nk16)
+            // P V in chunks of PCH keys, double-buffered P tiles (pend: MMAs of this tile still reading them)
+            const int nch = (nk16 + PCH - 1) / PCH;
+            int pend[2] = {0, 0};
+            for (int jc = 0; jc < nch && ok; ++jc) {
+                const int u = jc & 1;
+                uint8_t* pt = sP + (size_t)u * NP * PCB;
+                if (pend[u]) {  // chunk jc - 2's MMAs read this tile
+                    ok = __syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0;
+                    pph[u] ^= 1;
+                    pend[u] = 0;
+                    tc::tc_fence_after();
+                    if (!ok) break;
+                }
+                const int c0 = jc * PCH + half * 16;  // this thread's 16 keys of the chunk
+                uint32_t pk[8], pl[8];
+                if (c0 > plim_w || c0 >= nk16) {  // invisible to the warp's rows, or past the MMA's keys: P = 0
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = pl[j] = 0u;
+                    for (int j = 0; j < 8; ++j) pk[j] = pl[j] = 0u;
                 } else {
-                    uint32_t r[32];
-                    tc::tmem_ld32(tmem + lane_base + c0, r);
-                    const bool full = c0 + 31 <= plim;
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + c0, r);
+                    const bool full = c0 + 15 <= plim;
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
+                    for (int j = 0; j < 16; j += 2) {
                         float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
                         float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
                         if (!full) {
@@ -265,40 +291,46 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                     }
                 }
 #pragma unroll
-                for (int j8 = 0; j8 < 4; ++j8)
-                    if (c0 + j8 * 8 < nk16) {
-                        *reinterpret_cast<uint4*>(sP + core_off(row, c0 + j8 * 8, Npad)) =
-                            make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
-                        if (SPLIT)
-                            *reinterpret_cast<uint4*>(sP + pb + core_off(row, c0 + j8 * 8, Npad)) =
-                                make_uint4(pl[4 * j8], pl[4 * j8 + 1], pl[4 * j8 + 2], pl[4 * j8 + 3]);
-                    }
-            }
-            __syncthreads();  // both halves read s_red (max) before it is reused for sums
-            s_red[half][row] = sum;
-            tc::tc_fence_before();
-            fence_proxy_async_smem();
-            __syncthreads();
-            sum = s_red[0][row] + s_red[1][row];
-            if (tid == 0) {
-                tc::tc_fence_after();
-                const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
-                constexpr int NPROD = SPLIT ? 3 : 1;  // (P plane, V plane): hi.hi, hi.lo, lo.hi
-#pragma unroll
-                for (int pr = 0; pr < NPROD; ++pr) {
-                    const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
-                    const uint64_t dp = desc_kmajor_none(tc::smem_u32(sP + pp * pb), 128, (Npad / 8) * 128);
-                    const uint64_t dv = desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128);
-                    for (int ks = 0; ks < nk16 / 16; ++ks)
-                        tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
-                                     (pr | ks) > 0 ? 1u : 0u);
+                for (int j8 = 0; j8 < 2; ++j8) {
+                    const uint32_t off = core_off(row, half * 16 + j8 * 8, PCH);
+                    *reinterpret_cast<uint4*>(pt + off) = make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+                    if (SPLIT)
+                        *reinterpret_cast<uint4*>(pt + PCB + off) =
+                            make_uint4(pl[4 * j8], pl[4 * j8 + 1], pl[4 * j8 + 2], pl[4 * j8 + 3]);
                 }
-                tc::mma_commit(bar);
+                tc::fence_proxy_async_smem();
+                tc::tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc::tc_fence_after();
+                    const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
+                    const int kk = min(PCH, nk16 - jc * PCH);  // keys of this chunk the MMA covers
+                    constexpr int NPROD = SPLIT ? 3 : 1;     // (P plane, V plane): hi.hi, hi.lo, lo.hi
+#pragma unroll
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
+                        const uint64_t dp = desc_kmajor_none(tc::smem_u32(pt + pp * PCB), 128, (PCH / 8) * 128);
+                        const uint64_t dv = desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128) +
+                                            (uint64_t)(((jc * PCH / 8) * 128) >> 4);
+                        for (int ks = 0; ks < kk / 16; ++ks)
+                            tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
+                                         (jc | pr | ks) > 0 ? 1u : 0u);
+                    }
+                    tc::mma_commit(&pbar[u]);
+                }
+                pend[u] = 1;
             }
-            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
-            phase ^= 1;
+            // the last chunk's MMAs (and every earlier one) have completed
+            for (int u = 0; u < 2; ++u)
+                if (pend[u]) {
+                    ok = (__syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0) && ok;
+                    pph[u] ^= 1;
+                }
             tc::tc_fence_after();
             if (!ok) break;
+            s_red[half][row] = sum;
+            __syncthreads();
+            sum = s_red[0][row] + s_red[1][row];
             {
                 // each of the row's two threads stores half of the DH output columns
                 uint32_t r[16];

@@ -108,6 +108,7 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
     if (blockIdx.x == 0 && tid == 0) {  // the lists the classify and patch kernels fill next
         counters[CNT_V] = 0;
         counters[CNT_TCL] = counters[CNT_SCL] = counters[CNT_TCW] = counters[CNT_SCW] = 0;
+        counters[CNT_EX] = 0;
     }
     if (blockIdx.x == 0)
         for (int b = tid; b < 2 * ch.S; b += blockDim.x) rc_cnt[b] = 0;  // head and tail counts per sample
@@ -345,9 +346,9 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 //   6. only a row that is searched (certificate not met) has o + delta written
 //      to O; a certified row keeps the sample's codeword and writes nothing else.
 //      With split operands (the path whose Q/K/V carry a BF16 lo plane) a row
-//      that the certificate does not settle is recomputed over all keys from the
-//      split operands instead, so every output that reaches the search carries
-//      FP32-grade error.
+//      that the certificate does not settle is listed instead, and
+//      k_inc_exact_delta forms its correction from the split operands in FP32,
+//      so every output that reaches the search carries FP32-grade error.
 //
 // The bound B.  The kernel reads only the hi planes: q~ = bf16(q), k~, v~ (each
 // within 2^-9 relative of the exact value, or equal to it on the plain BF16
@@ -423,8 +424,8 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                const float* __restrict__ codebook, const float* __restrict__ wd, int* __restrict__ code,
                int* __restrict__ vq_rows, const int* __restrict__ act_off, int2* __restrict__ rc_rows,
                int* __restrict__ rc_cnt, const int* __restrict__ list_tc, const short* __restrict__ dpos,
-               const int* __restrict__ dcnt, int split, uint32_t tmem_cols, int* __restrict__ status,
-               long long* __restrict__ stats) {
+               const int* __restrict__ dcnt, int split, int2* __restrict__ ex_rows, uint32_t tmem_cols,
+               int* __restrict__ status, long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     constexpr int DH = 32;
@@ -749,10 +750,11 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                         md = 1;
                 }
             }
-            // split operands: a row the certificate does not settle is recomputed from them
-            if (split && md == 1) md = 2;
+            // split operands: a row the certificate does not settle gets its exact correction
+            // from them (k_inc_exact_delta) before the search
+            if (split && md == 1 && half == 0) ex_rows[atomicAdd(&ch.counters[CNT_EX], 1)] = make_int2(rc + p, p);
             // a searched row: o + delta goes to O for the vector quantizer
-            if (__any_sync(0xffffffffu, md == 1)) {
+            if (!split && __any_sync(0xffffffffu, md == 1)) {
                 float* xo = O + (size_t)(rc + (p >= 0 ? p : 0)) * d;
                 for (int hh = 0; hh < HH; ++hh) {
                     const int h = h0 + hh;
@@ -806,6 +808,110 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
         atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_FULL]), (unsigned long long)sCnt[2]);
         atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_PPAIRS]), (unsigned long long)sCnt[3]);
     }
+}
+
+// ---- split operands: exact correction of the rows the certificate did not settle -------
+// One warp per listed row (row r of configuration c, position p, the sample's query):
+// lane l holds dims [l PER, (l + 1) PER) of every vector, a head (32 dims) spans 32 / PER
+// lanes.  For each changed position k < p of c (ascending in dpos), with q, k and v read
+// as hi + lo from the two planes and the sample's softmax maximum m and sum l,
+//   e_s = exp(q . k_s / sqrt(32) - m),  e_c = exp(q . k_c / sqrt(32) - m),
+//   o' = o + (sum e_c (v_c - o) - e_s (v_s - o)) / (l - sum e_s + sum e_c)
+// in FP32; o' goes to O[r] for the nearest-codeword search.  The patch kernel lists only
+// rows without cancellation or overflow of the new scores (its guard), and at most
+// PATCH_TC_KEYS changed positions.
+template <int PER>
+__device__ __forceinline__ void ld_split(const __nv_bfloat16* __restrict__ p, size_t lo_off, float (&x)[PER]) {
+#pragma unroll
+    for (int i = 0; i < PER; i += 4) {
+        const uint2 h = *reinterpret_cast<const uint2*>(p + i);
+        const uint2 l = *reinterpret_cast<const uint2*>(p + lo_off + i);
+        const float2 h0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.x));
+        const float2 h1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h.y));
+        const float2 l0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&l.x));
+        const float2 l1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&l.y));
+        x[i] = h0.x + l0.x;
+        x[i + 1] = h0.y + l0.y;
+        x[i + 2] = h1.x + l1.x;
+        x[i + 3] = h1.y + l1.y;
+    }
+}
+
+template <int PER>
+__global__ void __launch_bounds__(256)
+k_inc_exact_delta(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
+                  float* __restrict__ O, const float2* __restrict__ bstat, const short* __restrict__ dpos,
+                  const int* __restrict__ dcnt, const int2* __restrict__ list, const int* __restrict__ n_list) {
+    constexpr int LPH = 32 / PER;  // lanes per head (32 dims)
+    const int n = *n_list;
+    const int d = ch.d, H = ch.heads, ld = 3 * d;
+    const int lane = threadIdx.x & 31, h = lane / LPH;
+    const float rs = 0.17677669529663688f;  // 1 / sqrt(32)
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+        const int2 e = list[i];
+        const int r = e.x, p = e.y;
+        const int c = ch.row_cfg[r], b = ch.cfg_sample[c];
+        const int rb = ch.cfg_row[ch.cfg_off[b]], rc = ch.cfg_row[c];
+        const int* ub = uid + rb;
+        const int* uc = uid + rc;
+        float q[PER], o[PER], acc[PER];
+        ld_split<PER>(qkv + (size_t)ub[p] * ld + lane * PER, lo_off, q);
+#pragma unroll
+        for (int t = 0; t < PER; t += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(O + (size_t)(rb + p) * d + lane * PER + t);
+            o[t] = x.x; o[t + 1] = x.y; o[t + 2] = x.z; o[t + 3] = x.w;
+            acc[t] = acc[t + 1] = acc[t + 2] = acc[t + 3] = 0.f;
+        }
+        const float2 ml = bstat[((size_t)b * ch.N + p) * H + h];  // (maximum scaled score, sum)
+        float sum_s = 0.f, sum_c = 0.f;
+        const int nd = min(dcnt[c], INC_MAX_KEYS);
+        const short* dp = dpos + (size_t)c * INC_MAX_KEYS;
+        for (int k = 0; k < nd; ++k) {
+            const int kp = dp[k];
+            if (kp >= p) break;  // ascending: the rest lie after the row
+            float ks[PER], kc[PER];
+            ld_split<PER>(qkv + (size_t)ub[kp] * ld + d + lane * PER, lo_off, ks);
+            ld_split<PER>(qkv + (size_t)uc[kp] * ld + d + lane * PER, lo_off, kc);
+            float ss = 0.f, scv = 0.f;
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                ss = fmaf(q[t], ks[t], ss);
+                scv = fmaf(q[t], kc[t], scv);
+            }
+#pragma unroll
+            for (int w = LPH / 2; w > 0; w >>= 1) {
+                ss += __shfl_xor_sync(0xffffffffu, ss, w);
+                scv += __shfl_xor_sync(0xffffffffu, scv, w);
+            }
+            const float es = __expf(ss * rs - ml.x), ec = __expf(scv * rs - ml.x);
+            float vs[PER], vc[PER];
+            ld_split<PER>(qkv + (size_t)ub[kp] * ld + 2 * d + lane * PER, lo_off, vs);
+            ld_split<PER>(qkv + (size_t)uc[kp] * ld + 2 * d + lane * PER, lo_off, vc);
+#pragma unroll
+            for (int t = 0; t < PER; ++t) acc[t] = fmaf(ec, vc[t] - o[t], fmaf(-es, vs[t] - o[t], acc[t]));
+            sum_s += es;
+            sum_c += ec;
+        }
+        const float inv = 1.f / (ml.y - sum_s + sum_c);
+#pragma unroll
+        for (int t = 0; t < PER; t += 4)
+            *reinterpret_cast<float4*>(O + (size_t)r * d + lane * PER + t) =
+                make_float4(fmaf(acc[t], inv, o[t]), fmaf(acc[t + 1], inv, o[t + 1]), fmaf(acc[t + 2], inv, o[t + 2]),
+                            fmaf(acc[t + 3], inv, o[t + 3]));
+    }
+}
+
+cudaError_t launch_inc_exact_delta(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, size_t lo_off, float* O,
+                                   const float2* bstat, const short* dpos, const int* dcnt, const int2* list,
+                                   const int* n_list_dev, cudaStream_t st, int grid) {
+    if (ch.d / ch.heads != 32) return cudaErrorInvalidValue;
+    if (ch.d == 256)
+        k_inc_exact_delta<8><<<grid, 256, 0, st>>>(ch, uid, qkv, lo_off, O, bstat, dpos, dcnt, list, n_list_dev);
+    else if (ch.d == 128)
+        k_inc_exact_delta<4><<<grid, 256, 0, st>>>(ch, uid, qkv, lo_off, O, bstat, dpos, dcnt, list, n_list_dev);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 // ---- connected configurations: correction of the unchanged-query rows ----------------
@@ -1341,7 +1447,7 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                                const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
                                const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
                                const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int split,
-                               int* status, long long* stats, cudaStream_t st, int grid) {
+                               int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid) {
     if (!incremental_supported(ch.d, ch.heads)) return cudaErrorInvalidValue;
     const int kb = inc_patch_keys(ch.d);
     const size_t smem = inc_patch_smem(ch.d, ch.N);
@@ -1370,8 +1476,8 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                 granted_tc = smem_tc;
             }
             k_inc_patch_tc<<<grid, 256, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows,
-                                                      act_off, rc_rows, rc_cnt, list_tc, dpos, dcnt, split, cols,
-                                                      status, stats);
+                                                      act_off, rc_rows, rc_cnt, list_tc, dpos, dcnt, split, ex_rows,
+                                                      cols, status, stats);
             return cudaGetLastError();
         }
     }
@@ -1425,16 +1531,17 @@ cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, 
                              const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int* status,
                              long long* stats, cudaStream_t st, int grid) {
     return launch_inc_patch_t<float>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off, rc_rows,
-                                     rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, 0, status, stats, st, grid);
+                                     rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, 0, nullptr, status, stats, st,
+                                     grid);
 }
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                              const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
                              int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
                              const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
-                             int split, int* status, long long* stats, cudaStream_t st, int grid) {
+                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid) {
     return launch_inc_patch_t<__nv_bfloat16>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off,
-                                             rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, split, status,
-                                             stats, st, grid);
+                                             rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, split, ex_rows,
+                                             status, stats, st, grid);
 }
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
                                  const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,

@@ -68,11 +68,11 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_HALF, S_COUNT };
+             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_HALF, S_EXACT, S_COUNT };
 const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
                                     "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward",
                                     "inc_certificate", "inc_classify", "inc_patch", "inc_recompute",
-                                    "inc_recompute_whole", "half_block"};
+                                    "inc_recompute_whole", "half_block", "inc_exact_delta"};
 static_assert(S_COUNT <= VQNQS_MAX_STAGES, "stage table larger than the ABI's VQNQS_MAX_STAGES");
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
@@ -134,7 +134,7 @@ struct Plan {
     int hash_bits = 0;
     size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, cfg_row, row_cfg, act_cnt, act_off, act_rows,
         uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, bstat, cert,
-        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, total;
+        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, ex_rows, total;
 };
 
 // Workspace layout for chunks of at most S samples, C configurations and R rows.
@@ -189,6 +189,7 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.list_simt = take((size_t)p.Cmax * sizeof(int));
     p.dpos = take((size_t)p.Cmax * INC_MAX_KEYS * sizeof(short));
     p.dcnt = take((size_t)p.Cmax * sizeof(int));
+    p.ex_rows = take((size_t)p.Rmax * sizeof(int2));  // split operands: rows for the exact correction
     p.total = o;
     return p;
 }
@@ -428,9 +429,15 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             if (tc_inc) {
                 // tensor cores: rows patched, their changed rows recomputed against the sample's keys,
                 // configurations with many changes recomputed whole
+                int2* ex_rows = at<int2>(ws, P.ex_rows);
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
                                                       vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
-                                                      dcnt, 1, split ? 1 : 0, ctx->status, ctx->stats, st, g_cfg));
+                                                      dcnt, 1, split ? 1 : 0, ex_rows, ctx->status, ctx->stats, st,
+                                                      g_cfg));
+                if (split)
+                    VQ_STAGE(S_EXACT, 1, launch_inc_exact_delta(ch, uid_cur, qkv16, qkv_lo, O, bstat, dpos, dcnt,
+                                                                ex_rows, counters + CNT_EX, st,
+                                                                grid_for(ctx, P.Rmax, 8, 8)));
                 VQ_STAGE(S_RECOMP, 1, launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos,
                                                                dcnt, ctx->status, ctx->stats, st, ctx->num_sms,
                                                                qkv_lo));
@@ -441,7 +448,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
             } else if (bf16) {
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
                                                       vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
-                                                      dcnt, 0, 0, ctx->status, ctx->stats, st, g_cfg));
+                                                      dcnt, 0, 0, nullptr, ctx->status, ctx->stats, st, g_cfg));
                 VQ_STAGE(S_RECOMP, 1, launch_inc_attention(ch, uid_cur, qkv16, O, act_off, rc_rows, rc_cnt, 0,
                                                            ctx->stats, st, ctx->num_sms));
             } else {

@@ -25,7 +25,8 @@ enum {
     CNT_TCW = 6,    //   work counters of the two patch kernels (next list entry)
     CNT_SCW = 7,
     CNT_U0 = 8,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
-    CNT_SLOTS = 8 + VQNQS_MAX_LAYERS + 2
+    CNT_EX = 8 + VQNQS_MAX_LAYERS + 2,  // split operands: patched rows listed for the exact correction
+    CNT_SLOTS = CNT_EX + 1
 };
 
 // Slots of the context's persistent device statistics (int64).
@@ -298,7 +299,8 @@ cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codeb
                              const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
                              int* counters, int* rc_cnt, cudaStream_t st);
 // wd: the layer's ||W_a - W_c|| table; split (BF16 qkv only): the Q/K/V in qkv are the hi plane of split
-// operands, and rows the certificate does not settle are recomputed instead of searched with o + delta
+// operands, and rows the certificate does not settle are listed in ex_rows (count in CNT_EX) for
+// launch_inc_exact_delta instead of being written with the BF16 correction
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, float* O, const float2* bstat,
                              const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
                              const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
@@ -308,7 +310,12 @@ cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat1
                              const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
                              int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
                              const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
-                             int split, int* status, long long* stats, cudaStream_t st, int grid);
+                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid);
+// split operands: o + delta of the listed rows (row, position) from the hi + lo planes of Q/K/V in FP32
+// (one warp per row; d_model in {128, 256}, d_model / heads = 32); n_list_dev[0] rows
+cudaError_t launch_inc_exact_delta(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, size_t lo_off, float* O,
+                                   const float2* bstat, const short* dpos, const int* dcnt, const int2* list,
+                                   const int* n_list_dev, cudaStream_t st, int grid);
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
                                  const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,
                                  int num_sms);

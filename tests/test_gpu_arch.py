@@ -9,11 +9,13 @@ half-block of Table 1's networks.
 * BF16 GEMMs with H = 2 at 8x8, d_model 128: as close to FP32 as the
   one-head BF16 path.
 * Table 1's bandwidths at 16x16 (three blocks, d_model 256, 8 attention heads,
-  64 codes per head; H = 1, 2, 4 = 6, 12, 24 bits): oracle parity on sampled
-  configurations and the unique-row fraction and FLOP reduction per bandwidth.
+  64 codes per head; H = 1, 2, 4 = 6, 12, 24 bits): oracle parity on 16 samples
+  (stored FP64 oracle values, tests/golden/eloc_arch16_h*.txt) and the
+  unique-row fraction and FLOP reduction per bandwidth.
 * The final half-block, FP32 plain and reuse (one and two quantizer heads)
   against the oracle, BF16 against FP32, and Table 1's network (three blocks,
-  half-block, two heads of 64 codes) at 16x16 on sampled configurations.
+  half-block, two heads of 64 codes) at 16x16 on 16 samples against stored
+  oracle values.
 * The entry points defined for one head and no half-block refuse the variants.
 """
 import numpy as np
@@ -21,6 +23,7 @@ import pytest
 import torch
 
 import synthetic_inputs as si
+from golden_values import check_fp32_against_golden, eloc_variant
 from oracle import hamiltonian, model
 
 pytestmark = pytest.mark.gpu
@@ -105,8 +108,8 @@ def test_table1_bandwidths_16x16():
         uniq = [u / rows for u in st["unique_rows"][1:]]
         print(f"H = {H} ({H * 6} bits): unique-row fraction per layer {', '.join(f'{u:.4f}' for u in uniq)}; "
               f"FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
-        P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H)
-        check(P, spins[:2], e[:2], L, max_miss=0.5)
+        want, gap = eloc_variant(f"arch16_h{H}")
+        check_fp32_against_golden(rel_err(e[:len(want)], want, N), gap)
         assert st["device_status"] == 0
 
 
@@ -174,8 +177,8 @@ def test_table1_network_16x16_sampled():
     e = m.local_energy(s, REUSE).cpu().numpy()
     st = m.stats()
     print(f"Table 1 network, 12 bits: quantized-ops FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
-    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True)
-    check(P, spins[:2], e[:2], L, max_miss=0.5)
+    want, gap = eloc_variant("table1_12b")
+    check_fp32_against_golden(rel_err(e[:len(want)], want, N), gap)
     e16 = m.local_energy(s, REUSE | BF16).cpu().numpy()
     assert np.median(rel_err(e16, e, N)) <= 1e-2
     assert m.stats()["device_status"] == 0
@@ -246,8 +249,8 @@ def test_all_variants_16x16_sampled():
     e = m.local_energy(s, REUSE).cpu().numpy()
     st = m.stats()
     print(f"G = 4, 12 bits, half-block: quantized-ops FLOP reduction {st['flops_full'] / st['flops_done']:.2f}")
-    P = model.parse_blob(w, N, layers, d, heads, K, vq_heads=H, half_block=True, token_group=G)
-    check(P, spins[:2], e[:2], L, max_miss=0.5)
+    want, gap = eloc_variant("table1_12b_g4")
+    check_fp32_against_golden(rel_err(e[:len(want)], want, N), gap)
     e16 = m.local_energy(s, REUSE | BF16).cpu().numpy()
     assert np.median(rel_err(e16, e, N)) <= 1e-2
     assert m.stats()["device_status"] == 0

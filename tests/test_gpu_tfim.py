@@ -70,9 +70,11 @@ def test_chain64_fp32_and_bf16():
 def test_chain384_paper_size_sampled():
     """Sec. 4's largest chain: 384 sites, one block of width 256 with 8 heads."""
     from paper_2212_11296_gb300 import BF16, INCREMENTAL, REUSE
-    m, P, spins, s = make(384, False, 1.0, 1.0, 1, 256, 8, 64, 8)
+    from golden_values import check_fp32_against_golden, eloc_variant
+    m, P, spins, s = make(384, False, 1.0, 1.0, 1, 256, 8, 64, 16)
     e = m.local_energy(s, REUSE).cpu().numpy()
-    check(P, spins[:2], e[:2], False, 1.0, 1.0, max_miss=0.5)
+    want, gap = eloc_variant("chain384")  # stored FP64 oracle values of these 16 chains
+    check_fp32_against_golden(rel_err(e, want, 384), gap)
     eb = m.local_energy(s, REUSE | BF16 | INCREMENTAL).cpu().numpy()
     d = rel_err(eb, e.astype(np.float64), 384)
     print(f"384 sites, BF16 incremental vs FP32 reuse: median {np.median(d):.2e} max {d.max():.2e}")
