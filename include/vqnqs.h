@@ -154,11 +154,15 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
  *               d_model / vq_heads values, segment h goes to its nearest
  *               codeword among the K of its own codebook, and the quantized
  *               vector is the concatenation.  K is the codewords per head;
- *               vq_heads in 1..8, d_model / vq_heads a multiple of 8,
- *               vq_heads * ceil(log2 K) <= 31 (a row's code packs c_h in bits
- *               [h * b, (h + 1) * b), b = ceil(log2 K)), so 64 codes allow up
- *               to 5 heads.  Each layer's codebook block (K * d_model floats)
- *               is read as [vq_heads][K][d_model / vq_heads].
+ *               vq_heads in 1..8, d_model / vq_heads a multiple of 8.  A row's
+ *               code packs c_h in bits [h * b, (h + 1) * b), b = ceil(log2 K),
+ *               32 / b heads per 32-bit word, at most two words (64 codes: up
+ *               to 5 heads in one word, Table 1's 8 heads = 48 bits in two;
+ *               two-word codes are given a dense id per chunk before the
+ *               per-location deduplication, and vqnqs_codes /
+ *               vqnqs_local_energy_codes refuse them).  Each layer's codebook
+ *               block (K * d_model floats) is read as
+ *               [vq_heads][K][d_model / vq_heads].
  *   token_group G in {1, 2, 4}: each token is a group of G consecutive spins
  *               (Sec. 3.1 tokens as particle groups): the token at position t
  *               is the value of group t - 1, sum_k s[(t-1) G + k] 2^k, with
@@ -308,7 +312,12 @@ int vqnqs_local_energy_codes(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, fl
  *   dev_seeds   DEVICE float [B] or NULL;  dev_e_loc  DEVICE float [B] or NULL (not both)
  *   dev_O       DEVICE float [B][P] or NULL (per-sample gradients)
  *   dev_grad    DEVICE float [P] or NULL (at least one of O, grad)
- *   flags       accepted for symmetry; the backward always computes in FP32
+ *   flags       VQNQS_BF16: the summed gradient's contractions (dX = dY W^T, dW = X^T dY
+ *               and the recomputed forward GEMMs) run on the tensor cores with split
+ *               operands (hi + lo BF16 pairs, three MMAs, FP32 accumulation) when
+ *               d_model % 64 == 0, K % 64 == 0, the chunk's rows are a multiple of 8,
+ *               one quantizer head, no half-block and single-spin tokens; the per-sample
+ *               O path, the attention backward and the row-wise steps stay FP32
  * Activations are recomputed layer by layer from the stored residual stream.
  * Scratch: vqnqs_grad_workspace_bytes(ctx, B, chunk_samples) bytes. */
 size_t vqnqs_grad_workspace_bytes(const vqnqs_ctx* ctx, int B, int chunk_samples);
@@ -452,7 +461,8 @@ int vqnqs_reset_stats(vqnqs_ctx* ctx);
  * Stage names: config, active_rows, embed, ln1, qkv_gemm, attention, vq_argmin, dedupe,
  * post_ln, mlp_up, mlp_down, head, eloc, mean_var, backward, inc_certificate,
  * inc_classify, inc_patch, inc_recompute, inc_recompute_whole, half_block,
- * inc_exact_delta. */
+ * inc_exact_delta, bwd_recompute, bwd_gemm, bwd_attention, bwd_rowwise (the last
+ * four inside backward). */
 typedef struct vqnqs_stage_time {
     char name[24];
     int64_t calls;     /* times the stage ran */

@@ -374,8 +374,9 @@ class VQNQS:
 
     def grad_log_psi(self, spins: torch.Tensor, seeds: torch.Tensor | None = None,
                      e_loc: torch.Tensor | None = None, want_O: bool = False, want_grad: bool = True,
-                     chunk_samples: int = 0, stream=None):
-        """(O [B, P] or None, grad [P] or None); see vqnqs_grad_log_psi."""
+                     chunk_samples: int = 0, flags: int = 0, stream=None):
+        """(O [B, P] or None, grad [P] or None); see vqnqs_grad_log_psi (flags: BF16 puts the summed
+        gradient's contractions on the tensor cores with split operands)."""
         _check_dev(spins, torch.uint8, "spins")
         B = spins.shape[0]
         P = self.num_params
@@ -388,13 +389,14 @@ class VQNQS:
         ws = torch.empty(int(lib().vqnqs_grad_workspace_bytes(self._h, B, int(chunk_samples))), dtype=torch.uint8,
                          device=dev)
         ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else 0)
-        self._check(lib().vqnqs_grad_log_psi(self._h, B, ptr(spins), ptr(seeds), ptr(e_loc), ptr(O), ptr(grad), 0,
+        self._check(lib().vqnqs_grad_log_psi(self._h, B, ptr(spins), ptr(seeds), ptr(e_loc), ptr(O), ptr(grad),
+                                             int(flags),
                                              ptr(ws), ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
                     "vqnqs_grad_log_psi")
         return O, grad
 
     def energy_grad_partials(self, spins: torch.Tensor, e_loc: torch.Tensor, chunk_samples: int = 0,
-                             stream=None) -> torch.Tensor:
+                             flags: int = 0, stream=None) -> torch.Tensor:
         """This rank's FP64 partial sums [2P + 3] of the sharded energy gradient
         (sum E O, sum O, sum E, sum E^2, n; see vqnqs_energy_grad_partials)."""
         _check_dev(spins, torch.uint8, "spins")
@@ -406,7 +408,7 @@ class VQNQS:
                          dtype=torch.uint8, device=spins.device)
         self._check(lib().vqnqs_energy_grad_partials(self._h, B, ctypes.c_void_p(spins.data_ptr()),
                                                      ctypes.c_void_p(e_loc.data_ptr()), ctypes.c_void_p(part.data_ptr()),
-                                                     0, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                     int(flags), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                                      ctypes.c_void_p(_stream_ptr(stream))),
                     "vqnqs_energy_grad_partials")
         return part

@@ -132,6 +132,51 @@ __global__ void k_pairs_lookup(int R, const int* __restrict__ uid, const int* __
     }
 }
 
+// ---- two-word codes: a dense code id per distinct (hi, lo) pair ------------------
+// Over the listed rows (act_rows[0 .. counters[a_slot])): insert every pair, then
+// replace the row's lo word by the pair's id; tab_hi / tab_lo [id] give the words back.
+__global__ void k_words_insert(const int* __restrict__ counters, int a_slot, const int* __restrict__ rows,
+                               const int* __restrict__ lo, const int* __restrict__ hi,
+                               unsigned long long* __restrict__ keys, int* __restrict__ vals, unsigned long long mask,
+                               int* __restrict__ count, int* __restrict__ tab_hi, int* __restrict__ tab_lo,
+                               int* __restrict__ status) {
+    const int n = counters[a_slot];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = rows[i];
+        if (!hash_insert(keys, vals, mask, hi[r], lo[r], count, tab_hi, tab_lo)) atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
+    }
+}
+__global__ void k_words_lookup(const int* __restrict__ counters, int a_slot, const int* __restrict__ rows,
+                               int* __restrict__ lo, const int* __restrict__ hi,
+                               const unsigned long long* __restrict__ keys, const int* __restrict__ vals,
+                               unsigned long long mask, int* __restrict__ status) {
+    const int n = counters[a_slot];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = rows[i];
+        int id = hash_lookup(keys, vals, mask, hi[r], lo[r]);
+        if (id < 0) {
+            atomicOr(status, VQNQS_DEV_HASH_OVERFLOW);
+            id = 0;
+        }
+        lo[r] = id;
+    }
+}
+
+cudaError_t launch_code_words(int* counters, int a_slot, int cnt_slot, const int* rows, int Rmax, int* lo,
+                              const int* hi, unsigned long long* keys, int* vals, int hash_bits, int* tab_hi,
+                              int* tab_lo, int* status, cudaStream_t st, int num_sms) {
+    const size_t H = (size_t)1 << hash_bits;
+    const unsigned long long mask = (unsigned long long)H - 1ULL;
+    int grid = (Rmax + 255) / 256;
+    if (grid > 8 * num_sms) grid = 8 * num_sms;
+    if (grid < 1) grid = 1;
+    k_hash_clear<<<8 * num_sms, 256, 0, st>>>(keys, H, counters, cnt_slot);
+    k_words_insert<<<grid, 256, 0, st>>>(counters, a_slot, rows, lo, hi, keys, vals, mask, &counters[cnt_slot], tab_hi,
+                                         tab_lo, status);
+    k_words_lookup<<<grid, 256, 0, st>>>(counters, a_slot, rows, lo, hi, keys, vals, mask, status);
+    return cudaGetLastError();
+}
+
 __global__ void k_identity_keys(const int* __restrict__ uid_cur, const int* __restrict__ code,
                                 int* __restrict__ counters, int u_slot_next, int* __restrict__ uid_next,
                                 int* __restrict__ rep_uid, int* __restrict__ rep_code) {

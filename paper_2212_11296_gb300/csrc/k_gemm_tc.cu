@@ -438,11 +438,16 @@ int tc_pick_bn(int N) {
 }
 
 cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows) {
+    return make_tmap_bf16_strided(map, base, rows, cols, cols, box_rows);
+}
+
+cudaError_t make_tmap_bf16_strided(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
+                                   int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || (cols * 2) % 16) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld * 2) % 16 || cols > ld) return cudaErrorInvalidValue;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
@@ -453,7 +458,7 @@ cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, i
 
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms, int BN, bool split) {
+                           int* status, cudaStream_t st, int num_sms, int BN, bool split, long long a_inner) {
     if (BN <= 0) BN = tc_pick_bn(N);
     if (!BN || N % BN || K % TC_BK || K <= 0 || epi < 0 || epi > 4 || (epi == 2 && !R)) return cudaErrorInvalidValue;
     if (Arows < 1) return cudaSuccess;  // no rows to compute
@@ -462,7 +467,9 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
     const int a_lo_row = split ? (int)Arows : 0;
     const int c_lo_row = split && epi < 2 ? (int)Arows : 0;
     CUtensorMap ta, tcm, trm;
-    cudaError_t e = make_tmap_bf16(&ta, A, split ? 2 * Arows : Arows, K, TC_BM);
+    // a_inner: A's stored row length when it is shorter than K (K blocks past it read zeros)
+    cudaError_t e = a_inner > 0 ? make_tmap_bf16_strided(&ta, A, split ? 2 * Arows : Arows, a_inner, a_inner, TC_BM)
+                                : make_tmap_bf16(&ta, A, split ? 2 * Arows : Arows, K, TC_BM);
     if (e != cudaSuccess) return e;
     e = make_tmap_out(&tcm, Cout, c_lo_row ? 2 * Arows : Arows, N, epi >= 2);
     if (e != cudaSuccess) return e;

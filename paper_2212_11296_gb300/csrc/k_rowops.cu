@@ -54,25 +54,31 @@ __global__ void k_layernorm(const float* __restrict__ X, const int* __restrict__
 // y = x[rep_uid] + T[rep_code]  (T = codebook @ W_o + b_o), then A = LN2(y).
 // With H quantizer heads the code packs c_h in bits [h * bits, (h + 1) * bits)
 // and T holds one table per head (b_o in head 0's): y = x + sum_h T_h[c_h].
+// Two-word codes (tab_lo given): rep_code is a code id whose words are
+// tab_lo[id] (heads 0 .. hpw-1) and tab_hi[id] (the rest), hpw = 32 / bits.
 template <int PER>
 __global__ void k_residual_vq_ln(const float* __restrict__ X, const int* __restrict__ rep_uid,
                                  const int* __restrict__ rep_code, const float* __restrict__ T,
                                  const int* __restrict__ counters, int u_slot, const float* __restrict__ g,
                                  const float* __restrict__ b, int d, float* __restrict__ Y,
                                  float* __restrict__ A_f32, __nv_bfloat16* __restrict__ A_bf16, int vq_heads, int K,
-                                 int bits, size_t lo_off) {
+                                 int bits, size_t lo_off, const int* __restrict__ tab_lo,
+                                 const int* __restrict__ tab_hi) {
     const int U = counters[u_slot];
     const int mask = vq_heads == 1 ? -1 : (1 << bits) - 1;
+    const int hpw = bits > 0 ? 32 / bits : 1;
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < U; u += gridDim.x * wpb) {
         const float* x = X + (size_t)rep_uid[u] * d;
-        const int code = rep_code[u];
+        const int code = tab_lo ? tab_lo[rep_code[u]] : rep_code[u];
+        const int code_hi = tab_lo ? tab_hi[rep_code[u]] : 0;
         const float* t = T + (size_t)(code & mask) * d;
         float y[PER], a[PER];
 #pragma unroll
         for (int i = 0; i < PER; ++i) y[i] = t[lane + 32 * i];
         for (int h = 1; h < vq_heads; ++h) {
-            const float* th = T + ((size_t)h * K + ((code >> (h * bits)) & mask)) * d;
+            const int wd = h / hpw, f = h - wd * hpw;
+            const float* th = T + ((size_t)h * K + (((wd ? code_hi : code) >> (f * bits)) & mask)) * d;
 #pragma unroll
             for (int i = 0; i < PER; ++i) y[i] += th[lane + 32 * i];
         }
@@ -134,6 +140,17 @@ __global__ void k_transpose_bf16(const float* __restrict__ W, int rows, int cols
         }
 }
 
+// dst[r][c] = bf16(src[r][c]) (hi plane), dst[plane_rows + r][c] = bf16(src[r][c] - hi) (lo plane)
+__global__ void k_split_planes(const float* __restrict__ src, long long n, int cols, __nv_bfloat16* __restrict__ dst,
+                               long long lo_off) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float x = src[i];
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        dst[i] = h;
+        dst[lo_off + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
 // every d_model the context accepts: 32 .. 1024 in steps of 32
 #define VQ_DISPATCH_PER(d, KERNEL, ...)                                 \
     switch ((d) / 32) {                                                 \
@@ -181,9 +198,9 @@ cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, co
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
                                   float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads, int K,
-                                  int bits, size_t lo_off) {
+                                  int bits, size_t lo_off, const int* tab_lo, const int* tab_hi) {
     VQ_DISPATCH_PER(d, k_residual_vq_ln, X, rep_uid, rep_code, T, counters, u_slot, g, b, d, Y, A_f32, A_bf16,
-                    vq_heads, K, bits, lo_off);
+                    vq_heads, K, bits, lo_off, tab_lo, tab_hi);
     return cudaGetLastError();
 }
 
@@ -192,6 +209,15 @@ cudaError_t launch_table_T(const float* codebook, const float* w_o, const float*
     if (vq_heads < 1 || d % vq_heads) return cudaErrorInvalidValue;
     int grid = vq_heads * K < 1024 ? vq_heads * K : 1024;
     k_table_T<<<grid, 256, d * sizeof(float), st>>>(codebook, w_o, b_o, K, d, vq_heads, T, cnorm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_planes(const float* src, long long rows, int cols, __nv_bfloat16* dst, long long plane_rows,
+                                cudaStream_t st, int cap) {
+    const long long n = rows * cols;
+    long long g = (n + 255) / 256;
+    if (g > cap) g = cap;
+    k_split_planes<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(src, n, cols, dst, plane_rows * cols);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,9 @@
 //
 // With H quantizer heads each segment o_h (d / H values, row stride d) is
 // assigned against its own codebook by one launch, and the packed code holds
-// c_h in bits [h * bits, (h + 1) * bits).
+// c_h in bits [h * bits, (h + 1) * bits).  Codes wider than one word (Table 1's
+// 8 heads of 64 codes: 48 bits) take two: head h goes to word h / hpw at bit
+// (h % hpw) * bits, hpw = 32 / bits heads per word.
 //
 // The o . W_j products are a [rows x d] x [d x K] contraction tiled like the
 // FP32 GEMM (128 rows x 128 codewords per pass, 8x8 per thread); the epilogue
@@ -175,16 +177,20 @@ cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act
 
 cudaError_t launch_vq_argmin_heads(const float* O, const int* counters, const int* act_rows, const float* codebook,
                                    const float* cnorm, int K, int d, int vq_heads, int bits, int* code,
-                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot) {
+                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot,
+                                   int* code_hi) {
     const int dq = d / vq_heads;
-    if (d % vq_heads || dq % VQ_BK) return cudaErrorInvalidValue;
+    if (d % vq_heads || dq % VQ_BK || bits < 1) return cudaErrorInvalidValue;
+    const int hpw = 32 / bits;  // heads per code word
+    if (vq_heads > hpw && !code_hi) return cudaErrorInvalidValue;
     int tiles = (Rmax + VQ_BM - 1) / VQ_BM;
     int grid = tiles < 2 * num_sms ? tiles : 2 * num_sms;
     if (grid < 1) grid = 1;
-    for (int h = 0; h < vq_heads; ++h) {  // segment h: its own codebook, its bits of the packed code
+    for (int h = 0; h < vq_heads; ++h) {  // segment h: its own codebook, its bits of its code word
+        const int w = h / hpw, f = h - w * hpw;
         k_vq_argmin<<<grid, VQ_THREADS, 0, st>>>(O + (size_t)h * dq, d, counters, act_rows,
-                                                 codebook + (size_t)h * K * dq, cnorm + (size_t)h * K, K, dq, code,
-                                                 h * bits, h > 0 ? 1 : 0, near_ties, a_slot);
+                                                 codebook + (size_t)h * K * dq, cnorm + (size_t)h * K, K, dq,
+                                                 w ? code_hi : code, f * bits, f > 0 ? 1 : 0, near_ties, a_slot);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -15,6 +15,7 @@ using namespace vq;
 struct vqnqs_ctx {
     int L = 0, N = 0, periodic = 0, layers = 0, d = 0, heads = 0, K = 0, nb = 0;
     int vq_heads = 1, vq_bits = 0;  // quantizer heads; bits of one head's field in a packed code
+    int vq_words = 1;               // 32-bit words of a code (2 when the heads need more than 32 bits)
     int half_block = 0;             // final attention-only half-block (its weights in hw)
     int G = 1, P = 0;               // spins per token; positions (rows) per sample = N / G
     int model = MODEL_HEISENBERG;
@@ -39,6 +40,9 @@ struct vqnqs_ctx {
     int bn[3] = {0, 0, 0};           // output tile width of the QKV, MLP up, MLP down GEMMs
     int lp_scratch_cap = 65536;
     long long* stats = nullptr;    // ST_* slots
+    bool bwd_tc = false;           // the backward's contractions can run on the tensor cores (split operands)
+    int* dims = nullptr;           // device ints {d, 3d, 4d, K}: row counts of the backward's weight-gradient GEMMs
+    float* zeros = nullptr;        // device zeros [max(4d, K)]: bias of those GEMMs
     std::vector<void*> owned;      // device allocations freed by destroy
     std::string err;
     // stage timing (vqnqs_profile_*) and launch counting
@@ -68,11 +72,13 @@ int fail(vqnqs_ctx* c, int code, const std::string& msg) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 enum Stage { S_CONFIG, S_ACTIVE, S_EMBED, S_LN1, S_QKV, S_ATTN, S_VQ, S_DEDUPE, S_POSTLN, S_MLP1, S_MLP2, S_HEAD, S_ELOC,
-             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_HALF, S_EXACT, S_COUNT };
+             S_MEANVAR, S_BACKWARD, S_CERT, S_CLASSIFY, S_PATCH, S_RECOMP, S_RECOMP_WHOLE, S_HALF, S_EXACT,
+             S_BWD_RECOMP, S_BWD_GEMM, S_BWD_ATTN, S_BWD_ROWS, S_COUNT };
 const char* kStageNames[S_COUNT] = {"config", "active_rows", "embed", "ln1", "qkv_gemm", "attention", "vq_argmin", "dedupe",
                                     "post_ln", "mlp_up", "mlp_down", "head", "eloc", "mean_var", "backward",
                                     "inc_certificate", "inc_classify", "inc_patch", "inc_recompute",
-                                    "inc_recompute_whole", "half_block", "inc_exact_delta"};
+                                    "inc_recompute_whole", "half_block", "inc_exact_delta", "bwd_recompute",
+                                    "bwd_gemm", "bwd_attention", "bwd_rowwise"};
 static_assert(S_COUNT <= VQNQS_MAX_STAGES, "stage table larger than the ABI's VQNQS_MAX_STAGES");
 
 cudaEvent_t take_event(vqnqs_ctx* c) {
@@ -134,7 +140,7 @@ struct Plan {
     int hash_bits = 0;
     size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, cfg_row, row_cfg, act_cnt, act_off, act_rows,
         uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, bstat, cert,
-        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, ex_rows, total;
+        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, ex_rows, code_hi, tab_lo, tab_hi, total;
 };
 
 // Workspace layout for chunks of at most S samples, C configurations and R rows.
@@ -190,6 +196,11 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.dpos = take((size_t)p.Cmax * INC_MAX_KEYS * sizeof(short));
     p.dcnt = take((size_t)p.Cmax * sizeof(int));
     p.ex_rows = take((size_t)p.Rmax * sizeof(int2));  // split operands: rows for the exact correction
+    // two-word codes: the high words, and the words of each code id
+    const size_t wbytes = c->vq_words > 1 ? (size_t)p.Rmax * sizeof(int) : 0;
+    p.code_hi = take(wbytes);
+    p.tab_lo = take(wbytes);
+    p.tab_hi = take(wbytes);
     p.total = o;
     return p;
 }
@@ -245,6 +256,15 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
             VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
             VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
         }
+        if (ctx->bwd_tc) {  // the backward's split weight planes
+            const int cap = ctx->num_sms * 16;
+            VQ_CK(launch_split_planes(w.w_qkv, d, 3 * d, w.wqkv_s, d, st, cap));
+            VQ_CK(launch_split_planes(w.w_1, d, 4 * d, w.w1_s, d, st, cap));
+            VQ_CK(launch_split_planes(w.w_2, 4 * d, d, w.w2_s, 4 * d, st, cap));
+            VQ_CK(launch_split_planes(w.w_o, d, d, w.wo_s, d, st, cap));
+            VQ_CK(launch_split_planes(w.codebook, K, d, w.cb_s, K, st, cap));
+            VQ_CK(launch_transpose_bf16(w.codebook, K, d, w.cbT_s, st, true));
+        }
     }
     if (ctx->half_block) {
         VQ_CK(launch_transpose_bf16(ctx->hw.w_qkv, d, 3 * d, ctx->hw.wqkv_t, st));
@@ -261,6 +281,18 @@ int build_weight_tmaps(vqnqs_ctx* ctx) {
         VQ_CK(make_tmap_bf16(&w.tm_wqkv, w.wqkv_t, 2 * 3 * d, (int)d, ctx->bn[0]));
         VQ_CK(make_tmap_bf16(&w.tm_w1, w.w1_t, 2 * 4 * d, (int)d, ctx->bn[1]));
         VQ_CK(make_tmap_bf16(&w.tm_w2, w.w2_t, 2 * d, 4 * (int)d, ctx->bn[2]));
+    }
+    if (ctx->bwd_tc) {  // B operands of the backward's dX = dY W^T: box rows = the output tile width
+        const int K = ctx->K;
+        for (int l = 0; l < ctx->layers; ++l) {
+            LayerW& w = ctx->lw[l];
+            VQ_CK(make_tmap_bf16(&w.tm_wqkv_s, w.wqkv_s, 2 * d, 3 * (int)d, tc_pick_bn((int)d)));
+            VQ_CK(make_tmap_bf16(&w.tm_w1_s, w.w1_s, 2 * d, 4 * (int)d, tc_pick_bn((int)d)));
+            VQ_CK(make_tmap_bf16(&w.tm_w2_s, w.w2_s, 8 * d, (int)d, tc_pick_bn(4 * (int)d)));
+            VQ_CK(make_tmap_bf16(&w.tm_wo_s, w.wo_s, 2 * d, (int)d, tc_pick_bn((int)d)));
+            VQ_CK(make_tmap_bf16(&w.tm_cb_s, w.cb_s, 2LL * K, (int)d, tc_pick_bn(K)));
+            VQ_CK(make_tmap_bf16(&w.tm_cbT_s, w.cbT_s, 2 * d, K, tc_pick_bn((int)d)));
+        }
     }
     if (ctx->half_block) {
         VQ_CK(make_tmap_bf16(&ctx->hw.tm_wqkv, ctx->hw.wqkv_t, 3 * d, (int)d, ctx->bn[0]));
@@ -360,6 +392,9 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
     const bool inc = with_bonds && (flags & VQNQS_INCREMENTAL) != 0;
     // split operands: BF16 lo planes after the hi ones (elements) of the LN outputs, Q/K/V and MLP hidden rows
     const bool split = bf16 && (flags & VQNQS_BF16_SPLIT) != 0;
+    // two-word codes: the words of each code id (the residual step decodes the heads' fields)
+    const int* tab_lo = ctx->vq_words > 1 ? at<int>(ws, P.tab_lo) : nullptr;
+    const int* tab_hi = ctx->vq_words > 1 ? at<int>(ws, P.tab_hi) : nullptr;
     const size_t a_lo = split ? (size_t)P.Umax * d : 0;
     const size_t qkv_lo = split ? (size_t)P.Umax * 3 * d : 0;
     int* act_rows = at<int>(ws, P.act_rows);
@@ -461,11 +496,19 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         }
         const int* vq_list = inc ? vq_rows : act_rows;
         const int vq_slot = inc ? CNT_V : CNT_A;
-        if (ctx->vq_heads > 1)  // one search per quantizer head, FP32 on the CUDA cores
+        if (ctx->vq_heads > 1) {  // one search per quantizer head, FP32 on the CUDA cores
+            int* code_hi = ctx->vq_words > 1 ? at<int>(ws, P.code_hi) : nullptr;
             VQ_STAGE(S_VQ, ctx->vq_heads,
                      launch_vq_argmin_heads(O, counters, vq_list, w.codebook, w.cnorm, K, d, ctx->vq_heads,
                                             ctx->vq_bits, code, ctx->stats + ST_NEAR_TIES, Rmax, st, ctx->num_sms,
-                                            vq_slot));
+                                            vq_slot, code_hi));
+            if (code_hi)  // two-word codes: a dense id per distinct code, the dedupe keys on the id
+                VQ_STAGE(S_DEDUPE, 3,
+                         launch_code_words(counters, vq_slot, CNT_CW, vq_list, Rmax, code, code_hi,
+                                           at<unsigned long long>(ws, P.keys), at<int>(ws, P.vals), P.hash_bits,
+                                           at<int>(ws, P.tab_hi), at<int>(ws, P.tab_lo), ctx->status, st,
+                                           ctx->num_sms));
+        }
         else if (bf16 && vq_tc_supported(K, d))
             VQ_STAGE(S_VQ, 1, launch_vq_tc(w.tm_cb_hi, w.tm_cb_lo, O, counters, vq_list, w.cnorm, K, d, code,
                                            ctx->stats + ST_NEAR_TIES, ctx->status, st, ctx->num_sms, Rmax, vq_slot));
@@ -487,7 +530,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         if (bf16) {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, nullptr, A16, st, g_urows, ctx->vq_heads, K,
-                                                        ctx->vq_bits, a_lo));
+                                                        ctx->vq_bits, a_lo, tab_lo, tab_hi));
             // split: the hidden rows' lo plane follows the hi one (Umax rows of 4d, over the dead attention output)
             VQ_STAGE(S_MLP1, 1, launch_gemm_tc(A16, Umax, w.tm_w1, w.b_1, nullptr, Hid16, counters, un, 4 * d, d, 1,
                                                ctx->status, st, ctx->num_sms, ctx->bn[1], split));
@@ -496,7 +539,7 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         } else {
             VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X_cur, rep_uid, rep_code, w.T, counters, un, w.ln2_g, w.ln2_b,
                                                         d, Y, A, nullptr, st, g_urows, ctx->vq_heads, K,
-                                                        ctx->vq_bits));
+                                                        ctx->vq_bits, 0, tab_lo, tab_hi));
             VQ_STAGE(S_MLP1, 1, launch_sgemm(A, w.w_1, w.b_1, nullptr, Hid, counters, un, Umax, 4 * d, d,
                                              EPI_BIAS_GELU, st, ctx->num_sms));
             VQ_STAGE(S_MLP2, 1, launch_sgemm(Hid, w.w_2, w.b_2, Y, X_next, counters, un, Umax, d, 4 * d,
@@ -594,6 +637,8 @@ int run(vqnqs_ctx* ctx, int B, const uint8_t* spins, float* e_loc, double* mean_
     ctx->err.clear();
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
     if (int rc = check_flags(ctx, flags)) return rc;
+    if ((codes || cfg_codes) && ctx->vq_words > 1)
+        return fail(ctx, VQNQS_ERR_ARG, "codes: the quantizer's codes are wider than 32 bits");
     if (B == 0) return VQNQS_OK;
     if (!spins) return fail(ctx, VQNQS_ERR_ARG, "spins is NULL");
     if (with_bonds && !e_loc) return fail(ctx, VQNQS_ERR_ARG, "e_loc is NULL");
@@ -650,7 +695,7 @@ struct GradPlan {
     long long R = 0;
     size_t seeds, counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b,
         rep_uid, rep_code, code, X, dX, dY, A1, Oatt, Y, V, A2, dA, dV, dO, dgam, dbet, Af, QKV, dQKV, H1, G4, dG4, OW,
-        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, total;
+        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, s16, tw, total;
 };
 
 GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
@@ -682,6 +727,10 @@ GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     p.stat = take(R * c->heads * 3 * f);
     p.cfg_row = take((S + 1) * sizeof(int));
     p.row_cfg = take(R * sizeof(int));
+    // tensor-core backward: one activation as split planes [2R][max(4d, K)], and the two transposed
+    // split operands of a weight-gradient GEMM, [2 in][R] and [2 out][R] with in + out <= max(5d, K + d)
+    p.s16 = take(c->bwd_tc ? R * std::max(4 * d, K) * 4 : 0);
+    p.tw = take(c->bwd_tc ? R * std::max(5 * d, K + d) * 4 : 0);
     p.total = o;
     return p;
 }
@@ -694,10 +743,12 @@ int grad_default_chunk(const vqnqs_ctx* c) {
 // One chunk: forward with saved residual streams, then the backward.  OUT is the
 // gradient base of this chunk (grad, or O + first sample * P), groups of G rows.
 int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins, int S, const float* seeds,
-               float* OUT, int G, long long ostride, cudaStream_t st) {
+               float* OUT, int G, long long ostride, cudaStream_t st, int flags) {
     const int N = ctx->N, d = ctx->d, K = ctx->K, Ly = ctx->layers, H = ctx->heads;
     const int R = S * N, ng = R / G;
     const int cap = ctx->num_sms * 16, sms = ctx->num_sms;
+    // the summed gradient's contractions on the tensor cores (split operands) with VQNQS_BF16
+    const bool tcb = ctx->bwd_tc && (flags & VQNQS_BF16) && G == R && R % 8 == 0;
     int* counters = at<int>(ws, P.counters);
     Chunk ch;
     ch.spins = spins; ch.bonds = ctx->bonds_all; ch.g = uniform_groups(ctx, S); ch.s0 = 0; ch.S = S;
@@ -729,32 +780,76 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     VQ_STAGE(S_ACTIVE, 3, launch_active_rows(ch, 0, at<int>(ws, P.act_cnt), at<int>(ws, P.act_off), act, ctx->stats,
                                              st, grid_for(ctx, S, 8, 16)));
     VQ_STAGE(S_EMBED, 1, launch_embed(ch, ctx->tok_emb, ctx->pos_emb, 0, X(0), uid, st, g_rows));
+    __nv_bfloat16* S16 = tcb ? at<__nv_bfloat16>(ws, P.s16) : nullptr;  // split planes of one activation
+    __nv_bfloat16* TW = tcb ? at<__nv_bfloat16>(ws, P.tw) : nullptr;    // transposed split planes
+    const long long Kp = ((long long)R + 63) / 64 * 64;                  // row count rounded to the K step
     for (int l = 0; l < Ly; ++l) {
         const LayerW& w = ctx->lw[l];
-        VQ_STAGE(S_LN1, 1, launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
-        VQ_STAGE(S_QKV, 1, launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
+        if (tcb) {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, S16, st, g_rows,
+                                                (size_t)R * d));
+            VQ_STAGE(S_QKV, 1, launch_gemm_tc(S16, R, w.tm_wqkv, w.b_qkv, nullptr, QKV, counters, CNT_R, 3 * d, d, 3,
+                                              ctx->status, st, sms, ctx->bn[0], true));
+        } else {
+            VQ_STAGE(S_LN1, 1, launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
+            VQ_STAGE(S_QKV, 1, launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS,
+                                            st, sms));
+        }
         VQ_STAGE(S_ATTN, 1, launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
         VQ_STAGE(S_VQ, 1, launch_vq_argmin(Oatt, counters, act, w.codebook, w.cnorm, K, d, code(l),
                                            ctx->stats + ST_NEAR_TIES, R, st, sms));
         VQ_STAGE(S_DEDUPE, 1, launch_dedupe(ch, uid, code(l), CNT_U0 + l + 1, R, nullptr, nullptr, 0, uid_b, rep_uid,
                                             rep_code, 0, ctx->status, st, sms));
-        VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X(l), rep_uid, rep_code, w.T, counters, CNT_R, w.ln2_g, w.ln2_b, d,
-                                                    Y, A2, nullptr, st, g_rows));
-        VQ_STAGE(S_MLP1, 1, launch_sgemm(A2, w.w_1, w.b_1, nullptr, G4, counters, CNT_R, R, 4 * d, d, EPI_BIAS_GELU,
-                                         st, sms));
-        VQ_STAGE(S_MLP2, 1, launch_sgemm(G4, w.w_2, w.b_2, Y, X(l + 1), counters, CNT_R, R, d, 4 * d, EPI_BIAS_RESID,
-                                         st, sms));
+        if (tcb) {  // MLP hidden rows as split planes [2R][4d] in the H1 buffer
+            __nv_bfloat16* H16 = reinterpret_cast<__nv_bfloat16*>(H1);
+            VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X(l), rep_uid, rep_code, w.T, counters, CNT_R, w.ln2_g, w.ln2_b,
+                                                        d, Y, nullptr, S16, st, g_rows, 1, K, 0, (size_t)R * d));
+            VQ_STAGE(S_MLP1, 1, launch_gemm_tc(S16, R, w.tm_w1, w.b_1, nullptr, H16, counters, CNT_R, 4 * d, d, 1,
+                                               ctx->status, st, sms, ctx->bn[1], true));
+            VQ_STAGE(S_MLP2, 1, launch_gemm_tc(H16, R, w.tm_w2, w.b_2, Y, X(l + 1), counters, CNT_R, d, 4 * d, 2,
+                                               ctx->status, st, sms, ctx->bn[2], true));
+        } else {
+            VQ_STAGE(S_POSTLN, 1, launch_residual_vq_ln(X(l), rep_uid, rep_code, w.T, counters, CNT_R, w.ln2_g, w.ln2_b,
+                                                        d, Y, A2, nullptr, st, g_rows));
+            VQ_STAGE(S_MLP1, 1, launch_sgemm(A2, w.w_1, w.b_1, nullptr, G4, counters, CNT_R, R, 4 * d, d,
+                                             EPI_BIAS_GELU, st, sms));
+            VQ_STAGE(S_MLP2, 1, launch_sgemm(G4, w.w_2, w.b_2, Y, X(l + 1), counters, CNT_R, R, d, 4 * d,
+                                             EPI_BIAS_RESID, st, sms));
+        }
     }
 
     StageScope s_bwd(ctx, S_BACKWARD, 0, st);
     auto gg = [&](bool ta, bool tb, const float* A, const float* B, float* C, int M, int Nn, int Kk, int lda, int ldb,
                   int ldc, long long sA, long long sB, long long sC, int batch, int acc) {
-        ctx->launches += 1;
+        StageScope sc(ctx, S_BWD_GEMM, 1, st);
         return launch_gemm_gen(ta, tb, A, B, C, M, Nn, Kk, lda, ldb, ldc, sA, sB, sC, batch, acc, st, sms);
     };
     auto colsum = [&](const float* Xm, int ncol, size_t off) {
-        ctx->launches += 1;
+        StageScope sc(ctx, S_BWD_ROWS, 1, st);
         return launch_colsum(Xm, R, G, ncol, OUT + off, ostride, 1, st, cap);
+    };
+    // split-operand tensor-core contractions (tcb): C[R][Nn] = A[R][kdim] W^T with W's split planes
+    // as the B operand (map tmW, Nn rows) ...
+    auto gx = [&](const float* A, int kdim, const CUtensorMap& tmW, int Nn, float* C) -> cudaError_t {
+        StageScope sc(ctx, S_BWD_GEMM, 2, st);
+        cudaError_t e = launch_split_planes(A, R, kdim, S16, R, st, cap);
+        if (e != cudaSuccess) return e;
+        return launch_gemm_tc(S16, R, tmW, ctx->zeros, nullptr, C, counters, CNT_R, Nn, kdim, 3, ctx->status, st, sms,
+                              tc_pick_bn(Nn), true);
+    };
+    // ... and C[in][out] += X^T dY summed over the R rows (the weight gradient): both operands
+    // transposed into K-major split planes, the row count padded to the K step with zeros
+    auto gw = [&](const float* Xs, int in, int dim_slot, const float* dYs, int out, float* C) -> cudaError_t {
+        StageScope sc(ctx, S_BWD_GEMM, 3, st);
+        __nv_bfloat16* XT = TW;                            // [2 in][R]
+        __nv_bfloat16* YT = TW + (size_t)2 * in * R;       // [2 out][R]
+        cudaError_t e = launch_transpose_bf16(Xs, R, in, XT, st, true);
+        if (e == cudaSuccess) e = launch_transpose_bf16(dYs, R, out, YT, st, true);
+        CUtensorMap tmY;
+        if (e == cudaSuccess) e = make_tmap_bf16_strided(&tmY, YT, 2LL * out, R, R, tc_pick_bn(out));
+        if (e != cudaSuccess) return e;
+        return launch_gemm_tc(XT, in, tmY, ctx->zeros, C, C, ctx->dims, dim_slot, out, (int)Kp, 2, ctx->status, st, sms,
+                              tc_pick_bn(out), true, R);
     };
     // head
     ctx->launches += 1;
@@ -768,58 +863,94 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         const LayerW& w = ctx->lw[l];
         const auto& o = po.l[l];
         // recompute the block internals from x_l
-        ctx->launches += 7;
-        VQ_CK(launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
-        VQ_CK(launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
-        VQ_CK(launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
-        VQ_CK(launch_quant_residual(X(l), code(l), w.T, w.codebook, R, d, Y, V, st, cap));
-        VQ_CK(launch_layernorm(Y, counters, CNT_R, w.ln2_g, w.ln2_b, d, A2, nullptr, st, g_rows));
-        VQ_CK(launch_sgemm(A2, w.w_1, w.b_1, nullptr, H1, counters, CNT_R, R, 4 * d, d, EPI_BIAS, st, sms));
-        VQ_CK(launch_gelu_fwd(H1, G4, (size_t)R * 4 * d, st, cap));
+        {
+            StageScope sc(ctx, S_BWD_RECOMP, 7, st);
+            if (tcb) {
+                VQ_CK(launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, S16, st, g_rows, (size_t)R * d));
+                VQ_CK(launch_gemm_tc(S16, R, w.tm_wqkv, w.b_qkv, nullptr, QKV, counters, CNT_R, 3 * d, d, 3,
+                                     ctx->status, st, sms, ctx->bn[0], true));
+            } else {
+                VQ_CK(launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
+                VQ_CK(launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
+            }
+            VQ_CK(launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
+            VQ_CK(launch_quant_residual(X(l), code(l), w.T, w.codebook, R, d, Y, V, st, cap));
+            if (tcb) {
+                VQ_CK(launch_layernorm(Y, counters, CNT_R, w.ln2_g, w.ln2_b, d, A2, S16, st, g_rows, (size_t)R * d));
+                VQ_CK(launch_gemm_tc(S16, R, w.tm_w1, w.b_1, nullptr, H1, counters, CNT_R, 4 * d, d, 3, ctx->status, st,
+                                     sms, ctx->bn[1], true));
+            } else {
+                VQ_CK(launch_layernorm(Y, counters, CNT_R, w.ln2_g, w.ln2_b, d, A2, nullptr, st, g_rows));
+                VQ_CK(launch_sgemm(A2, w.w_1, w.b_1, nullptr, H1, counters, CNT_R, R, 4 * d, d, EPI_BIAS, st, sms));
+            }
+            VQ_CK(launch_gelu_fwd(H1, G4, (size_t)R * 4 * d, st, cap));
+        }
         // MLP: x' = y + GELU(LN2(y) W1 + b1) W2 + b2, dX holds d/dx'
-        VQ_CK(gg(true, false, G4, dX, OUT + o.w2, 4 * d, d, G, 4 * d, d, d, (long long)G * 4 * d, (long long)G * d,
-                 ostride, ng, 1));
+        if (tcb) VQ_CK(gw(G4, 4 * d, 2, dX, d, OUT + o.w2));
+        else VQ_CK(gg(true, false, G4, dX, OUT + o.w2, 4 * d, d, G, 4 * d, d, d, (long long)G * 4 * d, (long long)G * d,
+                      ostride, ng, 1));
         VQ_CK(colsum(dX, d, o.b2));
-        VQ_CK(gg(false, true, dX, w.w_2, dG4, R, 4 * d, d, d, d, 4 * d, 0, 0, 0, 1, 0));
+        if (tcb) VQ_CK(gx(dX, d, w.tm_w2_s, 4 * d, dG4));
+        else VQ_CK(gg(false, true, dX, w.w_2, dG4, R, 4 * d, d, d, d, 4 * d, 0, 0, 0, 1, 0));
         ctx->launches += 1;
         VQ_CK(launch_gelu_bwd(H1, dG4, (size_t)R * 4 * d, st, cap));
-        VQ_CK(gg(true, false, A2, dG4, OUT + o.w1, d, 4 * d, G, d, 4 * d, 4 * d, (long long)G * d,
-                 (long long)G * 4 * d, ostride, ng, 1));
+        if (tcb) VQ_CK(gw(A2, d, 0, dG4, 4 * d, OUT + o.w1));
+        else VQ_CK(gg(true, false, A2, dG4, OUT + o.w1, d, 4 * d, G, d, 4 * d, 4 * d, (long long)G * d,
+                      (long long)G * 4 * d, ostride, ng, 1));
         VQ_CK(colsum(dG4, 4 * d, o.b1));
-        VQ_CK(gg(false, true, dG4, w.w_1, dA, R, d, 4 * d, 4 * d, 4 * d, d, 0, 0, 0, 1, 0));
+        if (tcb) VQ_CK(gx(dG4, 4 * d, w.tm_w1_s, d, dA));
+        else VQ_CK(gg(false, true, dG4, w.w_1, dA, R, d, 4 * d, 4 * d, 4 * d, d, 0, 0, 0, 1, 0));
         VQ_CK(cudaMemcpyAsync(dY, dX, (size_t)R * d * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ctx->launches += 1;
         VQ_CK(launch_ln_bwd(Y, dA, w.ln2_g, R, d, dY, 1, dgam, dbet, st, cap));
         VQ_CK(colsum(dgam, d, o.ln2_g));
         VQ_CK(colsum(dbet, d, o.ln2_b));
         // y = x + V W_o + b_o
-        VQ_CK(gg(false, true, dY, w.w_o, dV, R, d, d, d, d, d, 0, 0, 0, 1, 0));
-        VQ_CK(gg(true, false, V, dY, OUT + o.wo, d, d, G, d, d, d, (long long)G * d, (long long)G * d, ostride, ng, 1));
+        if (tcb) {
+            VQ_CK(gx(dY, d, w.tm_wo_s, d, dV));
+            VQ_CK(gw(V, d, 0, dY, d, OUT + o.wo));
+        } else {
+            VQ_CK(gg(false, true, dY, w.w_o, dV, R, d, d, d, d, d, 0, 0, 0, 1, 0));
+            VQ_CK(gg(true, false, V, dY, OUT + o.wo, d, d, G, d, d, d, (long long)G * d, (long long)G * d, ostride, ng,
+                     1));
+        }
         VQ_CK(colsum(dY, d, o.bo));
         // straight-through quantizer (Eq. st)
-        VQ_CK(gg(false, true, Oatt, w.codebook, OW, R, K, d, d, d, K, 0, 0, 0, 1, 0));
-        VQ_CK(gg(false, true, dV, w.codebook, DG, R, K, d, d, d, K, 0, 0, 0, 1, 0));
+        if (tcb) {
+            VQ_CK(gx(Oatt, d, w.tm_cb_s, K, OW));
+            VQ_CK(gx(dV, d, w.tm_cb_s, K, DG));
+        } else {
+            VQ_CK(gg(false, true, Oatt, w.codebook, OW, R, K, d, d, d, K, 0, 0, 0, 1, 0));
+            VQ_CK(gg(false, true, dV, w.codebook, DG, R, K, d, d, d, K, 0, 0, 0, 1, 0));
+        }
         ctx->launches += 1;
         VQ_CK(launch_st_rows(OW, DG, Oatt, w.cnorm, R, K, d, alpha, arow, st, cap));
-        VQ_CK(gg(false, false, alpha, w.codebook, dO, R, d, K, K, d, d, 0, 0, 0, 1, 0));
+        if (tcb) VQ_CK(gx(alpha, K, w.tm_cbT_s, d, dO));
+        else VQ_CK(gg(false, false, alpha, w.codebook, dO, R, d, K, K, d, d, 0, 0, 0, 1, 0));
         ctx->launches += 1;
         VQ_CK(launch_st_do(Oatt, arow, R, d, dO, st, cap));
-        VQ_CK(gg(true, false, alpha, Oatt, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d, ostride,
-                 ng, 1));
+        if (tcb) VQ_CK(gw(alpha, K, 3, Oatt, d, OUT + o.cb));
+        else VQ_CK(gg(true, false, alpha, Oatt, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d,
+                      ostride, ng, 1));
         ctx->launches += 3;
         VQ_CK(launch_colsum(alpha, R, G, K, csumK, K, 0, st, cap));
         VQ_CK(launch_sub_scaled_rows(OUT + o.cb, csumK, w.codebook, K, d, ng, ostride, st, cap));
         VQ_CK(launch_onehot(code(l), R, K, onehot, st, cap));
-        VQ_CK(gg(true, false, onehot, dV, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d, ostride,
-                 ng, 1));
+        if (tcb) VQ_CK(gw(onehot, K, 3, dV, d, OUT + o.cb));
+        else VQ_CK(gg(true, false, onehot, dV, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d,
+                      ostride, ng, 1));
         // attention
-        ctx->launches += 2;
-        VQ_CK(launch_attention_bwd(QKV, dO, S, N, d, H, dQKV, at<float>(ws, P.stat), st, cap));
+        {
+            StageScope sc(ctx, S_BWD_ATTN, 2, st);
+            VQ_CK(launch_attention_bwd(QKV, dO, S, N, d, H, dQKV, at<float>(ws, P.stat), st, cap));
+        }
         // qkv = LN1(x) W_qkv + b_qkv
-        VQ_CK(gg(true, false, A1, dQKV, OUT + o.wqkv, d, 3 * d, G, d, 3 * d, 3 * d, (long long)G * d,
-                 (long long)G * 3 * d, ostride, ng, 1));
+        if (tcb) VQ_CK(gw(A1, d, 0, dQKV, 3 * d, OUT + o.wqkv));
+        else VQ_CK(gg(true, false, A1, dQKV, OUT + o.wqkv, d, 3 * d, G, d, 3 * d, 3 * d, (long long)G * d,
+                      (long long)G * 3 * d, ostride, ng, 1));
         VQ_CK(colsum(dQKV, 3 * d, o.bqkv));
-        VQ_CK(gg(false, true, dQKV, w.w_qkv, dA, R, d, 3 * d, 3 * d, 3 * d, d, 0, 0, 0, 1, 0));
+        if (tcb) VQ_CK(gx(dQKV, 3 * d, w.tm_wqkv_s, d, dA));
+        else VQ_CK(gg(false, true, dQKV, w.w_qkv, dA, R, d, 3 * d, 3 * d, 3 * d, d, 0, 0, 0, 1, 0));
         VQ_CK(cudaMemcpyAsync(dX, dY, (size_t)R * d * sizeof(float), cudaMemcpyDeviceToDevice, st));
         ctx->launches += 1;
         VQ_CK(launch_ln_bwd(X(l), dA, w.ln1_g, R, d, dX, 1, dgam, dbet, st, cap));
@@ -864,8 +995,9 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
         return VQNQS_ERR_ARG;
     int vq_bits = 1;
     while ((1 << vq_bits) < K) ++vq_bits;
+    // heads of vq_bits each: 32 / vq_bits per code word, at most two words
     if (vq_heads < 1 || vq_heads > 8 || d_model % vq_heads || (d_model / vq_heads) % 8 ||
-        (vq_heads > 1 && vq_heads * vq_bits > 31))
+        (vq_heads > 1 && vq_heads > 2 * (32 / vq_bits)))
         return VQNQS_ERR_ARG;
     if (!(token_group == 1 || token_group == 2 || token_group == 4) || N % token_group) return VQNQS_ERR_ARG;
     const int dh = d_model / heads;
@@ -875,6 +1007,7 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     ctx->L = L; ctx->N = N; ctx->periodic = periodic ? 1 : 0; ctx->J = J; ctx->Gamma = Gamma;
     ctx->layers = layers; ctx->d = d_model; ctx->heads = heads; ctx->K = K;
     ctx->vq_heads = vq_heads; ctx->vq_bits = vq_heads > 1 ? vq_bits : 0;
+    ctx->vq_words = vq_heads > 1 && vq_heads > 32 / vq_bits ? 2 : 1;
     ctx->half_block = half_block ? 1 : 0;
     ctx->G = token_group;
     ctx->P = N / token_group;
@@ -916,6 +1049,19 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
     ctx->stats = static_cast<long long*>(dalloc(ST_SLOTS * sizeof(long long)));
     ctx->lw.resize(layers);
     const size_t d = d_model;
+    // the backward's contractions on the tensor cores: shapes the split GEMM takes, one quantizer
+    // head, no half-block, single-spin tokens
+    ctx->bwd_tc = d_model % 64 == 0 && K % 64 == 0 && vq_heads == 1 && !half_block && token_group == 1;
+    if (ctx->bwd_tc) {
+        const int dims[4] = {d_model, 3 * d_model, 4 * d_model, K};
+        ctx->dims = static_cast<int*>(dalloc(sizeof(dims)));
+        const size_t nz = (size_t)std::max(4 * d_model, K);
+        ctx->zeros = static_cast<float*>(dalloc(nz * sizeof(float)));
+        if (!ctx->dims || !ctx->zeros) return bail(VQNQS_ERR_OOM);
+        if (cudaMemcpy(ctx->dims, dims, sizeof(dims), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(ctx->zeros, 0, nz * sizeof(float)) != cudaSuccess)
+            return bail(VQNQS_ERR_CUDA);
+    }
     for (int l = 0; l < layers; ++l) {
         LayerW& w = ctx->lw[l];
         w.T = static_cast<float*>(dalloc((size_t)vq_heads * K * d * sizeof(float)));
@@ -929,6 +1075,16 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
         w.wd = static_cast<float*>(dalloc((size_t)K * K * sizeof(float)));
         if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo || !w.wd)
             return bail(VQNQS_ERR_OOM);
+        if (ctx->bwd_tc) {
+            const size_t b2 = 2 * sizeof(__nv_bfloat16);
+            w.wqkv_s = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * b2));
+            w.w1_s = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * b2));
+            w.w2_s = static_cast<__nv_bfloat16*>(dalloc(4 * d * d * b2));
+            w.wo_s = static_cast<__nv_bfloat16*>(dalloc(d * d * b2));
+            w.cb_s = static_cast<__nv_bfloat16*>(dalloc((size_t)K * d * b2));
+            w.cbT_s = static_cast<__nv_bfloat16*>(dalloc((size_t)K * d * b2));
+            if (!w.wqkv_s || !w.w1_s || !w.w2_s || !w.wo_s || !w.cb_s || !w.cbT_s) return bail(VQNQS_ERR_OOM);
+        }
     }
     if (ctx->half_block) {
         ctx->hw.wqkv_t = static_cast<__nv_bfloat16*>(dalloc(3 * d * d * sizeof(__nv_bfloat16)));
@@ -1200,7 +1356,8 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
     if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: no final half-block");
     if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "grad_log_psi: one spin per token");
     if (B < 0) return fail(ctx, VQNQS_ERR_ARG, "B must be >= 0");
-    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL)) return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
+    if (flags & ~(VQNQS_REUSE | VQNQS_BF16 | VQNQS_INCREMENTAL | VQNQS_BF16_SPLIT))
+        return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
         if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
@@ -1241,8 +1398,8 @@ int vqnqs_grad_log_psi(vqnqs_ctx* ctx, int B, const uint8_t* spins, const float*
         const int S = (B - s0) < lo ? (B - s0) : lo;
         const uint8_t* sp = spins + (size_t)s0 * ctx->N;
         int rc;
-        if (O) rc = grad_chunk(ctx, P, ws, sp, S, nullptr, O + (size_t)s0 * Pn, ctx->N, Pn, st);
-        else rc = grad_chunk(ctx, P, ws, sp, S, weighted ? sd + s0 : nullptr, grad, S * ctx->N, 0, st);
+        if (O) rc = grad_chunk(ctx, P, ws, sp, S, nullptr, O + (size_t)s0 * Pn, ctx->N, Pn, st, flags);
+        else rc = grad_chunk(ctx, P, ws, sp, S, weighted ? sd + s0 : nullptr, grad, S * ctx->N, 0, st, flags);
         if (rc != VQNQS_OK) return rc;
     }
     if (O && grad) {  // grad = sum_b w_b O_b

@@ -26,7 +26,8 @@ enum {
     CNT_SCW = 7,
     CNT_U0 = 8,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
     CNT_EX = 8 + VQNQS_MAX_LAYERS + 2,  // split operands: patched rows listed for the exact correction
-    CNT_SLOTS = CNT_EX + 1
+    CNT_CW = CNT_EX + 1,                // two-word codes: distinct (hi, lo) code pairs of the layer
+    CNT_SLOTS = CNT_CW + 1
 };
 
 // Slots of the context's persistent device statistics (int64).
@@ -72,6 +73,11 @@ struct LayerW {
     CUtensorMap tm_cb_hi, tm_cb_lo;       // their TMA maps (valid when vq_tc_supported)
     __nv_bfloat16* wo_t = nullptr;        // final half-block only: BF16 transpose of W_o
     CUtensorMap tm_wo;                    //   and its TMA map
+    // tensor-core backward (split operands): the weights as stored, each as a BF16 hi plane and a lo
+    // plane after it ([2 rows][cols]), as the B operand of dX = dY W^T; the codebook also transposed
+    __nv_bfloat16 *wqkv_s = nullptr, *w1_s = nullptr, *w2_s = nullptr, *wo_s = nullptr, *cb_s = nullptr,
+                  *cbT_s = nullptr;
+    CUtensorMap tm_wqkv_s, tm_w1_s, tm_w2_s, tm_wo_s, tm_cb_s, tm_cbT_s;
 };
 
 // Lattice groups of a batch (one group for a single lattice, up to MAX_GROUPS
@@ -202,7 +208,8 @@ cudaError_t launch_layernorm(const float* X, const int* counters, int u_slot, co
 cudaError_t launch_residual_vq_ln(const float* X, const int* rep_uid, const int* rep_code, const float* T,
                                   const int* counters, int u_slot, const float* g, const float* b, int d, float* Y,
                                   float* A_f32, __nv_bfloat16* A_bf16, cudaStream_t st, int grid, int vq_heads = 1,
-                                  int K = 0, int bits = 0, size_t lo_off = 0);
+                                  int K = 0, int bits = 0, size_t lo_off = 0, const int* tab_lo = nullptr,
+                                  const int* tab_hi = nullptr);
 // T and cnorm of a layer's codebook ([vq_heads][K][d / vq_heads])
 cudaError_t launch_table_T(const float* codebook, const float* w_o, const float* b_o, int K, int d, int vq_heads,
                            float* T, float* cnorm, cudaStream_t st);
@@ -243,12 +250,20 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
 int tc_pick_bn(int N);
 cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows);
+// the same for rows of ld elements of which the first cols are read (cols <= ld; ld * 2 % 16 == 0)
+cudaError_t make_tmap_bf16_strided(CUtensorMap* map, const void* base, long long rows, long long cols, long long ld,
+                                   int box_rows);
 // BN = output tile width (64, 128, 192 or 256 dividing N; 0 picks the widest); tmB's box must be [BN x 64].
 // split: A is [2 Arows][K] (hi plane, then lo plane), tmB covers [2N][K] (hi rows, then lo rows), three
 // passes per K block; BF16 outputs (epi 0, 1) are [2 Arows][N] (hi, then lo plane).
+// a_inner > 0: A's rows hold a_inner elements (K may exceed it; those K blocks read zeros)
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms, int BN = 0, bool split = false);
+                           int* status, cudaStream_t st, int num_sms, int BN = 0, bool split = false,
+                           long long a_inner = 0);
+// dst [2 plane_rows][cols] BF16: row r of src (FP32 [rows][cols]) split into hi (row r) and lo (row plane_rows + r)
+cudaError_t launch_split_planes(const float* src, long long rows, int cols, __nv_bfloat16* dst, long long plane_rows,
+                                cudaStream_t st, int cap);
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st);
 cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream_t st);
 
@@ -256,10 +271,16 @@ cudaError_t launch_timeout_probe(int* status, long long limit_cycles, cudaStream
 cudaError_t launch_vq_argmin(const float* O, const int* counters, const int* act_rows, const float* codebook,
                              const float* cnorm, int K, int d, int* code, long long* near_ties, int Rmax,
                              cudaStream_t st, int num_sms, int a_slot = CNT_A);
-// the same per quantizer head: segment h of every row against codebook h, packed codes
+// the same per quantizer head: segment h of every row against codebook h, packed codes (heads beyond
+// 32 / bits per word go to the second word code_hi)
 cudaError_t launch_vq_argmin_heads(const float* O, const int* counters, const int* act_rows, const float* codebook,
                                    const float* cnorm, int K, int d, int vq_heads, int bits, int* code,
-                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot = CNT_A);
+                                   long long* near_ties, int Rmax, cudaStream_t st, int num_sms, int a_slot = CNT_A,
+                                   int* code_hi = nullptr);
+// two-word codes: the listed rows' (hi, lo) code words -> a dense code id in lo (k_dedupe.cu)
+cudaError_t launch_code_words(int* counters, int a_slot, int cnt_slot, const int* rows, int Rmax, int* lo,
+                              const int* hi, unsigned long long* keys, int* vals, int hash_bits, int* tab_hi,
+                              int* tab_lo, int* status, cudaStream_t st, int num_sms);
 
 cudaError_t launch_assign_setup(int* counters, int* rows, int R, cudaStream_t st);
 

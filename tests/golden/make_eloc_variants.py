@@ -13,6 +13,8 @@ variant's blob segments; samples ``make_samples(16, 16, seed=1)`` or
   table1_12b                       the same with 2 quantizer heads and the final
                                    attention-only half-block (Table 1's network)
   table1_12b_g4                    table1_12b with tokens of 4 spins
+  table1_48b                       Table 1's 48-bit network: 8 quantizer heads of
+                                   64 codes and the final half-block
   chain384                         open transverse-field Ising chain, 384 sites,
                                    J = Gamma = 1, 1 block, d_model 256, 8 heads,
                                    64 codes (Sec. 4's largest chain)
@@ -42,6 +44,7 @@ WORKLOADS = {
     "arch16_h4": (16, 3, 256, 8, 64, 4, False, 1, False),
     "table1_12b": (16, 3, 256, 8, 64, 2, True, 1, False),
     "table1_12b_g4": (16, 3, 256, 8, 64, 2, True, 4, False),
+    "table1_48b": (16, 3, 256, 8, 64, 8, True, 1, False),
     "chain384": (384, 1, 256, 8, 64, 1, False, 1, True),
 }
 

@@ -125,8 +125,8 @@ def test_one_head_entry_points_refuse_several():
         m.grad_log_psi(s)
     with pytest.raises(VQNQSError, match="ERR_ARG"):
         m.sample(torch.rand(4, L * L, device="cuda"))
-    with pytest.raises(VQNQSError):  # 8 heads of 64 codes: 48 bits do not fit a packed code
-        VQNQS(4, True, 1.0, 1, 64, 2, 64, si.make_weights(16, 1, 64, 64), vq_heads=8)
+    with pytest.raises(VQNQSError):  # 8 heads of 16-bit codes: 128 bits exceed the two code words
+        VQNQS(4, True, 1.0, 1, 64, 2, 40000, si.make_weights(16, 1, 64, 40000), vq_heads=8)
     with pytest.raises(VQNQSError):  # d_model not a multiple of the heads
         VQNQS(4, True, 1.0, layers, d, heads, K, w, vq_heads=3)
 
@@ -306,3 +306,31 @@ def test_graph_replay_with_variants():
         direct = m.local_energy(s, flags)
         g = LocalEnergyGraph(m, [(L, B)], flags)
         assert torch.equal(g(s).clone(), direct)
+
+
+def test_table1_48_bit_network_16x16():
+    """Table 1's widest quantizer: 8 heads of 64 codes (48 bits, two code words;
+    each distinct code gets a dense id before the per-location deduplication),
+    three blocks and the final half-block, FP32 reuse against 16 stored oracle
+    values (tests/golden/eloc_table1_48b.txt), reuse bitwise equal to plain, and
+    the code-returning entry points refuse the wide codes."""
+    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS, VQNQSError
+    L, layers, d, heads, K, B, H = 16, 3, 256, 8, 64, 16, 8
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0, half_block=True)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H, half_block=True)
+    m.reset_stats()
+    e = m.local_energy(s, REUSE)
+    st = m.stats()
+    print(f"Table 1 network, 48 bits: quantized-ops FLOP reduction {st['flops_full'] / st['flops_done']:.2f}, "
+          f"unique-row fraction {[round(u / st['rows'], 4) for u in st['unique_rows'][1:]]}")
+    assert st["device_status"] == 0
+    want, gap = eloc_variant("table1_48b")
+    check_fp32_against_golden(rel_err(e.cpu().numpy(), want, N), gap)
+    assert torch.equal(e, m.local_energy(s, 0))
+    db = rel_err(m.local_energy(s, REUSE | BF16).cpu().numpy(), e.cpu().numpy().astype(np.float64), N)
+    print(f"48 bits BF16 vs FP32: median {np.median(db):.2e} max {db.max():.2e}")
+    assert db.max() <= 0.1
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        m.codes(s)

@@ -83,3 +83,38 @@ def test_differentiation_config_20x20_sampled():
     O, _ = m.grad_log_psi(s, want_O=True, want_grad=False)
     want = gradient.per_sample_O(P, spins)
     assert close(O.cpu().numpy(), want, 1e-3)
+
+
+def test_tensor_core_energy_gradient_matches_oracle_and_fp32():
+    """VQNQS_BF16: the summed gradient's GEMMs (recomputed forward, dX = dY W^T,
+    dW = X^T dY) on the tensor cores with split operands, d_model 64 and K 64:
+    the energy gradient against the oracle's (1e-3 of its largest entry, as the
+    FP32 backward) and against the FP32 backward (1e-4)."""
+    from paper_2212_11296_gb300 import BF16
+    m, P, spins = setup(4, 2, 64, 2, 64, 16, std=0.3)
+    s = torch.as_tensor(spins).cuda()
+    e = m.local_energy(s, 0)
+    _, g_tc = m.grad_log_psi(s, e_loc=e, flags=BF16)
+    _, g32 = m.grad_log_psi(s, e_loc=e)
+    e_ora = hamiltonian.local_energy(P, spins, 4, True, 1.0)
+    want = gradient.energy_gradient(gradient.per_sample_O(P, spins), e_ora)
+    assert close(g_tc.cpu().numpy()[None], want[None], 1e-3)
+    assert close(g_tc.cpu().numpy()[None], g32.cpu().numpy()[None].astype(np.float64), 1e-4)
+    # seeded sums too (the weight-gradient GEMMs accumulate over rows)
+    seeds = torch.linspace(-1, 1, 16, device="cuda")
+    _, a = m.grad_log_psi(s, seeds=seeds, flags=BF16)
+    _, b = m.grad_log_psi(s, seeds=seeds)
+    assert close(a.cpu().numpy()[None], b.cpu().numpy()[None].astype(np.float64), 1e-4)
+    assert m.stats()["device_status"] == 0
+
+
+def test_tensor_core_gradient_differentiation_config_against_fp32():
+    """20x20, 12 layers, d 384, 12 heads, K 512, 2 samples: the tensor-core
+    gradient against the FP32 backward (1e-4 of the largest entry)."""
+    from paper_2212_11296_gb300 import BF16
+    m, P, spins = setup(20, 12, 384, 12, 512, 2)
+    s = torch.as_tensor(spins).cuda()
+    seeds = torch.tensor([1.0, -0.5], device="cuda")
+    _, a = m.grad_log_psi(s, seeds=seeds, flags=BF16)
+    _, b = m.grad_log_psi(s, seeds=seeds)
+    assert close(a.cpu().numpy()[None], b.cpu().numpy()[None].astype(np.float64), 1e-4)
