@@ -337,13 +337,13 @@ def grad_bench(args) -> dict:
     per-stage times."""
     import torch
     import synthetic_inputs as si
-    from paper_2212_11296_gb300 import BF16, REUSE, VQNQS
+    from paper_2212_11296_gb300 import BF16, INCREMENTAL, REUSE, VQNQS
     L, layers, d, heads, K, B = 20, 12, 384, 12, 512, 512
     N = L * L
     blob = si.make_weights(N, layers, d, K, seed=0)
     spins = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
     m = VQNQS(L, True, 1.0, layers, d, heads, K, blob)
-    flags = REUSE | BF16
+    flags = REUSE | BF16 | INCREMENTAL
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     ws = m.workspace(flags)
@@ -379,7 +379,8 @@ def grad_bench(args) -> dict:
             "ms_per_step": ms / args.steps, "eloc_ms_per_step": sum(te) / args.steps,
             "backward_ms_per_step": sum(tg) / args.steps,
             "config": {"workload": f"{L}x{L} periodic Heisenberg J=1, {layers} layers d_model {d} heads {heads} "
-                                   f"codebook {K}, {B} uniform S_z=0 samples", "eloc_path": "VQ-reuse BF16",
+                                   f"codebook {K}, {B} uniform S_z=0 samples",
+                       "eloc_path": "VQ-reuse incremental BF16 (CUDA-core corrections at 400 positions)",
                        "backward": "hand-written, activation recomputation; GEMMs on the tensor cores with split "
                                    "BF16 operands, attention backward and row-wise steps FP32"},
             "grad_vs_fp32_backward_max_rel": rel32,
@@ -397,6 +398,9 @@ def main():
                     help="comma list of reuse,bf16,incremental,split for the timed path (split: BF16 tensor-core "
                          "products from hi + lo operand pairs, FP32-grade)")
     ap.add_argument("--plain-runs", type=int, default=5, help="timed runs of the plain FP32 leg (median)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="samples per chunk of the timed path's workspace (0: picked by the library's chunk-size "
+                         "autotuner on the first 512 samples)")
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
@@ -451,7 +455,13 @@ def main():
     stream = torch.cuda.current_stream()
     spins = torch.as_tensor(spins_np).cuda()
     out = torch.empty(B, dtype=torch.float32, device="cuda")
-    ws = m.workspace(flags)
+    tuning = None
+    if args.chunk <= 0:  # the library's autotuner picks the chunk size (fewer, larger launches)
+        tuning = m.autotune_chunk(spins[:min(512, B)].contiguous(), flags, candidates=(8, 15, 30, 60))
+        args.chunk = tuning["best"]
+        m._ws.clear()
+        torch.cuda.empty_cache()
+    ws = m.workspace(flags, args.chunk)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -633,6 +643,9 @@ def main():
         "device_status": st["device_status"],
         "gemm_tc": gemm,
         "stages": stages,
+        "chunk_samples": args.chunk,
+        "autotune_chunk": ({"samples": min(512, B), "ms": {str(k): v for k, v in tuning["ms"].items()}}
+                           if tuning else None),
     }
     if flags & INCREMENTAL:  # row outcomes over the timed steps, summed over layers
         res["incremental"] = {k: st[k] for k in ("inc_base_rows", "inc_patched_rows", "inc_certified_rows",

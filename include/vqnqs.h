@@ -441,6 +441,17 @@ typedef struct vqnqs_tuning {
 } vqnqs_tuning;
 int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* dev_ws, size_t ws_bytes, vqnqs_tuning* out, void* stream);
 
+/* Chunk-size tuner of the local-energy path: for each candidate chunk size
+ * (samples per chunk, HOST int cand[n_cand]) whose workspace fits ws_bytes,
+ * evaluates the local energies of the B DEVICE samples once untimed and twice
+ * timed with `flags`, writes the average milliseconds per evaluation to HOST
+ * ms[i] (-1 when the candidate does not fit) and the fastest candidate to
+ * *best.  Larger chunks mean fewer, larger launches; the caller then sizes its
+ * workspace with vqnqs_workspace_bytes(ctx, *best, flags).  B <= 65536;
+ * synchronises `stream`. */
+int vqnqs_autotune_chunk(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int flags, const int* cand, int n_cand,
+                         void* dev_ws, size_t ws_bytes, int* best, float* ms, void* stream);
+
 /* Snapshot of the counters; synchronises the device first. */
 int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out);
 

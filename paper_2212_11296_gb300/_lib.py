@@ -111,6 +111,9 @@ SIGNATURES = [
     ("vqnqs_compress_workspace_bytes", ctypes.c_size_t, [ctypes.c_int]),
     ("vqnqs_compress_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 7 +
      [ctypes.c_size_t, ctypes.c_void_p]),
+    ("vqnqs_autotune_chunk", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("vqnqs_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(Tuning), ctypes.c_void_p]),
     ("vqnqs_compress_rows_noalloc", ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 7),

@@ -272,6 +272,21 @@ class VQNQS:
         return {"qkv_bn": t.qkv_bn, "mlp_up_bn": t.mlp_up_bn, "mlp_down_bn": t.mlp_down_bn,
                 "ms": [[t.ms[s][i] for i in range(4)] for s in range(3)]}
 
+    def autotune_chunk(self, spins: torch.Tensor, flags: int = 0, candidates=(8, 15, 30, 60), stream=None) -> dict:
+        """Times the local energies of ``spins`` at each candidate chunk size (samples per
+        chunk; see vqnqs_autotune_chunk) and returns {"best": samples, "ms": {size: ms}}."""
+        _check_dev(spins, torch.uint8, "spins")
+        cand = [int(c) for c in candidates]
+        ws = self.workspace(flags, max(cand))
+        arr = (ctypes.c_int * len(cand))(*cand)
+        ms = (ctypes.c_float * len(cand))()
+        best = ctypes.c_int()
+        self._check(lib().vqnqs_autotune_chunk(self._h, spins.shape[0], ctypes.c_void_p(spins.data_ptr()), int(flags),
+                                               arr, len(cand), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                               ctypes.byref(best), ms, ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_autotune_chunk")
+        return {"best": best.value, "ms": {c: float(ms[i]) for i, c in enumerate(cand)}}
+
     def stats(self) -> dict:
         s = _lib.Stats()
         self._check(lib().vqnqs_get_stats(self._h, ctypes.byref(s)), "vqnqs_get_stats")

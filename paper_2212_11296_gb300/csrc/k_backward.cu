@@ -202,6 +202,34 @@ __global__ void k_colsum(const float* __restrict__ X, int rows, int G, int ncol,
     }
 }
 
+// The same for one group of many rows, in two fixed-order stages: block (x, y) sums its 32
+// columns over row slab y (8 row lanes, coalesced 128-byte row segments) into part[y][n];
+// then out[n] (+)= sum over the slabs in slab order.
+__global__ void k_colsum_slabs(const float* __restrict__ X, int rows, int ncol, int slab, float* __restrict__ part) {
+    __shared__ float red[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * slab, r1 = min(rows, r0 + slab);
+    float s = 0.f;
+    if (n < ncol)
+        for (int r = r0 + threadIdx.y; r < r1; r += 8) s += X[(size_t)r * ncol + n];
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < ncol) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        part[(size_t)blockIdx.y * ncol + n] = t;
+    }
+}
+__global__ void k_colsum_finish(const float* __restrict__ part, int slabs, int ncol, float* __restrict__ out,
+                                int accumulate) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ncol; n += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int y = 0; y < slabs; ++y) s += part[(size_t)y * ncol + n];
+        out[n] = accumulate ? out[n] + s : s;
+    }
+}
+
 // Embedding backward: dtok[t] (+)= sum of dX0 rows with token t; dpos[p] (+)= sum over the
 // group's samples of dX0[b][p].  Groups of G samples (G = all samples for the summed
 // gradient, G = 1 for per-sample gradients).
@@ -403,8 +431,19 @@ cudaError_t launch_quant_residual(const float* X, const int* code, const float* 
     return cudaGetLastError();
 }
 cudaError_t launch_colsum(const float* X, int rows, int G, int ncol, float* out, long long out_stride, int accumulate,
-                          cudaStream_t st, int cap) {
+                          cudaStream_t st, int cap, float* part, int part_cap) {
     const long long groups = (rows + G - 1) / G;
+    if (groups == 1 && part && rows > 4096) {  // one long group: row slabs in parallel, then a fixed-order sum
+        int slabs = (rows + 1023) / 1024;
+        if ((long long)slabs * ncol > part_cap) slabs = part_cap / ncol;
+        if (slabs > 1) {
+            const int slab = (rows + slabs - 1) / slabs;
+            slabs = (rows + slab - 1) / slab;
+            k_colsum_slabs<<<dim3((ncol + 31) / 32, slabs), dim3(32, 8), 0, st>>>(X, rows, ncol, slab, part);
+            k_colsum_finish<<<(ncol + 255) / 256, 256, 0, st>>>(part, slabs, ncol, out, accumulate);
+            return cudaGetLastError();
+        }
+    }
     k_colsum<<<g_grid(groups * ncol, 256, cap), 256, 0, st>>>(X, rows, G, ncol, out, out_stride, accumulate);
     return cudaGetLastError();
 }

@@ -695,8 +695,10 @@ struct GradPlan {
     long long R = 0;
     size_t seeds, counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b,
         rep_uid, rep_code, code, X, dX, dY, A1, Oatt, Y, V, A2, dA, dV, dO, dgam, dbet, Af, QKV, dQKV, H1, G4, dG4, OW,
-        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, s16, tw, total;
+        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, s16, tw, colpart, total;
 };
+
+constexpr int kColParts = 1 << 20;  // floats of partial column sums (slabs x columns)
 
 GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     GradPlan p;
@@ -731,6 +733,7 @@ GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     // split operands of a weight-gradient GEMM, [2 in][R] and [2 out][R] with in + out <= max(5d, K + d)
     p.s16 = take(c->bwd_tc ? R * std::max(4 * d, K) * 4 : 0);
     p.tw = take(c->bwd_tc ? R * std::max(5 * d, K + d) * 4 : 0);
+    p.colpart = take((size_t)kColParts * f);  // row-slab partial column sums
     p.total = o;
     return p;
 }
@@ -824,9 +827,10 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         StageScope sc(ctx, S_BWD_GEMM, 1, st);
         return launch_gemm_gen(ta, tb, A, B, C, M, Nn, Kk, lda, ldb, ldc, sA, sB, sC, batch, acc, st, sms);
     };
+    float* colpart = at<float>(ws, P.colpart);
     auto colsum = [&](const float* Xm, int ncol, size_t off) {
         StageScope sc(ctx, S_BWD_ROWS, 1, st);
-        return launch_colsum(Xm, R, G, ncol, OUT + off, ostride, 1, st, cap);
+        return launch_colsum(Xm, R, G, ncol, OUT + off, ostride, 1, st, cap, colpart, kColParts);
     };
     // split-operand tensor-core contractions (tcb): C[R][Nn] = A[R][kdim] W^T with W's split planes
     // as the B operand (map tmW, Nn rows) ...
@@ -933,7 +937,7 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         else VQ_CK(gg(true, false, alpha, Oatt, OUT + o.cb, K, d, G, K, d, d, (long long)G * K, (long long)G * d,
                       ostride, ng, 1));
         ctx->launches += 3;
-        VQ_CK(launch_colsum(alpha, R, G, K, csumK, K, 0, st, cap));
+        VQ_CK(launch_colsum(alpha, R, G, K, csumK, K, 0, st, cap, colpart, kColParts));
         VQ_CK(launch_sub_scaled_rows(OUT + o.cb, csumK, w.codebook, K, d, ng, ostride, st, cap));
         VQ_CK(launch_onehot(code(l), R, K, onehot, st, cap));
         if (tcb) VQ_CK(gw(onehot, K, 3, dV, d, OUT + o.cb));
@@ -1562,6 +1566,48 @@ int vqnqs_autotune(vqnqs_ctx* ctx, int M, void* ws, size_t ws_bytes, vqnqs_tunin
     out->mlp_up_bn = ctx->bn[1];
     out->mlp_down_bn = ctx->bn[2];
     return build_weight_tmaps(ctx);
+}
+
+int vqnqs_autotune_chunk(vqnqs_ctx* ctx, int B, const uint8_t* spins, int flags, const int* cand, int n_cand, void* ws,
+                         size_t ws_bytes, int* best, float* ms, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B <= 0 || !spins || !cand || n_cand <= 0 || !best || !ms || !ws)
+        return fail(ctx, VQNQS_ERR_ARG, "autotune_chunk: need samples, candidates, workspace and outputs");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* e_loc = ctx->lp_scratch;  // local energies go to the context's scratch (B <= its capacity)
+    if (B > ctx->lp_scratch_cap) return fail(ctx, VQNQS_ERR_ARG, "autotune_chunk: at most 65536 samples");
+    cudaEvent_t e0, e1;
+    VQ_CK(cudaEventCreate(&e0));
+    VQ_CK(cudaEventCreate(&e1));
+    *best = 0;
+    float best_ms = 1e30f;
+    int rc = VQNQS_OK;
+    for (int i = 0; i < n_cand && rc == VQNQS_OK; ++i) {
+        ms[i] = -1.f;
+        if (cand[i] <= 0) continue;
+        const size_t need = make_plan(ctx, cand[i], true).total;
+        if (need > ws_bytes) continue;  // does not fit the given workspace
+        // a workspace of exactly this plan makes run() use chunks of cand[i] samples
+        rc = run(ctx, B, spins, e_loc, nullptr, nullptr, flags, ws, need, stream, true);
+        if (rc != VQNQS_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = fail(ctx, VQNQS_ERR_CUDA, "event"); break; }
+        for (int rep = 0; rep < 2 && rc == VQNQS_OK; ++rep)
+            rc = run(ctx, B, spins, e_loc, nullptr, nullptr, flags, ws, need, stream, true);
+        if (rc != VQNQS_OK) break;
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            rc = fail(ctx, VQNQS_ERR_CUDA, "autotune_chunk: event timing");
+            break;
+        }
+        ms[i] = t / 2.f;
+        if (ms[i] < best_ms) { best_ms = ms[i]; *best = cand[i]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == VQNQS_OK && *best == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "autotune_chunk: no candidate fits");
+    return rc;
 }
 
 // ---- autoregressive sampling -----------------------------------------------------

@@ -373,8 +373,10 @@ cudaError_t launch_st_do(const float* O, const float* arow, int R, int d, float*
 cudaError_t launch_onehot(const int* code, int R, int K, float* Hm, cudaStream_t st, int cap);
 cudaError_t launch_quant_residual(const float* X, const int* code, const float* T, const float* cb, int R, int d,
                                   float* Y, float* V, cudaStream_t st, int cap);
+// out[z][n] (+)= sum of rows z G .. z G + G - 1 of column n; a single group of many rows is summed
+// in row slabs through part (part_cap floats) when given, in a fixed order
 cudaError_t launch_colsum(const float* X, int rows, int G, int ncol, float* out, long long out_stride, int accumulate,
-                          cudaStream_t st, int cap);
+                          cudaStream_t st, int cap, float* part = nullptr, int part_cap = 0);
 cudaError_t launch_embed_bwd(const float* dX0, const uint8_t* spins, int S, int N, int d, int G, float* dtok,
                              float* dpos, long long out_stride, int accumulate, cudaStream_t st, int cap);
 cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N, int d, int H, float* dQKV,
