@@ -482,9 +482,10 @@ class LocalEnergyGraph:
     with one spins tensor per group; the spins are copied into the graph's
     input buffer, the graph is replayed, and the E_loc buffer is returned (valid
     until the next call).  The first, uncaptured evaluation performs every
-    one-time set-up (kernel attributes, module loading) before capture."""
+    one-time set-up (kernel attributes, module loading) before capture.
+    ``chunk_samples`` sizes the workspace (vqnqs_workspace_bytes; 0: the default)."""
 
-    def __init__(self, model: VQNQS, shapes, flags: int = 0):
+    def __init__(self, model: VQNQS, shapes, flags: int = 0, chunk_samples: int = 0):
         self.model, self.flags = model, int(flags)
         self.Ls = [int(L) for L, _ in shapes]
         self.Bs = [int(B) for _, B in shapes]
@@ -492,7 +493,7 @@ class LocalEnergyGraph:
         total_sites = sum(L * L * B for L, B in zip(self.Ls, self.Bs))
         self.spins = torch.zeros(total_sites, dtype=torch.uint8, device="cuda")
         self.out = torch.empty(sum(self.Bs), dtype=torch.float32, device="cuda")
-        self.ws = torch.empty(model.workspace_bytes(self.flags), dtype=torch.uint8, device="cuda")
+        self.ws = torch.empty(model.workspace_bytes(self.flags, chunk_samples), dtype=torch.uint8, device="cuda")
         self._run()
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()

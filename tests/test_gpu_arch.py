@@ -329,7 +329,7 @@ def test_table1_48_bit_network_16x16():
     want, gap = eloc_variant("table1_48b")
     # eight quantizer heads make eight assignments per row, so near-tie flips are more frequent
     # (each sample beyond 1e-5 must still meet an oracle near tie)
-    check_fp32_against_golden(rel_err(e.cpu().numpy(), want, N), gap, flip_tol=5e-4)
+    check_fp32_against_golden(rel_err(e.cpu().numpy(), want, N), gap, flip_tol=5e-4, min_within=0.5)
     assert torch.equal(e, m.local_energy(s, 0))
     db = rel_err(m.local_energy(s, REUSE | BF16).cpu().numpy(), e.cpu().numpy().astype(np.float64), N)
     print(f"48 bits BF16 vs FP32: median {np.median(db):.2e} max {db.max():.2e}")
