@@ -325,76 +325,67 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 }
 
 // ---- connected configurations on the tensor cores (BF16 path, dh = 32) ----------------
-// One CTA of 256 threads takes configurations from the tensor-core list.  Per
-// tile of up to 128 patched rows, tile row r is TMEM lane r and belongs to two
-// threads, r and r + 128, each of which takes half of the heads:
-//   1. the rows' queries (the sample's: a patched row's input is unchanged) are
-//      copied into shared memory with cp.async (K-major, d columns), the
-//      changed positions' keys beside them and their values transposed;
-//   2. per head h: S_h = Q_h [K_s; K_c]_h^T (M = 128, N = 32): the sample's keys
-//      at the changed positions in columns 0..15, the configuration's in 16..31;
-//   3. per row and head: the BF16 weights e = exp(s / sqrt(dh) - m) of the
-//      changed keys before the row (the sample's negated) as the A operand;
-//   4. per head: E_h [V_s; V_c]_h (N = 32) into the TMEM columns the scores came
-//      from: sum_k e_c v_c - e_s v_s;
-//   5. per row: delta = (acc - (sum e_c - sum e_s) o) / l' with the sample's
-//      outputs o read by the row's own threads; delta goes back to TMEM, the two
-//      threads' partial norms are added, and the certificate is checked as in
-//      k_inc_patch with ||delta|| replaced by ||delta|| + B, B a bound on the
-//      error of the BF16 computation (below), and each listed candidate's
+// One work item = (sample b, tile of 128 positions, slice z of b's connected
+// configurations).  The item stages what belongs to the sample once: the tile's
+// queries (BF16, K-major) in shared memory, the sample's outputs o of the tile's rows in
+// TMEM columns [d, 2d), ||o_h||, ||q~_h|| and the softmax statistics in registers, and
+// the rows' certificates in shared memory.  It then walks the slice (every `slices`-th
+// configuration of b with at most PATCH_TC_KEYS changed positions and its first changed
+// position inside the tile).  Tile row r is TMEM lane r and belongs to threads r and
+// r + 128, each of which takes half of the heads.  Per configuration c:
+//   1. the changed positions' keys are staged beside each other (the sample's in slots
+//      0..15, c's in 16..31, zero-filled) and their values transposed;
+//   2. per head h: S_h = Q_h [K_s; K_c]_h^T (M = 128, N = 32) into TMEM columns 32h..;
+//   3. a tile row is patched when its position is at or after c's first changed position
+//      and not itself changed; per such row and head, the BF16 weights
+//      e = exp(s / sqrt(dh) - m) of the changed keys before the row (the sample's
+//      negated) form the A operand;
+//   4. per head: E_h [V_s; V_c]_h (N = 32) into the columns the scores came from:
+//      sum_k e_c v_c - e_s v_s;
+//   5. per row: delta = (acc - (sum e_c - sum e_s) o) / l' with o read from TMEM; delta
+//      goes back to TMEM, the two threads' partial norms are added, and the certificate
+//      is checked as in k_inc_patch with ||delta|| replaced by ||delta|| + B, B a bound
+//      on the error of the BF16 computation (below), and each listed candidate's
 //      projection by |delta . (W_j - W_c)| + B ||W_j - W_c||;
-//   6. only a row that is searched (certificate not met) has o + delta written
-//      to O; a certified row keeps the sample's codeword and writes nothing else.
-//      With split operands (the path whose Q/K/V carry a BF16 lo plane) a row
-//      that the certificate does not settle is listed instead, and
-//      k_inc_exact_delta forms its correction from the split operands in FP32,
-//      so every output that reaches the search carries FP32-grade error.
+//   6. only a row that is searched (certificate not met) has o + delta written to O; a
+//      certified row keeps the sample's codeword and writes nothing else.  With split
+//      operands (the path whose Q/K/V carry a BF16 lo plane) a row that the certificate
+//      does not settle is listed instead, and k_inc_exact_delta forms its correction from
+//      the split operands in FP32, so every output that reaches the search carries
+//      FP32-grade error.  c's changed positions inside the tile are listed for the
+//      recompute and the search.
 //
 // The bound B.  The kernel reads only the hi planes: q~ = bf16(q), k~, v~ (each
 // within 2^-9 relative of the exact value, or equal to it on the plain BF16
 // path), e~ = exp2(s~ sl2 - m) with s~ = q~ . k~ accumulated in FP32, and the
 // MMA takes e^ = bf16(e~).  Per head, |s~ - s| <= 2^-8 (1 + 2^-7) ||q~|| ||k~||
 // (two relative 2^-9 perturbations plus the 32-term FP32 sum), so
-// |e~ / e - 1| <= tau = 2^dx - 1 + 2^-20 with dx = 2^-8 1.01 sl2 ||q~|| ||k~||
-// (the 2^-20 covers ex2.approx and the rounding of its argument; 2^dx - 1 is
-// bounded by y + y^2, y = dx ln 2, which holds for y <= 1), and
+// |e~ / e - 1| <= tau = 2^dx - 1 + 2^-20 with dx = 2^-8 1.01 sl2 ||q~|| kmax, kmax
+// the largest ||k~|| among the head's changed keys (the sample's and the
+// configuration's; the 2^-20 covers ex2.approx and the rounding of its argument;
+// 2^dx - 1 is bounded by y + y^2, y = dx ln 2, which holds for y <= 1), and
 // e^ v~ - e v = (e^ - e) v~ + e (v~ - v) has norm <= e (tau + 2^-8) ||v~||.
-// With A = sum_k e~ (tau + 2^-8) ||v~|| and T = sum_k e~ tau over the row's
-// changed keys (the sample's and the configuration's), the numerator and the
-// weight sum w differ from exact by at most 1.1 (A + T ||o||) and the
-// normaliser by at most 1.1 T (e <= 1.1 e~ while tau <= 0.1), so
+// With A = (tau + 2^-8) sum_k e~ ||v~|| and T = tau sum_k e~ over the row's
+// changed keys, the numerator and the weight sum w differ from exact by at most
+// 1.1 (A + T ||o||) and the normaliser by at most 1.1 T (e <= 1.1 e~ while
+// tau <= 0.1), so
 //   ||delta~_h - delta_h|| <= B_h = 1.1 (A + T (||o_h|| + ||delta~_h||)) / (l~' - 1.1 T)
-// per head and B = sqrt(sum_h B_h^2).  A row with tau > 0.1 for some key, or
+// per head and B = sqrt(sum_h B_h^2).  A row with tau > 0.1, or
 // l~' - 1.1 T <= l~' / 2, is recomputed over all keys.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-size_t patch_tc_smem(int d, int heads, int N) {
-    return 128 + (size_t)128 * d * 2 + (size_t)heads * 4096 + (size_t)2 * 128 * (2 + CERT_T) * 4 + 64 +
-           (size_t)4 * N * 4 + (size_t)((N + 15) & ~15) + (size_t)2 * heads * 32 * 4;
-}
-
-// e~ (tau + 2^-8) ||v~|| and e~ tau of one changed key (see the bound B above), with
-// 2^dx - 1 = e^y - 1 <= y + y^2 for y = dx ln 2 <= 1; sets guard when tau would exceed 0.1
-__device__ __forceinline__ void patch_err_terms(float e, float dx, float vn, float& acc_a, float& acc_t, bool& guard) {
-    const float y = dx * 0.69314718f * 1.0001f;
-    const float tau = fmaf(y, y, y) + 9.5367431640625e-07f;  // + 2^-20
-    if (y > 0.09f) guard = true;
-    acc_a = fmaf(e * (tau + 3.90625e-3f), vn, acc_a);
-    acc_t = fmaf(e, tau, acc_t);
-}
-
 // The BF16 weights of one head for a row with nk changed keys before it (nk <= NKB):
 // e_s = exp(s_s / sqrt(dh) - m) negated in slots 0..15, e_c in 16..31, zeros beyond
 // nk; seb, sec their sums; guard set when a new score overflows the sample's max.
-// Also the error bound's sums over the row's changed keys: aa += e (tau + 2^-8) ||v~||,
-// at += e tau (patch_err_terms), with dx = qn ||k~|| per key (qn = 2^-8 1.01 sl2 ||q~||).
+// sv += sum_k e ||v~|| over the row's changed keys (vn2[k] = (||v~_s||, ||v~_c||) of
+// slot pair k), the value-norm sum of the bound B above.
 template <int NKB>
 __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float sl2, float m2, bool& guard, float& seb,
-                                              float& sec, uint32_t (&e16)[16], float qn, const float* __restrict__ kn,
-                                              const float* __restrict__ vn, float& aa, float& at) {
+                                              float& sec, uint32_t (&e16)[16], const float2* __restrict__ vn2,
+                                              float& sv) {
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         float eb = 0.f, ec = 0.f;
@@ -403,8 +394,8 @@ __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float s
             if (xc > 115.f) guard = true;
             eb = ex2_approx(__uint_as_float(s[kk]) * sl2 - m2);
             ec = ex2_approx(fminf(xc, 115.f));
-            patch_err_terms(eb, qn * kn[kk], vn[kk], aa, at, guard);
-            patch_err_terms(ec, qn * kn[16 + kk], vn[16 + kk], aa, at, guard);
+            const float2 v = vn2[kk];
+            sv = fmaf(eb, v.x, fmaf(ec, v.y, sv));
         }
         seb += eb;
         sec += ec;
@@ -418,45 +409,92 @@ __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float s
     }
 }
 
-__global__ void __launch_bounds__(256, 2)
-k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
-               float* __restrict__ O, const float2* __restrict__ bstat, const CertRow* __restrict__ cert,
-               const float* __restrict__ codebook, const float* __restrict__ wd, int* __restrict__ code,
-               int* __restrict__ vq_rows, const int* __restrict__ act_off, int2* __restrict__ rc_rows,
-               int* __restrict__ rc_cnt, const int* __restrict__ list_tc, const short* __restrict__ dpos,
-               const int* __restrict__ dcnt, int split, int2* __restrict__ ex_rows, uint32_t tmem_cols,
-               int* __restrict__ status, long long* __restrict__ stats) {
+constexpr int RES_THREADS = 512;  // four threads per tile row, a quarter of the heads each
+constexpr int RES_LCAP = 1024;    // list entries gathered before one flush to the global lists
+
+struct ResLayout {
+    size_t q, e, k, v, cert, n2, pr, kx, vn, dp, vq, full, bar, total;
+};
+__host__ __device__ inline ResLayout res_layout(int d, int H) {
+    ResLayout L;
+    size_t o = 0;
+    auto a128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+    L.q = o;    o += a128((size_t)128 * d * 2);
+    L.e = o;    o += a128((size_t)128 * d * 2);
+    L.k = o;    o += (size_t)H * 2048;
+    L.v = o;    o += (size_t)H * 2048;
+    L.cert = o; o += a128(128 * sizeof(CertRow));
+    L.n2 = o;   o += 4 * 128 * sizeof(float2);
+    L.pr = o;   o += 4 * 128 * CERT_T * sizeof(float);
+    L.kx = o;   o += (size_t)H * sizeof(float);
+    L.vn = o;   o += (size_t)H * 32 * sizeof(float);
+    L.dp = o;   o += 2 * 32 * sizeof(int);
+    L.vq = o;   o += RES_LCAP * sizeof(int);
+    L.full = o; o += RES_LCAP * sizeof(int2);
+    L.bar = o;  o += 64;
+    L.total = o + 128;  // + alignment of the dynamic base
+    return L;
+}
+
+// The first connected configuration of sample b's slice from c (stepping by `slices`, below
+// cb1) patched on the tensor cores whose first changed position is before tend; -1 if none.
+// Every thread of a warp gets the same answer (32 candidates per round).
+__device__ __forceinline__ int res_next_cfg(const Chunk& ch, const int* __restrict__ dcnt, int c, int cb1,
+                                            int slices, int tend) {
+    const int lane = threadIdx.x & 31;
+    for (; c < cb1; c += 32 * slices) {
+        const int cc = c + lane * slices;
+        bool f = false;
+        if (cc < cb1) f = dcnt[cc] <= PATCH_TC_KEYS && cfg_first_changed(ch.cfg_i[cc], ch.cfg_j[cc]) < tend;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (m) return c + (__ffs(m) - 1) * slices;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(RES_THREADS, 1)
+k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv,
+                float* __restrict__ O, const float2* __restrict__ bstat, const CertRow* __restrict__ cert,
+                const float* __restrict__ codebook, const float* __restrict__ wd, int* __restrict__ code,
+                int* __restrict__ vq_rows, const int* __restrict__ act_off, int2* __restrict__ rc_rows,
+                int* __restrict__ rc_cnt, const short* __restrict__ dpos, const int* __restrict__ dcnt, int split,
+                int2* __restrict__ ex_rows, int slices, uint32_t tmem_cols, int* __restrict__ status,
+                long long* __restrict__ stats) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     constexpr int DH = 32;
-    const int d = ch.d, H = ch.heads, NM = ch.N;  // d == 32 H
-    const int HH = H / 2;                         // heads per thread
-    uint8_t* sQE = smem;                          // [128 x d] queries, then [128 x d] weights
-    uint8_t* sK = sQE + 128 * d * 2;              // per head [32 keys x 32 dims]
-    uint8_t* sVt = sK + H * 2048;                 // per head [32 dims x 32 keys]
-    // [2 halves][128]: partial ||delta~||^2 and B^2 (B^2 = -1: the thread's heads need a recompute)
-    float2* sN2 = reinterpret_cast<float2*>(sVt + H * 2048);
-    float* sP = reinterpret_cast<float*>(sN2 + 256);        // [2 halves][128][CERT_T]: partial projections
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sP + 256 * CERT_T);
+    constexpr int HQ = 2;                         // most heads per thread (H <= 8)
+    const int d = ch.d, H = ch.heads, NM = ch.N;  // d == 32 H, H in {4, 8}
+    const int hq = H / 4;                         // heads per thread
+    const ResLayout L = res_layout(d, H);
+    uint8_t* sQ = smem + L.q;    // [128 x d] the tile's queries
+    uint8_t* sE = smem + L.e;    // [128 x d] the weights, head h in columns 32h .. 32h + 31
+    uint8_t* sK = smem + L.k;    // per head [32 key slots x 32 dims]
+    uint8_t* sV = smem + L.v;    // per head [32 key slots x 32 dims], read as the MN-major B operand
+    const CertRow* sCert = reinterpret_cast<const CertRow*>(smem + L.cert);  // [128]
+    float2* sN2 = reinterpret_cast<float2*>(smem + L.n2);  // [4 quarters][128]: ||delta~||^2, B^2 (-1: guard)
+    float* sP = reinterpret_cast<float*>(smem + L.pr);     // [4 quarters][128][CERT_T]: projections
+    float* sKx = reinterpret_cast<float*>(smem + L.kx);    // [H] largest ||k~|| of the key slots
+    float2* sVn = reinterpret_cast<float2*>(smem + L.vn);  // [H][16] ||v~|| of slot pairs (sample's, c's)
+    int* sD = reinterpret_cast<int*>(smem + L.dp);         // [2][32] changed positions (this, next)
+    int* sVq = reinterpret_cast<int*>(smem + L.vq);        // rows to search
+    int2* sFull = reinterpret_cast<int2*>(smem + L.full);  // rows to recompute (row, position)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
-    int* sD = reinterpret_cast<int*>(tmem_holder + 4);  // [PATCH_TC_KEYS]
-    int* sRows = sD + PATCH_TC_KEYS;                    // [NM]
-    int* sVq = sRows + NM;                              // [NM]
-    int* sFull = sVq + NM;                              // [NM]
-    uint8_t* sFlag = reinterpret_cast<uint8_t*>(sFull + NM);  // [NM]
-    float* sKn = reinterpret_cast<float*>(sFlag + ((NM + 15) & ~15));  // [H][32]: ||k~|| of the key slots
-    float* sVn = sKn + H * 32;                                         // [H][32]: ||v~||
-    __shared__ int s_warp[32];
     __shared__ int sNvq, sNfull, sBase[2], s_item;
     __shared__ long long sCnt[4];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int half = tid >> 7, r = tid & 127;
-    const int h0 = half * HH;
+    const int qq = tid >> 7, r = tid & 127;
+    const int h0 = qq * hq;
     const int ld = 3 * d;
+    const int nkv = H * 32 * (DH / 8);  // 16-byte chunks of one configuration's keys (or values)
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);
+    const float cdx = 3.90625e-3f * 1.01f * sl2;  // 2^-8 (1 + 2^-7), log2 units
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         tc::fence_barrier_init();
+        sNvq = 0;
+        sNfull = 0;
     }
     if (tid < 4) sCnt[tid] = 0;
     if (warp == 0) tc::tmem_alloc(tmem_holder, tmem_cols);
@@ -464,101 +502,163 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // warps w and w + 4 share TMEM lanes
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;  // warps w, w + 4, w + 8, w + 12 share lanes
+    const uint32_t t_acc = tmem + lane_base, t_o = tmem + lane_base + (uint32_t)d;
     uint32_t phase = 0;
     bool ok = true;
-    long long n_patched = 0, n_cert = 0, n_full = 0, n_pairs = 0;
-    for (int item; ok && (item = next_item(ch.counters, CNT_TCW, CNT_TCL, &s_item)) >= 0;) {
-        const int c = list_tc[item];
-        const int b = ch.cfg_sample[c];
-        const int rc = ch.cfg_row[c], rb = ch.cfg_row[ch.cfg_off[b]];
-        const int N = cfg_N(ch, c);
-        const int p0 = cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]);
-        const int* uc = uid + rc;
+    unsigned n_patched = 0, n_cert = 0, n_full = 0, n_pairs = 0;  // this thread's counts
+    const int ntile = (NM + 127) / 128;
+    const int items = ch.S * ntile * slices;
+
+    // keys (part 1) or values (part 2) of configuration c's changed positions, the sample's
+    // in slots 0..15 and c's in 16..31, zero-filled, into dst with cp.async; dl: c's changed
+    // positions in shared memory.  Both tiles take the K-major core layout of [32 slots x 32
+    // dims] per head; the value MMA reads theirs as an MN-major B operand.
+    auto stage_kv = [&](uint8_t* dst, int part, const int* ub, const int* uc, const int* dl, int nd) {
+        for (int u = tid; u < nkv; u += RES_THREADS) {
+            const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
+            const int n = rem & 31, t8 = (rem >> 5) * 8;
+            const int kk = n & 15;
+            const __nv_bfloat16* x = qkv;
+            if (kk < nd) x = qkv + (size_t)(n < 16 ? ub[dl[kk]] : uc[dl[kk]]) * ld + part * d + h * DH + t8;
+            cp_async16(tc::smem_u32(dst + h * 2048 + tc::core_off(n, t8, DH)), x, kk < nd ? 16 : 0);
+        }
+    };
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&ch.counters[CNT_TCW], 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= items || !ok) break;
+        const int tq = item / (ch.S * slices);  // the last tiles (most patched rows) first
+        const int rest = item - tq * ch.S * slices;
+        const int b = rest / slices, z = rest - b * slices;
+        const int t0 = (ntile - 1 - tq) * 128;
+        const int N = sample_N(ch, b);
+        if (t0 >= N) continue;
+        const int tend = min(N, t0 + 128);
+        const int cb0 = ch.cfg_off[b], cb1 = ch.cfg_off[b + 1];
+        int c = res_next_cfg(ch, dcnt, cb0 + 1 + z, cb1, slices, tend);
+        if (c < 0) continue;
+        const int rb = ch.cfg_row[cb0];
         const int* ub = uid + rb;
-        const int nd = dcnt[c];  // <= PATCH_TC_KEYS
-        for (int p = tid; p < N; p += blockDim.x) sFlag[p] = 0;
-        __syncthreads();
-        if (tid < nd) {
-            sD[tid] = dpos[(size_t)c * INC_MAX_KEYS + tid];
-            sFlag[sD[tid]] = 1;
+        const int p = t0 + r;
+        const bool valid = p < N;
+        // ---- the sample's tile: queries and certificate rows (cp.async), outputs into TMEM
+        for (int u = tid; u < 128 * (d / 8); u += RES_THREADS) {
+            const int rr = u / (d / 8), k8 = (u - rr * (d / 8)) * 8;
+            const bool in = t0 + rr < N;
+            const __nv_bfloat16* src = in ? qkv + (size_t)ub[t0 + rr] * ld + k8 : qkv;
+            cp_async16(tc::smem_u32(sQ + tc::core_off(rr, k8, d)), src, in ? 16 : 0);
         }
-        __syncthreads();
-        const int np = block_compact(p0, N, [&](int p) { return sFlag[p] == 0; }, sRows, NM, s_warp);
-        if (tid < nd) {  // changed positions: recompute, then search
-            sVq[tid] = rc + sD[tid];
-            sFull[tid] = rc + sD[tid];
+        {
+            constexpr int CW = (int)(sizeof(CertRow) / 16);  // 16-byte words of a certificate row
+            const uint8_t* cg = reinterpret_cast<const uint8_t*>(cert + (size_t)b * NM + t0);
+            for (int u = tid; u < 128 * CW; u += RES_THREADS) {
+                const bool in = t0 + u / CW < N;
+                cp_async16(tc::smem_u32(smem + L.cert + (size_t)u * 16),
+                           in ? cg + (size_t)u * 16 : reinterpret_cast<const uint8_t*>(cert), in ? 16 : 0);
+            }
         }
-        if (tid == 0) { sNvq = nd; sNfull = nd; }
-        n_full += tid == 0 ? nd : 0;
-        for (int t0 = 0; t0 < np && ok; t0 += 128) {
-            const int nrow = min(128, np - t0);
-            const int p = r < nrow ? sRows[t0 + r] : -1;
-            // keys of the changed positions, zero-filled to 16 + 16 per head
-            for (int u = tid; u < H * 32 * (DH / 8); u += blockDim.x) {
-                const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
-                const int n = rem & 31, t8 = (rem >> 5) * 8;  // key slot, first of 8 dims
-                const int kk = n & 15;
-                const __nv_bfloat16* x = qkv;
-                if (kk < nd) x = qkv + (size_t)(n < 16 ? ub[sD[kk]] : uc[sD[kk]]) * ld + d + h * DH + t8;
-                cp_async16(tc::smem_u32(sK + h * 2048 + tc::core_off(n, t8, DH)), x, kk < nd ? 16 : 0);
-            }
-            // the row's query: thread (r, half) copies chunks half, half + 2, ...
-            {
-                const __nv_bfloat16* qrow = p >= 0 ? qkv + (size_t)ub[p] * ld : qkv;
-                const int nb = p >= 0 ? 16 : 0;
-                for (int k8 = half * 8; k8 < d; k8 += 16)
-                    cp_async16(tc::smem_u32(sQE + tc::core_off(r, k8, d)), qrow + k8, nb);
-            }
-            // values, transposed: dims are the rows of the [dims x keys] operand
-            for (int u0 = tid; u0 < H * 32 * (DH / 8); u0 += 4 * blockDim.x) {
-                uint4 vv[4];
+        float on[HQ], qn[HQ];
+        float2 mls[HQ];
+        {
+            const float* orow = O + (size_t)(rb + (valid ? p : 0)) * d;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int u = u0 + i * blockDim.x;
-                    const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
-                    const int n = rem & 31, t8 = (rem >> 5) * 8, kk = n & 15;
-                    vv[i] = make_uint4(0, 0, 0, 0);
-                    if (u < H * 32 * (DH / 8) && kk < nd)
-                        vv[i] = *reinterpret_cast<const uint4*>(
-                            qkv + (size_t)(n < 16 ? ub[sD[kk]] : uc[sD[kk]]) * ld + 2 * d + h * DH + t8);
+            for (int hh = 0; hh < HQ; ++hh) {
+                on[hh] = 0.f;
+                mls[hh] = make_float2(0.f, 1.f);
+                if (hh >= hq) continue;
+                const int h = h0 + hh;
+                uint32_t a[32];
+                float s2 = 0.f;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float4 o4 = valid ? *reinterpret_cast<const float4*>(orow + h * 32 + 4 * t)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    a[4 * t] = __float_as_uint(o4.x);
+                    a[4 * t + 1] = __float_as_uint(o4.y);
+                    a[4 * t + 2] = __float_as_uint(o4.z);
+                    a[4 * t + 3] = __float_as_uint(o4.w);
+                    s2 = fmaf(o4.x, o4.x, fmaf(o4.y, o4.y, fmaf(o4.z, o4.z, fmaf(o4.w, o4.w, s2))));
                 }
+                on[hh] = sqrtf(s2);
+                tc::tmem_st32(t_o + h * 32, a);
+                if (valid) mls[hh] = bstat[((size_t)b * NM + p) * H + h];
+            }
+        }
+        // the first configuration's changed positions, keys and values
+        int buf = 0;
+        int nd = dcnt[c], rc = ch.cfg_row[c], p0 = cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]);
+        if (tid < nd) sD[tid] = dpos[(size_t)c * INC_MAX_KEYS + tid];
+        __syncthreads();
+        stage_kv(sK, 1, ub, uid + rc, sD, nd);
+        stage_kv(sV, 2, ub, uid + rc, sD, nd);
+        cp_async_wait_all();
+        __syncthreads();
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int u = u0 + i * blockDim.x;
-                    if (u >= H * 32 * (DH / 8)) break;
-                    const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
-                    const int n = rem & 31, t8 = (rem >> 5) * 8;
-                    const __nv_bfloat16* ve = reinterpret_cast<const __nv_bfloat16*>(&vv[i]);
+        for (int hh = 0; hh < HQ; ++hh) {  // ||q~_h|| in the bound's units
+            qn[hh] = 0.f;
+            if (hh >= hq) continue;
+            float s2 = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        *reinterpret_cast<__nv_bfloat16*>(sVt + h * 2048 + tc::core_off(t8 + e, n, 32)) = ve[e];
+            for (int c8 = 0; c8 < 4; ++c8) {
+                const uint4 u = *reinterpret_cast<const uint4*>(sQ + tc::core_off(r, (h0 + hh) * 32 + c8 * 8, d));
+                const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(b2[k]);
+                    s2 = fmaf(f.x, f.x, fmaf(f.y, f.y, s2));
                 }
             }
-            cp_async_wait_all();
+            qn[hh] = cdx * sqrtf(s2);
+        }
+        const CertRow& cr = sCert[r];
+        // ---- the slice's configurations; the next one's keys and values load during this one
+        while (ok) {
+            const int* dl = sD + buf * 32;
+            // staged keys and values of c: slot norms (one slot of one tile per thread; a warp
+            // covers the 32 slots of one head): the values' per slot, the keys' largest per head
+            for (int u = tid; u < 2 * H * 32; u += RES_THREADS) {
+                const int kv = u / (H * 32), hn = u - kv * (H * 32);
+                const int h = hn >> 5, n = hn & 31;
+                const uint8_t* tile = (kv ? sV : sK) + h * 2048;
+                float s2 = 0.f;
+#pragma unroll
+                for (int c8 = 0; c8 < 4; ++c8) {
+                    const uint4 x = *reinterpret_cast<const uint4*>(tile + tc::core_off(n, c8 * 8, DH));
+                    const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&x);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 f = __bfloat1622float2(b2[k]);
+                        s2 = fmaf(f.x, f.x, fmaf(f.y, f.y, s2));
+                    }
+                }
+                const float nrm = sqrtf(s2);
+                if (kv) {
+                    reinterpret_cast<float*>(sVn)[h * 32 + (n & 15) * 2 + (n >> 4)] = nrm;
+                } else {
+                    // non-negative floats order as their bit patterns
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(nrm));
+                    if (n == 0) sKx[h] = __uint_as_float(mx);
+                }
+            }
+            // this row's role: patched (at or after p0, not changed), with nk changed keys before it
+            int nk = 0;
+            bool changed = false;
+            for (int k = 0; k < nd; ++k) {
+                const int q = dl[k];
+                nk += q < p;
+                changed |= q == p;
+            }
+            const bool prow = valid && p >= p0 && !changed;
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
-            // norms of the staged key and value slots (zero-filled slots give 0); read after the
-            // next block-wide barrier
-            for (int u = tid; u < H * 32; u += blockDim.x) {
-                const int h = u >> 5, n = u & 31;
-                float kk2 = 0.f, vv2 = 0.f;
-#pragma unroll
-                for (int t = 0; t < DH; ++t) {
-                    const float kx = __bfloat162float(
-                        *reinterpret_cast<const __nv_bfloat16*>(sK + h * 2048 + tc::core_off(n, t, DH)));
-                    const float vx = __bfloat162float(
-                        *reinterpret_cast<const __nv_bfloat16*>(sVt + h * 2048 + tc::core_off(t, n, 32)));
-                    kk2 = fmaf(kx, kx, kk2);
-                    vv2 = fmaf(vx, vx, vv2);
-                }
-                sKn[u] = sqrtf(kk2);
-                sVn[u] = sqrtf(vv2);
-            }
-            if (tid == 0) {
+            if (tid == 0) {  // S_h = Q_h [K_s; K_c]_h^T
                 tc::tc_fence_after();
-                const uint64_t dq = tc::desc_kmajor_none(tc::smem_u32(sQE), 128, (d / 8) * 128);
+                const uint64_t dq = tc::desc_kmajor_none(tc::smem_u32(sQ), 128, (d / 8) * 128);
                 for (int h = 0; h < H; ++h) {
                     const uint64_t dk = tc::desc_kmajor_none(tc::smem_u32(sK + h * 2048), 128, (DH / 8) * 128);
 #pragma unroll
@@ -568,59 +668,53 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 }
                 tc::mma_commit(bar);
             }
+            // the next configuration of the slice, while the scores form
+            const int cn = res_next_cfg(ch, dcnt, c + slices, cb1, slices, tend);
+            int nd_n = 0, rc_n = 0, p0_n = 0;
+            int* dl_n = sD + (buf ^ 1) * 32;
+            if (cn >= 0) {
+                nd_n = dcnt[cn];
+                rc_n = ch.cfg_row[cn];
+                p0_n = cfg_first_changed(ch.cfg_i[cn], ch.cfg_j[cn]);
+                if (tid < nd_n) dl_n[tid] = dpos[(size_t)cn * INC_MAX_KEYS + tid];
+            }
             ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
             phase ^= 1;
             tc::tc_fence_after();
             if (!ok) break;
-            float w[4], inv[4];  // per own head: sum e_c - sum e_s, 1 / l'
-            float ea[4], et[4];  // per own head: the bound's sums A and T, times 1.1 / (l~' - 1.1 T)
+            if (cn >= 0) stage_kv(sK, 1, ub, uid + rc_n, dl_n, nd_n);  // the score MMAs are done with sK
+            float w[HQ], inv[HQ], ea[HQ], et[HQ];
             bool guard = false;
-            int nk = 0;  // changed keys before this row
-            while (p >= 0 && nk < nd && sD[nk] < p) ++nk;
-            // warps w and w + 4 hold the same rows: both skip a tile's padding rows together
-            const bool wact = __any_sync(0xffffffffu, p >= 0);
-            const int nkw = __reduce_max_sync(0xffffffffu, nk);
+            // warps sharing TMEM lanes hold the same rows: they skip rows without work together
+            const bool wact = __any_sync(0xffffffffu, prow);
+            const int nkw = __reduce_max_sync(0xffffffffu, prow ? nk : 0);
+            const int nkr = prow ? nk : 0;
             if (wact) {
-                float2 mls[4];
-                const float2* bs = bstat + ((size_t)b * NM + (p >= 0 ? p : 0)) * H + h0;
 #pragma unroll
-                for (int hh = 0; hh < 4; ++hh) mls[hh] = (hh < HH && p >= 0) ? bs[hh] : make_float2(0.f, 1.f);
-                const float cdx = 3.90625e-3f * 1.01f * sl2;  // 2^-8 (1 + 2^-7), log2 units
-#pragma unroll
-                for (int hh = 0; hh < 4; ++hh) {
-                    if (hh >= HH) break;
+                for (int hh = 0; hh < HQ; ++hh) {
+                    if (hh >= hq) break;
                     const int h = h0 + hh;
-                    // ||q~|| of this head, from the staged query before its columns take the weights
-                    float qn = 0.f;
-#pragma unroll
-                    for (int c8 = 0; c8 < 4; ++c8) {
-                        const uint4 u = *reinterpret_cast<const uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d));
-                        const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float2 f = __bfloat1622float2(b2[k]);
-                            qn = fmaf(f.x, f.x, fmaf(f.y, f.y, qn));
-                        }
-                    }
-                    qn = cdx * sqrtf(qn);
                     uint32_t s[32];
-                    tc::tmem_ld32(tmem + lane_base + h * 32, s);
+                    tc::tmem_ld32(t_acc + h * 32, s);
                     const float2 ml = mls[hh];
                     const float m2 = ml.x * 1.4426950408889634f;
-                    float seb = 0.f, sec = 0.f;
-                    uint32_t e16[16];  // the 32 weights as packed BF16 pairs
-                    float aa = 0.f, at = 0.f;  // the error bound's sums A and T
-                    const float* kn = sKn + h * 32;
-                    const float* vn = sVn + h * 32;
+                    float seb = 0.f, sec = 0.f, sv = 0.f;
+                    uint32_t e16[16];
+                    const float2* vn2 = sVn + h * 16;
                     if (nkw <= 4)
-                        patch_weights<4>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
+                        patch_weights<4>(s, nkr, sl2, m2, guard, seb, sec, e16, vn2, sv);
                     else if (nkw <= 8)
-                        patch_weights<8>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
+                        patch_weights<8>(s, nkr, sl2, m2, guard, seb, sec, e16, vn2, sv);
                     else
-                        patch_weights<16>(s, nk, sl2, m2, guard, seb, sec, e16, qn, kn, vn, aa, at);
+                        patch_weights<16>(s, nkr, sl2, m2, guard, seb, sec, e16, vn2, sv);
+                    // the bound's A and T from tau of the head's largest changed key norm
+                    const float y = qn[hh] * sKx[h] * (0.69314718f * 1.0001f);
+                    if (y > 0.09f) guard = true;
+                    const float tau = fmaf(y, y, y) + 9.5367431640625e-07f;  // + 2^-20
+                    const float aa = (tau + 3.90625e-3f) * sv, at = tau * (seb + sec);
 #pragma unroll
                     for (int c8 = 0; c8 < 4; ++c8)
-                        *reinterpret_cast<uint4*>(sQE + tc::core_off(r, h * 32 + c8 * 8, d)) =
+                        *reinterpret_cast<uint4*>(sE + tc::core_off(r, h * 32 + c8 * 8, d)) =
                             make_uint4(e16[4 * c8], e16[4 * c8 + 1], e16[4 * c8 + 2], e16[4 * c8 + 3]);
                     if (!(seb <= 0.5f * ml.y)) guard = true;  // cancellation
                     w[hh] = sec - seb;
@@ -635,15 +729,16 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             tc::fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0) {  // E_h [V_s; V_c]_h into the columns the scores came from
                 tc::tc_fence_after();
-                const uint64_t de = tc::desc_kmajor_none(tc::smem_u32(sQE), 128, (d / 8) * 128);
+                const uint64_t de = tc::desc_kmajor_none(tc::smem_u32(sE), 128, (d / 8) * 128);
                 for (int h = 0; h < H; ++h) {
-                    const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sVt + h * 2048), 128, (32 / 8) * 128);
+                    // MN-major B: 8-slot groups (K) 512 bytes apart, 8-dim groups (N) 128 bytes apart
+                    const uint64_t dv = tc::desc_kmajor_none(tc::smem_u32(sV + h * 2048), 512, 128);
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks)
-                        tc::mma_bf16(tmem + h * 32, de + (uint64_t)(h * 32 + ks * 16), dv + (uint64_t)(ks * 16),
-                                     tc::idesc_bf16_f32(128, DH), ks > 0 ? 1u : 0u);
+                        tc::mma_bf16(tmem + h * 32, de + (uint64_t)(h * 32 + ks * 16), dv + (uint64_t)(ks * 64),
+                                     tc::idesc_bf16_f32_bmn(128, DH), ks > 0 ? 1u : 0u);
                 }
                 tc::mma_commit(bar);
             }
@@ -651,146 +746,164 @@ k_inc_patch_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             phase ^= 1;
             tc::tc_fence_after();
             if (!ok) break;
-            // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm
-            const float* orow = O + (size_t)(rb + (p >= 0 ? p : 0)) * d;
+            if (cn >= 0) stage_kv(sV, 2, ub, uid + rc_n, dl_n, nd_n);  // the value MMAs are done with sV
+            // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm and B^2
             float n2 = 0.f, b2 = 0.f;
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-                if (hh >= HH || !wact) break;
+            for (int hh = 0; hh < HQ; ++hh) {
+                if (hh >= hq || !wact) break;
                 const int h = h0 + hh;
-                float4 o4[8];
+                float hn2 = 0.f;
 #pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    o4[t] = p >= 0 ? *reinterpret_cast<const float4*>(orow + h * 32 + 4 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
-                uint32_t a[32];
-                tc::tmem_ld32(tmem + lane_base + h * 32, a);
-                float hn2 = 0.f, on2 = 0.f;
+                for (int c16 = 0; c16 < 32; c16 += 16) {  // two 16-column halves of the head
+                    uint32_t a[16], o[16];
+                    tc::tmem_ld16(t_acc + h * 32 + c16, a);
+                    tc::tmem_ld16(t_o + h * 32 + c16, o);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const float d0 = (__uint_as_float(a[4 * t]) - w[hh] * o4[t].x) * inv[hh];
-                    const float d1 = (__uint_as_float(a[4 * t + 1]) - w[hh] * o4[t].y) * inv[hh];
-                    const float d2 = (__uint_as_float(a[4 * t + 2]) - w[hh] * o4[t].z) * inv[hh];
-                    const float d3 = (__uint_as_float(a[4 * t + 3]) - w[hh] * o4[t].w) * inv[hh];
-                    hn2 = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, hn2))));
-                    on2 = fmaf(o4[t].x, o4[t].x, fmaf(o4[t].y, o4[t].y, fmaf(o4[t].z, o4[t].z, fmaf(o4[t].w, o4[t].w, on2))));
-                    a[4 * t] = __float_as_uint(d0);
-                    a[4 * t + 1] = __float_as_uint(d1);
-                    a[4 * t + 2] = __float_as_uint(d2);
-                    a[4 * t + 3] = __float_as_uint(d3);
+                    for (int t = 0; t < 16; ++t) {
+                        const float dv = (__uint_as_float(a[t]) - w[hh] * __uint_as_float(o[t])) * inv[hh];
+                        hn2 = fmaf(dv, dv, hn2);
+                        a[t] = __float_as_uint(dv);
+                    }
+                    tc::tmem_st16(t_acc + h * 32 + c16, a);
                 }
                 n2 += hn2;
                 // B_h = 1.1 (A + T (||o_h|| + ||delta~_h||)) / (l~' - 1.1 T)
-                const float bh = ea[hh] + et[hh] * (sqrtf(on2) + sqrtf(hn2));
+                const float bh = ea[hh] + et[hh] * (on[hh] + sqrtf(hn2));
                 b2 = fmaf(bh, bh, b2);
-                tc::tmem_st32(tmem + lane_base + h * 32, a);
             }
             sN2[tid] = make_float2(n2, guard ? -1.f : b2);
             __syncthreads();
-            {  // the same sums, in the same order, for both threads of the row
-                const float2 a0 = sN2[r], a1 = sN2[128 + r];
-                n2 = a0.x + a1.x;
-                guard = a0.y < 0.f || a1.y < 0.f;
+            float bnd;
+            {  // the same sums, in the same order, for the row's four threads
+                const float2 a0 = sN2[r], a1 = sN2[128 + r], a2 = sN2[256 + r], a3 = sN2[384 + r];
+                n2 = ((a0.x + a1.x) + a2.x) + a3.x;
+                guard = a0.y < 0.f || a1.y < 0.f || a2.y < 0.f || a3.y < 0.f;
+                bnd = guard ? 0.f : sqrtf(((a0.y + a1.y) + a2.y) + a3.y);
             }
-            const float bnd = guard ? 0.f : sqrtf(sN2[r].y + sN2[128 + r].y);
-            const CertRow* cr = cert + ((size_t)b * NM + (p >= 0 ? p : 0));
             int md = -1, nc = 0;
-            if (p >= 0) {
+            if (prow) {
                 if (guard) {
                     md = 2;
                 } else {
                     // ||delta|| <= ||delta~|| + B for the exact correction of these inputs
                     const float dn = sqrtf(n2) + bnd;
-                    if (!(dn < cr->next)) {
+                    if (!(dn < cr.next)) {
                         md = 1;
                     } else {
-                        while (nc < cr->n && cr->rho[nc] <= dn) ++nc;
+                        while (nc < cr.n && cr.rho[nc] <= dn) ++nc;
                         md = nc ? 3 : 0;
                     }
                 }
             }
             // pass B: exact check of the listed candidates, each thread over its heads
-            // (md agrees between warps w and w + 4, so their TMEM loads stay warp-uniform)
-            if (__any_sync(0xffffffffu, md == 3)) {
-                float proj[CERT_T];
+            // (md agrees between the warps of a row, so their TMEM loads stay warp-uniform)
+            if (__syncthreads_or(md == 3)) {
+                if (__any_sync(0xffffffffu, md == 3)) {
+                    float proj[CERT_T];
 #pragma unroll
-                for (int i = 0; i < CERT_T; ++i) proj[i] = 0.f;
-                const float* wc = codebook + (size_t)(md == 3 ? cr->code : 0) * d;
-                for (int hh = 0; hh < HH; ++hh) {
-                    const int h = h0 + hh;
-                    uint32_t a[32];
-                    tc::tmem_ld32(tmem + lane_base + h * 32, a);
-                    if (md == 3) {
-                        for (int i = 0; i < nc; ++i) {
-                            const float* wj = codebook + (size_t)cr->j[i] * d + h * 32;
-                            float sacc = 0.f;
+                    for (int i = 0; i < CERT_T; ++i) proj[i] = 0.f;
+                    const float* wc = codebook + (size_t)(md == 3 ? cr.code : 0) * d;
+                    for (int hc = 0; hc < 2 * hq; ++hc) {  // 16-column halves of the own heads
+                        const int col = (h0 + (hc >> 1)) * 32 + (hc & 1) * 16;
+                        uint32_t a[16];
+                        tc::tmem_ld16(t_acc + col, a);
+                        if (md == 3) {
 #pragma unroll
-                            for (int t = 0; t < 32; t += 4) {
-                                const float4 a4 = *reinterpret_cast<const float4*>(wj + t);
-                                const float4 c4 = *reinterpret_cast<const float4*>(wc + h * 32 + t);
-                                sacc = fmaf(__uint_as_float(a[t]), a4.x - c4.x, sacc);
-                                sacc = fmaf(__uint_as_float(a[t + 1]), a4.y - c4.y, sacc);
-                                sacc = fmaf(__uint_as_float(a[t + 2]), a4.z - c4.z, sacc);
-                                sacc = fmaf(__uint_as_float(a[t + 3]), a4.w - c4.w, sacc);
+                            for (int i = 0; i < CERT_T; ++i) {
+                                if (i >= nc) break;
+                                const float* wj = codebook + (size_t)cr.j[i] * d + col;
+                                float sacc = 0.f;
+#pragma unroll
+                                for (int t = 0; t < 16; t += 4) {
+                                    const float4 a4 = *reinterpret_cast<const float4*>(wj + t);
+                                    const float4 c4 = *reinterpret_cast<const float4*>(wc + col + t);
+                                    sacc = fmaf(__uint_as_float(a[t]), a4.x - c4.x, sacc);
+                                    sacc = fmaf(__uint_as_float(a[t + 1]), a4.y - c4.y, sacc);
+                                    sacc = fmaf(__uint_as_float(a[t + 2]), a4.z - c4.z, sacc);
+                                    sacc = fmaf(__uint_as_float(a[t + 3]), a4.w - c4.w, sacc);
+                                }
+                                proj[i] += sacc;
                             }
-                            proj[i] += sacc;
                         }
                     }
-                }
-                if (md == 3) {
+                    if (md == 3) {
 #pragma unroll
-                    for (int i = 0; i < CERT_T; ++i) sP[tid * CERT_T + i] = proj[i];
+                        for (int i = 0; i < CERT_T; ++i) sP[tid * CERT_T + i] = proj[i];
+                    }
                 }
-            }
-            __syncthreads();
-            if (md == 3) {
-                md = 0;
-                for (int i = 0; i < nc; ++i) {
-                    const float wj = wd[(size_t)cr->code * ch.K + cr->j[i]];  // ||W_j - W_c||
-                    if (!(cr->gap[i] - 2.f * (sP[r * CERT_T + i] + sP[(128 + r) * CERT_T + i] + bnd * wj) > cr->eta))
-                        md = 1;
+                __syncthreads();
+                if (md == 3) {
+                    md = 0;
+                    for (int i = 0; i < nc; ++i) {
+                        const float wj = wd[(size_t)cr.code * ch.K + cr.j[i]];  // ||W_j - W_c||
+                        const float pj = ((sP[r * CERT_T + i] + sP[(128 + r) * CERT_T + i]) +
+                                          sP[(256 + r) * CERT_T + i]) + sP[(384 + r) * CERT_T + i];
+                        if (!(cr.gap[i] - 2.f * (pj + bnd * wj) > cr.eta)) md = 1;
+                    }
                 }
             }
             // split operands: a row the certificate does not settle gets its exact correction
             // from them (k_inc_exact_delta) before the search
-            if (split && md == 1 && half == 0) ex_rows[atomicAdd(&ch.counters[CNT_EX], 1)] = make_int2(rc + p, p);
+            if (split && md == 1 && qq == 0) ex_rows[atomicAdd(&ch.counters[CNT_EX], 1)] = make_int2(rc + p, p);
             // a searched row: o + delta goes to O for the vector quantizer
             if (!split && __any_sync(0xffffffffu, md == 1)) {
-                float* xo = O + (size_t)(rc + (p >= 0 ? p : 0)) * d;
-                for (int hh = 0; hh < HH; ++hh) {
-                    const int h = h0 + hh;
-                    uint32_t a[32];
-                    tc::tmem_ld32(tmem + lane_base + h * 32, a);
+                float* xo = O + (size_t)(rc + (p < N ? p : 0)) * d;
+                for (int hc = 0; hc < 2 * hq; ++hc) {  // 16-column halves of the own heads
+                    const int col = (h0 + (hc >> 1)) * 32 + (hc & 1) * 16;
+                    uint32_t a[16], o[16];
+                    tc::tmem_ld16(t_acc + col, a);
+                    tc::tmem_ld16(t_o + col, o);
                     if (md == 1) {
 #pragma unroll
-                        for (int t = 0; t < 32; t += 4) {
-                            const float4 o4 = *reinterpret_cast<const float4*>(orow + h * 32 + t);
-                            *reinterpret_cast<float4*>(xo + h * 32 + t) =
-                                make_float4(o4.x + __uint_as_float(a[t]), o4.y + __uint_as_float(a[t + 1]),
-                                            o4.z + __uint_as_float(a[t + 2]), o4.w + __uint_as_float(a[t + 3]));
-                        }
+                        for (int t = 0; t < 16; t += 4)
+                            *reinterpret_cast<float4*>(xo + col + t) = make_float4(
+                                __uint_as_float(o[t]) + __uint_as_float(a[t]),
+                                __uint_as_float(o[t + 1]) + __uint_as_float(a[t + 1]),
+                                __uint_as_float(o[t + 2]) + __uint_as_float(a[t + 2]),
+                                __uint_as_float(o[t + 3]) + __uint_as_float(a[t + 3]));
                     }
                 }
             }
-            if (half == 0) {
-                if (md == 0) code[rc + p] = cr->code;
+            if (qq == 0) {
+                if (md == 0) code[rc + p] = cr.code;
                 if (md >= 1) sVq[atomicAdd(&sNvq, 1)] = rc + p;
-                if (md == 2) sFull[atomicAdd(&sNfull, 1)] = rc + p;
+                if (md == 2) sFull[atomicAdd(&sNfull, 1)] = make_int2(rc + p, p);
                 n_patched += (md == 0 || md == 1);
                 n_cert += md == 0;
                 n_full += md == 2;
-                n_pairs += p >= 0 ? nk : 0;
+                n_pairs += prow ? nk : 0;
             }
+            // c's changed positions inside the tile: recomputed, then searched
+            if (tid < nd && dl[tid] >= t0 && dl[tid] < tend) {
+                sVq[atomicAdd(&sNvq, 1)] = rc + dl[tid];
+                sFull[atomicAdd(&sNfull, 1)] = make_int2(rc + dl[tid], dl[tid]);
+                ++n_full;
+            }
+            cp_async_wait_all();
             tc::tc_fence_before();
-            __syncthreads();  // TMEM and the staging space are free for the next tile
+            __syncthreads();
+            // the gathered lists go out when another configuration might not fit, and at the end
+            const bool last = cn < 0;
+            if (last || sNvq > RES_LCAP - 144 || sNfull > RES_LCAP - 144) {
+                if (tid == 0) {
+                    sBase[0] = sNvq ? atomicAdd(&ch.counters[CNT_V], sNvq) : 0;
+                    sBase[1] = sNfull ? act_off[cb0] + atomicAdd(&rc_cnt[b], sNfull) : 0;
+                }
+                __syncthreads();
+                for (int i = tid; i < sNvq; i += RES_THREADS) vq_rows[sBase[0] + i] = sVq[i];
+                for (int i = tid; i < sNfull; i += RES_THREADS) rc_rows[sBase[1] + i] = sFull[i];
+                __syncthreads();
+                if (tid == 0) { sNvq = 0; sNfull = 0; }
+                __syncthreads();
+            }
+            if (last) break;
+            c = cn;
+            nd = nd_n;
+            rc = rc_n;
+            p0 = p0_n;
+            buf ^= 1;
         }
-        __syncthreads();
-        if (tid == 0) {  // one atomic per list
-            sBase[0] = sNvq ? atomicAdd(&ch.counters[CNT_V], sNvq) : 0;
-            sBase[1] = sNfull ? act_off[ch.cfg_off[b]] + atomicAdd(&rc_cnt[b], sNfull) : 0;
-        }
-        __syncthreads();
-        for (int i = tid; i < sNvq; i += blockDim.x) vq_rows[sBase[0] + i] = sVq[i];
-        for (int i = tid; i < sNfull; i += blockDim.x) rc_rows[sBase[1] + i] = make_int2(sFull[i], sFull[i] - rc);
     }
     atomicAdd(reinterpret_cast<unsigned long long*>(&sCnt[0]), (unsigned long long)n_patched);
     atomicAdd(reinterpret_cast<unsigned long long*>(&sCnt[1]), (unsigned long long)n_cert);
@@ -1464,19 +1577,32 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
     }
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
         if (use_tc) {  // the classify kernel left no configuration to the CUDA cores
-            const uint32_t cols = ch.heads * 32 <= 128 ? 128 : 256;
-            size_t smem_tc = patch_tc_smem(ch.d, ch.heads, ch.N);
-            if (smem_tc > 227 * 1024) return cudaErrorInvalidValue;
+            const int d = ch.d;
+            const uint32_t cols = 2 * d <= 256 ? 256 : 512;  // scores/sums and the sample's outputs
+            if (2 * d > 512) return cudaErrorInvalidValue;
+            const size_t smem = res_layout(d, ch.heads).total;
+            if (smem > 227 * 1024) return cudaErrorInvalidValue;
             // the TMEM columns of the CTAs resident on one SM must fit in its 512
-            const size_t max_ctas = 512 / cols;
-            if ((228 * 1024) / smem_tc > max_ctas) smem_tc = (228 * 1024) / (max_ctas + 1) + 1024;
-            static size_t granted_tc = 0;
-            if (smem_tc > granted_tc) {
-                cudaFuncSetAttribute(k_inc_patch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tc);
-                granted_tc = smem_tc;
+            const int per_sm = (int)(512 / cols);
+            size_t smem_req = smem;
+            if ((size_t)(228 * 1024) / smem_req > (size_t)per_sm) smem_req = (228 * 1024) / (per_sm + 1) + 1024;
+            static size_t granted_res = 0;
+            if (smem_req > granted_res) {
+                cudaFuncSetAttribute(k_inc_patch_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_req);
+                granted_res = smem_req;
             }
-            k_inc_patch_tc<<<grid, 256, smem_tc, st>>>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows,
-                                                      act_off, rc_rows, rc_cnt, list_tc, dpos, dcnt, split, ex_rows,
+            int dev = 0, sms = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return cudaErrorInvalidDevice;
+            const int g = (sms > 0 ? sms : 1) * per_sm;
+            // items (sample, tile, slice): about four per CTA
+            const int ntile = (ch.N + 127) / 128;
+            const int sb = ch.S * ntile;
+            int slices = (4 * g + sb - 1) / sb;
+            slices = slices < 1 ? 1 : (slices > 64 ? 64 : slices);
+            k_inc_patch_res<<<g, RES_THREADS, smem_req, st>>>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows,
+                                                      act_off, rc_rows, rc_cnt, dpos, dcnt, split, ex_rows, slices,
                                                       cols, status, stats);
             return cudaGetLastError();
         }

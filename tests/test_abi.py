@@ -94,7 +94,7 @@ def test_create_arch_rejects_bad_variants_without_touching_a_gpu(lib):
     # (L, layers, d, heads, K, vq_heads, half_block, token_group)
     for L, layers, d, heads, K, H, half, G in [
             (4, 2, 32, 4, 16, 3, 0, 1),    # d_model not a multiple of the quantizer heads
-            (4, 1, 64, 2, 64, 8, 0, 1),    # 8 heads x 6 bits = 48 bits: over the 31-bit packed code
+            (4, 1, 64, 2, 512, 8, 0, 1),   # 8 heads x 9 bits: three heads per 32-bit word, over two words
             (4, 2, 32, 4, 16, 1, 0, 3),    # three spins per token
             (3, 2, 32, 4, 16, 1, 0, 2),    # 9 sites: not a multiple of two
             (4, 2, 32, 4, 16, 9, 0, 1)]:   # more than 8 quantizer heads

@@ -56,9 +56,11 @@ def test_stage_work_of_the_incremental_bf16_path():
     d, K = 256, 256
     assert bench.stage_flops("vq_argmin", st, w, True, True) == (1000 * 2.0 * K * d, "tensor")
     assert bench.stage_flops("inc_certificate", st, w, True, True) == (3840 * 2.0 * K * d, "alu")
-    # the BF16 patch is rated by its rows' bytes: BF16 query + FP32 output read, FP32 output written
-    assert bench.stage_flops("inc_patch", st, w, True, True) == (4000 * 6.0 * d + 1000 * 4.0 * d, "hbm")
+    # patch: 8 d per (row, changed key) pair; recompute: 4 d per pair; tensor cores on the BF16 path
+    assert bench.stage_flops("inc_patch", st, w, True, True) == (9000 * 8.0 * d, "tensor")
     assert bench.stage_flops("inc_patch", st, w, False, True) == (9000 * 8.0 * d, "alu")
+    assert bench.stage_flops("inc_recompute", st, w, True, True) == (7000 * 4.0 * d, "tensor")
+    assert bench.stage_flops("inc_recompute", st, w, False, True) == (7000 * 4.0 * d, "alu")
     assert bench.stage_flops("qkv_gemm", st, w, True, True) == (sum(st["unique_rows"][:8]) * 6.0 * d * d, "tensor")
     assert bench.stage_flops("mlp_up", st, w, False, False) == (sum(st["unique_rows"][1:9]) * 8.0 * d * d, "alu")
     assert bench.stage_flops("dedupe", st, w, True, True) == (0.0, "hbm")
