@@ -181,8 +181,11 @@ int vqnqs_create_tfim(int N, int periodic, double J, double Gamma, int layers, i
  *               run per active row.
  * vq_heads = 1, half_block = 0, token_group = 1 is vqnqs_create.  With several heads the
  * quantizer search runs per head on the CUDA cores (FP32 distances, lowest
- * index on ties).  Local energies and log psi accept every flag combination
- * except VQNQS_INCREMENTAL; vqnqs_grad_log_psi, vqnqs_sample and
+ * index on ties).  Local energies and log psi accept every flag combination;
+ * VQNQS_INCREMENTAL with several heads needs a one-word code (heads x bits <= 32)
+ * and K <= 1024, and certifies a row when ||delta|| is below the smallest
+ * radius over its segments (each segment's code then provably stays);
+ * the final half-block and G > 1 refuse it.  vqnqs_grad_log_psi, vqnqs_sample and
  * vqnqs_vmc_step return VQNQS_ERR_ARG for any variant, vqnqs_vq_assign for
  * several heads, vqnqs_local_energy_ragged for G > 1; vqnqs_codes returns
  * packed codes.  The FLOP counters of

@@ -217,8 +217,11 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             // tcgen05.ld is warp-collective: which chunks are read is decided by the
             // warp's last row (q0 need not be 32-aligned), the masks per row
             const int plim_w = min(q0 + (warp & 3) * 32 + 31, N - 1);
+            // a warp whose rows all lie past the configuration's last position has nothing to
+            // compute: its P rows are zero and its outputs are not stored
+            const bool wpad = q0 + (warp & 3) * 32 >= N;
             float mx = -INFINITY;
-            for (int c0 = half * 32; c0 < nk32; c0 += 64) {
+            for (int c0 = half * 32; c0 < nk32 && !wpad; c0 += 64) {
                 if (c0 > plim_w) break;  // chunks wholly past the warp's diagonal are invisible
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + lane_base + c0, r);
@@ -256,7 +259,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
                 }
                 const int c0 = jc * PCH + half * 16;  // this thread's 16 keys of the chunk
                 uint32_t pk[8], pl[8];
-                if (c0 > plim_w || c0 >= nk16) {  // invisible to the warp's rows, or past the MMA's keys: P = 0
+                if (wpad || c0 > plim_w || c0 >= nk16) {  // no rows, invisible, or past the MMA's keys: P = 0
 #pragma unroll
                     for (int j = 0; j < 8; ++j) pk[j] = pl[j] = 0u;
                 } else {

@@ -256,6 +256,95 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
     }
 }
 
+// ---- s's rows with H > 1 quantizer heads (Eq. vq per segment) ---------------------------
+// One warp per sample row.  Segment h of the row (dq = d / H values) is assigned against
+// codebook h (distances ||o_h||^2 - 2 o_h . W_hj + ||W_hj||^2 in FP32, lowest index on
+// ties) and its code goes to bits [h bits, (h + 1) bits) of the packed code.  The row's
+// certificate keeps no candidate list: its radius is the smallest over the segments of
+//   min_{j != c_h} (g_hj - eta_h) / (2 ||W_hj - W_hc||),  g_hj = ||o_h - W_hj||^2 - ||o_h - W_hc||^2,
+// and since ||delta_h|| <= ||delta||, a connected row with ||delta|| below it keeps every
+// segment's code; any other goes to the per-head search.  wd holds H tables [K][K].
+__global__ void __launch_bounds__(256)
+k_base_cert_heads(Chunk ch, const float* __restrict__ O, const float* __restrict__ codebook,
+                  const float* __restrict__ cnorm, const float* __restrict__ wd, int K, int d, int H, int bits,
+                  int* __restrict__ code, CertRow* __restrict__ cert, long long* __restrict__ near_ties,
+                  int* __restrict__ counters, int* __restrict__ rc_cnt, long long* __restrict__ stats) {
+    extern __shared__ __align__(16) float smem_h[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float* sO = smem_h + warp * (d + K);  // this warp's row
+    float* sDist = sO + d;                // its distances to one codebook
+    const int N = ch.N, dq = d / H;
+    if (blockIdx.x == 0 && tid == 0) {  // the lists the classify and patch kernels fill next
+        counters[CNT_V] = 0;
+        counters[CNT_TCL] = counters[CNT_SCL] = counters[CNT_TCW] = counters[CNT_SCW] = 0;
+        counters[CNT_EX] = 0;
+    }
+    if (blockIdx.x == 0)
+        for (int b = tid; b < 2 * ch.S; b += blockDim.x) rc_cnt[b] = 0;
+    long long ties = 0, rows = 0;
+    for (int r = blockIdx.x * 8 + warp; r < ch.S * N; r += gridDim.x * 8) {
+        const int b = r / N, p = r - b * N;
+        if (p >= sample_N(ch, b)) continue;  // warp-uniform
+        const int row = ch.cfg_row[ch.cfg_off[b]] + p;
+        for (int t = lane; t < d; t += 32) sO[t] = O[(size_t)row * d + t];
+        __syncwarp();
+        float radius = INFINITY;
+        unsigned packed = 0;
+        for (int h = 0; h < H; ++h) {
+            const float* oh = sO + h * dq;
+            float osq = 0.f;
+            for (int t = lane; t < dq; t += 32) osq = fmaf(oh[t], oh[t], osq);
+            osq = warp_sum(osq);
+            const float* Wh = codebook + (size_t)h * K * dq;
+            const float* cn = cnorm + (size_t)h * K;
+            float v1 = INFINITY, v2 = INFINITY, cmax = 0.f;
+            int i1 = 0x7fffffff;
+            for (int j = lane; j < K; j += 32) {
+                float dot = 0.f;
+                for (int t = 0; t < dq; ++t) dot = fmaf(oh[t], Wh[(size_t)j * dq + t], dot);
+                const float v = fmaf(-2.f, dot, osq) + cn[j];
+                sDist[j] = v;
+                cmax = fmaxf(cmax, cn[j]);
+                if (v < v1 || (v == v1 && j < i1)) { v2 = v1; v1 = v; i1 = j; }
+                else if (v < v2) v2 = v;
+            }
+            for (int o = 16; o; o >>= 1) {
+                const float ov1 = __shfl_xor_sync(0xffffffffu, v1, o), ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
+                const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+                cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+                if (ov1 < v1 || (ov1 == v1 && oi1 < i1)) { v2 = fminf(v1, ov2); v1 = ov1; i1 = oi1; }
+                else v2 = fminf(v2, ov1);
+            }
+            __syncwarp();
+            const int c = i1;
+            const float eta = CERT_ETA_REL * (osq + cmax);
+            const float* wdh = wd + (size_t)h * K * K + (size_t)c * K;
+            float rmin = INFINITY;
+            for (int j = lane; j < K; j += 32) {
+                const float w = wdh[j];
+                if (j != c && w > 0.f) rmin = fminf(rmin, (sDist[j] - v1 - eta) / (2.f * w));
+            }
+            for (int o = 16; o; o >>= 1) rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+            radius = fminf(radius, rmin);
+            packed |= (unsigned)c << (h * bits);
+            if (lane == 0 && K > 1 && (v2 - v1) < NEAR_TIE_REL * fmaxf(v1, 1e-30f)) ++ties;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            code[row] = (int)packed;
+            CertRow* cr = cert + r;
+            cr->next = radius;
+            cr->eta = 0.f;
+            cr->n = 0;
+            cr->code = (int)packed;
+            ++rows;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && ties) atomicAdd(reinterpret_cast<unsigned long long*>(near_ties), (unsigned long long)ties);
+    if (lane == 0 && rows) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_BASE]), (unsigned long long)rows);
+}
+
 // ---- connected configurations: changed positions and the work lists ------------------
 // One warp per connected configuration: the positions whose row id differs from
 // the sample's (ascending, the first INC_MAX_KEYS kept) and their count.  With
@@ -525,6 +614,9 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
         }
     };
 
+    // the 128 threads of the four warps that hold tile rows 32 (warp % 4) .. + 31
+    auto quad_sync = [&]() { asm volatile("bar.sync %0, 128;" ::"r"(1 + (warp & 3)) : "memory"); };
+
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&ch.counters[CNT_TCW], 1);
         __syncthreads();
@@ -678,11 +770,10 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 p0_n = cfg_first_changed(ch.cfg_i[cn], ch.cfg_j[cn]);
                 if (tid < nd_n) dl_n[tid] = dpos[(size_t)cn * INC_MAX_KEYS + tid];
             }
-            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
+            // every thread waits for the scores itself (a timeout is settled at the end barrier)
+            ok = tc::mbar_wait(bar, phase, status) && ok;
             phase ^= 1;
             tc::tc_fence_after();
-            if (!ok) break;
-            if (cn >= 0) stage_kv(sK, 1, ub, uid + rc_n, dl_n, nd_n);  // the score MMAs are done with sK
             float w[HQ], inv[HQ], ea[HQ], et[HQ];
             bool guard = false;
             // warps sharing TMEM lanes hold the same rows: they skip rows without work together
@@ -742,10 +833,11 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 }
                 tc::mma_commit(bar);
             }
-            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
+            // the score MMAs are done with sK (every thread waited), and dl_n is visible
+            if (cn >= 0) stage_kv(sK, 1, ub, uid + rc_n, dl_n, nd_n);
+            ok = tc::mbar_wait(bar, phase, status) && ok;
             phase ^= 1;
             tc::tc_fence_after();
-            if (!ok) break;
             if (cn >= 0) stage_kv(sV, 2, ub, uid + rc_n, dl_n, nd_n);  // the value MMAs are done with sV
             // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm and B^2
             float n2 = 0.f, b2 = 0.f;
@@ -773,7 +865,7 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 b2 = fmaf(bh, bh, b2);
             }
             sN2[tid] = make_float2(n2, guard ? -1.f : b2);
-            __syncthreads();
+            quad_sync();
             float bnd;
             {  // the same sums, in the same order, for the row's four threads
                 const float2 a0 = sN2[r], a1 = sN2[128 + r], a2 = sN2[256 + r], a3 = sN2[384 + r];
@@ -798,8 +890,9 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
             }
             // pass B: exact check of the listed candidates, each thread over its heads
             // (md agrees between the warps of a row, so their TMEM loads stay warp-uniform)
-            if (__syncthreads_or(md == 3)) {
-                if (__any_sync(0xffffffffu, md == 3)) {
+            // md agrees between the four warps of a quad (the same rows), so they enter together
+            if (__any_sync(0xffffffffu, md == 3)) {
+                {
                     float proj[CERT_T];
 #pragma unroll
                     for (int i = 0; i < CERT_T; ++i) proj[i] = 0.f;
@@ -832,7 +925,7 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                         for (int i = 0; i < CERT_T; ++i) sP[tid * CERT_T + i] = proj[i];
                     }
                 }
-                __syncthreads();
+                quad_sync();
                 if (md == 3) {
                     md = 0;
                     for (int i = 0; i < nc; ++i) {
@@ -882,7 +975,8 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
             }
             cp_async_wait_all();
             tc::tc_fence_before();
-            __syncthreads();
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) break;
             // the gathered lists go out when another configuration might not fit, and at the end
             const bool last = cn < 0;
             if (last || sNvq > RES_LCAP - 144 || sNfull > RES_LCAP - 144) {
@@ -1543,6 +1637,24 @@ cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codeb
     const int blocks = (ch.S * ch.N + CERT_RB - 1) / CERT_RB;
     k_base_cert<CERT_RB><<<blocks, 256, smem, st>>>(ch, O, codebook, cnorm, wd, K, d, code, cert, stats + ST_NEAR_TIES,
                                            counters, rc_cnt, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_base_cert_heads(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
+                                   const float* wd, int K, int d, int H, int bits, int* code, CertRow* cert,
+                                   long long* stats, int* counters, int* rc_cnt, cudaStream_t st, int num_sms) {
+    const size_t smem = (size_t)8 * (d + K) * sizeof(float);
+    if (H < 2 || d % H || H * bits > 32 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    static size_t granted = 0;
+    if (smem > granted) {
+        cudaFuncSetAttribute(k_base_cert_heads, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        granted = smem;
+    }
+    const int rows = ch.S * ch.N;
+    int blocks = (rows + 7) / 8;
+    if (blocks > 4 * num_sms) blocks = 4 * num_sms;
+    k_base_cert_heads<<<blocks, 256, smem, st>>>(ch, O, codebook, cnorm, wd, K, d, H, bits, code, cert,
+                                                 stats + ST_NEAR_TIES, counters, rc_cnt, stats);
     return cudaGetLastError();
 }
 

@@ -255,6 +255,10 @@ int build_tables(vqnqs_ctx* ctx, cudaStream_t st) {
         if (ctx->vq_heads == 1) {  // the tensor-core search and the incremental certificate: one head
             VQ_CK(launch_split_tf32(w.codebook, (size_t)K * d, w.cb_hi, w.cb_lo, st));
             VQ_CK(launch_codeword_dist(w.codebook, K, d, w.wd, st));
+        } else if (ctx->vq_words == 1 && K <= 1024) {  // the incremental certificate per quantizer head
+            const int dq = d / ctx->vq_heads;
+            for (int h = 0; h < ctx->vq_heads; ++h)
+                VQ_CK(launch_codeword_dist(w.codebook + (size_t)h * K * dq, K, dq, w.wd + (size_t)h * K * K, st));
         }
         if (ctx->bwd_tc) {  // the backward's split weight planes
             const int cap = ctx->num_sms * 16;
@@ -453,8 +457,13 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
         }
         if (inc) {
             // the samples' rows: codeword and certificate; then the connected configurations
-            VQ_STAGE(S_CERT, 1, launch_base_cert(ch, O, w.codebook, w.cnorm, w.wd, K, d, code, cert, ctx->stats,
-                                                 counters, rc_cnt, st));
+            if (ctx->vq_heads > 1)
+                VQ_STAGE(S_CERT, 1, launch_base_cert_heads(ch, O, w.codebook, w.cnorm, w.wd, K, d, ctx->vq_heads,
+                                                           ctx->vq_bits, code, cert, ctx->stats, counters, rc_cnt,
+                                                           st, ctx->num_sms));
+            else
+                VQ_STAGE(S_CERT, 1, launch_base_cert(ch, O, w.codebook, w.cnorm, w.wd, K, d, code, cert, ctx->stats,
+                                                     counters, rc_cnt, st));
             const int g_cfg = grid_for(ctx, P.Cmax, 1, 3);
             const bool tc_inc = bf16 && patch_tc_supported(d, ctx->heads) &&
                                 attention_tc_supported(N, d / ctx->heads, split) &&
@@ -609,7 +618,9 @@ int check_flags(vqnqs_ctx* ctx, int flags) {
         return fail(ctx, VQNQS_ERR_ARG, "unknown flag bits");
     if (flags & VQNQS_INCREMENTAL) {
         if (!(flags & VQNQS_REUSE)) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs VQNQS_REUSE");
-        if (ctx->vq_heads > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL needs one quantizer head");
+        if (ctx->vq_heads > 1 && (ctx->vq_words > 1 || ctx->K > 1024))
+            return fail(ctx, VQNQS_ERR_ARG,
+                        "VQNQS_INCREMENTAL with several quantizer heads needs a one-word code and K <= 1024");
         if (ctx->half_block) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: no final half-block");
         if (ctx->G > 1) return fail(ctx, VQNQS_ERR_ARG, "VQNQS_INCREMENTAL: one spin per token");
         if (!incremental_supported(ctx->d, ctx->heads))
@@ -1076,7 +1087,7 @@ int create_ctx(int model, int L, int N, int periodic, double J, double Gamma, in
         w.w2_t = static_cast<__nv_bfloat16*>(dalloc(2 * 4 * d * d * sizeof(__nv_bfloat16)));
         w.cb_hi = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
         w.cb_lo = static_cast<float*>(dalloc((size_t)K * d * sizeof(float)));
-        w.wd = static_cast<float*>(dalloc((size_t)K * K * sizeof(float)));
+        w.wd = static_cast<float*>(dalloc((size_t)vq_heads * K * K * sizeof(float)));  // one table per head
         if (!w.T || !w.cnorm || !w.wqkv_t || !w.w1_t || !w.w2_t || !w.cb_hi || !w.cb_lo || !w.wd)
             return bail(VQNQS_ERR_OOM);
         if (ctx->bwd_tc) {

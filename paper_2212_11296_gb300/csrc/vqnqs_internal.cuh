@@ -319,6 +319,11 @@ cudaError_t launch_codeword_dist(const float* W, int K, int d, float* wd, cudaSt
 cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
                              const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
                              int* counters, int* rc_cnt, cudaStream_t st);
+// the same with H > 1 quantizer heads (packed codes of `bits` per head, one word): the row's radius is the
+// smallest over its segments, no candidate list; wd holds H tables [K][K]
+cudaError_t launch_base_cert_heads(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
+                                   const float* wd, int K, int d, int H, int bits, int* code, CertRow* cert,
+                                   long long* stats, int* counters, int* rc_cnt, cudaStream_t st, int num_sms);
 // wd: the layer's ||W_a - W_c|| table; split (BF16 qkv only): the Q/K/V in qkv are the hi plane of split
 // operands, and rows the certificate does not settle are listed in ex_rows (count in CNT_EX) for
 // launch_inc_exact_delta instead of being written with the BF16 correction

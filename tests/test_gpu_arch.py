@@ -16,6 +16,8 @@ half-block of Table 1's networks.
   against the oracle, BF16 against FP32, and Table 1's network (three blocks,
   half-block, two heads of 64 codes) at 16x16 on 16 samples against stored
   oracle values.
+* The incremental path with 2 and 4 quantizer heads at 16x16 against the same
+  stored values (FP32 and split BF16).
 * The entry points defined for one head and no half-block refuse the variants.
 """
 import numpy as np
@@ -113,14 +115,52 @@ def test_table1_bandwidths_16x16():
         assert st["device_status"] == 0
 
 
+@pytest.mark.parametrize("H", [2, 4])
+def test_incremental_several_heads_16x16(H):
+    """The incremental path with H quantizer heads (each segment's radius, the row's the
+    smallest) against the stored FP64 oracle values of Table 1's bandwidth workload, and
+    equal in outcome to the reuse path: FP32 within the FP32 criterion, split BF16 within
+    the raw 2e-3 bar."""
+    from paper_2212_11296_gb300 import BF16, BF16_SPLIT, INCREMENTAL, REUSE, VQNQS
+    L, layers, d, heads, K, B = 16, 3, 256, 8, 64, 16
+    N = L * L
+    w = si.make_weights(N, layers, d, K, seed=0)
+    s = torch.as_tensor(si.make_samples(L, B, seed=1)).cuda()
+    m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=H)
+    want, gap = eloc_variant(f"arch16_h{H}")
+    m.reset_stats()
+    e32 = m.local_energy(s, REUSE | INCREMENTAL).cpu().numpy()
+    st = m.stats()
+    print(f"H = {H}: patched rows {st['inc_patched_rows']}, certified {st['inc_certified_rows']}, "
+          f"searched {st['inc_searched_rows']}")
+    # the row radius (smallest over the segments, against ||delta|| of the whole row) still
+    # certifies a good share of the patched rows: about 60 % with two heads, 40 % with four
+    assert st["inc_certified_rows"] > 0.25 * st["inc_patched_rows"]
+    # four heads of 64 codes meet oracle near ties (gap < 1e-7) in every sample: the patched
+    # outputs round differently from a full recompute, so more samples sit past 1e-5
+    check_fp32_against_golden(rel_err(e32, want, N), gap, min_within=0.75 if H == 2 else 0.5)
+    es = m.local_energy(s, REUSE | BF16 | INCREMENTAL | BF16_SPLIT).cpu().numpy()
+    err = rel_err(es, want, N)
+    print(f"split BF16: max {err.max():.3e}, median {np.median(err):.3e}")
+    assert err.max() <= 2e-3 and np.median(err) <= (1e-5 if H == 2 else 5e-5)  # near ties, as above
+    assert m.stats()["device_status"] == 0
+
+
 def test_one_head_entry_points_refuse_several():
     from paper_2212_11296_gb300 import INCREMENTAL, REUSE, VQNQS, VQNQSError
     L, layers, d, heads, K = 4, 2, 32, 4, 16
     w = si.make_weights(L * L, layers, d, K, seed=0)
     m = VQNQS(L, True, 1.0, layers, d, heads, K, w, vq_heads=2)
     s = torch.as_tensor(si.make_samples(L, 4, seed=1)).cuda()
+    # the incremental path takes several heads only with a one-word code and K <= 1024
+    w48 = si.make_weights(L * L, 1, 64, 64, seed=0)
+    m48 = VQNQS(L, True, 1.0, 1, 64, 2, 64, w48, vq_heads=8)  # 8 x 6 bits: two words
     with pytest.raises(VQNQSError, match="ERR_ARG"):
-        m.local_energy(s, REUSE | INCREMENTAL)
+        m48.local_energy(s, REUSE | INCREMENTAL)
+    wbig = si.make_weights(L * L, 1, 64, 2048, seed=0)
+    mbig = VQNQS(L, True, 1.0, 1, 64, 2, 2048, wbig, vq_heads=2)
+    with pytest.raises(VQNQSError, match="ERR_ARG"):
+        mbig.local_energy(s, REUSE | INCREMENTAL)
     with pytest.raises(VQNQSError, match="ERR_ARG"):
         m.grad_log_psi(s)
     with pytest.raises(VQNQSError, match="ERR_ARG"):
