@@ -73,7 +73,8 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
     the attention stage covers the samples' own rows only; the certificate is a
     2 K d distance pass per sample row; a patch costs 8 d per (row, changed
     key) pair (two scores and two value updates per head); a recomputed row 4 d
-    per query-key pair.  On the BF16 path the patch and the recompute run these
+    per query-key pair, the configurations recomputed whole likewise (their rows
+    from the first changed position).  On the BF16 path the patch and the recompute run these
     products on the tensor cores and are rated against the BF16 tensor peak
     (algorithmic FLOPs: split operands take three MMAs per product, which are
     not counted); their DRAM bytes are reported beside the rate."""
@@ -94,6 +95,8 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
         return st["inc_patch_pairs"] * 8.0 * d, tc
     if stage == "inc_recompute":
         return st["inc_full_pairs"] * 4.0 * d, tc
+    if stage == "inc_recompute_whole":
+        return st["inc_whole_pairs"] * 4.0 * d, tc
     if stage == "qkv_gemm":
         return sum(U[:Ly]) * 6.0 * d * d, tc
     if stage in ("mlp_up", "mlp_down"):
@@ -650,7 +653,7 @@ def main():
     if flags & INCREMENTAL:  # row outcomes over the timed steps, summed over layers
         res["incremental"] = {k: st[k] for k in ("inc_base_rows", "inc_patched_rows", "inc_certified_rows",
                                                  "inc_full_rows", "inc_searched_rows", "inc_patch_pairs",
-                                                 "inc_full_pairs")}
+                                                 "inc_full_pairs", "inc_whole_pairs")}
     if world == 1 and not args.no_cpu_baseline:
         vals, dt, cores = cpu_oracle(spins_np, w)
         n = len(vals)

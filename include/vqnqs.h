@@ -115,6 +115,8 @@ typedef struct vqnqs_stats {
     int64_t inc_searched_rows;                /* rows given to the nearest-codeword search */
     int64_t inc_patch_pairs;                  /* (patched row, changed key) pairs, per head */
     int64_t inc_full_pairs;                   /* causal query-key pairs of the recomputed rows, per head */
+    int64_t inc_whole_pairs;                  /* causal query-key pairs, per head, of the configurations
+                                                 recomputed whole (rows from the first changed position) */
 } vqnqs_stats;
 
 /* Number of floats in the weight blob for the layout above. */

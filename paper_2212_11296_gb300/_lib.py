@@ -45,6 +45,7 @@ class Stats(ctypes.Structure):
         ("inc_searched_rows", ctypes.c_int64),
         ("inc_patch_pairs", ctypes.c_int64),
         ("inc_full_pairs", ctypes.c_int64),
+        ("inc_whole_pairs", ctypes.c_int64),
     ]
 
 

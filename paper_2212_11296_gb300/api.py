@@ -298,7 +298,7 @@ class VQNQS:
             "inc_base_rows": s.inc_base_rows, "inc_patched_rows": s.inc_patched_rows,
             "inc_certified_rows": s.inc_certified_rows, "inc_full_rows": s.inc_full_rows,
             "inc_searched_rows": s.inc_searched_rows, "inc_patch_pairs": s.inc_patch_pairs,
-            "inc_full_pairs": s.inc_full_pairs,
+            "inc_full_pairs": s.inc_full_pairs, "inc_whole_pairs": s.inc_whole_pairs,
         }
 
     def check_timeout_path(self, limit_cycles: int = 1_000_000, stream=None):

@@ -362,7 +362,7 @@ __global__ void k_inc_classify(Chunk ch, const int* __restrict__ uid, int tc_ok,
     const int C = ch.counters[CNT_C];
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    long long full_rows = 0;
+    long long full_rows = 0, whole_pairs = 0;
     for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += nw) {
         const int ci = ch.cfg_i[c];
         if (ci < 0) continue;  // the sample itself (warp-uniform)
@@ -399,9 +399,13 @@ __global__ void k_inc_classify(Chunk ch, const int* __restrict__ uid, int tc_ok,
             base = __shfl_sync(0xffffffffu, base, 0);
             for (int p = p0 + lane; p < N; p += 32) vq_rows[base + p - p0] = rc + p;
             full_rows += lane == 0 ? N - p0 : 0;
+            // rows p0 .. N - 1, row p attending to keys 0 .. p
+            whole_pairs += lane == 0 ? (long long)(N - p0) * (N + p0 + 1) / 2 : 0;
         }
     }
     if (full_rows) atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_FULL]), (unsigned long long)full_rows);
+    if (whole_pairs)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_WPAIRS]), (unsigned long long)whole_pairs);
 }
 
 // Next entry of a work list for the whole CTA (-1 when the list is done).

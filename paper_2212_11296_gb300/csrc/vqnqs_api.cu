@@ -1298,6 +1298,7 @@ int vqnqs_get_stats(vqnqs_ctx* ctx, vqnqs_stats* out) {
     out->inc_searched_rows = st[ST_INC_VQ];
     out->inc_patch_pairs = st[ST_INC_PPAIRS];
     out->inc_full_pairs = st[ST_INC_FPAIRS];
+    out->inc_whole_pairs = st[ST_INC_WPAIRS];
     // analytic FLOPs, 2 per multiply-add
     const double d = ctx->d, K = ctx->K, N = ctx->P, Ly = ctx->layers;
     const double rows = (double)out->rows, cfgs = (double)out->configs;

@@ -46,6 +46,7 @@ enum {
     ST_INC_VQ,                             //   rows given to the codeword search
     ST_INC_PPAIRS,                         //   (patched row, changed key) pairs, per head
     ST_INC_FPAIRS,                         //   query-key pairs of the recomputed rows, per head
+    ST_INC_WPAIRS,                         //   causal query-key pairs of configurations recomputed whole
     ST_SLOTS
 };
 

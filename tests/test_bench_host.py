@@ -52,7 +52,7 @@ def test_stage_work_of_the_incremental_bf16_path():
     w = {"d_model": 256, "K": 256, "layers": 8, "L": 16}
     st = {"unique_rows": [10, 20, 30, 40, 50, 60, 70, 80, 90], "inc_searched_rows": 1000, "active_rows": 5000,
           "samples": 15, "attn_pairs": 0, "inc_base_rows": 3840, "inc_patched_rows": 4000,
-          "inc_patch_pairs": 9000, "inc_full_pairs": 7000}
+          "inc_patch_pairs": 9000, "inc_full_pairs": 7000, "inc_whole_pairs": 11000}
     d, K = 256, 256
     assert bench.stage_flops("vq_argmin", st, w, True, True) == (1000 * 2.0 * K * d, "tensor")
     assert bench.stage_flops("inc_certificate", st, w, True, True) == (3840 * 2.0 * K * d, "alu")
@@ -61,6 +61,7 @@ def test_stage_work_of_the_incremental_bf16_path():
     assert bench.stage_flops("inc_patch", st, w, False, True) == (9000 * 8.0 * d, "alu")
     assert bench.stage_flops("inc_recompute", st, w, True, True) == (7000 * 4.0 * d, "tensor")
     assert bench.stage_flops("inc_recompute", st, w, False, True) == (7000 * 4.0 * d, "alu")
+    assert bench.stage_flops("inc_recompute_whole", st, w, True, True) == (11000 * 4.0 * d, "tensor")
     assert bench.stage_flops("qkv_gemm", st, w, True, True) == (sum(st["unique_rows"][:8]) * 6.0 * d * d, "tensor")
     assert bench.stage_flops("mlp_up", st, w, False, False) == (sum(st["unique_rows"][1:9]) * 8.0 * d * d, "alu")
     assert bench.stage_flops("dedupe", st, w, True, True) == (0.0, "hbm")
