@@ -45,6 +45,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 using tc::tmem_ld16;
+using tc::cp_async16;
+using tc::cp_async_wait_all;
 
 // 8 consecutive BF16 values (16-byte aligned) as floats; with SPLIT the value is hi + lo,
 // the lo plane lo_off elements further on
@@ -114,10 +116,11 @@ __device__ __forceinline__ float operand_value(float x) {
 constexpr int PCH = 32;
 constexpr size_t PCB = (size_t)128 * PCH * 2;
 __host__ __device__ constexpr size_t rows_tile_bytes(int Npad) { return (size_t)Npad * DH * 2; }
+// Q and the two P tiles, or (while an item is staged) the V staging rows and the sample's row ids
 __host__ __device__ constexpr size_t rows_region_bytes(int Npad, int NP) {
-    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16)
+    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16) + (size_t)Npad * 4
                ? (size_t)NP * 128 * DH * 2 + 2 * NP * PCB
-               : (size_t)NP * Npad * (2 * DH + 16);
+               : (size_t)NP * Npad * (2 * DH + 16) + (size_t)Npad * 4;
 }
 __host__ __device__ constexpr size_t rows_smem_bytes(int Npad, bool split) {
     return 128 + (split ? 2 : 1) * 2 * rows_tile_bytes(Npad) + rows_region_bytes(Npad, split ? 2 : 1) + 64;
@@ -193,23 +196,25 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
         const int N = sample_N(ch, b);
         const int* ub = uid + rb;
         __syncthreads();  // the previous item's readers of the shared tiles are done
-        // s's keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
+        // s's row ids, then its keys (position-fastest mapping: each 8-thread phase writes 128
+        // contiguous bytes) and values (row-major staging rows, transposed below) with cp.async
+        int* s_uid = reinterpret_cast<int*>(sStage + NP * pb);
+        for (int j = tid; j < N; j += AR_THREADS) s_uid[j] = ub[j];
+        __syncthreads();
         for (int pl = 0; pl < NP; ++pl) {
             const __nv_bfloat16* src = qkv + pl * lo_off;
             for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
                 const int j = u % Npad, kb = u / Npad;
-                uint4 kv = make_uint4(0, 0, 0, 0);
-                if (j < N) kv = *reinterpret_cast<const uint4*>(src + (size_t)ub[j] * ld + d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sK + pl * tb + tc::core_off(j, kb * 8, DH)) = kv;
+                cp_async16(tc::smem_u32(sK + pl * tb + tc::core_off(j, kb * 8, DH)),
+                           j < N ? src + (size_t)s_uid[j] * ld + d + h * DH + kb * 8 : qkv, j < N ? 16 : 0);
             }
-            // s's values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
             for (int u = tid; u < Npad * (DH / 8); u += AR_THREADS) {
                 const int j = u / (DH / 8), kb = u - j * (DH / 8);
-                uint4 vv = make_uint4(0, 0, 0, 0);
-                if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)ub[j] * ld + 2 * d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sStage + pl * pb + j * VS + kb * 16) = vv;
+                cp_async16(tc::smem_u32(sStage + pl * pb + j * VS + kb * 16),
+                           j < N ? src + (size_t)s_uid[j] * ld + 2 * d + h * DH + kb * 8 : qkv, j < N ? 16 : 0);
             }
         }
+        cp_async_wait_all();
         __syncthreads();
         for (int pl = 0; pl < NP; ++pl)
             for (int blk = warp; blk < (Npad / 8) * (DH / 32); blk += AR_THREADS / 32) {
@@ -228,17 +233,16 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
                 rrow = e.x;
                 p = e.y;
             }
-            for (int pl = 0; pl < NP; ++pl)
-                for (int u = tid; u < 128 * (DH / 8); u += AR_THREADS) {
-                    const int r = u & 127, kb = u >> 7;
-                    uint4 qv = make_uint4(0, 0, 0, 0);
-                    if (t0 + r < n) {
-                        const int2 e = lst[t0 + r];
-                        qv = *reinterpret_cast<const uint4*>(qkv + pl * lo_off + (size_t)uid[e.x] * ld + h * DH +
-                                                             kb * 8);
+            {  // this thread's query row is tile row `row` (the u loop steps by a multiple of 128)
+                const size_t qoff = rrow >= 0 ? (size_t)uid[rrow] * ld + h * DH : 0;
+                for (int pl = 0; pl < NP; ++pl)
+                    for (int u = tid; u < 128 * (DH / 8); u += AR_THREADS) {
+                        const int kb = u >> 7;
+                        cp_async16(tc::smem_u32(sQ + pl * 128 * DH * 2 + tc::core_off(row, kb * 8, DH)),
+                                   qkv + pl * lo_off + qoff + kb * 8, rrow >= 0 ? 16 : 0);
                     }
-                    *reinterpret_cast<uint4*>(sQ + pl * 128 * DH * 2 + tc::core_off(r, kb * 8, DH)) = qv;
-                }
+                cp_async_wait_all();
+            }
             // the tile's key range: up to its largest position (warp maxima for uniform TMEM reads)
             const int pw = __reduce_max_sync(0xffffffffu, p);
             if (lane == 0 && half == 0) s_pw[warp] = pw;

@@ -39,6 +39,8 @@ constexpr int AT_THREADS = 256;
 constexpr int AT_MAX_N = 448;  // keys per configuration handled in one TMEM tile
 
 using tc::core_off;
+using tc::cp_async16;
+using tc::cp_async_wait_all;
 using tc::desc_kmajor_none;
 using tc::fence_proxy_async_smem;
 
@@ -69,10 +71,11 @@ __device__ __forceinline__ void split_pack2(float a, float b, uint32_t& hi, uint
 constexpr int PCH = 32;                      // keys per P chunk
 constexpr size_t PCB = (size_t)128 * PCH * 2;  // one plane of one P chunk tile
 __host__ __device__ constexpr size_t attn_tile_bytes(int Npad, int DH) { return (size_t)Npad * DH * 2; }
+// Q and the two P tiles, or (while an item is staged) the V staging rows and the item's row ids
 __host__ __device__ constexpr size_t attn_region_bytes(int Npad, int DH, int NP) {
-    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16)
+    return (size_t)NP * 128 * DH * 2 + 2 * NP * PCB > (size_t)NP * Npad * (2 * DH + 16) + (size_t)Npad * 4
                ? (size_t)NP * 128 * DH * 2 + 2 * NP * PCB
-               : (size_t)NP * Npad * (2 * DH + 16);
+               : (size_t)NP * Npad * (2 * DH + 16) + (size_t)Npad * 4;
 }
 __host__ __device__ constexpr size_t attn_smem_bytes(int Npad, int DH, bool split) {
     return 128 + (split ? 2 : 1) * 2 * attn_tile_bytes(Npad, DH) + attn_region_bytes(Npad, DH, split ? 2 : 1) + 64;
@@ -96,6 +99,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint8_t* sP = sQ + NP * 128 * DH * 2;          // [2 tiles][NP][128 x PCH]
     uint8_t* sStage = sQ;                          // [NP][Npad x VS]
     const size_t pb = (size_t)Npad * VS;           // one staging plane
+    int* s_uid = reinterpret_cast<int*>(sStage + NP * pb);  // [Npad] the item's row ids, while staging
     uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + attn_region_bytes(Npad, DH, NP));  // S MMAs
     uint64_t* pbar = bar + 1;                      // [2]: MMAs reading P tile 0 / 1
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pbar + 2);
@@ -128,23 +132,25 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
         const int N = cfg_N(ch, c);
         const int* urow = uid + ch.cfg_row[c];
         const int p0 = prefix_reuse ? cfg_p0(ch, c) : 0;
-        // keys: position-fastest mapping, so each 8-thread phase writes 128 contiguous bytes
+        // the row ids first, then every key and value row with cp.async (all copies in flight
+        // at once); keys: position-fastest mapping, so each 8-thread phase writes 128
+        // contiguous bytes; values: row-major staging rows, transposed below
+        for (int j = tid; j < N; j += AT_THREADS) s_uid[j] = urow[j];
+        __syncthreads();
         for (int pl = 0; pl < NP; ++pl) {
             const __nv_bfloat16* src = qkv + pl * lo_off;
             for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
                 const int j = u % Npad, kb = u / Npad;
-                uint4 kv = make_uint4(0, 0, 0, 0);
-                if (j < N) kv = *reinterpret_cast<const uint4*>(src + (size_t)urow[j] * ld + d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sK + pl * tb + core_off(j, kb * 8, DH)) = kv;
+                cp_async16(tc::smem_u32(sK + pl * tb + core_off(j, kb * 8, DH)),
+                           j < N ? src + (size_t)s_uid[j] * ld + d + h * DH + kb * 8 : qkv, j < N ? 16 : 0);
             }
-            // values: row-major staging, then 8x8 transposes into the [DH x Npad] operand
             for (int u = tid; u < Npad * (DH / 8); u += AT_THREADS) {
                 const int j = u / (DH / 8), kb = u - j * (DH / 8);
-                uint4 vv = make_uint4(0, 0, 0, 0);
-                if (j < N) vv = *reinterpret_cast<const uint4*>(src + (size_t)urow[j] * ld + 2 * d + h * DH + kb * 8);
-                *reinterpret_cast<uint4*>(sStage + pl * pb + j * VS + kb * 16) = vv;
+                cp_async16(tc::smem_u32(sStage + pl * pb + j * VS + kb * 16),
+                           j < N ? src + (size_t)s_uid[j] * ld + 2 * d + h * DH + kb * 8 : qkv, j < N ? 16 : 0);
             }
         }
+        cp_async_wait_all();
         __syncthreads();
         for (int pl = 0; pl < NP; ++pl) {
             uint8_t* stg = sStage + pl * pb;
@@ -173,15 +179,17 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             const int nk = min(N, q0 + 128);             // keys this tile can see
             const int nk16 = (nk + 15) & ~15;            // MMA N (multiple of 16)
             const int nk32 = (nk + 31) & ~31;            // columns read back
-            for (int pl = 0; pl < NP; ++pl)
-                for (int u = tid; u < 128 * (DH / 8); u += AT_THREADS) {
-                    const int r = u & 127, kb = u >> 7;
-                    uint4 qv = make_uint4(0, 0, 0, 0);
-                    if (q0 + r < N)
-                        qv = *reinterpret_cast<const uint4*>(qkv + pl * lo_off + (size_t)urow[q0 + r] * ld + h * DH +
-                                                             kb * 8);
-                    *reinterpret_cast<uint4*>(sQ + pl * 128 * DH * 2 + core_off(r, kb * 8, DH)) = qv;
-                }
+            {  // this thread's query row is tile row `row` (the u loop steps by a multiple of 128)
+                const bool qin = q0 + row < N;
+                const size_t qoff = qin ? (size_t)urow[q0 + row] * ld + h * DH : 0;
+                for (int pl = 0; pl < NP; ++pl)
+                    for (int u = tid; u < 128 * (DH / 8); u += AT_THREADS) {
+                        const int kb = u >> 7;
+                        cp_async16(tc::smem_u32(sQ + pl * 128 * DH * 2 + core_off(row, kb * 8, DH)),
+                                   qkv + pl * lo_off + qoff + kb * 8, qin ? 16 : 0);
+                    }
+                cp_async_wait_all();
+            }
             fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();

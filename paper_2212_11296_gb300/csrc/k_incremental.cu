@@ -465,10 +465,8 @@ __device__ __forceinline__ int next_item(int* counters, int work_slot, int list_
 //   ||delta~_h - delta_h|| <= B_h = 1.1 (A + T (||o_h|| + ||delta~_h||)) / (l~' - 1.1 T)
 // per head and B = sqrt(sum_h B_h^2).  A row with tau > 0.1, or
 // l~' - 1.1 T <= l~' / 2, is recomputed over all keys.
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+using tc::cp_async16;
+using tc::cp_async_wait_all;
 
 // The BF16 weights of one head for a row with nk changed keys before it (nk <= NKB):
 // e_s = exp(s_s / sqrt(dh) - m) negated in slots 0..15, e_c in 16..31, zeros beyond

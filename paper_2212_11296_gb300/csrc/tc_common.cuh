@@ -182,6 +182,14 @@ __device__ __forceinline__ uint32_t core_off(int r, int k, int kd) {
     return (uint32_t)((r >> 3) * (kd >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// 16 bytes global -> shared without a register round trip; src_bytes < 16 zero-fills the rest
+// (0: the destination is zeroed and src is not read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+// Waits for all of this thread's cp.async copies.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Orders this thread's generic-proxy shared-memory writes before later
 // async-proxy (tensor core, TMA) reads.
 __device__ __forceinline__ void fence_proxy_async_smem() {
