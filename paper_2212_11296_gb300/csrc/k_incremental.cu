@@ -519,7 +519,7 @@ __host__ __device__ inline ResLayout res_layout(int d, int H) {
     L.pr = o;   o += 4 * 128 * CERT_T * sizeof(float);
     L.kx = o;   o += (size_t)H * sizeof(float);
     L.vn = o;   o += (size_t)H * 32 * sizeof(float);
-    L.dp = o;   o += 2 * 32 * sizeof(int);
+    L.dp = o;   o += 2 * 64 * sizeof(int);
     L.vq = o;   o += RES_LCAP * sizeof(int);
     L.full = o; o += RES_LCAP * sizeof(int2);
     L.bar = o;  o += 64;
@@ -567,7 +567,9 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
     float* sP = reinterpret_cast<float*>(smem + L.pr);     // [4 quarters][128][CERT_T]: projections
     float* sKx = reinterpret_cast<float*>(smem + L.kx);    // [H] largest ||k~|| of the key slots
     float2* sVn = reinterpret_cast<float2*>(smem + L.vn);  // [H][16] ||v~|| of slot pairs (sample's, c's)
-    int* sD = reinterpret_cast<int*>(smem + L.dp);         // [2][32] changed positions (this, next)
+    // [2 configurations: this, next][64]: changed positions in 0..15, their row ids in 32..63
+    // (the sample's in 32..47, the configuration's in 48..63)
+    int* sD = reinterpret_cast<int*>(smem + L.dp);
     int* sVq = reinterpret_cast<int*>(smem + L.vq);        // rows to search
     int2* sFull = reinterpret_cast<int2*>(smem + L.full);  // rows to recompute (row, position)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
@@ -603,16 +605,25 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
 
     // keys (part 1) or values (part 2) of configuration c's changed positions, the sample's
     // in slots 0..15 and c's in 16..31, zero-filled, into dst with cp.async; dl: c's changed
-    // positions in shared memory.  Both tiles take the K-major core layout of [32 slots x 32
-    // dims] per head; the value MMA reads theirs as an MN-major B operand.
-    auto stage_kv = [&](uint8_t* dst, int part, const int* ub, const int* uc, const int* dl, int nd) {
+    // positions and their row ids in shared memory (layout of sD).  Both tiles take the
+    // K-major core layout of [32 slots x 32 dims] per head; the value MMA reads theirs as an
+    // MN-major B operand.
+    auto stage_kv = [&](uint8_t* dst, int part, const int* dl, int nd) {
         for (int u = tid; u < nkv; u += RES_THREADS) {
             const int h = u / (32 * (DH / 8)), rem = u - h * 32 * (DH / 8);
             const int n = rem & 31, t8 = (rem >> 5) * 8;
-            const int kk = n & 15;
-            const __nv_bfloat16* x = qkv;
-            if (kk < nd) x = qkv + (size_t)(n < 16 ? ub[dl[kk]] : uc[dl[kk]]) * ld + part * d + h * DH + t8;
-            cp_async16(tc::smem_u32(dst + h * 2048 + tc::core_off(n, t8, DH)), x, kk < nd ? 16 : 0);
+            const bool in = (n & 15) < nd;
+            cp_async16(tc::smem_u32(dst + h * 2048 + tc::core_off(n, t8, DH)),
+                       in ? qkv + (size_t)dl[32 + n] * ld + part * d + h * DH + t8 : qkv, in ? 16 : 0);
+        }
+    };
+    // c's changed positions and their row ids into dl (threads 0 .. nd - 1)
+    auto load_changed = [&](int* dl, int c, int nd, const int* ub, const int* uc) {
+        if (tid < nd) {
+            const int q = dpos[(size_t)c * INC_MAX_KEYS + tid];
+            dl[tid] = q;
+            dl[32 + tid] = ub[q];
+            dl[48 + tid] = uc[q];
         }
     };
 
@@ -685,10 +696,10 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
         // the first configuration's changed positions, keys and values
         int buf = 0;
         int nd = dcnt[c], rc = ch.cfg_row[c], p0 = cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]);
-        if (tid < nd) sD[tid] = dpos[(size_t)c * INC_MAX_KEYS + tid];
+        load_changed(sD, c, nd, ub, uid + rc);
         __syncthreads();
-        stage_kv(sK, 1, ub, uid + rc, sD, nd);
-        stage_kv(sV, 2, ub, uid + rc, sD, nd);
+        stage_kv(sK, 1, sD, nd);
+        stage_kv(sV, 2, sD, nd);
         cp_async_wait_all();
         __syncthreads();
 #pragma unroll
@@ -711,7 +722,7 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
         const CertRow& cr = sCert[r];
         // ---- the slice's configurations; the next one's keys and values load during this one
         while (ok) {
-            const int* dl = sD + buf * 32;
+            const int* dl = sD + buf * 64;
             // staged keys and values of c: slot norms (one slot of one tile per thread; a warp
             // covers the 32 slots of one head): the values' per slot, the keys' largest per head
             for (int u = tid; u < 2 * H * 32; u += RES_THREADS) {
@@ -765,12 +776,12 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
             // the next configuration of the slice, while the scores form
             const int cn = res_next_cfg(ch, dcnt, c + slices, cb1, slices, tend);
             int nd_n = 0, rc_n = 0, p0_n = 0;
-            int* dl_n = sD + (buf ^ 1) * 32;
+            int* dl_n = sD + (buf ^ 1) * 64;
             if (cn >= 0) {
                 nd_n = dcnt[cn];
                 rc_n = ch.cfg_row[cn];
                 p0_n = cfg_first_changed(ch.cfg_i[cn], ch.cfg_j[cn]);
-                if (tid < nd_n) dl_n[tid] = dpos[(size_t)cn * INC_MAX_KEYS + tid];
+                load_changed(dl_n, cn, nd_n, ub, uid + rc_n);
             }
             // every thread waits for the scores itself (a timeout is settled at the end barrier)
             ok = tc::mbar_wait(bar, phase, status) && ok;
@@ -836,11 +847,11 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 tc::mma_commit(bar);
             }
             // the score MMAs are done with sK (every thread waited), and dl_n is visible
-            if (cn >= 0) stage_kv(sK, 1, ub, uid + rc_n, dl_n, nd_n);
+            if (cn >= 0) stage_kv(sK, 1, dl_n, nd_n);
             ok = tc::mbar_wait(bar, phase, status) && ok;
             phase ^= 1;
             tc::tc_fence_after();
-            if (cn >= 0) stage_kv(sV, 2, ub, uid + rc_n, dl_n, nd_n);  // the value MMAs are done with sV
+            if (cn >= 0) stage_kv(sV, 2, dl_n, nd_n);  // the value MMAs are done with sV
             // pass A: delta = (acc - w o) / l' for the own heads, back into TMEM; partial norm and B^2
             float n2 = 0.f, b2 = 0.f;
 #pragma unroll
