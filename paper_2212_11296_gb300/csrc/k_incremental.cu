@@ -1086,31 +1086,41 @@ k_inc_exact_delta(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __
         float sum_s = 0.f, sum_c = 0.f;
         const int nd = min(dcnt[c], INC_MAX_KEYS);
         const short* dp = dpos + (size_t)c * INC_MAX_KEYS;
-        for (int k = 0; k < nd; ++k) {
-            const int kp = dp[k];
-            if (kp >= p) break;  // ascending: the rest lie after the row
-            float ks[PER], kc[PER];
-            ld_split<PER>(qkv + (size_t)ub[kp] * ld + d + lane * PER, lo_off, ks);
-            ld_split<PER>(qkv + (size_t)uc[kp] * ld + d + lane * PER, lo_off, kc);
-            float ss = 0.f, scv = 0.f;
-#pragma unroll
-            for (int t = 0; t < PER; ++t) {
-                ss = fmaf(q[t], ks[t], ss);
-                scv = fmaf(q[t], kc[t], scv);
+        // 32 changed positions at a time: lane k holds the k-th one and its two row ids, so
+        // the key loop below issues its key and value loads without dependent index loads
+        for (int k0 = 0; k0 < nd; k0 += 32) {
+            int kp_l = 0x7fffffff, ub_l = 0, uc_l = 0;
+            if (k0 + lane < nd) {
+                kp_l = dp[k0 + lane];
+                ub_l = ub[kp_l];
+                uc_l = uc[kp_l];
             }
+            const int nk = __popc(__ballot_sync(0xffffffffu, kp_l < p));  // ascending: these lie before the row
+            for (int k = 0; k < nk; ++k) {
+                const int ukb = __shfl_sync(0xffffffffu, ub_l, k), ukc = __shfl_sync(0xffffffffu, uc_l, k);
+                float ks[PER], kc[PER], vs[PER], vc[PER];
+                ld_split<PER>(qkv + (size_t)ukb * ld + d + lane * PER, lo_off, ks);
+                ld_split<PER>(qkv + (size_t)ukc * ld + d + lane * PER, lo_off, kc);
+                ld_split<PER>(qkv + (size_t)ukb * ld + 2 * d + lane * PER, lo_off, vs);
+                ld_split<PER>(qkv + (size_t)ukc * ld + 2 * d + lane * PER, lo_off, vc);
+                float ss = 0.f, scv = 0.f;
 #pragma unroll
-            for (int w = LPH / 2; w > 0; w >>= 1) {
-                ss += __shfl_xor_sync(0xffffffffu, ss, w);
-                scv += __shfl_xor_sync(0xffffffffu, scv, w);
+                for (int t = 0; t < PER; ++t) {
+                    ss = fmaf(q[t], ks[t], ss);
+                    scv = fmaf(q[t], kc[t], scv);
+                }
+#pragma unroll
+                for (int w = LPH / 2; w > 0; w >>= 1) {
+                    ss += __shfl_xor_sync(0xffffffffu, ss, w);
+                    scv += __shfl_xor_sync(0xffffffffu, scv, w);
+                }
+                const float es = __expf(ss * rs - ml.x), ec = __expf(scv * rs - ml.x);
+#pragma unroll
+                for (int t = 0; t < PER; ++t) acc[t] = fmaf(ec, vc[t] - o[t], fmaf(-es, vs[t] - o[t], acc[t]));
+                sum_s += es;
+                sum_c += ec;
             }
-            const float es = __expf(ss * rs - ml.x), ec = __expf(scv * rs - ml.x);
-            float vs[PER], vc[PER];
-            ld_split<PER>(qkv + (size_t)ub[kp] * ld + 2 * d + lane * PER, lo_off, vs);
-            ld_split<PER>(qkv + (size_t)uc[kp] * ld + 2 * d + lane * PER, lo_off, vc);
-#pragma unroll
-            for (int t = 0; t < PER; ++t) acc[t] = fmaf(ec, vc[t] - o[t], fmaf(-es, vs[t] - o[t], acc[t]));
-            sum_s += es;
-            sum_c += ec;
+            if (nk < 32) break;  // the next block lies after the row
         }
         const float inv = 1.f / (ml.y - sum_s + sum_c);
 #pragma unroll
