@@ -408,32 +408,39 @@ k_attention_rows_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* 
 #pragma unroll
                         for (int t = 0; t < 8; ++t) q[t8 + t] = x[t];
                     }
-                    float m2 = mb, lsub = 0.f;  // log2-unit maximum; removed weight
-                    // the new maximum first
-                    for (int i = 0; i < nd; ++i) {
-                        const int k = dp[i];
-                        if (k > p) break;  // ascending
-                        const float sc = dot_dh<SPLIT>(q, qkv + (size_t)uc[k] * ld + d + h * DH, lo_off);
-                        m2 = fmaxf(m2, sc * sl2);
-                    }
-                    const float rs = ex2_approx(mb - m2);  // rescale of s's part (1 if no new maximum)
+                    // one pass over the changed keys before the row (ascending) with a running
+                    // maximum m2 for the configuration's weights (add and ladd are rescaled when
+                    // it grows); the next key's position and row ids load while this one is used
+                    float m2 = mb, lsub = 0.f, ladd = 0.f;  // log2-unit maximum; removed and added weight
                     float add[16];
 #pragma unroll
                     for (int t = 0; t < 16; ++t) add[t] = 0.f;
-                    float ladd = 0.f;
-                    for (int i = 0; i < nd; ++i) {
-                        const int k = dp[i];
-                        if (k > p) break;
-                        const float sb = dot_dh<SPLIT>(q, qkv + (size_t)ub[k] * ld + d + h * DH, lo_off);
-                        const float sc = dot_dh<SPLIT>(q, qkv + (size_t)uc[k] * ld + d + h * DH, lo_off);
+                    int kn = nd > 0 ? dp[0] : 0x7fffffff;
+                    int ubn = 0, ucn = 0;
+                    if (kn <= p) { ubn = ub[kn]; ucn = uc[kn]; }
+                    for (int i = 0; i < nd && kn <= p; ++i) {
+                        const int ukb = ubn, ukc = ucn;
+                        kn = i + 1 < nd ? dp[i + 1] : 0x7fffffff;
+                        if (kn <= p) { ubn = ub[kn]; ucn = uc[kn]; }
+                        const float sb = dot_dh<SPLIT>(q, qkv + (size_t)ukb * ld + d + h * DH, lo_off);
+                        const float sc = dot_dh<SPLIT>(q, qkv + (size_t)ukc * ld + d + h * DH, lo_off);
                         const float eb = ex2_approx(fmaf(sb, sl2, -mb));  // as s's softmax added it
                         const float ebq = operand_value<SPLIT>(eb);
-                        const float ec = ex2_approx(fmaf(sc, sl2, -m2));
-                        axpy16<SPLIT>(-ebq, qkv + (size_t)ub[k] * ld + 2 * d + h * DH + half * 16, lo_off, a);
-                        axpy16<SPLIT>(ec, qkv + (size_t)uc[k] * ld + 2 * d + h * DH + half * 16, lo_off, add);
+                        axpy16<SPLIT>(-ebq, qkv + (size_t)ukb * ld + 2 * d + h * DH + half * 16, lo_off, a);
+                        const float xc = sc * sl2;
+                        if (xc > m2) {  // a new maximum: rescale what was added so far
+                            const float f = ex2_approx(m2 - xc);
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) add[t] *= f;
+                            ladd *= f;
+                            m2 = xc;
+                        }
+                        const float ec = ex2_approx(xc - m2);
+                        axpy16<SPLIT>(ec, qkv + (size_t)ukc * ld + 2 * d + h * DH + half * 16, lo_off, add);
                         lsub += eb;
                         ladd += ec;
                     }
+                    const float rs = ex2_approx(mb - m2);  // rescale of s's part (1 if no new maximum)
                     if (h == 0 && half == 0) pairs += p + 1;
                     const float inv = 1.f / (rs * (sum - lsub) + ladd);
                     float* dst = O + (size_t)rrow * d + h * DH + half * 16;
