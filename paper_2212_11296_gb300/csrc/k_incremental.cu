@@ -502,6 +502,7 @@ __device__ __forceinline__ void patch_weights(uint32_t (&s)[32], int nk, float s
 
 constexpr int RES_THREADS = 512;  // four threads per tile row, a quarter of the heads each
 constexpr int RES_LCAP = 1024;    // list entries gathered before one flush to the global lists
+constexpr int RES_MAX_CFG = 544;  // a sample's connected configurations one item may walk (N <= 256: <= 513)
 
 struct ResLayout {
     size_t q, e, k, v, cert, n2, pr, kx, vn, dp, vq, full, bar, total;
@@ -525,22 +526,6 @@ __host__ __device__ inline ResLayout res_layout(int d, int H) {
     L.bar = o;  o += 64;
     L.total = o + 128;  // + alignment of the dynamic base
     return L;
-}
-
-// The first connected configuration of sample b's slice from c (stepping by `slices`, below
-// cb1) patched on the tensor cores whose first changed position is before tend; -1 if none.
-// Every thread of a warp gets the same answer (32 candidates per round).
-__device__ __forceinline__ int res_next_cfg(const Chunk& ch, const int* __restrict__ dcnt, int c, int cb1,
-                                            int slices, int tend) {
-    const int lane = threadIdx.x & 31;
-    for (; c < cb1; c += 32 * slices) {
-        const int cc = c + lane * slices;
-        bool f = false;
-        if (cc < cb1) f = dcnt[cc] <= PATCH_TC_KEYS && cfg_first_changed(ch.cfg_i[cc], ch.cfg_j[cc]) < tend;
-        const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (m) return c + (__ffs(m) - 1) * slices;
-    }
-    return -1;
 }
 
 __global__ void __launch_bounds__(RES_THREADS, 1)
@@ -575,6 +560,8 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L.bar);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + 1);
     __shared__ int sNvq, sNfull, sBase[2], s_item;
+    __shared__ int sCL[RES_MAX_CFG];  // the item's configurations, as indices into its slice
+    __shared__ int s_warp[32];
     __shared__ long long sCnt[4];
     const int tid = threadIdx.x, warp = tid >> 5;
     const int qq = tid >> 7, r = tid & 127;
@@ -617,13 +604,14 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                        in ? qkv + (size_t)dl[32 + n] * ld + part * d + h * DH + t8 : qkv, in ? 16 : 0);
         }
     };
-    // c's changed positions and their row ids into dl (threads 0 .. nd - 1)
-    auto load_changed = [&](int* dl, int c, int nd, const int* ub, const int* uc) {
-        if (tid < nd) {
-            const int q = dpos[(size_t)c * INC_MAX_KEYS + tid];
-            dl[tid] = q;
-            dl[32 + tid] = ub[q];
-            dl[48 + tid] = uc[q];
+    // c's changed positions and their row ids into dl (lanes 0 .. nd - 1 of warp w0)
+    auto load_changed = [&](int* dl, int c, int nd, const int* ub, const int* uc, int w0) {
+        const int k = tid - 32 * w0;
+        if (k >= 0 && k < nd) {
+            const int q = dpos[(size_t)c * INC_MAX_KEYS + k];
+            dl[k] = q;
+            dl[32 + k] = ub[q];
+            dl[48 + k] = uc[q];
         }
     };
 
@@ -644,8 +632,20 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
         if (t0 >= N) continue;
         const int tend = min(N, t0 + 128);
         const int cb0 = ch.cfg_off[b], cb1 = ch.cfg_off[b + 1];
-        int c = res_next_cfg(ch, dcnt, cb0 + 1 + z, cb1, slices, tend);
-        if (c < 0) continue;
+        // the slice's configurations patched here (at most PATCH_TC_KEYS changed positions, the
+        // first inside the tile or before it), in order; the walk below reads them from smem
+        const int cs0 = cb0 + 1 + z;
+        const int ncand = cs0 < cb1 ? (cb1 - cs0 + slices - 1) / slices : 0;
+        const int nC = block_compact(
+            0, min(ncand, RES_MAX_CFG),
+            [&](int i) {
+                const int cc = cs0 + i * slices;
+                return dcnt[cc] <= PATCH_TC_KEYS && cfg_first_changed(ch.cfg_i[cc], ch.cfg_j[cc]) < tend;
+            },
+            sCL, RES_MAX_CFG, s_warp);
+        if (nC == 0) continue;
+        int ci = 0;
+        int c = cs0 + sCL[0] * slices;
         const int rb = ch.cfg_row[cb0];
         const int* ub = uid + rb;
         const int p = t0 + r;
@@ -696,7 +696,7 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
         // the first configuration's changed positions, keys and values
         int buf = 0;
         int nd = dcnt[c], rc = ch.cfg_row[c], p0 = cfg_first_changed(ch.cfg_i[c], ch.cfg_j[c]);
-        load_changed(sD, c, nd, ub, uid + rc);
+        load_changed(sD, c, nd, ub, uid + rc, 0);
         __syncthreads();
         stage_kv(sK, 1, sD, nd);
         stage_kv(sV, 2, sD, nd);
@@ -773,15 +773,16 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 }
                 tc::mma_commit(bar);
             }
-            // the next configuration of the slice, while the scores form
-            const int cn = res_next_cfg(ch, dcnt, c + slices, cb1, slices, tend);
+            // the next configuration of the slice, while the scores form (its changed positions by
+            // the last warp: warp 0 issues the MMAs)
+            const int cn = ci + 1 < nC ? cs0 + sCL[ci + 1] * slices : -1;
             int nd_n = 0, rc_n = 0, p0_n = 0;
             int* dl_n = sD + (buf ^ 1) * 64;
             if (cn >= 0) {
                 nd_n = dcnt[cn];
                 rc_n = ch.cfg_row[cn];
                 p0_n = cfg_first_changed(ch.cfg_i[cn], ch.cfg_j[cn]);
-                load_changed(dl_n, cn, nd_n, ub, uid + rc_n);
+                load_changed(dl_n, cn, nd_n, ub, uid + rc_n, RES_THREADS / 32 - 1);
             }
             // every thread waits for the scores itself (a timeout is settled at the end barrier)
             ok = tc::mbar_wait(bar, phase, status) && ok;
@@ -1005,6 +1006,7 @@ k_inc_patch_res(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __re
                 __syncthreads();
             }
             if (last) break;
+            ++ci;
             c = cn;
             nd = nd_n;
             rc = rc_n;
@@ -1713,6 +1715,8 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
         if (use_tc) {  // the classify kernel left no configuration to the CUDA cores
             const int d = ch.d;
+            // a sample has at most 2N + 1 configurations: one item's walk list holds them all
+            if (2 * ch.N + 1 > RES_MAX_CFG) return cudaErrorInvalidValue;
             const uint32_t cols = 2 * d <= 256 ? 256 : 512;  // scores/sums and the sample's outputs
             if (2 * d > 512) return cudaErrorInvalidValue;
             const size_t smem = res_layout(d, ch.heads).total;
