@@ -262,125 +262,180 @@ __global__ void k_embed_bwd(const float* __restrict__ dX0, const uint8_t* __rest
 }
 
 // ---- causal attention backward, one CTA per (sample, head), FP32 ----------------
-// Inputs per row: QKV [R][3d] and dO [R][d].  The query-side kernel recomputes
-// each row's softmax statistics (m_p, l_p) and D_p = dO_p . O_p, stores them in
-// stat [R][H][3] and accumulates dQ_p = scale sum_{j<=p} dS_pj K_j; the key-side
-// kernel then accumulates dK_j = scale sum_{p>=j} dS_pj Q_p and
-// dV_j = sum_{p>=j} P_pj dO_p, with dS_pj = P_pj (dO_p . V_j - D_p).
-__device__ __forceinline__ void attn_bwd_stage(const float* __restrict__ QKV, const float* __restrict__ dO,
-                                               size_t r0, int N, int d, int h, int DH, float* sQ, float* sK,
-                                               float* sV, float* sdO) {
-    const int ld = 3 * d;
-    for (int e = threadIdx.x; e < N * DH; e += blockDim.x) {
-        const int j = e / DH, t = e - j * DH;
-        const float* src = QKV + (r0 + j) * ld + h * DH + t;
-        sQ[e] = src[0];
-        sK[e] = src[d];
-        sV[e] = src[2 * d];
-        sdO[e] = dO[(r0 + j) * d + h * DH + t];
-    }
-}
+// Inputs per row: QKV [R][3d], the attention output O [R][d], dO [R][d] and the forward's
+// softmax statistics stats [R][H] = (m_p, l_p) (maximum scaled score, sum of exp(s - m_p)).
+// With P_pj = exp(s_pj - m_p) / l_p, s_pj = q_p . k_j / sqrt(dh), D_p = dO_p . O_p and
+// dS_pj = P_pj (dO_p . v_j - D_p):
+//   dQ_p = scale sum_{j<=p} dS_pj k_j            (query-side kernel, which also stores D_p)
+//   dK_j = scale sum_{p>=j} dS_pj q_p,  dV_j = sum_{p>=j} P_pj dO_p   (key-side kernel).
+// Two threads per row (or key), each holding half of the head's dims; a dot product is
+// the pair's two halves added with one shuffle.  Every lane of a warp reads the same key
+// (query-side) or the same query row (key-side) from shared memory in each step, so the
+// reads are broadcasts; on the key side a warp walks the query rows from its first key
+// with the rows before a lane's key masked.
+constexpr int ABWD_THREADS = 512;  // 256 rows (or keys) per pass, two threads each
 
 template <int DH>
-__global__ void __launch_bounds__(512) k_attention_bwd_q(const float* __restrict__ QKV, const float* __restrict__ dO,
-                                                         int S, int N, int d, int H, float* __restrict__ dQKV,
-                                                         float* __restrict__ stat) {
-    extern __shared__ __align__(16) float sm[];
-    float *sQ = sm, *sK = sQ + (size_t)N * DH, *sV = sK + (size_t)N * DH, *sdO = sV + (size_t)N * DH;
-    const float scale = rsqrtf((float)DH);
-    for (int item = blockIdx.x; item < S * H; item += gridDim.x) {
-        const int b = item / H, h = item - b * H;
-        const size_t r0 = (size_t)b * N;
-        attn_bwd_stage(QKV, dO, r0, N, d, h, DH, sQ, sK, sV, sdO);
-        __syncthreads();
-        const int p = threadIdx.x;
-        if (p < N) {
-            float m = -INFINITY, l = 0.f, acc[DH];
-#pragma unroll
-            for (int t = 0; t < DH; ++t) acc[t] = 0.f;
-            for (int j = 0; j <= p; ++j) {
-                float s = 0.f;
-#pragma unroll
-                for (int t = 0; t < DH; ++t) s = fmaf(sQ[p * DH + t], sK[j * DH + t], s);
-                s *= scale;
-                const float mn = fmaxf(m, s);
-                const float corr = expf(m - mn), e = expf(s - mn);
-                l = l * corr + e;
-#pragma unroll
-                for (int t = 0; t < DH; ++t) acc[t] = fmaf(e, sV[j * DH + t], acc[t] * corr);
-                m = mn;
-            }
-            float Dp = 0.f;
-#pragma unroll
-            for (int t = 0; t < DH; ++t) Dp = fmaf(sdO[p * DH + t], acc[t] / l, Dp);
-            float* so = stat + ((r0 + p) * H + h) * 3;
-            so[0] = m; so[1] = l; so[2] = Dp;
-            float dq[DH];
-#pragma unroll
-            for (int t = 0; t < DH; ++t) dq[t] = 0.f;
-            for (int j = 0; j <= p; ++j) {
-                float s = 0.f, dp = 0.f;
-#pragma unroll
-                for (int t = 0; t < DH; ++t) {
-                    s = fmaf(sQ[p * DH + t], sK[j * DH + t], s);
-                    dp = fmaf(sdO[p * DH + t], sV[j * DH + t], dp);
-                }
-                const float P = expf(s * scale - m) / l;
-                const float dS = P * (dp - Dp);
-#pragma unroll
-                for (int t = 0; t < DH; ++t) dq[t] = fmaf(dS, sK[j * DH + t], dq[t]);
-            }
-            float* dst = dQKV + (r0 + p) * (size_t)(3 * d) + h * DH;
-#pragma unroll
-            for (int t = 0; t < DH; ++t) dst[t] = dq[t] * scale;
-        }
-        __syncthreads();
-    }
-}
-
-template <int DH>
-__global__ void __launch_bounds__(512) k_attention_bwd_kv(const float* __restrict__ QKV, const float* __restrict__ dO,
+__global__ void __launch_bounds__(ABWD_THREADS) k_attention_bwd_q(const float* __restrict__ QKV, const float* __restrict__ O,
+                                                          const float* __restrict__ dO, const float2* __restrict__ stats,
                                                           int S, int N, int d, int H, float* __restrict__ dQKV,
-                                                          const float* __restrict__ stat) {
+                                                          float* __restrict__ Dst) {
+    constexpr int HD = DH / 2;  // dims per thread
     extern __shared__ __align__(16) float sm[];
-    float *sQ = sm, *sK = sQ + (size_t)N * DH, *sV = sK + (size_t)N * DH, *sdO = sV + (size_t)N * DH;
-    float *sM = sdO + (size_t)N * DH, *sL = sM + N, *sD = sL + N;
+    float *sK = sm, *sV = sK + (size_t)N * DH;
     const float scale = rsqrtf((float)DH);
+    const int ld = 3 * d;
+    const int hf = threadIdx.x & 1;
     for (int item = blockIdx.x; item < S * H; item += gridDim.x) {
         const int b = item / H, h = item - b * H;
         const size_t r0 = (size_t)b * N;
-        attn_bwd_stage(QKV, dO, r0, N, d, h, DH, sQ, sK, sV, sdO);
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
-            const float* si = stat + ((r0 + p) * H + h) * 3;
-            sM[p] = si[0]; sL[p] = si[1]; sD[p] = si[2];
+        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+            const int j = e / (DH / 4), t = (e - j * (DH / 4)) * 4;
+            const float* src = QKV + (r0 + j) * ld + h * DH + t;
+            *reinterpret_cast<float4*>(sK + j * DH + t) = *reinterpret_cast<const float4*>(src + d);
+            *reinterpret_cast<float4*>(sV + j * DH + t) = *reinterpret_cast<const float4*>(src + 2 * d);
         }
         __syncthreads();
-        const int j = threadIdx.x;
-        if (j < N) {
-            float dk[DH], dv[DH];
+        for (int pb = 0; pb < N; pb += ABWD_THREADS / 2) {
+        const int p = pb + (threadIdx.x >> 1);
+        const bool act = p < N;
+        const size_t row = r0 + (act ? p : 0);
+        float q[HD], g[HD], dq[HD];
+        float Dp = 0.f;
 #pragma unroll
-            for (int t = 0; t < DH; ++t) { dk[t] = 0.f; dv[t] = 0.f; }
-            for (int q = j; q < N; ++q) {
-                float s = 0.f, dp = 0.f;
+        for (int t = 0; t < HD; t += 4) {
+            const float4 q4 = *reinterpret_cast<const float4*>(QKV + row * ld + h * DH + hf * HD + t);
+            const float4 g4 = *reinterpret_cast<const float4*>(dO + row * d + h * DH + hf * HD + t);
+            const float4 o4 = *reinterpret_cast<const float4*>(O + row * d + h * DH + hf * HD + t);
+            q[t] = q4.x; q[t + 1] = q4.y; q[t + 2] = q4.z; q[t + 3] = q4.w;
+            g[t] = g4.x; g[t + 1] = g4.y; g[t + 2] = g4.z; g[t + 3] = g4.w;
+            Dp = fmaf(g4.x, o4.x, fmaf(g4.y, o4.y, fmaf(g4.z, o4.z, fmaf(g4.w, o4.w, Dp))));
+            dq[t] = dq[t + 1] = dq[t + 2] = dq[t + 3] = 0.f;
+        }
+        Dp += __shfl_xor_sync(0xffffffffu, Dp, 1);
+        const float2 ml = stats[row * H + h];
+        const float il = 1.f / ml.y;
+        // warp-uniform walk over the keys of the warp's last row; keys after a lane's row are masked
+        const int pw = min(N - 1, pb + (int)((threadIdx.x | 31) >> 1));
+        for (int j = 0; j <= pw; ++j) {
+            const float* kj = sK + j * DH + hf * HD;
+            const float* vj = sV + j * DH + hf * HD;
+            float s = 0.f, dp = 0.f;
 #pragma unroll
-                for (int t = 0; t < DH; ++t) {
-                    s = fmaf(sQ[q * DH + t], sK[j * DH + t], s);
-                    dp = fmaf(sdO[q * DH + t], sV[j * DH + t], dp);
-                }
-                const float P = expf(s * scale - sM[q]) / sL[q];
-                const float dS = P * (dp - sD[q]);
-#pragma unroll
-                for (int t = 0; t < DH; ++t) {
-                    dk[t] = fmaf(dS, sQ[q * DH + t], dk[t]);
-                    dv[t] = fmaf(P, sdO[q * DH + t], dv[t]);
-                }
+            for (int t = 0; t < HD; t += 4) {
+                const float4 k4 = *reinterpret_cast<const float4*>(kj + t);
+                const float4 v4 = *reinterpret_cast<const float4*>(vj + t);
+                s = fmaf(q[t], k4.x, fmaf(q[t + 1], k4.y, fmaf(q[t + 2], k4.z, fmaf(q[t + 3], k4.w, s))));
+                dp = fmaf(g[t], v4.x, fmaf(g[t + 1], v4.y, fmaf(g[t + 2], v4.z, fmaf(g[t + 3], v4.w, dp))));
             }
-            float* dst = dQKV + (r0 + j) * (size_t)(3 * d) + h * DH;
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            dp += __shfl_xor_sync(0xffffffffu, dp, 1);
+            const float P = (act && j <= p) ? __expf(s * scale - ml.x) * il : 0.f;
+            const float dS = P * (dp - Dp);
 #pragma unroll
-            for (int t = 0; t < DH; ++t) {
-                dst[d + t] = dk[t] * scale;
-                dst[2 * d + t] = dv[t];
+            for (int t = 0; t < HD; t += 4) {
+                const float4 k4 = *reinterpret_cast<const float4*>(kj + t);
+                dq[t] = fmaf(dS, k4.x, dq[t]);
+                dq[t + 1] = fmaf(dS, k4.y, dq[t + 1]);
+                dq[t + 2] = fmaf(dS, k4.z, dq[t + 2]);
+                dq[t + 3] = fmaf(dS, k4.w, dq[t + 3]);
             }
+        }
+        if (act) {
+            float* dst = dQKV + row * (size_t)ld + h * DH + hf * HD;
+#pragma unroll
+            for (int t = 0; t < HD; t += 4)
+                *reinterpret_cast<float4*>(dst + t) =
+                    make_float4(dq[t] * scale, dq[t + 1] * scale, dq[t + 2] * scale, dq[t + 3] * scale);
+            if (hf == 0) Dst[row * H + h] = Dp;
+        }
+        }
+        __syncthreads();
+    }
+}
+
+template <int DH>
+__global__ void __launch_bounds__(ABWD_THREADS) k_attention_bwd_kv(const float* __restrict__ QKV, const float* __restrict__ dO,
+                                                           const float2* __restrict__ stats,
+                                                           const float* __restrict__ Dst, int S, int N, int d, int H,
+                                                           float* __restrict__ dQKV) {
+    constexpr int HD = DH / 2;
+    extern __shared__ __align__(16) float sm[];
+    float *sQ = sm, *sG = sQ + (size_t)N * DH;
+    float *sM = sG + (size_t)N * DH, *sIL = sM + N, *sD = sIL + N;
+    const float scale = rsqrtf((float)DH);
+    const int ld = 3 * d;
+    const int hf = threadIdx.x & 1;
+    for (int item = blockIdx.x; item < S * H; item += gridDim.x) {
+        const int b = item / H, h = item - b * H;
+        const size_t r0 = (size_t)b * N;
+        for (int e = threadIdx.x; e < N * (DH / 4); e += blockDim.x) {
+            const int q = e / (DH / 4), t = (e - q * (DH / 4)) * 4;
+            *reinterpret_cast<float4*>(sQ + q * DH + t) =
+                *reinterpret_cast<const float4*>(QKV + (r0 + q) * ld + h * DH + t);
+            *reinterpret_cast<float4*>(sG + q * DH + t) = *reinterpret_cast<const float4*>(dO + (r0 + q) * d + h * DH + t);
+        }
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            const float2 ml = stats[(r0 + q) * H + h];
+            sM[q] = ml.x;
+            sIL[q] = 1.f / ml.y;
+            sD[q] = Dst[(r0 + q) * H + h];
+        }
+        __syncthreads();
+        for (int jb = 0; jb < N; jb += ABWD_THREADS / 2) {
+        const int j = jb + (threadIdx.x >> 1);
+        const int jw = jb + ((threadIdx.x & ~31) >> 1);  // the warp's first key
+        const bool act = j < N;
+        const size_t row = r0 + (act ? j : 0);
+        float k[HD], v[HD], dk[HD], dv[HD];
+#pragma unroll
+        for (int t = 0; t < HD; t += 4) {
+            const float4 k4 = *reinterpret_cast<const float4*>(QKV + row * ld + d + h * DH + hf * HD + t);
+            const float4 v4 = *reinterpret_cast<const float4*>(QKV + row * ld + 2 * d + h * DH + hf * HD + t);
+            k[t] = k4.x; k[t + 1] = k4.y; k[t + 2] = k4.z; k[t + 3] = k4.w;
+            v[t] = v4.x; v[t + 1] = v4.y; v[t + 2] = v4.z; v[t + 3] = v4.w;
+            dk[t] = dk[t + 1] = dk[t + 2] = dk[t + 3] = 0.f;
+            dv[t] = dv[t + 1] = dv[t + 2] = dv[t + 3] = 0.f;
+        }
+        for (int q = jw; q < N; ++q) {  // warp-uniform walk; rows before this lane's key are masked
+            const float* qq = sQ + q * DH + hf * HD;
+            const float* gq = sG + q * DH + hf * HD;
+            float s = 0.f, dp = 0.f;
+#pragma unroll
+            for (int t = 0; t < HD; t += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(qq + t);
+                const float4 g4 = *reinterpret_cast<const float4*>(gq + t);
+                s = fmaf(k[t], q4.x, fmaf(k[t + 1], q4.y, fmaf(k[t + 2], q4.z, fmaf(k[t + 3], q4.w, s))));
+                dp = fmaf(v[t], g4.x, fmaf(v[t + 1], g4.y, fmaf(v[t + 2], g4.z, fmaf(v[t + 3], g4.w, dp))));
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            dp += __shfl_xor_sync(0xffffffffu, dp, 1);
+            const bool vis = act && q >= j;
+            const float P = vis ? __expf(s * scale - sM[q]) * sIL[q] : 0.f;
+            const float dS = P * (dp - sD[q]);
+#pragma unroll
+            for (int t = 0; t < HD; t += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(qq + t);
+                const float4 g4 = *reinterpret_cast<const float4*>(gq + t);
+                dk[t] = fmaf(dS, q4.x, dk[t]);
+                dk[t + 1] = fmaf(dS, q4.y, dk[t + 1]);
+                dk[t + 2] = fmaf(dS, q4.z, dk[t + 2]);
+                dk[t + 3] = fmaf(dS, q4.w, dk[t + 3]);
+                dv[t] = fmaf(P, g4.x, dv[t]);
+                dv[t + 1] = fmaf(P, g4.y, dv[t + 1]);
+                dv[t + 2] = fmaf(P, g4.z, dv[t + 2]);
+                dv[t + 3] = fmaf(P, g4.w, dv[t + 3]);
+            }
+        }
+        if (act) {
+            float* dst = dQKV + row * (size_t)ld + h * DH + hf * HD;
+#pragma unroll
+            for (int t = 0; t < HD; t += 4) {
+                *reinterpret_cast<float4*>(dst + d + t) =
+                    make_float4(dk[t] * scale, dk[t + 1] * scale, dk[t + 2] * scale, dk[t + 3] * scale);
+                *reinterpret_cast<float4*>(dst + 2 * d + t) = make_float4(dv[t], dv[t + 1], dv[t + 2], dv[t + 3]);
+            }
+        }
         }
         __syncthreads();
     }
@@ -454,24 +509,24 @@ cudaError_t launch_embed_bwd(const float* dX0, const uint8_t* spins, int S, int 
                                                                         out_stride, accumulate);
     return cudaGetLastError();
 }
-cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N, int d, int H, float* dQKV,
-                                 float* stat, cudaStream_t st, int cap) {
+cudaError_t launch_attention_bwd(const float* QKV, const float* O, const float* dO, const float2* stats, int S, int N,
+                                 int d, int H, float* dQKV, float* Dst, cudaStream_t st, int cap) {
     const int DH = d / H;
-    const int threads = ((N + 31) / 32) * 32;
-    const size_t smem = ((size_t)4 * N * DH + 3 * N) * sizeof(float);
-    if (threads > 512 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    const int threads = ABWD_THREADS;
+    const size_t smem = ((size_t)2 * N * DH + 3 * N) * sizeof(float);
+    if (smem > 227 * 1024 || DH % 8) return cudaErrorInvalidValue;
     const int grid = g_grid((long long)S * H, 1, cap);
     static size_t granted[3] = {};
     switch (DH) {
-#define VQ_ABWD(X)                                                                                           \
-    case X:                                                                                                  \
-        if (smem > granted[X / 16]) {                                                                        \
-            cudaFuncSetAttribute(k_attention_bwd_q<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-            cudaFuncSetAttribute(k_attention_bwd_kv<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);\
-            granted[X / 16] = smem;                                                                          \
-        }                                                                                                    \
-        k_attention_bwd_q<X><<<grid, threads, smem, st>>>(QKV, dO, S, N, d, H, dQKV, stat);                  \
-        k_attention_bwd_kv<X><<<grid, threads, smem, st>>>(QKV, dO, S, N, d, H, dQKV, stat);                 \
+#define VQ_ABWD(X)                                                                                            \
+    case X:                                                                                                   \
+        if (smem > granted[X / 16]) {                                                                         \
+            cudaFuncSetAttribute(k_attention_bwd_q<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+            cudaFuncSetAttribute(k_attention_bwd_kv<X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            granted[X / 16] = smem;                                                                           \
+        }                                                                                                     \
+        k_attention_bwd_q<X><<<grid, threads, smem, st>>>(QKV, O, dO, stats, S, N, d, H, dQKV, Dst);          \
+        k_attention_bwd_kv<X><<<grid, threads, smem, st>>>(QKV, dO, stats, Dst, S, N, d, H, dQKV);            \
         break;
         VQ_ABWD(8)
         VQ_ABWD(16)

@@ -888,7 +888,9 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
                 VQ_CK(launch_layernorm(X(l), counters, CNT_R, w.ln1_g, w.ln1_b, d, A1, nullptr, st, g_rows));
                 VQ_CK(launch_sgemm(A1, w.w_qkv, w.b_qkv, nullptr, QKV, counters, CNT_R, R, 3 * d, d, EPI_BIAS, st, sms));
             }
-            VQ_CK(launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8)));
+            // the softmax statistics of every row and head go to the attention backward
+            VQ_CK(launch_attention_f32(ch, uid, QKV, Oatt, 0, st, grid_for(ctx, (long long)S * H, 1, 8), nullptr, 0,
+                                       at<float2>(ws, P.stat)));
             VQ_CK(launch_quant_residual(X(l), code(l), w.T, w.codebook, R, d, Y, V, st, cap));
             if (tcb) {
                 VQ_CK(launch_layernorm(Y, counters, CNT_R, w.ln2_g, w.ln2_b, d, A2, S16, st, g_rows, (size_t)R * d));
@@ -957,7 +959,8 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         // attention
         {
             StageScope sc(ctx, S_BWD_ATTN, 2, st);
-            VQ_CK(launch_attention_bwd(QKV, dO, S, N, d, H, dQKV, at<float>(ws, P.stat), st, cap));
+            VQ_CK(launch_attention_bwd(QKV, Oatt, dO, at<float2>(ws, P.stat), S, N, d, H, dQKV,
+                                       at<float>(ws, P.stat) + 2 * (size_t)R * H, st, cap));
         }
         // qkv = LN1(x) W_qkv + b_qkv
         if (tcb) VQ_CK(gw(A1, d, 0, dQKV, 3 * d, OUT + o.wqkv));

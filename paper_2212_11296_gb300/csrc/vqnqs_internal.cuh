@@ -385,8 +385,10 @@ cudaError_t launch_colsum(const float* X, int rows, int G, int ncol, float* out,
                           cudaStream_t st, int cap, float* part = nullptr, int part_cap = 0);
 cudaError_t launch_embed_bwd(const float* dX0, const uint8_t* spins, int S, int N, int d, int G, float* dtok,
                              float* dpos, long long out_stride, int accumulate, cudaStream_t st, int cap);
-cudaError_t launch_attention_bwd(const float* QKV, const float* dO, int S, int N, int d, int H, float* dQKV,
-                                 float* stat, cudaStream_t st, int cap);
+// stats [R][H]: the forward's (maximum scaled score, sum of exp(score - maximum)) per row and head; O the
+// forward's attention output; Dst [R][H] receives dO . O per row and head
+cudaError_t launch_attention_bwd(const float* QKV, const float* O, const float* dO, const float2* stats, int S, int N,
+                                 int d, int H, float* dQKV, float* Dst, cudaStream_t st, int cap);
 cudaError_t launch_seeds_from_eloc(const float* e_loc, int B, float* seeds, cudaStream_t st);
 // sharded energy gradient: partials [2P + 3] = (sum E O, sum O, sum E, sum E^2, n), and their combination
 cudaError_t launch_grad_partials(const float* s_eo, const float* s_o, long long P, const float* e_loc, int B,
