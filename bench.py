@@ -377,6 +377,17 @@ def grad_bench(args) -> dict:
     rel32 = float((g - g32).abs().max().item() / g32.abs().max().item())
     st = m.stats()
     ms = sum(te) + sum(tg)
+    stages = {k: {"ms": v[2], "launches": v[1]} for k, v in prof.items() if v[1] > 0}
+    # the backward's tensor-core GEMMs, algorithmic FLOPs over the B N rows per layer: dX and dW
+    # of W_qkv (2 x 6 d^2), W_o (2 x 2 d^2), W_1 and W_2 (4 x 8 d^2), and the straight-through
+    # quantizer's o W^T, alpha W, alpha^T o and onehot^T dV (4 x 2 K d)
+    R = B * N
+    gemm_flops = layers * R * (48.0 * d * d + 8.0 * K * d)
+    pk = measured_peaks()
+    if "bwd_gemm" in stages and stages["bwd_gemm"]["ms"] > 0:
+        tf = gemm_flops / (stages["bwd_gemm"]["ms"] / 1e3) / 1e12
+        stages["bwd_gemm"].update({"flops": gemm_flops, "tflops": tf, "bound": "tensor",
+                                   "frac": tf / pk["bf16_tflops"], "peak_source": f"bf16 dense, sustained ({pk['src']})"})
     return {"metric": "energy-gradient samples/sec at 20x20 (E_loc + backward)", "unit": "samples/s",
             "value": B * args.steps / (ms / 1e3), "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "eloc_ms_per_step": sum(te) / args.steps,
@@ -385,9 +396,10 @@ def grad_bench(args) -> dict:
                                    f"codebook {K}, {B} uniform S_z=0 samples",
                        "eloc_path": "VQ-reuse BF16",
                        "backward": "hand-written, activation recomputation; GEMMs on the tensor cores with split "
-                                   "BF16 operands, attention backward and row-wise steps FP32"},
+                                   "BF16 operands (the dW products are one long K loop over the rows: few output "
+                                   "tiles), attention backward and row-wise steps FP32 on the CUDA cores"},
             "grad_vs_fp32_backward_max_rel": rel32,
-            "backward_stages": {k: {"ms": v[2], "launches": v[1]} for k, v in prof.items() if v[1] > 0},
+            "backward_stages": stages,
             "grad_norm": float(g.norm().item()), "device_status": st["device_status"], "clocks": clk.summary()}
 
 
