@@ -218,6 +218,16 @@ __global__ void k_embed_rows(Chunk ch, const float* __restrict__ tok_emb, const 
                              int reuse, float* __restrict__ X0, int* __restrict__ uid0) {
     const int N = ch.N, d = ch.d, V = (1 << ch.G) + 1;
     const int R = ch.counters[CNT_R];
+    if (reuse) {  // row ids only: one thread per row
+        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+            const int c = ch.row_cfg[r], p = r - ch.cfg_row[c];
+            int t = ch.G == 1 ? BOS : (1 << ch.G);
+            if (p > 0) t = cfg_group(ch, sample_spins(ch, ch.cfg_sample[c]), c, p - 1);
+            uid0[r] = p * V + t;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) ch.counters[CNT_U0] = V * N;
+        return;
+    }
     // one warp per row
     int lane = threadIdx.x & 31;
     int wpb = blockDim.x >> 5;
