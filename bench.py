@@ -419,6 +419,8 @@ def main():
     ap.add_argument("--samples", type=int, default=WORKLOAD["samples_per_gpu"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay measurement")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the incremental kernels' default work split (no vqnqs_autotune_incremental)")
     ap.add_argument("--gemm-only", action="store_true",
                     help="run only the tensor-core GEMM probe (three shapes at M = 131072) and print it")
     ap.add_argument("--grad", action="store_true",
@@ -477,6 +479,9 @@ def main():
         m._ws.clear()
         torch.cuda.empty_cache()
     ws = m.workspace(flags, args.chunk)
+    inc_tuning = None
+    if (flags & INCREMENTAL) and (flags & BF16) and not args.no_tune:  # the incremental kernels' work split
+        inc_tuning = m.autotune_incremental(spins[:min(512, B)].contiguous(), flags, chunk_samples=args.chunk)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -661,6 +666,11 @@ def main():
         "chunk_samples": args.chunk,
         "autotune_chunk": ({"samples": min(512, B), "ms": {str(k): v for k, v in tuning["ms"].items()}}
                            if tuning else None),
+        "autotune_incremental": ({"samples": min(512, B), "patch_items_per_cta": inc_tuning["patch_items"],
+                                  "rows_items_per_sm": inc_tuning["rows_slices"],
+                                  "patch_ms": {str(k): v for k, v in inc_tuning["patch_ms"].items()},
+                                  "rows_ms": {str(k): v for k, v in inc_tuning["rows_ms"].items()}}
+                                 if inc_tuning else None),
     }
     if flags & INCREMENTAL:  # row outcomes over the timed steps, summed over layers
         res["incremental"] = {k: st[k] for k in ("inc_base_rows", "inc_patched_rows", "inc_certified_rows",

@@ -57,6 +57,11 @@ class StageTime(ctypes.Structure):
 MAX_STAGES = 32
 
 
+class IncTuning(ctypes.Structure):
+    _fields_ = [("patch_items", ctypes.c_int), ("rows_slices", ctypes.c_int), ("patch_ms", ctypes.c_float * 3),
+                ("rows_ms", ctypes.c_float * 3)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("qkv_bn", ctypes.c_int), ("mlp_up_bn", ctypes.c_int), ("mlp_down_bn", ctypes.c_int),
                 ("ms", (ctypes.c_float * 4) * 3)]
@@ -117,6 +122,9 @@ SIGNATURES = [
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("vqnqs_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                       ctypes.POINTER(Tuning), ctypes.c_void_p]),
+    ("vqnqs_autotune_incremental", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(IncTuning),
+                                                  ctypes.c_void_p]),
     ("vqnqs_compress_rows_noalloc", ctypes.c_int, [ctypes.c_int] + [ctypes.c_void_p] * 7),
     ("vqnqs_check_timeout_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]),
     ("vqnqs_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),

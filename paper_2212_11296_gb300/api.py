@@ -287,6 +287,22 @@ class VQNQS:
                     "vqnqs_autotune_chunk")
         return {"best": best.value, "ms": {c: float(ms[i]) for i, c in enumerate(cand)}}
 
+    def autotune_incremental(self, spins: torch.Tensor, flags: int, chunk_samples: int = 0, stream=None) -> dict:
+        """Picks the incremental path's work split (patch items per CTA, changed-row items per
+        SM; see vqnqs_autotune_incremental) by timing the local energies of ``spins`` with
+        ``flags`` (chunks of ``chunk_samples``, 0: the default), keeps it for this model and returns
+        {"patch_items", "rows_slices", "patch_ms": {items: ms}, "rows_ms": {items: ms}}."""
+        _check_dev(spins, torch.uint8, "spins")
+        ws = self.workspace(flags, chunk_samples)
+        t = _lib.IncTuning()
+        self._check(lib().vqnqs_autotune_incremental(self._h, spins.shape[0], ctypes.c_void_p(spins.data_ptr()),
+                                                     int(flags), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                                     ctypes.byref(t), ctypes.c_void_p(_stream_ptr(stream))),
+                    "vqnqs_autotune_incremental")
+        return {"patch_items": t.patch_items, "rows_slices": t.rows_slices,
+                "patch_ms": {n: float(t.patch_ms[i]) for i, n in enumerate((2, 4, 8))},
+                "rows_ms": {n: float(t.rows_ms[i]) for i, n in enumerate((1, 2, 4))}}
+
     def stats(self) -> dict:
         s = _lib.Stats()
         self._check(lib().vqnqs_get_stats(self._h, ctypes.byref(s)), "vqnqs_get_stats")

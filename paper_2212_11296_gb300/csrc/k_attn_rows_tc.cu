@@ -473,7 +473,7 @@ bool attention_rows_tc_supported(int N, int d, int heads) {
 cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                      const int2* list, const int* act_off, const int* count, const short* dpos,
                                      const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms,
-                                     size_t lo_off) {
+                                     size_t lo_off, int slices_per_sm) {
     if (!attention_rows_tc_supported(ch.N, ch.d, ch.heads)) return cudaErrorInvalidValue;
     const bool split = lo_off != 0;
     const int Npad = (ch.N + 31) & ~31;
@@ -485,7 +485,7 @@ cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv
     size_t smem_req = smem;
     if ((228 * 1024) / smem_req > max_ctas) smem_req = (228 * 1024) / (max_ctas + 1) + 1024;
     const int sh = ch.S * ch.heads;
-    int slices = (2 * num_sms + sh - 1) / sh;
+    int slices = ((slices_per_sm < 1 ? 1 : slices_per_sm) * num_sms + sh - 1) / sh;
     if (slices < 1) slices = 1;
     if (slices > 64) slices = 64;
 #define VQ_ROWS(SP, SLOT)                                                                                         \

@@ -1697,7 +1697,8 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                                const CertRow* cert, const float* codebook, const float* wd, int* code, int* vq_rows,
                                const int* act_off, int2* rc_rows, int* rc_cnt, const int* list_tc,
                                const int* list_simt, const short* dpos, const int* dcnt, int use_tc, int split,
-                               int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid) {
+                               int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid,
+                               int items_per_cta) {
     if (!incremental_supported(ch.d, ch.heads)) return cudaErrorInvalidValue;
     const int kb = inc_patch_keys(ch.d);
     const size_t smem = inc_patch_smem(ch.d, ch.N);
@@ -1735,10 +1736,11 @@ cudaError_t launch_inc_patch_t(const Chunk& ch, const int* uid, const T* qkv, fl
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
                 return cudaErrorInvalidDevice;
             const int g = (sms > 0 ? sms : 1) * per_sm;
-            // items (sample, tile, slice): about four per CTA
+            // items (sample, tile, slice): about items_per_cta per CTA
             const int ntile = (ch.N + 127) / 128;
             const int sb = ch.S * ntile;
-            int slices = (4 * g + sb - 1) / sb;
+            const int ipc = items_per_cta < 1 ? 1 : items_per_cta;
+            int slices = (ipc * g + sb - 1) / sb;
             slices = slices < 1 ? 1 : (slices > 64 ? 64 : slices);
             k_inc_patch_res<<<g, RES_THREADS, smem_req, st>>>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows,
                                                       act_off, rc_rows, rc_cnt, dpos, dcnt, split, ex_rows, slices,
@@ -1797,16 +1799,17 @@ cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const float* qkv, 
                              long long* stats, cudaStream_t st, int grid) {
     return launch_inc_patch_t<float>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off, rc_rows,
                                      rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, 0, nullptr, status, stats, st,
-                                     grid);
+                                     grid, 4);
 }
 cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                              const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
                              int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
                              const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
-                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid) {
+                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid,
+                             int items_per_cta) {
     return launch_inc_patch_t<__nv_bfloat16>(ch, uid, qkv, O, bstat, cert, codebook, wd, code, vq_rows, act_off,
                                              rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, use_tc, split, ex_rows,
-                                             status, stats, st, grid);
+                                             status, stats, st, grid, items_per_cta);
 }
 cudaError_t launch_inc_attention(const Chunk& ch, const int* uid, const float* qkv, float* O, const int* act_off,
                                  const int2* rc_rows, const int* rc_cnt, int tail_only, long long* stats, cudaStream_t st,

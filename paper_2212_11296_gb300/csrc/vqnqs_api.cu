@@ -38,6 +38,8 @@ struct vqnqs_ctx {
     int assign_rows_cap = 1 << 22;
     float* lp_scratch = nullptr;     // log psi target of vqnqs_codes when the caller passes none
     int bn[3] = {0, 0, 0};           // output tile width of the QKV, MLP up, MLP down GEMMs
+    int patch_items = 4;             // tensor-core patch: work items per CTA (sample, tile, slice)
+    int rows_slices = 2;             // changed-row kernel: (sample, head, slice) items per SM
     int lp_scratch_cap = 65536;
     long long* stats = nullptr;    // ST_* slots
     bool bwd_tc = false;           // the backward's contractions can run on the tensor cores (split operands)
@@ -477,14 +479,14 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
                                                       vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,
                                                       dcnt, 1, split ? 1 : 0, ex_rows, ctx->status, ctx->stats, st,
-                                                      g_cfg));
+                                                      g_cfg, ctx->patch_items));
                 if (split)
                     VQ_STAGE(S_EXACT, 1, launch_inc_exact_delta(ch, uid_cur, qkv16, qkv_lo, O, bstat, dpos, dcnt,
                                                                 ex_rows, counters + CNT_EX, st,
                                                                 grid_for(ctx, P.Rmax, 8, 8)));
                 VQ_STAGE(S_RECOMP, 1, launch_attention_rows_tc(ch, uid_cur, qkv16, O, rc_rows, act_off, rc_cnt, dpos,
                                                                dcnt, ctx->status, ctx->stats, st, ctx->num_sms,
-                                                               qkv_lo));
+                                                               qkv_lo, ctx->rows_slices));
                 VQ_STAGE(S_RECOMP_WHOLE, 1,
                          launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
                                              grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
@@ -1623,6 +1625,71 @@ int vqnqs_autotune_chunk(vqnqs_ctx* ctx, int B, const uint8_t* spins, int flags,
     cudaEventDestroy(e1);
     if (rc == VQNQS_OK && *best == 0) return fail(ctx, VQNQS_ERR_WORKSPACE, "autotune_chunk: no candidate fits");
     return rc;
+}
+
+int vqnqs_autotune_incremental(vqnqs_ctx* ctx, int B, const uint8_t* spins, int flags, void* ws, size_t ws_bytes,
+                               vqnqs_inc_tuning* out, void* stream) {
+    if (!ctx) return VQNQS_ERR_ARG;
+    ctx->err.clear();
+    if (B <= 0 || !spins || !out || !ws) return fail(ctx, VQNQS_ERR_ARG, "autotune_incremental: need samples and output");
+    if (!(flags & VQNQS_INCREMENTAL) || !(flags & VQNQS_BF16))
+        return fail(ctx, VQNQS_ERR_ARG, "autotune_incremental: needs VQNQS_BF16 | VQNQS_INCREMENTAL");
+    if (B > ctx->lp_scratch_cap) return fail(ctx, VQNQS_ERR_ARG, "autotune_incremental: at most 65536 samples");
+    const int rc0 = check_flags(ctx, flags);
+    if (rc0 != VQNQS_OK) return rc0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* e_loc = ctx->lp_scratch;
+    static const int kPatch[3] = {2, 4, 8}, kRows[3] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    VQ_CK(cudaEventCreate(&e0));
+    VQ_CK(cudaEventCreate(&e1));
+    int rc = VQNQS_OK;
+    // one local-energy evaluation untimed, then two timed, per setting
+    auto time_it = [&](float* ms) {
+        rc = run(ctx, B, spins, e_loc, nullptr, nullptr, flags, ws, ws_bytes, stream, true);
+        if (rc != VQNQS_OK) return;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = fail(ctx, VQNQS_ERR_CUDA, "event"); return; }
+        for (int rep = 0; rep < 2 && rc == VQNQS_OK; ++rep)
+            rc = run(ctx, B, spins, e_loc, nullptr, nullptr, flags, ws, ws_bytes, stream, true);
+        if (rc != VQNQS_OK) return;
+        float t = 0.f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+            rc = fail(ctx, VQNQS_ERR_CUDA, "autotune_incremental: event timing");
+            return;
+        }
+        *ms = t / 2.f;
+    };
+    const int keep_p = ctx->patch_items, keep_r = ctx->rows_slices;
+    // the patch's items per CTA first (with the current changed-row setting), then the changed rows'
+    float best = 1e30f;
+    int bp = keep_p;
+    for (int i = 0; i < 3 && rc == VQNQS_OK; ++i) {
+        ctx->patch_items = kPatch[i];
+        out->patch_ms[i] = -1.f;
+        time_it(&out->patch_ms[i]);
+        if (rc == VQNQS_OK && out->patch_ms[i] < best) { best = out->patch_ms[i]; bp = kPatch[i]; }
+    }
+    ctx->patch_items = bp;
+    best = 1e30f;
+    int br = keep_r;
+    for (int i = 0; i < 3 && rc == VQNQS_OK; ++i) {
+        ctx->rows_slices = kRows[i];
+        out->rows_ms[i] = -1.f;
+        time_it(&out->rows_ms[i]);
+        if (rc == VQNQS_OK && out->rows_ms[i] < best) { best = out->rows_ms[i]; br = kRows[i]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != VQNQS_OK) {
+        ctx->patch_items = keep_p;
+        ctx->rows_slices = keep_r;
+        return rc;
+    }
+    ctx->rows_slices = br;
+    out->patch_items = bp;
+    out->rows_slices = br;
+    return VQNQS_OK;
 }
 
 // ---- autoregressive sampling -----------------------------------------------------

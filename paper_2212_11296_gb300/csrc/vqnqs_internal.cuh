@@ -311,7 +311,7 @@ bool attention_rows_tc_supported(int N, int d, int heads);
 cudaError_t launch_attention_rows_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O,
                                      const int2* list, const int* act_off, const int* count, const short* dpos,
                                      const int* dcnt, int* status, long long* stats, cudaStream_t st, int num_sms,
-                                     size_t lo_off = 0);
+                                     size_t lo_off = 0, int slices_per_sm = 2);
 // per connected configuration: changed positions (first INC_MAX_KEYS), their count, and the work list it joins
 // (BF16 path: tensor-core patch, or recomputed whole with its rows searched; FP32 path: CUDA-core patch)
 cudaError_t launch_inc_classify(const Chunk& ch, const int* uid, int tc_ok, int* list_tc, int* list_simt, short* dpos,
@@ -337,7 +337,8 @@ cudaError_t launch_inc_patch(const Chunk& ch, const int* uid, const __nv_bfloat1
                              const float2* bstat, const CertRow* cert, const float* codebook, const float* wd,
                              int* code, int* vq_rows, const int* act_off, int2* rc_rows, int* rc_cnt,
                              const int* list_tc, const int* list_simt, const short* dpos, const int* dcnt, int use_tc,
-                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid);
+                             int split, int2* ex_rows, int* status, long long* stats, cudaStream_t st, int grid,
+                             int items_per_cta = 4);
 // split operands: o + delta of the listed rows (row, position) from the hi + lo planes of Q/K/V in FP32
 // (one warp per row; d_model in {128, 256}, d_model / heads = 32); n_list_dev[0] rows
 cudaError_t launch_inc_exact_delta(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, size_t lo_off, float* O,

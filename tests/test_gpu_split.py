@@ -161,3 +161,19 @@ def test_incremental_split_codes_equal_full_search(ctx16):
             g = gaps[l][0].numpy()[rows]
             print(f"sample {b} configuration {k} layer {l} rows {rows}: oracle gaps {g}")
             assert np.all(g < 1e-4)
+
+
+def test_incremental_work_split_tuner_keeps_results(ctx16):
+    """vqnqs_autotune_incremental only reassigns work to CTAs: the local energies after it
+    (with the chosen split) equal those before it bitwise, and the choices are the offered ones."""
+    from paper_2212_11296_gb300 import BF16, BF16_SPLIT, INCREMENTAL, REUSE
+    m, spins, s_dev = ctx16
+    flags = REUSE | BF16 | BF16_SPLIT | INCREMENTAL
+    sub = s_dev[:8].contiguous()
+    before = m.local_energy(sub, flags)
+    t = m.autotune_incremental(sub, flags)
+    print(t)
+    assert t["patch_items"] in (2, 4, 8) and t["rows_slices"] in (1, 2, 4)
+    assert all(v > 0 for v in t["patch_ms"].values()) and all(v > 0 for v in t["rows_ms"].values())
+    assert torch.equal(m.local_energy(sub, flags), before)
+    assert m.stats()["device_status"] == 0
