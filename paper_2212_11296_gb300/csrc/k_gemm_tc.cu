@@ -87,7 +87,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
           const float* __restrict__ bias, const float* __restrict__ R, void* __restrict__ Cout,
           const int* __restrict__ counters, int u_slot, int N, int K, int a_lo_row, int c_lo_row,
-          int* __restrict__ status) {
+          int* __restrict__ status, int ksplit) {
     using C = TcCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -104,9 +104,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     const int M = counters[u_slot];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_tiles = N / BN, m_tiles = (M + TC_BM - 1) / TC_BM, total = m_tiles * n_tiles;
+    const int n_tiles = N / BN, m_tiles = (M + TC_BM - 1) / TC_BM, tiles_mn = m_tiles * n_tiles;
+    // split K: work item t = (split sk, output tile); split sk takes K blocks [sk KBs, (sk + 1) KBs)
+    // and writes its partial tile at row sk * Mpad of the output
+    const int total = tiles_mn * ksplit;
     const int KB = K / TC_BK;
-    const int KBT = a_lo_row > 0 ? 3 * KB : KB;  // K blocks over all passes
+    const int KBs = (KB + ksplit - 1) / ksplit;
+    const int NPASS = a_lo_row > 0 ? 3 : 1;  // split operands: three passes
+    const int Mpad = m_tiles * TC_BM;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -128,12 +133,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             bool ok = true;
             int it = 0;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
-                for (int kbt = 0; kbt < KBT; ++kbt, ++it) {
+                const int sk = t / tiles_mn, tt = t - sk * tiles_mn;
+                const int m0 = (tt / n_tiles) * TC_BM, n0 = (tt % n_tiles) * BN;
+                const int kb0 = sk * KBs, nkb = min(KB, kb0 + KBs) - kb0;
+                for (int kbt = 0; kbt < NPASS * nkb; ++kbt, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (it / C::STAGES) & 1;
                     // pass 0: A_hi Bt_hi, pass 1: A_hi Bt_lo, pass 2: A_lo Bt_hi
-                    const int pass = kbt / KB, kb = kbt - pass * KB;
+                    const int pass = kbt / nkb, kb = kb0 + kbt - pass * nkb;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1, status)) { ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
                     tc::tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * TC_BK, m0 + (pass == 2 ? a_lo_row : 0), &full[s]);
@@ -156,7 +163,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (!tc::mbar_wait(&acce[a], aph ^ 1, status)) { ok = false; break; }
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem + a * BN;
-                for (int kbt = 0; kbt < KBT; ++kbt, ++it) {
+                const int sk = t / tiles_mn;
+                const int nkb = min(KB, sk * KBs + KBs) - sk * KBs;
+                for (int kbt = 0; kbt < NPASS * nkb; ++kbt, ++it) {
                     const int s = it % C::STAGES;
                     const uint32_t ph = (it / C::STAGES) & 1;
                     if (!tc::mbar_wait(&full[s], ph, status)) { ok = false; break; }
@@ -195,9 +204,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const uint32_t aph = (i >> 1) & 1;
             if (!tc::mbar_wait(&accf[a], aph, status)) { ok = false; break; }
             tc::tc_fence_after();
-            const int m0 = (t / n_tiles) * TC_BM, n0 = (t % n_tiles) * BN;
+            const int sk = t / tiles_mn, tt = t - sk * tiles_mn;
+            const int m0 = (tt / n_tiles) * TC_BM, n0 = (tt % n_tiles) * BN;
             const int rb = m0 + q * 32;  // the chunk's first row
             const int row = rb + lane;
+            const int orow = sk * Mpad;  // this split's partial output rows
             const bool boxed = rb + 32 <= M;  // warp-uniform
 #pragma unroll 1
             for (int c = part * 32; c < BN && ok; c += 128) {
@@ -270,7 +281,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                                 : "memory");
                             tma_store_2d(&tmC, slot + 2048, n, rb + c_lo_row);
                         } else {
-                            tma_store_2d(&tmC, slot, n, rb);
+                            tma_store_2d(&tmC, slot, n, rb + orow);
                         }
                     }
                 } else if (row < M) {
@@ -283,7 +294,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         }
                     }
                     if (F32OUT) {
-                        float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + (size_t)row * N + n);
+                        float4* out = reinterpret_cast<float4*>(static_cast<float*>(Cout) + ((size_t)row + orow) * N + n);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) out[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     } else {
@@ -324,6 +335,18 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 }
 
 __global__ void k_set_int(int* p, int v) { *p = v; }
+
+// C[m][n] += sum over s (in order) of part[s * Mpad + m][n], m < M
+__global__ void k_splitk_add(const float* __restrict__ part, int ksplit, long long Mpad, int M, int N,
+                             float* __restrict__ C) {
+    const long long total = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long m = i / N, n = i - m * N;
+        float s = C[i];
+        for (int k = 0; k < ksplit; ++k) s += part[((long long)k * Mpad + m) * N + n];
+        C[i] = s;
+    }
+}
 
 // A bounded wait on an mbarrier that no thread arrives on: it must give up
 // after about limit_cycles and record VQNQS_DEV_TIMEOUT (exercises the
@@ -369,7 +392,7 @@ template <int BN, int EPI>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm, const CUtensorMap& trm,
                       const float* bias, const float* R, void* Cout,
                       const int* counters, int u_slot, int Mmax, int N, int K, int a_lo_row, int c_lo_row,
-                      int* status, cudaStream_t st, int num_sms) {
+                      int* status, cudaStream_t st, int num_sms, int ksplit) {
     using C = TcCfg<BN>;
     static bool attr = false;
     if (!attr) {
@@ -378,11 +401,11 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const CUtens
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    long long tiles = (long long)((Mmax + TC_BM - 1) / TC_BM) * (N / BN);
+    long long tiles = (long long)((Mmax + TC_BM - 1) / TC_BM) * (N / BN) * ksplit;
     int grid = (int)(tiles < num_sms ? tiles : num_sms);
     if (grid < 1) grid = 1;
     k_gemm_tc<BN, EPI><<<grid, TC_THREADS, C::SMEM, st>>>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, N, K,
-                                                          a_lo_row, c_lo_row, status);
+                                                          a_lo_row, c_lo_row, status, ksplit);
     return cudaGetLastError();
 }
 
@@ -390,10 +413,10 @@ template <int EPI>
 cudaError_t launch_epi(int BN, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tcm,
                        const CUtensorMap& trm, const float* bias, const float* R, void* Cout, const int* counters,
                        int u_slot, int Mmax, int N, int K, int a_lo_row, int c_lo_row, int* status, cudaStream_t st,
-                       int num_sms) {
+                       int num_sms, int ksplit) {
 #define VQ_BN(B)                                                                                                   \
     launch_bn<B, EPI>(ta, tb, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, a_lo_row, c_lo_row, status, st, \
-                      num_sms)
+                      num_sms, ksplit)
     switch (BN) {
         case 64: return VQ_BN(64);
         case 128: return VQ_BN(128);
@@ -423,6 +446,15 @@ cudaError_t make_tmap_out(CUtensorMap* map, const void* base, long long rows, in
 }
 
 }  // namespace
+
+cudaError_t launch_splitk_add(const float* part, int ksplit, long long Mpad, int M, int N, float* C, cudaStream_t st,
+                              int num_sms) {
+    const long long total = (long long)M * N;
+    long long g = (total + 255) / 256;
+    if (g > 8LL * num_sms) g = 8LL * num_sms;
+    k_splitk_add<<<(int)(g > 0 ? g : 1), 256, 0, st>>>(part, ksplit, Mpad, M, N, C);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_set_int(int* p, int v, cudaStream_t st) {
     k_set_int<<<1, 1, 0, st>>>(p, v);
@@ -458,9 +490,17 @@ cudaError_t make_tmap_bf16_strided(CUtensorMap* map, const void* base, long long
 
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
-                           int* status, cudaStream_t st, int num_sms, int BN, bool split, long long a_inner) {
+                           int* status, cudaStream_t st, int num_sms, int BN, bool split, long long a_inner,
+                           int ksplit) {
     if (BN <= 0) BN = tc_pick_bn(N);
     if (!BN || N % BN || K % TC_BK || K <= 0 || epi < 0 || epi > 4 || (epi == 2 && !R)) return cudaErrorInvalidValue;
+    if (ksplit < 1 || (ksplit > 1 && epi != 3)) return cudaErrorInvalidValue;  // split K: FP32 partial tiles
+    {  // every split takes at least one K block
+        const int KB = K / TC_BK;
+        if (ksplit > KB) ksplit = KB;
+        const int KBs = (KB + ksplit - 1) / ksplit;
+        ksplit = (KB + KBs - 1) / KBs;
+    }
     if (Arows < 1) return cudaSuccess;  // no rows to compute
     if (split && Arows > (1LL << 30)) return cudaErrorInvalidValue;
     // split: A (and a BF16 C) hold their lo plane Arows rows after the hi one
@@ -471,7 +511,8 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
     cudaError_t e = a_inner > 0 ? make_tmap_bf16_strided(&ta, A, split ? 2 * Arows : Arows, a_inner, a_inner, TC_BM)
                                 : make_tmap_bf16(&ta, A, split ? 2 * Arows : Arows, K, TC_BM);
     if (e != cudaSuccess) return e;
-    e = make_tmap_out(&tcm, Cout, c_lo_row ? 2 * Arows : Arows, N, epi >= 2);
+    const long long Mpad = (Arows + TC_BM - 1) / TC_BM * TC_BM;
+    e = make_tmap_out(&tcm, Cout, ksplit > 1 ? ksplit * Mpad : (c_lo_row ? 2 * Arows : Arows), N, epi >= 2);
     if (e != cudaSuccess) return e;
     if (epi == 2) {
         e = make_tmap_out(&trm, R, Arows, N, true);
@@ -482,7 +523,7 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtens
     const int Mmax = (int)Arows;
 #define VQ_EPI(E) \
     launch_epi<E>(BN, ta, tmB, tcm, trm, bias, R, Cout, counters, u_slot, Mmax, N, K, a_lo_row, c_lo_row, status, st, \
-                  num_sms)
+                  num_sms, ksplit)
     switch (epi) {
         case 0: return VQ_EPI(0);
         case 1: return VQ_EPI(1);

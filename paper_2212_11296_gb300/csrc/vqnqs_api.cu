@@ -708,10 +708,12 @@ struct GradPlan {
     long long R = 0;
     size_t seeds, counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, act_cnt, act_off, act_rows, uid_a, uid_b,
         rep_uid, rep_code, code, X, dX, dY, A1, Oatt, Y, V, A2, dA, dV, dO, dgam, dbet, Af, QKV, dQKV, H1, G4, dG4, OW,
-        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, s16, tw, colpart, total;
+        DG, alpha, onehot, arow, dlog, csumK, stat, cfg_row, row_cfg, s16, tw, colpart, kpart, total;
 };
 
 constexpr int kColParts = 1 << 20;  // floats of partial column sums (slabs x columns)
+constexpr int kSplitK = 16;              // K splits of a weight-gradient GEMM, at most
+constexpr size_t kSplitKElems = 1 << 20;  // floats of one split's partial result, at most (in x out <= 1 M)
 
 GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     GradPlan p;
@@ -747,6 +749,7 @@ GradPlan make_grad_plan(const vqnqs_ctx* c, int S, int B) {
     p.s16 = take(c->bwd_tc ? R * std::max(4 * d, K) * 4 : 0);
     p.tw = take(c->bwd_tc ? R * std::max(5 * d, K + d) * 4 : 0);
     p.colpart = take((size_t)kColParts * f);  // row-slab partial column sums
+    p.kpart = take(c->bwd_tc ? (size_t)kSplitK * kSplitKElems * f : 0);  // split-K partial weight gradients
     p.total = o;
     return p;
 }
@@ -841,6 +844,7 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         return launch_gemm_gen(ta, tb, A, B, C, M, Nn, Kk, lda, ldb, ldc, sA, sB, sC, batch, acc, st, sms);
     };
     float* colpart = at<float>(ws, P.colpart);
+    float* kpart = tcb ? at<float>(ws, P.kpart) : nullptr;
     auto colsum = [&](const float* Xm, int ncol, size_t off) {
         StageScope sc(ctx, S_BWD_ROWS, 1, st);
         return launch_colsum(Xm, R, G, ncol, OUT + off, ostride, 1, st, cap, colpart, kColParts);
@@ -857,7 +861,14 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
     // ... and C[in][out] += X^T dY summed over the R rows (the weight gradient): both operands
     // transposed into K-major split planes, the row count padded to the K step with zeros
     auto gw = [&](const float* Xs, int in, int dim_slot, const float* dYs, int out, float* C) -> cudaError_t {
-        StageScope sc(ctx, S_BWD_GEMM, 3, st);
+        // few output tiles over a long K (the rows): split K so that every SM takes a share,
+        // then add the partials into C in a fixed order
+        const long long tiles = (long long)((in + 127) / 128) * (out / tc_pick_bn(out));
+        const long long mpad = (in + 127) / 128 * 128;
+        int ks = (int)(sms / (tiles > 0 ? tiles : 1));
+        if (ks > kSplitK) ks = kSplitK;
+        if (ks > 1 && (size_t)ks * mpad * out > (size_t)kSplitK * kSplitKElems) ks = 1;
+        StageScope sc(ctx, S_BWD_GEMM, ks > 1 ? 4 : 3, st);
         __nv_bfloat16* XT = TW;                            // [2 in][R]
         __nv_bfloat16* YT = TW + (size_t)2 * in * R;       // [2 out][R]
         cudaError_t e = launch_transpose_bf16(Xs, R, in, XT, st, true);
@@ -865,6 +876,13 @@ int grad_chunk(vqnqs_ctx* ctx, const GradPlan& P, void* ws, const uint8_t* spins
         CUtensorMap tmY;
         if (e == cudaSuccess) e = make_tmap_bf16_strided(&tmY, YT, 2LL * out, R, R, tc_pick_bn(out));
         if (e != cudaSuccess) return e;
+        if (ks > 1) {
+            e = launch_gemm_tc(XT, in, tmY, ctx->zeros, nullptr, kpart, ctx->dims, dim_slot, out, (int)Kp, 3,
+                               ctx->status, st, sms, tc_pick_bn(out), true, R, ks);
+            if (e != cudaSuccess) return e;
+            const int KB = (int)(Kp / 64), KBs = (KB + ks - 1) / ks;  // the splits the kernel used
+            return launch_splitk_add(kpart, (KB + KBs - 1) / KBs, mpad, in, out, C, st, sms);
+        }
         return launch_gemm_tc(XT, in, tmY, ctx->zeros, C, C, ctx->dims, dim_slot, out, (int)Kp, 2, ctx->status, st, sms,
                               tc_pick_bn(out), true, R);
     };

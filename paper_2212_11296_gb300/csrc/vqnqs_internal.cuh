@@ -261,7 +261,12 @@ cudaError_t make_tmap_bf16_strided(CUtensorMap* map, const void* base, long long
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, long long Arows, const CUtensorMap& tmB, const float* bias,
                            const float* R, void* Cout, const int* counters, int u_slot, int N, int K, int epi,
                            int* status, cudaStream_t st, int num_sms, int BN = 0, bool split = false,
-                           long long a_inner = 0);
+                           long long a_inner = 0, int ksplit = 1);
+// ksplit > 1 (epi 3 only): the K blocks are divided into ksplit ranges, each written as an FP32
+// partial result at rows [s Mpad, s Mpad + Arows) of Cout (Mpad = Arows rounded up to 128), for
+// launch_splitk_add: C[m][n] += sum over s, in order, of those partials (m < M)
+cudaError_t launch_splitk_add(const float* part, int ksplit, long long Mpad, int M, int N, float* C, cudaStream_t st,
+                              int num_sms);
 // dst [2 plane_rows][cols] BF16: row r of src (FP32 [rows][cols]) split into hi (row r) and lo (row plane_rows + r)
 cudaError_t launch_split_planes(const float* src, long long rows, int cols, __nv_bfloat16* dst, long long plane_rows,
                                 cudaStream_t st, int cap);
