@@ -174,8 +174,11 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             }
         }
         __syncthreads();
-        // query tiles start at the first changed position: no row before it is computed
-        for (int q0 = p0; q0 < N && ok; q0 += 128) {
+        // query tiles aligned to the last position: a partial tile, if any, holds the first rows
+        // (fewest keys) rather than the last ones; warps whose rows all lie before p0 skip the
+        // softmax, and no row before p0 is stored
+        const int qs = max(0, N - 128 * ((N - p0 + 127) / 128));
+        for (int q0 = qs; q0 < N && ok; q0 += 128) {
             const int nk = min(N, q0 + 128);             // keys this tile can see
             const int nk16 = (nk + 15) & ~15;            // MMA N (multiple of 16)
             const int nk32 = (nk + 31) & ~31;            // columns read back
@@ -227,7 +230,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             const int plim_w = min(q0 + (warp & 3) * 32 + 31, N - 1);
             // a warp whose rows all lie past the configuration's last position has nothing to
             // compute: its P rows are zero and its outputs are not stored
-            const bool wpad = q0 + (warp & 3) * 32 >= N;
+            const bool wpad = q0 + (warp & 3) * 32 >= N || q0 + (warp & 3) * 32 + 31 < p0;
             float mx = -INFINITY;
             for (int c0 = half * 32; c0 < nk32 && !wpad; c0 += 64) {
                 if (c0 > plim_w) break;  // chunks wholly past the warp's diagonal are invisible
