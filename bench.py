@@ -369,6 +369,8 @@ def grad_bench(args) -> dict:
             tg.append(ev[1].elapsed_time(ev[2]))
     m.profile(True)
     m.profile_read()
+    m.local_energy(spins, flags, workspace=ws)
+    prof_e = m.profile_read()
     m.grad_log_psi(spins, e_loc=e, flags=BF16)
     prof = m.profile_read()
     m.profile(False)
@@ -399,6 +401,7 @@ def grad_bench(args) -> dict:
                                    "BF16 operands (the dW products are one long K loop over the rows: few output "
                                    "tiles), attention backward and row-wise steps FP32 on the CUDA cores"},
             "grad_vs_fp32_backward_max_rel": rel32,
+            "eloc_stages": {k: {"ms": v[2], "launches": v[1]} for k, v in prof_e.items() if v[1] > 0},
             "backward_stages": stages,
             "grad_norm": float(g.norm().item()), "device_status": st["device_status"], "clocks": clk.summary()}
 
