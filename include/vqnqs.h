@@ -88,7 +88,9 @@ enum {
 enum {
     VQNQS_DEV_BAD_SPIN = 1,       /* a spin byte was not 0 or 1 */
     VQNQS_DEV_HASH_OVERFLOW = 2,  /* a dedupe probe ran past its bound */
-    VQNQS_DEV_TIMEOUT = 4         /* a bounded wait gave up */
+    VQNQS_DEV_TIMEOUT = 4,        /* a bounded wait gave up */
+    VQNQS_DEV_NONFINITE = 8       /* a row reached the codeword search with no finite distance (its
+                                     values were not finite); it was given codeword 0 */
 };
 
 #define VQNQS_MAX_LAYERS 64

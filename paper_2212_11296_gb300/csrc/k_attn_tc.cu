@@ -77,8 +77,11 @@ __host__ __device__ constexpr size_t attn_region_bytes(int Npad, int DH, int NP)
                ? (size_t)NP * 128 * DH * 2 + 2 * NP * PCB
                : (size_t)NP * Npad * (2 * DH + 16) + (size_t)Npad * 4;
 }
+// (+ 1 KB beside the barriers for more than 256 keys: the row exchange then may not alias Q, which
+// the second key block's scores read again)
 __host__ __device__ constexpr size_t attn_smem_bytes(int Npad, int DH, bool split) {
-    return 128 + (split ? 2 : 1) * 2 * attn_tile_bytes(Npad, DH) + attn_region_bytes(Npad, DH, split ? 2 : 1) + 64;
+    return 128 + (split ? 2 : 1) * 2 * attn_tile_bytes(Npad, DH) + attn_region_bytes(Npad, DH, split ? 2 : 1) + 64 +
+           (Npad > 256 ? 1024 : 0);
 }
 
 template <int DH, bool SPLIT>
@@ -103,7 +106,8 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint64_t* bar = reinterpret_cast<uint64_t*>(sQ + attn_region_bytes(Npad, DH, NP));  // S MMAs
     uint64_t* pbar = bar + 1;                      // [2]: MMAs reading P tile 0 / 1
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pbar + 2);
-    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(sQ);  // [2][128], used once Q has been read
+    // [2][128] row exchange: over Q once Q has been read (at most 256 keys), else beside the barriers
+    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(Npad > 256 ? reinterpret_cast<uint8_t*>(bar) + 64 : sQ);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & 127, half = tid >> 7;  // two threads per query row
@@ -196,31 +200,35 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             fence_proxy_async_smem();
             tc::tc_fence_before();
             __syncthreads();
-            if (tid == 0) {
-                tc::tc_fence_after();
-                // (Q plane, K plane) pairs: hi.hi, then hi.lo and lo.hi with split operands
-                constexpr int NPROD = SPLIT ? 3 : 1;
-                for (int n0 = 0; n0 < nk16; n0 += 256) {
-                    const int nn = min(256, nk16 - n0);
-                    const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
+            // S = Q K^T for keys [kb, kb + n16) into TMEM columns [cb, cb + n16), issued by thread 0;
+            // every thread waits for it
+            auto scores = [&](int kb, int n16, int cb) {
+                if (tid == 0) {
+                    tc::tc_fence_after();
+                    // (Q plane, K plane) pairs: hi.hi, then hi.lo and lo.hi with split operands
+                    constexpr int NPROD = SPLIT ? 3 : 1;
+                    for (int n0 = 0; n0 < n16; n0 += 256) {
+                        const int nn = min(256, n16 - n0);
+                        const uint32_t idesc = tc::idesc_bf16_f32(128, nn);
 #pragma unroll
-                    for (int pr = 0; pr < NPROD; ++pr) {
-                        const int qp = pr == 2 ? 1 : 0, kp = pr == 1 ? 1 : 0;
-                        const uint64_t dq = desc_kmajor_none(tc::smem_u32(sQ + qp * 128 * DH * 2), 128, (DH / 8) * 128);
-                        const uint64_t dk = desc_kmajor_none(tc::smem_u32(sK + kp * tb), 128, (DH / 8) * 128);
-                        const uint64_t dkn = dk + (uint64_t)(((n0 / 8) * (DH / 8) * 128) >> 4);
+                        for (int pr = 0; pr < NPROD; ++pr) {
+                            const int qp = pr == 2 ? 1 : 0, kp = pr == 1 ? 1 : 0;
+                            const uint64_t dq =
+                                desc_kmajor_none(tc::smem_u32(sQ + qp * 128 * DH * 2), 128, (DH / 8) * 128);
+                            const uint64_t dk = desc_kmajor_none(tc::smem_u32(sK + kp * tb), 128, (DH / 8) * 128);
+                            const uint64_t dkn = dk + (uint64_t)((((kb + n0) / 8) * (DH / 8) * 128) >> 4);
 #pragma unroll
-                        for (int ks = 0; ks < DH / 16; ++ks)
-                            tc::mma_bf16(tmem + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16), idesc,
-                                         (pr | ks) > 0 ? 1u : 0u);
+                            for (int ks = 0; ks < DH / 16; ++ks)
+                                tc::mma_bf16(tmem + cb + n0, dq + (uint64_t)(ks * 16), dkn + (uint64_t)(ks * 16),
+                                             idesc, (pr | ks) > 0 ? 1u : 0u);
+                        }
                     }
+                    tc::mma_commit(bar);
                 }
-                tc::mma_commit(bar);
-            }
-            ok = __syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0;
-            phase ^= 1;
-            tc::tc_fence_after();
-            if (!ok) break;
+                ok = (__syncthreads_and(tc::mbar_wait(bar, phase, status)) != 0) && ok;
+                phase ^= 1;
+                tc::tc_fence_after();
+            };
             // softmax of query position p = q0 + row; this thread takes every other
             // 32-column chunk, starting with chunk `half`
             const int p = q0 + row;
@@ -231,98 +239,137 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             // a warp whose rows all lie past the configuration's last position has nothing to
             // compute: its P rows are zero and its outputs are not stored
             const bool wpad = q0 + (warp & 3) * 32 >= N || q0 + (warp & 3) * 32 + 31 < p0;
-            float mx = -INFINITY;
-            for (int c0 = half * 32; c0 < nk32 && !wpad; c0 += 64) {
-                if (c0 > plim_w) break;  // chunks wholly past the warp's diagonal are invisible
-                uint32_t r[32];
-                tc::tmem_ld32(tmem + lane_base + c0, r);
-                if (c0 + 31 <= plim) {
-                    float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
+            // the row's largest visible score among keys [kb, kend) held at TMEM column cb + k - kb
+            auto max_pass = [&](int cb, int kb, int kend) {
+                float mx = -INFINITY;
+                const int n32 = (kend - kb + 31) & ~31;
+                for (int c0 = half * 32; c0 < n32 && !wpad; c0 += 64) {
+                    const int k0 = kb + c0;
+                    if (k0 > plim_w) break;  // chunks wholly past the warp's diagonal are invisible
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + lane_base + cb + c0, r);
+                    if (k0 + 31 <= plim) {
+                        float m0 = __uint_as_float(r[0]), m1 = __uint_as_float(r[1]);
 #pragma unroll
-                    for (int j = 2; j < 32; j += 2) {
-                        m0 = fmaxf(m0, __uint_as_float(r[j]));
-                        m1 = fmaxf(m1, __uint_as_float(r[j + 1]));
+                        for (int j = 2; j < 32; j += 2) {
+                            m0 = fmaxf(m0, __uint_as_float(r[j]));
+                            m1 = fmaxf(m1, __uint_as_float(r[j + 1]));
+                        }
+                        mx = fmaxf(mx, fmaxf(m0, m1));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (k0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
                     }
-                    mx = fmaxf(mx, fmaxf(m0, m1));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c0 + j <= plim) mx = fmaxf(mx, __uint_as_float(r[j]));
                 }
+                return mx;
+            };
+            // more than 256 keys: two key blocks, [0, 256) and [256, nk), each taking at most
+            // 256 TMEM columns; the maxima of both are found first (block 1's scores, then
+            // block 0's over them), so P needs no rescaling
+            const bool two = nk16 > 256;
+            float mx;
+            if (!two) {
+                scores(0, nk16, 0);
+                if (!ok) break;
+                mx = max_pass(0, 0, nk);
+            } else {
+                scores(256, nk16 - 256, 0);
+                if (!ok) break;
+                const float m1 = max_pass(0, 256, nk);
+                tc::tc_fence_before();
+                __syncthreads();  // block 1's scores are read before block 0's overwrite them
+                scores(0, 256, 0);
+                if (!ok) break;
+                mx = fmaxf(max_pass(0, 0, 256), m1);
             }
             s_red[half][row] = mx;
             __syncthreads();
             mx = fmaxf(s_red[0][row], s_red[1][row]);
             const float mb = mx * sl2;
             float sum = 0.f;
-            // P V in chunks of PCH keys, double-buffered P tiles (pend: MMAs of this tile still reading them)
-            const int nch = (nk16 + PCH - 1) / PCH;
             int pend[2] = {0, 0};
-            for (int jc = 0; jc < nch && ok; ++jc) {
-                const int u = jc & 1;
-                uint8_t* pt = sP + (size_t)u * NP * PCB;
-                if (pend[u]) {  // chunk jc - 2's MMAs read this tile
-                    ok = __syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0;
-                    pph[u] ^= 1;
-                    pend[u] = 0;
-                    tc::tc_fence_after();
-                    if (!ok) break;
-                }
-                const int c0 = jc * PCH + half * 16;  // this thread's 16 keys of the chunk
-                uint32_t pk[8], pl[8];
-                if (wpad || c0 > plim_w || c0 >= nk16) {  // no rows, invisible, or past the MMA's keys: P = 0
+            // P V over keys [kb, kb + n16) whose scores sit at TMEM column cb + k - kb, in chunks of
+            // PCH keys through double-buffered P tiles (pend: MMAs still reading a tile); the
+            // output accumulates in TMEM columns [0, DH) (first: the first chunk overwrites them)
+            auto pv = [&](int cb, int kb, int n16, bool first) {
+                const int nch = (n16 + PCH - 1) / PCH;
+                for (int jc = 0; jc < nch && ok; ++jc) {
+                    const int u = jc & 1;
+                    uint8_t* pt = sP + (size_t)u * NP * PCB;
+                    if (pend[u]) {  // the MMAs of the chunk two before read this tile
+                        ok = __syncthreads_and(tc::mbar_wait(&pbar[u], pph[u], status)) != 0;
+                        pph[u] ^= 1;
+                        pend[u] = 0;
+                        tc::tc_fence_after();
+                        if (!ok) break;
+                    }
+                    const int c0 = jc * PCH + half * 16;  // this thread's 16 keys of the chunk
+                    const int k0 = kb + c0;
+                    uint32_t pk[8], pl[8];
+                    if (wpad || k0 > plim_w || c0 >= n16) {  // no rows, invisible, or past the MMA's keys
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) pk[j] = pl[j] = 0u;
-                } else {
-                    uint32_t r[16];
-                    tmem_ld16(tmem + lane_base + c0, r);
-                    const bool full = c0 + 15 <= plim;
+                        for (int j = 0; j < 8; ++j) pk[j] = pl[j] = 0u;
+                    } else {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + lane_base + cb + c0, r);
+                        const bool full = k0 + 15 <= plim;
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
-                        float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
-                        if (!full) {
-                            e0 = (c0 + j <= plim) ? e0 : 0.f;
-                            e1 = (c0 + j + 1 <= plim) ? e1 : 0.f;
-                        }
-                        sum += e0 + e1;
-                        if (SPLIT) {
-                            split_pack2(e0, e1, pk[j / 2], pl[j / 2]);
-                        } else {
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
-                            pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                        for (int j = 0; j < 16; j += 2) {
+                            float e0 = ex2_approx(fmaf(__uint_as_float(r[j]), sl2, -mb));
+                            float e1 = ex2_approx(fmaf(__uint_as_float(r[j + 1]), sl2, -mb));
+                            if (!full) {
+                                e0 = (k0 + j <= plim) ? e0 : 0.f;
+                                e1 = (k0 + j + 1 <= plim) ? e1 : 0.f;
+                            }
+                            sum += e0 + e1;
+                            if (SPLIT) {
+                                split_pack2(e0, e1, pk[j / 2], pl[j / 2]);
+                            } else {
+                                __nv_bfloat162 b2 = __floats2bfloat162_rn(e0, e1);
+                                pk[j / 2] = *reinterpret_cast<uint32_t*>(&b2);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int j8 = 0; j8 < 2; ++j8) {
-                    const uint32_t off = core_off(row, half * 16 + j8 * 8, PCH);
-                    *reinterpret_cast<uint4*>(pt + off) = make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
-                    if (SPLIT)
-                        *reinterpret_cast<uint4*>(pt + PCB + off) =
-                            make_uint4(pl[4 * j8], pl[4 * j8 + 1], pl[4 * j8 + 2], pl[4 * j8 + 3]);
+                    for (int j8 = 0; j8 < 2; ++j8) {
+                        const uint32_t off = core_off(row, half * 16 + j8 * 8, PCH);
+                        *reinterpret_cast<uint4*>(pt + off) =
+                            make_uint4(pk[4 * j8], pk[4 * j8 + 1], pk[4 * j8 + 2], pk[4 * j8 + 3]);
+                        if (SPLIT)
+                            *reinterpret_cast<uint4*>(pt + PCB + off) =
+                                make_uint4(pl[4 * j8], pl[4 * j8 + 1], pl[4 * j8 + 2], pl[4 * j8 + 3]);
+                    }
+                    tc::fence_proxy_async_smem();
+                    tc::tc_fence_before();
+                    __syncthreads();
+                    if (tid == 0) {
+                        tc::tc_fence_after();
+                        const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
+                        const int kk = min(PCH, n16 - jc * PCH);  // keys of this chunk the MMA covers
+                        constexpr int NPROD = SPLIT ? 3 : 1;     // (P plane, V plane): hi.hi, hi.lo, lo.hi
+#pragma unroll
+                        for (int pr = 0; pr < NPROD; ++pr) {
+                            const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
+                            const uint64_t dp = desc_kmajor_none(tc::smem_u32(pt + pp * PCB), 128, (PCH / 8) * 128);
+                            const uint64_t dv =
+                                desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128) +
+                                (uint64_t)((((kb + jc * PCH) / 8) * 128) >> 4);
+                            for (int ks = 0; ks < kk / 16; ++ks)
+                                tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
+                                             (!first || (jc | pr | ks) > 0) ? 1u : 0u);
+                        }
+                        tc::mma_commit(&pbar[u]);
+                    }
+                    pend[u] = 1;
                 }
-                tc::fence_proxy_async_smem();
+            };
+            pv(0, 0, two ? 256 : nk16, true);
+            if (two && ok) {
                 tc::tc_fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::tc_fence_after();
-                    const uint32_t idesc = tc::idesc_bf16_f32(128, DH);
-                    const int kk = min(PCH, nk16 - jc * PCH);  // keys of this chunk the MMA covers
-                    constexpr int NPROD = SPLIT ? 3 : 1;     // (P plane, V plane): hi.hi, hi.lo, lo.hi
-#pragma unroll
-                    for (int pr = 0; pr < NPROD; ++pr) {
-                        const int pp = pr == 2 ? 1 : 0, vp = pr == 1 ? 1 : 0;
-                        const uint64_t dp = desc_kmajor_none(tc::smem_u32(pt + pp * PCB), 128, (PCH / 8) * 128);
-                        const uint64_t dv = desc_kmajor_none(tc::smem_u32(sVt + vp * tb), 128, (Npad / 8) * 128) +
-                                            (uint64_t)(((jc * PCH / 8) * 128) >> 4);
-                        for (int ks = 0; ks < kk / 16; ++ks)
-                            tc::mma_bf16(tmem, dp + (uint64_t)(ks * 16), dv + (uint64_t)(ks * 16), idesc,
-                                         (jc | pr | ks) > 0 ? 1u : 0u);
-                    }
-                    tc::mma_commit(&pbar[u]);
-                }
-                pend[u] = 1;
+                __syncthreads();  // every read of block 0's scores is done
+                scores(256, nk16 - 256, 32);  // block 1 again, beside the output columns
+                if (ok) pv(32, 256, nk16 - 256, false);
             }
             // the last chunk's MMAs (and every earlier one) have completed
             for (int u = 0; u < 2; ++u)
@@ -378,6 +425,7 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const int Npad = (ch.N + 31) & ~31;
     uint32_t cols = 32;
     while ((int)cols < Npad) cols <<= 1;
+    if (cols > 256) cols = 256;  // more than 256 keys: two key blocks of at most 256 columns
     const size_t smem = attn_smem_bytes(Npad, DH, split);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     // the TMEM columns of all CTAs resident on one SM must fit in its 512: cap the

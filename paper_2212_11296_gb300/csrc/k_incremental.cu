@@ -200,7 +200,7 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
             if (ov1 < v1 || (ov1 == v1 && oi1 < i1)) { v2 = fminf(v1, ov2); v1 = ov1; i1 = oi1; }
             else v2 = fminf(v2, ov1);
         }
-        const int c = i1;
+        const int c = i1 < K ? i1 : 0;  // no finite distance: codeword 0
         const float eta = CERT_ETA_REL * (sOsq[r] + sCnMax);
         if (lane == 0) {
             code[row] = c;
@@ -316,7 +316,7 @@ k_base_cert_heads(Chunk ch, const float* __restrict__ O, const float* __restrict
                 else v2 = fminf(v2, ov1);
             }
             __syncwarp();
-            const int c = i1;
+            const int c = i1 < K ? i1 : 0;  // no finite distance: codeword 0
             const float eta = CERT_ETA_REL * (osq + cmax);
             const float* wdh = wd + (size_t)h * K * K + (size_t)c * K;
             float rmin = INFINITY;

@@ -140,7 +140,8 @@ k_vq_argmin(const float* __restrict__ O, int ldo, const int* __restrict__ counte
                 const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
                 if (m < R) {
                     const int r = act_rows ? act_rows[m] : m;
-                    code[r] = (accumulate ? code[r] : 0) | (best[i].i1 << shift);
+                    const int c = best[i].i1 < K ? best[i].i1 : 0;  // no finite distance: codeword 0
+                    code[r] = (accumulate ? code[r] : 0) | (c << shift);
                     const float l1 = best[i].v1 + osq[i], l2 = best[i].v2 + osq[i];
                     if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
                 }

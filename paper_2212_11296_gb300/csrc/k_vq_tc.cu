@@ -271,6 +271,10 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             tc::mbar_arrive(&acce[a]);
             const int m = t * VT_BM + row;
             if (m < R) {
+                if (best.i1 >= K) {  // no finite distance: codeword 0, and the status says so
+                    best.i1 = 0;
+                    atomicOr(status, VQNQS_DEV_NONFINITE);
+                }
                 code[act_rows[m]] = best.i1;
                 const float l1 = best.v1 + osq, l2 = best.v2 + osq;
                 if (K > 1 && (l2 - l1) < NEAR_TIE_REL * fmaxf(l1, 1e-30f)) ++ties;
