@@ -84,7 +84,8 @@ __host__ __device__ constexpr size_t attn_smem_bytes(int Npad, int DH, bool spli
            (Npad > 256 ? 1024 : 0);
 }
 
-template <int DH, bool SPLIT>
+// TWO: the item may hold more than 256 keys (two key blocks; Npad > 256)
+template <int DH, bool SPLIT, bool TWO>
 __global__ void __launch_bounds__(AT_THREADS, 2)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
                float* __restrict__ O, int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
@@ -107,7 +108,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     uint64_t* pbar = bar + 1;                      // [2]: MMAs reading P tile 0 / 1
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(pbar + 2);
     // [2][128] row exchange: over Q once Q has been read (at most 256 keys), else beside the barriers
-    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(Npad > 256 ? reinterpret_cast<uint8_t*>(bar) + 64 : sQ);
+    float (*s_red)[128] = reinterpret_cast<float (*)[128]>(TWO ? reinterpret_cast<uint8_t*>(bar) + 64 : sQ);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row = tid & 127, half = tid >> 7;  // two threads per query row
@@ -267,7 +268,7 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
             // more than 256 keys: two key blocks, [0, 256) and [256, nk), each taking at most
             // 256 TMEM columns; the maxima of both are found first (block 1's scores, then
             // block 0's over them), so P needs no rescaling
-            const bool two = nk16 > 256;
+            const bool two = TWO && nk16 > 256;
             float mx;
             if (!two) {
                 scores(0, nk16, 0);
@@ -434,22 +435,23 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
     const size_t max_ctas = 512 / cols;
     size_t smem_req = smem;
     if (smem_sm / smem_req > max_ctas) smem_req = smem_sm / (max_ctas + 1) + 1024;
-    static size_t granted[4] = {};  // attribute set once per instantiation and size, outside captures
-#define VQ_ATC(D, SP, SLOT)                                                                                    \
-    {                                                                                                          \
-        if (smem_req > granted[SLOT]) {                                                                        \
-            cudaFuncSetAttribute(k_attention_tc<D, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
-                                 (int)smem_req);                                                               \
-            granted[SLOT] = smem_req;                                                                          \
-        }                                                                                                      \
-        k_attention_tc<D, SP><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, lo_off, O, prefix_reuse, Npad,    \
-                                                                  cols, status, cfg_list, n_list, n_list_dev, \
-                                                                  stats);                                     \
+    static size_t granted[6] = {};  // attribute set once per instantiation and size, outside captures
+#define VQ_ATC(D, SP, TW, SLOT)                                                                                 \
+    {                                                                                                           \
+        if (smem_req > granted[SLOT]) {                                                                         \
+            cudaFuncSetAttribute(k_attention_tc<D, SP, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                 (int)smem_req);                                                                \
+            granted[SLOT] = smem_req;                                                                           \
+        }                                                                                                       \
+        k_attention_tc<D, SP, TW><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, lo_off, O, prefix_reuse,    \
+                                                                      Npad, cols, status, cfg_list, n_list,     \
+                                                                      n_list_dev, stats);                      \
     }
+    const bool two = Npad > 256;  // split operands take at most 256 positions (attention_tc_supported)
     if (DH == 16) {
-        if (split) VQ_ATC(16, true, 2) else VQ_ATC(16, false, 0)
+        if (split) VQ_ATC(16, true, false, 2) else if (two) VQ_ATC(16, false, true, 4) else VQ_ATC(16, false, false, 0)
     } else if (DH == 32) {
-        if (split) VQ_ATC(32, true, 3) else VQ_ATC(32, false, 1)
+        if (split) VQ_ATC(32, true, false, 3) else if (two) VQ_ATC(32, false, true, 5) else VQ_ATC(32, false, false, 1)
     } else {
         return cudaErrorInvalidValue;
     }
