@@ -463,7 +463,7 @@ int vqnqs_autotune_chunk(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int fl
  * VQNQS_INCREMENTAL; the workspace as for vqnqs_local_energy with these flags):
  * times the local energies of the B DEVICE samples (once untimed, twice timed per
  * setting) for the patch kernel's work items per CTA in {2, 4, 8}, keeps the
- * fastest, then for the changed-row kernel's items per SM in {1, 2, 4}, and keeps
+ * fastest, then for the changed-row kernel's items per SM in {1, 2, 4, 8, 16}, and keeps
  * both for this context (defaults 4 and 2).  Results do not depend on the setting
  * (each row is computed from its own inputs); only the assignment of work to CTAs
  * changes.  Writes the average milliseconds per evaluation to out (-1: not run).
@@ -471,7 +471,7 @@ int vqnqs_autotune_chunk(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int fl
 typedef struct vqnqs_inc_tuning {
     int patch_items, rows_slices;
     float patch_ms[3];  /* items per CTA 2, 4, 8 */
-    float rows_ms[3];   /* items per SM 1, 2, 4 */
+    float rows_ms[5];   /* items per SM 1, 2, 4, 8, 16 */
 } vqnqs_inc_tuning;
 int vqnqs_autotune_incremental(vqnqs_ctx* ctx, int B, const uint8_t* dev_spins, int flags, void* dev_ws,
                                size_t ws_bytes, vqnqs_inc_tuning* out, void* stream);

@@ -59,7 +59,7 @@ MAX_STAGES = 32
 
 class IncTuning(ctypes.Structure):
     _fields_ = [("patch_items", ctypes.c_int), ("rows_slices", ctypes.c_int), ("patch_ms", ctypes.c_float * 3),
-                ("rows_ms", ctypes.c_float * 3)]
+                ("rows_ms", ctypes.c_float * 5)]
 
 
 class Tuning(ctypes.Structure):

@@ -301,7 +301,7 @@ class VQNQS:
                     "vqnqs_autotune_incremental")
         return {"patch_items": t.patch_items, "rows_slices": t.rows_slices,
                 "patch_ms": {n: float(t.patch_ms[i]) for i, n in enumerate((2, 4, 8))},
-                "rows_ms": {n: float(t.rows_ms[i]) for i, n in enumerate((1, 2, 4))}}
+                "rows_ms": {n: float(t.rows_ms[i]) for i, n in enumerate((1, 2, 4, 8, 16))}}
 
     def stats(self) -> dict:
         s = _lib.Stats()

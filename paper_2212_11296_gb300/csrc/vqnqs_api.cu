@@ -1657,7 +1657,7 @@ int vqnqs_autotune_incremental(vqnqs_ctx* ctx, int B, const uint8_t* spins, int 
     if (rc0 != VQNQS_OK) return rc0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float* e_loc = ctx->lp_scratch;
-    static const int kPatch[3] = {2, 4, 8}, kRows[3] = {1, 2, 4};
+    static const int kPatch[3] = {2, 4, 8}, kRows[5] = {1, 2, 4, 8, 16};
     cudaEvent_t e0, e1;
     VQ_CK(cudaEventCreate(&e0));
     VQ_CK(cudaEventCreate(&e1));
@@ -1691,7 +1691,7 @@ int vqnqs_autotune_incremental(vqnqs_ctx* ctx, int B, const uint8_t* spins, int 
     ctx->patch_items = bp;
     best = 1e30f;
     int br = keep_r;
-    for (int i = 0; i < 3 && rc == VQNQS_OK; ++i) {
+    for (int i = 0; i < 5 && rc == VQNQS_OK; ++i) {
         ctx->rows_slices = kRows[i];
         out->rows_ms[i] = -1.f;
         time_it(&out->rows_ms[i]);

@@ -173,7 +173,7 @@ def test_incremental_work_split_tuner_keeps_results(ctx16):
     before = m.local_energy(sub, flags)
     t = m.autotune_incremental(sub, flags)
     print(t)
-    assert t["patch_items"] in (2, 4, 8) and t["rows_slices"] in (1, 2, 4)
+    assert t["patch_items"] in (2, 4, 8) and t["rows_slices"] in (1, 2, 4, 8, 16)
     assert all(v > 0 for v in t["patch_ms"].values()) and all(v > 0 for v in t["rows_ms"].values())
     assert torch.equal(m.local_energy(sub, flags), before)
     assert m.stats()["device_status"] == 0

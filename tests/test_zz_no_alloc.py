@@ -17,15 +17,21 @@ import synthetic_inputs as si
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(lib, uid, code):
+def _outputs(uid):
     R = uid.numel()
-    dev = uid.device
-    out = [torch.empty(R, dtype=torch.int32, device=dev) for _ in range(3)] + [torch.empty(1, dtype=torch.int32,
-                                                                                          device=dev)]
+    return [torch.empty(R, dtype=torch.int32, device=uid.device) for _ in range(3)] + [
+        torch.empty(1, dtype=torch.int32, device=uid.device)]
+
+
+def _call(lib, uid, code, out):
     p = lambda t: ctypes.c_void_p(t.data_ptr())
-    rc = lib.vqnqs_compress_rows_noalloc(R, p(uid), p(code), p(out[0]), p(out[1]), p(out[2]), p(out[3]),
-                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert rc == 0
+    return lib.vqnqs_compress_rows_noalloc(uid.numel(), p(uid), p(code), p(out[0]), p(out[1]), p(out[2]),
+                                           p(out[3]), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def _noalloc(lib, uid, code):
+    out = _outputs(uid)
+    assert _call(lib, uid, code, out) == 0
     return out
 
 
@@ -55,6 +61,51 @@ def test_noalloc_matches_compress_rows_twice():
         torch.cuda.synchronize()
         _same_result(ref, first, uid, code)
         _same_result(ref, second, uid, code)
+
+
+def test_noalloc_allocates_nothing_and_replays_in_a_graph():
+    """After a first eager call (which looks up the array's address), a call
+    takes no device memory, neither from PyTorch's allocator nor from the
+    driver, and a call captured into a CUDA graph gives the same result on
+    replay, also on a second input copied into the captured buffers."""
+    from paper_2212_11296_gb300 import VQNQS
+    from paper_2212_11296_gb300.api import lib
+    m = VQNQS(4, True, 1.0, 1, 64, 2, 4, si.make_weights(16, 1, 64, 4))
+    rng = np.random.default_rng(12)
+    R = 150000
+    inputs = []
+    for n_uid, n_code in [(3000, 256), (50000, 40)]:
+        uid = torch.as_tensor(rng.integers(0, n_uid, R).astype(np.int32)).cuda()
+        code = torch.as_tensor(rng.integers(0, n_code, R).astype(np.int32)).cuda()
+        inputs.append((uid, code, m.compress_rows(uid, code)))
+    uid, code = inputs[0][0].clone(), inputs[0][1].clone()
+    out = _outputs(uid)
+    assert _call(lib(), uid, code, out) == 0  # first call: address lookup, kernels loaded
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _call(lib(), uid, code, out) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] >= free0
+    _same_result(inputs[0][2], out, uid, code)
+
+    for t in out:
+        t.fill_(-7)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    rcs = []
+    with torch.cuda.graph(g):
+        rcs.append(_call(lib(), uid, code, out))
+    assert rcs == [0]
+    for u_in, c_in, ref in inputs:
+        uid.copy_(u_in)
+        code.copy_(c_in)
+        for t in out:
+            t.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        _same_result(ref, out, u_in, c_in)
 
 
 def test_noalloc_rejects_too_many_rows():
