@@ -21,6 +21,9 @@
 //      even with split operands, so two CTAs share an SM.
 // With prefix reuse, query tiles start at the configuration's first changed
 // position: rows before it are neither computed nor stored.
+// Items go to CTAs round-robin, or, given a work counter (zero at launch), each CTA
+// takes the next item from it when it finishes one: items of very different sizes
+// (configurations with different first changed positions) then leave no long tail.
 // Waits on the MMA barrier are bounded (VQNQS_DEV_TIMEOUT on expiry).
 //
 // Split operands (SPLIT): Q, K and V arrive as two BF16 planes, x = hi + lo
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(AT_THREADS, 2)
 k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __restrict__ qkv, size_t lo_off,
                float* __restrict__ O, int prefix_reuse, int Npad, uint32_t tmem_cols, int* __restrict__ status,
                const int* __restrict__ cfg_list, int n_list, const int* __restrict__ n_list_dev,
-               float2* __restrict__ stats) {
+               float2* __restrict__ stats, int* __restrict__ work) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
     const int d = ch.d, H = ch.heads;
@@ -130,8 +133,17 @@ k_attention_tc(Chunk ch, const int* __restrict__ uid, const __nv_bfloat16* __res
     const float sl2 = 1.4426950408889634f * rsqrtf((float)DH);  // log2(e) / sqrt(dh)
     const int C = cfg_list ? (n_list_dev ? *n_list_dev : n_list) : ch.counters[CNT_C];
     const int ld = 3 * d;
+    __shared__ int s_next;
+    // the next item: from the work counter (every thread has read the previous one: each
+    // item ends with a barrier) or round-robin
+    auto next_item = [&](int prev) {
+        if (!work) return prev < 0 ? (int)blockIdx.x : prev + (int)gridDim.x;
+        if (tid == 0) s_next = atomicAdd(work, 1);
+        __syncthreads();
+        return s_next;
+    };
 
-    for (int item = blockIdx.x; item < C * H && ok; item += gridDim.x) {
+    for (int item = next_item(-1); item < C * H && ok; item = next_item(item)) {
         const int ci = item / H, h = item - ci * H;
         const int c = cfg_list ? cfg_list[ci] : ci;
         const int N = cfg_N(ch, c);
@@ -419,7 +431,7 @@ bool attention_tc_supported(int N, int dh, bool split) {
 
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list, int n_list,
-                                float2* stats, const int* n_list_dev, size_t lo_off) {
+                                float2* stats, const int* n_list_dev, size_t lo_off, int* work) {
     const int DH = ch.d / ch.heads;
     const bool split = lo_off != 0;
     if (!attention_tc_supported(ch.N, DH, split)) return cudaErrorInvalidValue;
@@ -445,7 +457,7 @@ cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bflo
         }                                                                                                       \
         k_attention_tc<D, SP, TW><<<grid, AT_THREADS, smem_req, st>>>(ch, uid, qkv, lo_off, O, prefix_reuse,    \
                                                                       Npad, cols, status, cfg_list, n_list,     \
-                                                                      n_list_dev, stats);                      \
+                                                                      n_list_dev, stats, work);                \
     }
     const bool two = Npad > 256;  // split operands take at most 256 positions (attention_tc_supported)
     if (DH == 16) {

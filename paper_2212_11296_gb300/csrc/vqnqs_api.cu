@@ -489,8 +489,8 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
                                                                qkv_lo, ctx->rows_slices));
                 VQ_STAGE(S_RECOMP_WHOLE, 1,
                          launch_attention_tc(ch, uid_cur, qkv16, O, 1, ctx->status, st,
-                                             grid_for(ctx, P.Cmax * ctx->heads, 1, 4), list_simt, 0, nullptr,
-                                             counters + CNT_SCL, qkv_lo));
+                                             grid_for(ctx, P.Cmax * ctx->heads, 1, 2), list_simt, 0, nullptr,
+                                             counters + CNT_SCL, qkv_lo, counters + CNT_SCW));
             } else if (bf16) {
                 VQ_STAGE(S_PATCH, 1, launch_inc_patch(ch, uid_cur, qkv16, O, bstat, cert, w.codebook, w.wd, code,
                                                       vq_rows, act_off, rc_rows, rc_cnt, list_tc, list_simt, dpos,

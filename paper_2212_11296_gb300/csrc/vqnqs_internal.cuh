@@ -22,8 +22,8 @@ enum {
     CNT_V = 3,      // incremental path: rows of the current layer listed for the codeword search
     CNT_TCL = 4,    //   connected configurations patched on the tensor cores (list length)
     CNT_SCL = 5,    //   connected configurations patched on the CUDA cores (list length)
-    CNT_TCW = 6,    //   work counters of the two patch kernels (next list entry)
-    CNT_SCW = 7,
+    CNT_TCW = 6,    //   work counters of the two patch kernels (next list entry); on the
+    CNT_SCW = 7,    //   tensor-core path CNT_SCW feeds the attention of the whole recomputes
     CNT_U0 = 8,     // CNT_U0 + l: unique rows feeding layer l (l = 0..layers)
     CNT_EX = 8 + VQNQS_MAX_LAYERS + 2,  // split operands: patched rows listed for the exact correction
     CNT_CW = CNT_EX + 1,                // two-word codes: distinct (hi, lo) code pairs of the layer
@@ -245,7 +245,7 @@ bool attention_tc_supported(int N, int dh, bool split = false);
 cudaError_t launch_attention_tc(const Chunk& ch, const int* uid, const __nv_bfloat16* qkv, float* O, int prefix_reuse,
                                 int* status, cudaStream_t st, int grid, const int* cfg_list = nullptr,
                                 int n_list = 0, float2* stats = nullptr, const int* n_list_dev = nullptr,
-                                size_t lo_off = 0);
+                                size_t lo_off = 0, int* work = nullptr);
 
 // BF16 tensor-core GEMM (k_gemm_tc.cu): C[M,N] = A[M,K] @ Bt[N,K]^T + bias, M = counters[u_slot]
 // epi: 0 BF16 out, 1 BF16 out of GELU, 2 FP32 out + R, 3 FP32 out
