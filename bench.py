@@ -71,7 +71,8 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
     per unique row.  Pairs and rows are counted by the library (rows before a
     configuration's first exchanged site are not computed).  Incremental path:
     the attention stage covers the samples' own rows only; the certificate is a
-    2 K d distance pass per sample row; a patch costs 8 d per (row, changed
+    2 K d distance pass per sample row (on the BF16 path the tensor-core search's
+    distances, rated like the argmin); a patch costs 8 d per (row, changed
     key) pair (two scores and two value updates per head); a recomputed row 4 d
     per query-key pair, the configurations recomputed whole likewise (their rows
     from the first changed position).  On the BF16 path the patch and the recompute run these
@@ -90,7 +91,7 @@ def stage_flops(stage: str, st: dict, w: dict, bf16: bool, inc: bool = False) ->
             return st["samples"] * Ly * N * (N + 1) / 2 * 4.0 * d, tc
         return st["attn_pairs"] * Ly * 4.0 * d, tc
     if stage == "inc_certificate":
-        return st["inc_base_rows"] * 2.0 * K * d, "alu"
+        return st["inc_base_rows"] * 2.0 * K * d, tc
     if stage == "inc_patch":  # its scores and value sums run on the tensor cores on the BF16 path
         return st["inc_patch_pairs"] * 8.0 * d, tc
     if stage == "inc_recompute":

@@ -82,6 +82,71 @@ __device__ int block_compact(int lo, int hi, Pred pred, int* out, int cap, int* 
 
 }  // namespace
 
+// One warp, one sample row: the nearest codeword (lowest index on ties; codeword 0 when no
+// distance is finite) from the row's distances dist[0..K) to every codeword, the row's
+// near-tie count (added to `ties` by lane 0), and its certificate: the CERT_T smallest radii
+// rho_j = (g_j - eta) / (2 ||W_j - W_c||), g_j = dist[j] - dist[c], ascending (lowest index
+// first on equal radii) with j and g_j, then the next radius.  rho: K floats of the warp's
+// shared scratch.  Every lane returns the codeword.
+__device__ int cert_from_dist(const float* dist, float* rho, float eta, int K, const float* __restrict__ wd,
+                              CertRow* __restrict__ cr, int& ties) {
+    const int lane = threadIdx.x & 31;
+    float v1 = INFINITY, v2 = INFINITY;
+    int i1 = 0x7fffffff;
+    for (int j = lane; j < K; j += 32) {
+        const float v = dist[j];
+        if (v < v1 || (v == v1 && j < i1)) { v2 = v1; v1 = v; i1 = j; }
+        else if (v < v2) v2 = v;
+    }
+    for (int o = 16; o; o >>= 1) {
+        const float ov1 = __shfl_xor_sync(0xffffffffu, v1, o), ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
+        const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
+        if (ov1 < v1 || (ov1 == v1 && oi1 < i1)) { v2 = fminf(v1, ov2); v1 = ov1; i1 = oi1; }
+        else v2 = fminf(v2, ov1);
+    }
+    const int c = i1 < K ? i1 : 0;  // no finite distance: codeword 0
+    if (lane == 0 && K > 1 && (v2 - v1) < NEAR_TIE_REL * fmaxf(v1, 1e-30f)) ++ties;
+    for (int j = lane; j < K; j += 32) {
+        const float w = wd[(size_t)c * K + j];
+        rho[j] = (j == c || w <= 0.f) ? INFINITY : (dist[j] - v1 - eta) / (2.f * w);
+    }
+    __syncwarp();
+    // the CERT_T + 1 smallest radii, ascending (lowest index first on equal radii)
+    int n = 0;
+    for (int t = 0; t <= CERT_T; ++t) {
+        float bv = INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < K; j += 32) {
+            const float v = rho[j];
+            if (v < bv || (v == bv && j < bj)) { bv = v; bj = j; }
+        }
+        for (int o = 16; o; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
+        }
+        if (t == CERT_T || bv == INFINITY) {
+            if (lane == 0) cr->next = bv;
+            break;
+        }
+        if (lane == 0) {
+            cr->j[t] = bj;
+            cr->rho[t] = bv;
+            cr->gap[t] = dist[bj] - v1;
+        }
+        if (lane == (bj & 31)) rho[bj] = INFINITY;
+        ++n;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        cr->n = n;
+        cr->eta = eta;
+        cr->code = c;
+    }
+    __syncwarp();
+    return c;
+}
+
 // ---- s's rows: nearest codeword and its certificate ---------------------------------
 // One CTA of 256 threads per RB rows of the chunk's samples (row r = b * N + p),
 // thread j computing codeword j's distances to the RB rows.
@@ -180,70 +245,13 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
         }
     }
     __syncthreads();
-    float* rho = sRho + warp * K;
     int ties = 0;
     for (int r = warp; r < RB; r += 8) {
         const int row = sRow[r];
         if (row < 0) continue;  // warp-uniform
-        const float* dist = sDist + r * K;
-        // nearest (lowest index on ties) and second nearest distance
-        float v1 = INFINITY, v2 = INFINITY;
-        int i1 = 0x7fffffff;
-        for (int j = lane; j < K; j += 32) {
-            const float v = dist[j];
-            if (v < v1 || (v == v1 && j < i1)) { v2 = v1; v1 = v; i1 = j; }
-            else if (v < v2) v2 = v;
-        }
-        for (int o = 16; o; o >>= 1) {
-            const float ov1 = __shfl_xor_sync(0xffffffffu, v1, o), ov2 = __shfl_xor_sync(0xffffffffu, v2, o);
-            const int oi1 = __shfl_xor_sync(0xffffffffu, i1, o);
-            if (ov1 < v1 || (ov1 == v1 && oi1 < i1)) { v2 = fminf(v1, ov2); v1 = ov1; i1 = oi1; }
-            else v2 = fminf(v2, ov1);
-        }
-        const int c = i1 < K ? i1 : 0;  // no finite distance: codeword 0
-        const float eta = CERT_ETA_REL * (sOsq[r] + sCnMax);
-        if (lane == 0) {
-            code[row] = c;
-            if (K > 1 && (v2 - v1) < NEAR_TIE_REL * fmaxf(v1, 1e-30f)) ++ties;
-        }
-        for (int j = lane; j < K; j += 32) {
-            const float w = wd[(size_t)c * K + j];
-            rho[j] = (j == c || w <= 0.f) ? INFINITY : (dist[j] - v1 - eta) / (2.f * w);
-        }
-        __syncwarp();
-        // the CERT_T + 1 smallest radii, ascending (lowest index first on equal radii)
-        CertRow* cr = cert + (r0 + r);
-        int n = 0;
-        for (int t = 0; t <= CERT_T; ++t) {
-            float bv = INFINITY;
-            int bj = 0x7fffffff;
-            for (int j = lane; j < K; j += 32) {
-                const float v = rho[j];
-                if (v < bv || (v == bv && j < bj)) { bv = v; bj = j; }
-            }
-            for (int o = 16; o; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (ov < bv || (ov == bv && oj < bj)) { bv = ov; bj = oj; }
-            }
-            if (t == CERT_T || bv == INFINITY) {
-                if (lane == 0) cr->next = bv;
-                break;
-            }
-            if (lane == 0) {
-                cr->j[t] = bj;
-                cr->rho[t] = bv;
-                cr->gap[t] = dist[bj] - v1;
-            }
-            if (lane == (bj & 31)) rho[bj] = INFINITY;
-            ++n;
-            __syncwarp();
-        }
-        if (lane == 0) {
-            cr->n = n;
-            cr->eta = eta;
-            cr->code = c;
-        }
+        const int c = cert_from_dist(sDist + r * K, sRho + warp * K, CERT_ETA_REL * (sOsq[r] + sCnMax), K, wd,
+                                     cert + (r0 + r), ties);
+        if (lane == 0) code[row] = c;
         __syncwarp();
     }
     if (ties) atomicAdd(&sTies, ties);
@@ -254,6 +262,74 @@ k_base_cert(Chunk ch, const float* __restrict__ O, const float* __restrict__ cod
         for (int r = 0; r < RB; ++r) n += sRow[r] >= 0;
         atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_BASE]), (unsigned long long)n);
     }
+}
+
+// ---- s's rows from the tensor-core distances (BF16 path) ------------------------------
+// The distances come from the split-TF32 search of k_vq_tc (distance mode) over the
+// list below, so the samples' codes are the ones that search gives; the certificate is
+// taken from them as above.  Their error (about 2^-21 of ||o|| ||W||) is far inside eta.
+
+// The chunk's sample rows, in the order of the certificate rows: entry b N + p is the
+// row of position p of sample b (positions past the sample's length take its first row,
+// whose distances are computed and ignored); list[0] holds the count S N.
+__global__ void k_base_rows(Chunk ch, int* __restrict__ list) {
+    const int total = ch.S * ch.N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int b = i / ch.N, p = i - b * ch.N;
+        list[1 + i] = ch.cfg_row[ch.cfg_off[b]] + (p < sample_N(ch, b) ? p : 0);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) list[0] = total;
+}
+
+// One warp per sample row r = b N + p: its distances dist[r][0..K) and ||o||^2 = osq[r]
+// staged in shared memory, then code, near ties and certificate by cert_from_dist.
+__global__ void __launch_bounds__(256)
+k_base_cert_dist(Chunk ch, const float* __restrict__ dist, const float* __restrict__ osq,
+                 const float* __restrict__ cnorm, const float* __restrict__ wd, int K, int* __restrict__ code,
+                 CertRow* __restrict__ cert, long long* __restrict__ near_ties, int* __restrict__ counters,
+                 int* __restrict__ rc_cnt, long long* __restrict__ stats) {
+    extern __shared__ __align__(16) float smem_c[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float* sD = smem_c + (size_t)warp * 2 * K;  // this warp's row: distances, then radii
+    float* sRho = sD + K;
+    __shared__ float sCnMax;
+    __shared__ int sTies, sRows;
+    if (blockIdx.x == 0 && tid == 0) {  // the lists the classify and patch kernels fill next
+        counters[CNT_V] = 0;
+        counters[CNT_TCL] = counters[CNT_SCL] = counters[CNT_TCW] = counters[CNT_SCW] = 0;
+        counters[CNT_EX] = 0;
+    }
+    if (blockIdx.x == 0)
+        for (int b = tid; b < 2 * ch.S; b += blockDim.x) rc_cnt[b] = 0;  // head and tail counts per sample
+    if (tid == 0) { sTies = 0; sRows = 0; sCnMax = 0.f; }
+    __syncthreads();
+    {
+        float mx = 0.f;
+        for (int j = tid; j < K; j += blockDim.x) mx = fmaxf(mx, cnorm[j]);
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(reinterpret_cast<int*>(&sCnMax), __float_as_int(mx));  // non-negative floats
+    }
+    __syncthreads();
+    const int N = ch.N, total = ch.S * N;
+    int ties = 0, rows = 0;
+    for (int r = blockIdx.x * 8 + warp; r < total; r += gridDim.x * 8) {
+        const int b = r / N, p = r - b * N;
+        if (p >= sample_N(ch, b)) continue;  // warp-uniform
+        const float* dg = dist + (size_t)r * K;
+        for (int j = 4 * lane; j < K; j += 128)  // K is a multiple of 16
+            *reinterpret_cast<float4*>(sD + j) = *reinterpret_cast<const float4*>(dg + j);
+        __syncwarp();
+        const int c = cert_from_dist(sD, sRho, CERT_ETA_REL * (osq[r] + sCnMax), K, wd, cert + r, ties);
+        if (lane == 0) code[ch.cfg_row[ch.cfg_off[b]] + p] = c;
+        ++rows;
+        __syncwarp();
+    }
+    if (lane == 0 && ties) atomicAdd(&sTies, ties);
+    if (lane == 0 && rows) atomicAdd(&sRows, rows);
+    __syncthreads();
+    if (tid == 0 && sTies) atomicAdd(reinterpret_cast<unsigned long long*>(near_ties), (unsigned long long)sTies);
+    if (tid == 0 && sRows)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&stats[ST_INC_BASE]), (unsigned long long)sRows);
 }
 
 // ---- s's rows with H > 1 quantizer heads (Eq. vq per segment) ---------------------------
@@ -1662,6 +1738,31 @@ cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codeb
     const int blocks = (ch.S * ch.N + CERT_RB - 1) / CERT_RB;
     k_base_cert<CERT_RB><<<blocks, 256, smem, st>>>(ch, O, codebook, cnorm, wd, K, d, code, cert, stats + ST_NEAR_TIES,
                                            counters, rc_cnt, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_base_cert_tc(const Chunk& ch, const float* O, const CUtensorMap& tm_hi, const CUtensorMap& tm_lo,
+                                const float* cnorm, const float* wd, int K, int d, int* code, CertRow* cert,
+                                long long* stats, int* counters, int* rc_cnt, int* list, float* dist, float* osq,
+                                int* status, cudaStream_t st, int num_sms) {
+    const int total = ch.S * ch.N;
+    const size_t smem = (size_t)8 * 2 * K * sizeof(float);
+    if (K % 16 || smem > 227 * 1024) return cudaErrorInvalidValue;
+    static size_t granted = 0;
+    if (smem > granted && smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_base_cert_dist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        granted = smem;
+    }
+    int g = (total + 255) / 256;
+    if (g > 4 * num_sms) g = 4 * num_sms;
+    k_base_rows<<<g < 1 ? 1 : g, 256, 0, st>>>(ch, list);
+    cudaError_t e = launch_vq_tc(tm_hi, tm_lo, O, list, list + 1, cnorm, K, d, code, nullptr, status, st, num_sms,
+                                 total, 0, dist, osq);
+    if (e != cudaSuccess) return e;
+    int blocks = (total + 7) / 8;
+    if (blocks > 8 * num_sms) blocks = 8 * num_sms;
+    k_base_cert_dist<<<blocks < 1 ? 1 : blocks, 256, smem, st>>>(ch, dist, osq, cnorm, wd, K, code, cert,
+                                                                 stats + ST_NEAR_TIES, counters, rc_cnt, stats);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,10 @@
 //   warp 9     one thread: TMA of the codebook hi/lo chunks (precomputed per
 //              layer), running a ring slot ahead of the MMAs.
 // All waits are bounded (VQNQS_DEV_TIMEOUT).
+// Distance mode (dist_out given): instead of the assignment, the epilogue writes
+// every listed row's distances ||o||^2 - 2 o . W_j + ||W_j||^2 to dist_out[m][j]
+// and ||o||^2 to osq_out[m] (m: the row's index in the list); codes and the
+// near-tie count are left alone.
 #include "tc_common.cuh"
 
 namespace vq {
@@ -70,7 +74,8 @@ __global__ void __launch_bounds__(VT_THREADS, 1)
 k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
         const float* __restrict__ O, const int* __restrict__ counters, const int* __restrict__ act_rows,
         const float* __restrict__ cnorm, int K, int d, int* __restrict__ code, long long* __restrict__ near_ties,
-        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols, int ACC, int a_slot) {
+        int* __restrict__ status, int VT_STAGES, uint32_t tmem_cols, int ACC, int a_slot,
+        float* __restrict__ dist_out, float* __restrict__ osq_out) {
     constexpr int A_BYTES = VT_BM * VT_BK * 4;   // 16 KB per part
     constexpr int B_BYTES = KC * VT_BK * 4;      // per part and pass
     extern __shared__ uint8_t smem_raw[];
@@ -257,20 +262,37 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
             tc::tc_fence_after();
             VqBest best;
             best.v1 = INFINITY; best.i1 = 0x7fffffff; best.v2 = INFINITY;
+            const float osq = osq_s[a * VT_BM + row];
+            const int m = t * VT_BM + row;
             for (int c0 = 0; c0 < accw; c0 += 32) {
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + lb + a * accw + c0, r);
+                if (dist_out) {  // K is a multiple of 16: a group of four columns is all in or all out
+                    if (m < R) {
+                        float* dr = dist_out + (size_t)m * K + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            if (c0 + j < K)
+                                *reinterpret_cast<float4*>(dr + j) =
+                                    make_float4(fmaf(-2.f, __uint_as_float(r[j]), osq) + cn_s[c0 + j],
+                                                fmaf(-2.f, __uint_as_float(r[j + 1]), osq) + cn_s[c0 + j + 1],
+                                                fmaf(-2.f, __uint_as_float(r[j + 2]), osq) + cn_s[c0 + j + 2],
+                                                fmaf(-2.f, __uint_as_float(r[j + 3]), osq) + cn_s[c0 + j + 3]);
+                    }
+                    __syncwarp();  // the next tcgen05.ld is warp-collective
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int n = c0 + j;
                     if (n < K) vq_merge(best, fmaf(-2.f, __uint_as_float(r[j]), cn_s[n]), n);
                 }
             }
-            const float osq = osq_s[a * VT_BM + row];
             tc::tc_fence_before();
             tc::mbar_arrive(&acce[a]);
-            const int m = t * VT_BM + row;
-            if (m < R) {
+            if (dist_out) {
+                if (m < R) osq_out[m] = osq;
+            } else if (m < R) {
                 if (best.i1 >= K) {  // no finite distance: codeword 0, and the status says so
                     best.i1 = 0;
                     atomicOr(status, VQNQS_DEV_NONFINITE);
@@ -340,7 +362,8 @@ cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d
 
 cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
                          const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
-                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot) {
+                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot, float* dist_out,
+                         float* osq_out) {
     if (!vq_tc_supported(K, d)) return cudaErrorInvalidValue;
     const int KC = K > 256 ? 256 : K;
     const int passes = (K + KC - 1) / KC;
@@ -369,7 +392,8 @@ cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, con
             gr = smem;                                                                                     \
         }                                                                                                  \
         k_vq_tc<X><<<grid, VT_THREADS, smem, st>>>(tm_hi, tm_lo, O, counters, act_rows, cnorm, K, d, code,  \
-                                                   near_ties, status, stages, cols, acc, a_slot);          \
+                                                   near_ties, status, stages, cols, acc, a_slot, dist_out, \
+                                                   osq_out);                                               \
         return cudaGetLastError();                                                                         \
     }
     VQ_TC_CASE(16) VQ_TC_CASE(32) VQ_TC_CASE(48) VQ_TC_CASE(64) VQ_TC_CASE(96) VQ_TC_CASE(128) VQ_TC_CASE(192)

@@ -142,7 +142,8 @@ struct Plan {
     int hash_bits = 0;
     size_t counters, cnt, cfg_off, diag, cfg_sample, cfg_i, cfg_j, cfg_row, row_cfg, act_cnt, act_off, act_rows,
         uid_a, uid_b, code, X_a, X_b, A, Y, scratch, keys, vals, rep_uid, rep_code, logp, ratio, bstat, cert,
-        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, ex_rows, code_hi, tab_lo, tab_hi, total;
+        vq_rows, rc_rows, rc_cnt, list_tc, list_simt, dpos, dcnt, ex_rows, code_hi, tab_lo, tab_hi, blist, bdist, bosq,
+        total;
 };
 
 // Workspace layout for chunks of at most S samples, C configurations and R rows.
@@ -203,6 +204,12 @@ Plan make_plan_budget(const vqnqs_ctx* c, int S, long long C, long long R) {
     p.code_hi = take(wbytes);
     p.tab_lo = take(wbytes);
     p.tab_hi = take(wbytes);
+    // the samples' rows for the certificate from the tensor-core distances: list, distances, ||o||^2
+    const bool tc_cert = c->vq_heads == 1 && vq_tc_supported(c->K, c->d);
+    const size_t srows = (size_t)S * c->N;
+    p.blist = take(tc_cert ? (srows + 1) * sizeof(int) : 0);
+    p.bdist = take(tc_cert ? srows * c->K * sizeof(float) : 0);
+    p.bosq = take(tc_cert ? srows * sizeof(float) : 0);
     p.total = o;
     return p;
 }
@@ -463,6 +470,11 @@ int run_chunk(vqnqs_ctx* ctx, const Plan& P, void* ws, const uint8_t* spins, con
                 VQ_STAGE(S_CERT, 1, launch_base_cert_heads(ch, O, w.codebook, w.cnorm, w.wd, K, d, ctx->vq_heads,
                                                            ctx->vq_bits, code, cert, ctx->stats, counters, rc_cnt,
                                                            st, ctx->num_sms));
+            else if (bf16 && vq_tc_supported(K, d))  // the samples' codes from the search the connected rows get
+                VQ_STAGE(S_CERT, 3, launch_base_cert_tc(ch, O, w.tm_cb_hi, w.tm_cb_lo, w.cnorm, w.wd, K, d, code,
+                                                        cert, ctx->stats, counters, rc_cnt, at<int>(ws, P.blist),
+                                                        at<float>(ws, P.bdist), at<float>(ws, P.bosq), ctx->status,
+                                                        st, ctx->num_sms));
             else
                 VQ_STAGE(S_CERT, 1, launch_base_cert(ch, O, w.codebook, w.cnorm, w.wd, K, d, code, cert, ctx->stats,
                                                      counters, rc_cnt, st));

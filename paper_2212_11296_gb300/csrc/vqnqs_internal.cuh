@@ -306,7 +306,8 @@ cudaError_t make_tmap_codebook(CUtensorMap* map, const float* base, int K, int d
 cudaError_t launch_split_tf32(const float* W, size_t n, float* hi, float* lo, cudaStream_t st);
 cudaError_t launch_vq_tc(const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, const float* O, const int* counters,
                          const int* act_rows, const float* cnorm, int K, int d, int* code, long long* near_ties,
-                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot = CNT_A);
+                         int* status, cudaStream_t st, int num_sms, int Rmax, int a_slot = CNT_A,
+                         float* dist_out = nullptr, float* osq_out = nullptr);
 
 // incremental evaluation of the connected configurations (k_incremental.cu)
 bool incremental_supported(int d, int heads);
@@ -325,6 +326,12 @@ cudaError_t launch_codeword_dist(const float* W, int K, int d, float* wd, cudaSt
 cudaError_t launch_base_cert(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,
                              const float* wd, int K, int d, int* code, CertRow* cert, long long* stats,
                              int* counters, int* rc_cnt, cudaStream_t st);
+// the same from the split-TF32 tensor-core distances (k_vq_tc in distance mode) of the chunk's sample rows:
+// list holds S N + 1 ints, dist S N K floats and osq S N floats of workspace (K a multiple of 16)
+cudaError_t launch_base_cert_tc(const Chunk& ch, const float* O, const CUtensorMap& tm_hi, const CUtensorMap& tm_lo,
+                                const float* cnorm, const float* wd, int K, int d, int* code, CertRow* cert,
+                                long long* stats, int* counters, int* rc_cnt, int* list, float* dist, float* osq,
+                                int* status, cudaStream_t st, int num_sms);
 // the same with H > 1 quantizer heads (packed codes of `bits` per head, one word): the row's radius is the
 // smallest over its segments, no candidate list; wd holds H tables [K][K]
 cudaError_t launch_base_cert_heads(const Chunk& ch, const float* O, const float* codebook, const float* cnorm,

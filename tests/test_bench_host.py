@@ -55,7 +55,8 @@ def test_stage_work_of_the_incremental_bf16_path():
           "inc_patch_pairs": 9000, "inc_full_pairs": 7000, "inc_whole_pairs": 11000}
     d, K = 256, 256
     assert bench.stage_flops("vq_argmin", st, w, True, True) == (1000 * 2.0 * K * d, "tensor")
-    assert bench.stage_flops("inc_certificate", st, w, True, True) == (3840 * 2.0 * K * d, "alu")
+    assert bench.stage_flops("inc_certificate", st, w, True, True) == (3840 * 2.0 * K * d, "tensor")
+    assert bench.stage_flops("inc_certificate", st, w, False, True) == (3840 * 2.0 * K * d, "alu")
     # patch: 8 d per (row, changed key) pair; recompute: 4 d per pair; tensor cores on the BF16 path
     assert bench.stage_flops("inc_patch", st, w, True, True) == (9000 * 8.0 * d, "tensor")
     assert bench.stage_flops("inc_patch", st, w, False, True) == (9000 * 8.0 * d, "alu")
