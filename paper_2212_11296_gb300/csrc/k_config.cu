@@ -329,7 +329,7 @@ __global__ void k_eloc_ratio(Chunk ch, const int* __restrict__ uid, const float*
     const int V = 1 << ch.G;  // values of a token's spin group (2 for single spins)
     int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < C; c += gridDim.x * wpb) {
-        const int b = ch.cfg_sample[c], ci = ch.cfg_i[c], cj = ch.cfg_j[c];
+        const int b = ch.cfg_sample[c], ci = ch.cfg_i[c];
         const int N = sample_N(ch, b);
         const int* urow = uid + ch.cfg_row[c];
         const int* ubase = uid + ch.cfg_row[ch.cfg_off[b]];

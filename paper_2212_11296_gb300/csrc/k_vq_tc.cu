@@ -203,7 +203,7 @@ k_vq_tc(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUten
                 dst[q] = valid ? *reinterpret_cast<const float4*>(src + 4 * q) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
         // register ring: the chunks at distance 1 and 2 are in flight while this one is stored
-        float4 n1[VT_BK / 4], n2[VT_BK / 4];
+        float4 n1[VT_BK / 4];
         auto advance = [&](int& tt, int& kk) {
             if (++kk == KB) { kk = 0; tt += gridDim.x; }
         };
