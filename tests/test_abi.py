@@ -101,3 +101,33 @@ def test_create_arch_rejects_bad_variants_without_touching_a_gpu(lib):
         rc = lib.vqnqs_create_arch(L, 1, 1.0, layers, d, heads, K, H, half, G, ctypes.cast(w, ctypes.c_void_p),
                                    ctypes.byref(h))
         assert rc == 1 and not h.value, (L, d, K, H, G)
+
+
+def test_struct_mirrors_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets: a C
+    program built with the host compiler against include/vqnqs.h prints them."""
+    import shutil
+    import subprocess
+
+    from paper_2212_11296_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"vqnqs_stats": _lib.Stats, "vqnqs_stage_time": _lib.StageTime,
+               "vqnqs_inc_tuning": _lib.IncTuning, "vqnqs_tuning": _lib.Tuning}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "vqnqs.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'    printf("{cname} . %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(c, f): int(v) for c, f, v in (ln.split() for ln in out if ln.strip())}
+    for cname, py in mirrors.items():
+        assert got[(cname, ".")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
